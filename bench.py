@@ -1,0 +1,361 @@
+"""Benchmark of the prediction hot path on the paper-scale workload.
+
+One step = the whole path on one human of the ``paper_scale`` workload:
+the belief update over 50 observed steps (Eq. 3 / Eq. 7), then Algorithm 1
+for N = 100k particles over T = 150 steps with K = 36 headings, emplaced on a
+200 x 200 grid (counts zeroed and rebuilt every step). The metric is
+particle-steps per second (N * T per step), device-timed with CUDA events
+around each step on the launching stream; L2 is flushed (a 256 MiB write)
+before every timed step. ``e2e`` runs the same step through the host-buffer
+entry point pm_predict_host (inputs from pinned host memory, the posterior
+and the 24 MB histogram copied back every step).
+
+Multi-GPU (torchrun): every rank predicts its own human (human_id = rank), no
+data-path collective; value = all ranks' particle-steps / the slowest rank's
+time ("weak" scaling).
+
+``--impl reference`` times the FP64 CPU oracle (the reference arm) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "particle-steps/s"
+ROLLOUT_SOURCES = ["paper_2603_01122_gb300/csrc/pm_rollout.cu", "paper_2603_01122_gb300/csrc/pm_internal.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=20000, help="particles in the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(hu):
+    x0, y0, res, W, H = hu.grid
+    return {
+        "workload": "paper_scale",
+        "humans_per_gpu": 1,
+        "K": hu.K, "G": hu.G, "B": hu.B, "n_obs": hu.n_obs,
+        "n_particles": hu.n_particles, "horizon": hu.horizon,
+        "grid": f"{W}x{H}@{res:.3g}m", "dt": round(hu.dt, 6),
+        "l2": "flushed before every timed step (256 MiB write)",
+    }
+
+
+def sources_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(hu, n_particles, obs=None):
+    """Time the FP64 oracle (as it stands, one thread) on a bounded sample."""
+    import oracle
+    m = oracle.Model(hu.K, hu.speed, hu.dt, hu.goals, hu.beta)
+    if obs is None:
+        obs = oracle.simulate(m, hu.true_j, hu.start, hu.n_obs, hu.obs_seed, hu.human_id).astype(np.float32)
+    t0 = time.perf_counter()
+    post, _ = oracle.update_posterior(m, obs.astype(np.float64), hu.uniform_log_prior())
+    oracle.rollout(m, post.astype(np.float32), obs[-1], hu.horizon, hu.seed, hu.human_id, 0, n_particles,
+                   grid=hu.grid)
+    dt = time.perf_counter() - t0
+    ps = n_particles * hu.horizon
+    return {"value": ps / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{n_particles} of {hu.n_particles} particles x T={hu.horizon} + 50-step belief "
+                      f"update, FP64 C, 1 thread ({dt:.2f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    hu = workloads.paper_scale()
+    per_step = []
+    n = max(1000, args.cpu_sample // 4)
+    for _ in range(args.warmup):
+        oracle_sample(hu, max(200, n // 10))
+    for _ in range(args.steps):
+        r = oracle_sample(hu, n)
+        per_step.append(n * hu.horizon / r["value"])
+    total = sum(per_step)
+    value = n * hu.horizon * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (model-drawn observations, seeded)", "config": workload_config(hu),
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": f"{n} of {hu.n_particles} particles x T={hu.horizon} per step"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def load_profile_traffic(kernel_hash):
+    """DRAM bytes per launch of the rollout kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "rollout_paper_scale.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get("kernel_sources_hash") != kernel_hash:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def run_native(args):
+    import torch
+    import torch.distributed as tdist
+
+    import paper_2603_01122_gb300 as pm
+
+    rank, world, local = dist_env()
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    pm.build()
+    ctx = pm.pm_create(local)
+    stream = torch.cuda.Stream(device=dev)
+
+    hu = workloads.paper_scale()
+    human_id = hu.human_id + 1000 * rank
+    K, N, T = hu.K, hu.n_particles, hu.horizon
+    x0, y0, res, W, H = hu.grid
+    goals = torch.tensor(hu.goals, device=dev)
+    beta = torch.tensor(hu.beta, device=dev)
+    model = pm.make_model(K, hu.speed, hu.dt, goals, beta)
+    grid = pm.make_grid(x0, y0, res, W, H)
+
+    # Observed history drawn from the model by the library itself: one traced
+    # particle whose belief is a point mass on the true component.
+    J = hu.G * hu.B
+    onehot = torch.full((J,), -float("inf"), device=dev)
+    onehot[hu.true_j] = 0.0
+    hist_states = torch.empty((1, hu.n_obs, 2), device=dev)
+    pm.pm_predict_occupancy_traced(ctx, model, onehot, float(hu.start[0]), float(hu.start[1]), 1, hu.n_obs,
+                                   None, hu.obs_seed, human_id, None, None, 1, hist_states, None, None)
+    obs = torch.cat([torch.tensor(hu.start, device=dev).view(1, 2), hist_states[0]], 0).contiguous()
+    torch.cuda.synchronize()
+    obs_host = obs.cpu().numpy()
+    z0 = obs_host[-1]
+    prior = torch.tensor(hu.uniform_log_prior(), device=dev)
+    lb = torch.empty_like(prior)
+    counts = torch.empty((T, H, W), dtype=torch.int32, device=dev)
+    oob = torch.empty((T,), dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        lb.copy_(prior)
+        pm.pm_update_posterior(ctx, model, obs, hu.n_obs, lb, stream)
+        pm.pm_predict_occupancy(ctx, model, lb, float(z0[0]), float(z0[1]), N, T, grid, hu.seed, human_id,
+                                counts, oob, stream)
+
+    # SFU peak (roofline denominator), measured before the timed region
+    sfu = {"ex2": pm.pm_probe_sfu(ctx, 0), "sqrt": pm.pm_probe_sfu(ctx, 1), "rsqrt": pm.pm_probe_sfu(ctx, 2)}
+    info = pm.pm_device_info(ctx)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    phys = vis.split(",")[local] if vis and vis.split(",")[local].isdigit() else str(local)
+    with ClockSampler(phys) as clk:
+        wall0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.fill_(float(i))
+                ev[i][0].record(stream)
+                lb.copy_(prior)
+                pm.pm_update_posterior(ctx, model, obs, hu.n_obs, lb, stream)
+                ev[i][1].record(stream)
+                pm.pm_predict_occupancy(ctx, model, lb, float(z0[0]), float(z0[1]), N, T, grid, hu.seed,
+                                        human_id, counts, oob, stream)
+                ev[i][2].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if world > 1:
+        tdist.barrier()
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    roll_ms = [b.elapsed_time(c) for a, b, c in ev]
+    post_ms = [a.elapsed_time(b) for a, b, c in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * N * T / (ms_per_step * 1e-3)
+
+    # roofline of the dominant kernel (the rollout): algorithmic SFU results
+    # per launch (K exp + K sqrt per particle-step) / its event-timed duration
+    roll_avg_s = statistics.mean(roll_ms) * 1e-3
+    sfu_ops = 2.0 * K * N * T
+    achieved = sfu_ops / roll_avg_s / 1e9
+    peak = 2.0 / (1.0 / sfu["ex2"] + 1.0 / sfu["sqrt"]) / 1e9
+    khash = sources_hash(ROLLOUT_SOURCES)
+    traffic = load_profile_traffic(khash)
+
+    # e2e through the host-buffer entry point (pinned buffers)
+    goals_h = torch.tensor(hu.goals).pin_memory()
+    beta_h = torch.tensor(hu.beta).pin_memory()
+    obs_h = torch.tensor(obs_host).pin_memory()
+    prior_h = torch.tensor(hu.uniform_log_prior()).pin_memory()
+    post_h = torch.empty(J, dtype=torch.float32).pin_memory()
+    counts_h = torch.empty((T, H, W), dtype=torch.int32).pin_memory()
+    oob_h = torch.empty((T,), dtype=torch.int32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+
+    def host_call():
+        pm.pm_predict_host(ctx, model, goals_h, beta_h, obs_h, hu.n_obs, prior_h, N, T, grid, hu.seed,
+                           human_id, post_h, counts_h, oob_h, stream)
+
+    host_call()
+    e0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        host_call()
+    e2e_s = (time.perf_counter() - e0) / e2e_steps
+    h2d = (goals_h.numel() + beta_h.numel() + obs_h.numel() + prior_h.numel()) * 4
+    d2h = (post_h.numel() + counts_h.numel() + oob_h.numel()) * 4
+    e2e_value = N * T / e2e_s
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_value = world * N * T / float(t.item())
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded; observed history drawn from the model on the GPU)",
+            "config": workload_config(hu),
+            "gpu_launches": 2 * args.steps,
+            "wall_s": wall,
+            "breakdown_ms": {"posterior": statistics.mean(post_ms), "rollout": statistics.mean(roll_ms)},
+            "roofline": {"bound": "alu", "kernel": "rollout_kernel<36>", "achieved": achieved,
+                         "peak": peak, "unit": "G SFU results/s", "frac": achieved / peak,
+                         "traffic": traffic,
+                         "peak_source": "measured by pm_probe_sfu (ex2/sqrt 1:1 harmonic mean); "
+                                        f"ex2 {sfu['ex2'] / 1e9:.1f}, sqrt {sfu['sqrt'] / 1e9:.1f}, "
+                                        f"rsqrt {sfu['rsqrt'] / 1e9:.1f} G/s",
+                         "algorithmic": "2K SFU results (K ex2 + K sqrt) per particle-step"},
+            "device": info,
+            "clocks": clk.summary(),
+            "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "api": "pm_predict_host"},
+            "paper_context": "125 Hz for 1 human, n=8192, T<=10, |U|=96 on an RTX 2080 Ti (Table 1); not this metric",
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = oracle_sample(hu, args.cpu_sample)
+        print(json.dumps(line), flush=True)
+    pm.pm_destroy(ctx)
+    if world > 1:
+        tdist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

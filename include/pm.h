@@ -1,0 +1,191 @@
+/*
+ * pm.h -- C ABI of the GB300 (sm_103a) library for confidence-aware human
+ * prediction: the Bayesian belief update over (rationality beta, goal g), the
+ * particle rollout of Algorithm 1 and the per-step occupancy histogram of
+ * Lu, Bui, Lyu and Chen, "Fast Confidence-Aware Human Prediction via
+ * Hardware-accelerated Bayesian Inference for Safe Robot Navigation".
+ *
+ * Conventions for every call
+ *   - Plain pointers and sizes only. Unless stated otherwise a pointer is a
+ *     DEVICE pointer on the context's device, owned by the caller, and must
+ *     stay valid until the work queued on `stream` has finished.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Calls are stream-ordered and asynchronous unless stated.
+ *   - Every call returns a pm_status and never throws. Invalid sizes and
+ *     arguments are rejected with PM_EINVAL before anything is queued; the
+ *     message of the last failure on the calling thread is pm_last_error().
+ *   - There is no CPU fallback: every numeric step runs in this library's
+ *     CUDA kernels.
+ *   - Floats are IEEE binary32; log-beliefs are natural logarithms.
+ *
+ * Model (Sec. III-A, running example, and the readings of the open points):
+ *   state z = (x, y); controls are K headings theta_k = 2*pi*k/K
+ *   (counter-clockwise from +x) at one speed v; one step moves v*dt along the
+ *   heading (Eq. 1, forward Euler). The state-control value is
+ *     Q(z, theta; g) = -w1*v*dt - w2*|| z + v*dt*(cos theta, sin theta) - g ||
+ *   and the policy is the Boltzmann distribution pi(k | z; beta, g)
+ *   proportional to exp(beta * Q) (Eq. 2). The joint belief over
+ *   (beta, g) is a table of G*B log-probabilities indexed j = g*B + b.
+ */
+#ifndef PM_H_
+#define PM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PM_MAX_HEADINGS 64    /* K in [1, 64]                      */
+#define PM_MAX_COMPONENTS 256 /* G*B in [1, 256]                   */
+#define PM_MAX_GOALS 64       /* G in [1, 64]                      */
+#define PM_MAX_HORIZON 4096   /* T in [1, 4096]                    */
+
+typedef enum pm_status {
+    PM_OK = 0,
+    PM_EINVAL = 1,  /* invalid argument; nothing was queued                 */
+    PM_ENOMEM = 2,  /* a device or pinned allocation of the context failed */
+    PM_ECUDA = 3,   /* a CUDA runtime call or launch failed                */
+    PM_EDEVICE = 5  /* a kernel reported an error in its status word       */
+} pm_status;
+
+/* Opaque context: one device, its properties, scratch buffers and tuned
+ * launch parameters. Not thread-safe; use one context per host thread. */
+typedef struct pm_ctx pm_ctx;
+
+/* Human model. `goals` and `beta` are device pointers ([G][2] and [B]).
+ * `heading_off` bit k set disables heading k (Q = -inf, so pi = 0), the
+ * control masking of Sec. IV-B. beta values must be >= 0. */
+typedef struct pm_model {
+    int32_t K;
+    float speed; /* v  [m/s]            */
+    float dt;    /* Delta t [s]         */
+    float w1;    /* Q weight of -v*dt   */
+    float w2;    /* Q weight of distance */
+    int32_t G;
+    int32_t B;
+    const float *goals;
+    const float *beta;
+    uint64_t heading_off;
+} pm_model;
+
+/* Occupancy grid: cell (cx, cy) covers [x0 + cx*res, x0 + (cx+1)*res) x
+ * [y0 + cy*res, y0 + (cy+1)*res), 0 <= cx < W, 0 <= cy < H. A state is binned
+ * with FP32 operations: cx = floor((x - x0) * inv_res), inv_res = 1.0f/res. */
+typedef struct pm_grid {
+    float x0;
+    float y0;
+    float res;
+    int32_t W;
+    int32_t H;
+} pm_grid;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`. Allocates nothing on the device
+ * until a call needs scratch. */
+pm_status pm_create(pm_ctx **ctx, int device);
+
+/* Release the context and the device memory it owns. NULL is accepted. */
+void pm_destroy(pm_ctx *ctx);
+
+/* Message of the last failed call on the calling thread ("" if none). */
+const char *pm_last_error(void);
+
+/* Library version string. */
+const char *pm_version(void);
+
+/* ---- the hot path -------------------------------------------------------- */
+
+/* Bayesian update of the joint belief (Eq. 3), in log space (Eq. 7), over
+ * `n_obs` observed steps.
+ *   obs_xy      [n_obs+1][2] observed states z_t (device, FP32).
+ *   log_belief  [G*B] in/out (device): a normalised log-belief before the
+ *               call; the posterior after all n_obs steps on return.
+ * The control of step t is recovered from (z_t, z_{t+1}) by differential
+ * flatness: the heading of the displacement; Q is evaluated at that
+ * continuous heading and normalised over the K headings. A displacement
+ * shorter than 1e-6 m leaves the belief unchanged for that step. n_obs = 0
+ * is a no-op. Per-step log-likelihoods are summed in FP64 on the device and
+ * the LogSumExp normalisation is applied once, which equals the sequential
+ * form of Eq. 7 exactly in real arithmetic. */
+pm_status pm_update_posterior(pm_ctx *ctx, const pm_model *model, const float *obs_xy,
+                              int32_t n_obs, float *log_belief, void *stream);
+
+/* Algorithm 1 with the bootstrapped belief (Sec. III-B): `n_particles`
+ * particles start at (z0x, z0y), each draws (beta, g) once from
+ * exp(log_belief), then for t = 1..horizon samples a heading from
+ * pi(. | z_t; beta, g) at its own state and takes one Euler step; the
+ * states of step t are emplaced onto the grid.
+ *   log_belief  [G*B] (device), normalised.
+ *   counts      [horizon][H][W] uint32 (device), zeroed by the callee, then
+ *               counts[t-1][cy][cx] = particles in cell (cx, cy) after step t.
+ *   oob         [horizon] uint32 (device), zeroed by the callee: particles
+ *               outside the grid after step t (they stay alive).
+ * Invariant: sum(counts[t-1]) + oob[t-1] = n_particles. Occupancy
+ * probability = count / n_particles.
+ * Random numbers: Philox4x64-10 with key (seed, human_id) and counter
+ * (particle, block, purpose, 0); the (beta, g) draw of particle i uses word 0
+ * of block 0 of purpose 1; the heading draw of step t uses 32-bit word
+ * (t-1)&7 of block (t-1)>>3 of purpose 2 (word w is bits 32*(w&1).. of
+ * 64-bit output w>>1); u = (word >> 8) * 2^-24. Sampling takes the smallest
+ * index k whose running weight sum C_k exceeds u * (total). */
+pm_status pm_predict_occupancy(pm_ctx *ctx, const pm_model *model, const float *log_belief,
+                               float z0x, float z0y, int32_t n_particles, int32_t horizon,
+                               const pm_grid *grid, uint64_t seed, uint32_t human_id,
+                               uint32_t *counts, uint32_t *oob, void *stream);
+
+/* The same launch as pm_predict_occupancy, also recording the trajectories
+ * of particles [0, n_trace):
+ *   states      [n_trace][horizon][2] FP32 state after each step, or NULL
+ *   headings    [n_trace][horizon] uint8 heading index of each step, or NULL
+ *   components  [n_trace] int32 drawn component j, or NULL
+ * `counts`/`oob` may both be NULL to skip the histogram (then `grid` may be
+ * NULL too). n_trace <= n_particles. Used for parity checks and to draw
+ * synthetic observed trajectories from the model. */
+pm_status pm_predict_occupancy_traced(pm_ctx *ctx, const pm_model *model,
+                                      const float *log_belief, float z0x, float z0y,
+                                      int32_t n_particles, int32_t horizon, const pm_grid *grid,
+                                      uint64_t seed, uint32_t human_id, uint32_t *counts,
+                                      uint32_t *oob, int32_t n_trace, float *states,
+                                      uint8_t *headings, int32_t *components, void *stream);
+
+/* Convenience form with HOST buffers (what a robot-side caller holds):
+ * copies the model tables, observations and prior in, runs
+ * pm_update_posterior and pm_predict_occupancy on the context's own device
+ * buffers, copies the posterior and the histogram out, and returns when they
+ * are on the host. Host pointers: goals [G][2], beta [B], obs_xy
+ * [n_obs+1][2], log_prior [G*B], posterior_out [G*B], counts_out
+ * [horizon][H][W], oob_out [horizon]. The model's goals/beta fields are
+ * ignored. Page-locked host memory makes the copies asynchronous. The
+ * rollout starts at the last observed state. */
+pm_status pm_predict_host(pm_ctx *ctx, const pm_model *model, const float *goals,
+                          const float *beta, const float *obs_xy, int32_t n_obs,
+                          const float *log_prior, int32_t n_particles, int32_t horizon,
+                          const pm_grid *grid, uint64_t seed, uint32_t human_id,
+                          float *posterior_out, uint32_t *counts_out, uint32_t *oob_out,
+                          void *stream);
+
+/* ---- checks and measurement ---------------------------------------------- */
+
+/* Raw Philox4x64-10 blocks for counters (particle0 + i, block, purpose, 0),
+ * key (seed, human_id), i in [0, n): out [n][4] uint64 (device). */
+pm_status pm_philox_blocks(pm_ctx *ctx, uint64_t seed, uint32_t human_id, uint32_t purpose,
+                           uint64_t particle0, uint64_t block, int32_t n, uint64_t *out,
+                           void *stream);
+
+/* Throughput of the special-function unit measured on this device, in
+ * results per second: op 0 = ex2.approx.f32, 1 = sqrt.approx.f32,
+ * 2 = rsqrt.approx.f32. Synchronous (times its own launch with events). */
+pm_status pm_probe_sfu(pm_ctx *ctx, int op, double *results_per_s);
+
+/* Device properties the roofline uses: SM count, SM clock (kHz), and the
+ * compute capability as 10*major + minor. Any output may be NULL. */
+pm_status pm_device_info(pm_ctx *ctx, int *sm_count, int *clock_khz, int *cc);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PM_H_ */

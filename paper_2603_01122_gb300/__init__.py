@@ -1,0 +1,194 @@
+"""Thin Python binding of libpm (include/pm.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and forwards
+plain pointers and sizes; every numeric step runs in the library's CUDA
+kernels. Device buffers may be given as torch CUDA tensors (their data_ptr is
+passed) or as integers. There is no CPU fallback: if libpm.so has not been
+built, the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from ._build import LIB as _LIB_PATH
+from ._build import build  # noqa: F401  (re-exported for __graft_entry__)
+
+PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_EDEVICE = 0, 1, 2, 3, 5
+PM_MAX_HEADINGS, PM_MAX_COMPONENTS, PM_MAX_GOALS, PM_MAX_HORIZON = 64, 256, 64, 4096
+PURPOSE_SELECT, PURPOSE_STEP = 1, 2
+_STATUS = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ECUDA", 5: "PM_EDEVICE"}
+
+
+class PmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class pm_model(C.Structure):
+    _fields_ = [("K", C.c_int32), ("speed", C.c_float), ("dt", C.c_float), ("w1", C.c_float),
+                ("w2", C.c_float), ("G", C.c_int32), ("B", C.c_int32), ("goals", C.c_void_p),
+                ("beta", C.c_void_p), ("heading_off", C.c_uint64)]
+
+
+class pm_grid(C.Structure):
+    _fields_ = [("x0", C.c_float), ("y0", C.c_float), ("res", C.c_float), ("W", C.c_int32),
+                ("H", C.c_int32)]
+
+
+_lib = None
+_vp = C.c_void_p
+
+
+def _signatures(lib):
+    P = C.POINTER
+    sig = {
+        "pm_create": ([P(_vp), C.c_int], C.c_int),
+        "pm_destroy": ([_vp], None),
+        "pm_last_error": ([], C.c_char_p),
+        "pm_version": ([], C.c_char_p),
+        "pm_update_posterior": ([_vp, P(pm_model), _vp, C.c_int32, _vp, _vp], C.c_int),
+        "pm_predict_occupancy": ([_vp, P(pm_model), _vp, C.c_float, C.c_float, C.c_int32, C.c_int32,
+                                  P(pm_grid), C.c_uint64, C.c_uint32, _vp, _vp, _vp], C.c_int),
+        "pm_predict_occupancy_traced": ([_vp, P(pm_model), _vp, C.c_float, C.c_float, C.c_int32,
+                                         C.c_int32, P(pm_grid), C.c_uint64, C.c_uint32, _vp, _vp,
+                                         C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
+        "pm_predict_host": ([_vp, P(pm_model), _vp, _vp, _vp, C.c_int32, _vp, C.c_int32, C.c_int32,
+                             P(pm_grid), C.c_uint64, C.c_uint32, _vp, _vp, _vp, _vp], C.c_int),
+        "pm_philox_blocks": ([_vp, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint64,
+                              C.c_int32, _vp, _vp], C.c_int),
+        "pm_probe_sfu": ([_vp, C.c_int, P(C.c_double)], C.c_int),
+        "pm_device_info": ([_vp, P(C.c_int), P(C.c_int), P(C.c_int)], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name, None)
+        if fn is None:
+            continue
+        fn.argtypes = args
+        fn.restype = res
+    return sig
+
+
+def library():
+    """The loaded libpm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"libpm.so is not built ({_LIB_PATH}); run __graft_entry__.build()")
+        lib = C.CDLL(_LIB_PATH)
+        _signatures(lib)
+        _lib = lib
+    return _lib
+
+
+def _p(x):
+    """Device pointer of a torch tensor, an int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _hp(x):
+    """Host pointer of a numpy array or a pinned CPU torch tensor."""
+    if x is None:
+        return None
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(st):
+    if st != PM_OK:
+        raise PmError(st, library().pm_last_error().decode())
+
+
+def pm_version() -> str:
+    return library().pm_version().decode()
+
+
+def pm_last_error() -> str:
+    return library().pm_last_error().decode()
+
+
+def pm_create(device: int = 0) -> int:
+    h = _vp()
+    _check(library().pm_create(C.byref(h), int(device)))
+    return h.value
+
+
+def pm_destroy(ctx) -> None:
+    library().pm_destroy(ctx)
+
+
+def make_model(K, speed, dt, goals, beta, w1=1.0, w2=1.0, heading_off=0) -> pm_model:
+    """pm_model over device tensors ``goals`` [G, 2] and ``beta`` [B] (float32)."""
+    G = int(goals.shape[0])
+    B = int(beta.shape[0])
+    m = pm_model(int(K), float(speed), float(dt), float(w1), float(w2), G, B, _p(goals), _p(beta),
+                 int(heading_off))
+    m._keep = (goals, beta)  # keep the tensors alive with the struct
+    return m
+
+
+def make_grid(x0, y0, res, W, H) -> pm_grid:
+    return pm_grid(float(x0), float(y0), float(res), int(W), int(H))
+
+
+def pm_update_posterior(ctx, model: pm_model, obs_xy, n_obs, log_belief, stream=None):
+    _check(library().pm_update_posterior(ctx, C.byref(model), _p(obs_xy), int(n_obs), _p(log_belief),
+                                         _stream(stream)))
+
+
+def pm_predict_occupancy(ctx, model: pm_model, log_belief, z0x, z0y, n_particles, horizon,
+                         grid: pm_grid, seed, human_id, counts, oob, stream=None):
+    _check(library().pm_predict_occupancy(ctx, C.byref(model), _p(log_belief), float(z0x), float(z0y),
+                                          int(n_particles), int(horizon), C.byref(grid), int(seed),
+                                          int(human_id), _p(counts), _p(oob), _stream(stream)))
+
+
+def pm_predict_occupancy_traced(ctx, model: pm_model, log_belief, z0x, z0y, n_particles, horizon,
+                                grid, seed, human_id, counts, oob, n_trace, states=None,
+                                headings=None, components=None, stream=None):
+    g = C.byref(grid) if grid is not None else None
+    _check(library().pm_predict_occupancy_traced(
+        ctx, C.byref(model), _p(log_belief), float(z0x), float(z0y), int(n_particles), int(horizon), g,
+        int(seed), int(human_id), _p(counts), _p(oob), int(n_trace), _p(states), _p(headings),
+        _p(components), _stream(stream)))
+
+
+def pm_predict_host(ctx, model: pm_model, goals, beta, obs_xy, n_obs, log_prior, n_particles,
+                    horizon, grid: pm_grid, seed, human_id, posterior_out, counts_out, oob_out,
+                    stream=None):
+    """Host-buffer form: numpy arrays or (pinned) CPU tensors in and out."""
+    _check(library().pm_predict_host(ctx, C.byref(model), _hp(goals), _hp(beta), _hp(obs_xy), int(n_obs),
+                                     _hp(log_prior), int(n_particles), int(horizon), C.byref(grid),
+                                     int(seed), int(human_id), _hp(posterior_out), _hp(counts_out),
+                                     _hp(oob_out), _stream(stream)))
+
+
+def pm_philox_blocks(ctx, seed, human_id, purpose, particle0, block, n, out, stream=None):
+    _check(library().pm_philox_blocks(ctx, int(seed), int(human_id), int(purpose), int(particle0),
+                                      int(block), int(n), _p(out), _stream(stream)))
+
+
+def pm_probe_sfu(ctx, op: int) -> float:
+    v = C.c_double()
+    _check(library().pm_probe_sfu(ctx, int(op), C.byref(v)))
+    return v.value
+
+
+def pm_device_info(ctx):
+    sm, clk, cc = C.c_int(), C.c_int(), C.c_int()
+    _check(library().pm_device_info(ctx, C.byref(sm), C.byref(clk), C.byref(cc)))
+    return {"sm_count": sm.value, "clock_khz": clk.value, "cc": cc.value}

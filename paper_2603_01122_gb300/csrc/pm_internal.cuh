@@ -1,0 +1,132 @@
+// pm_internal.cuh -- device helpers and kernel argument blocks private to the
+// CUDA library (never shared with the CPU oracle).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pm.h"
+
+namespace pm {
+
+constexpr int kMaxK = PM_MAX_HEADINGS;
+constexpr int kMaxJ = PM_MAX_COMPONENTS;
+constexpr uint32_t kPurposeSelect = 1u;
+constexpr uint32_t kPurposeStep = 2u;
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+// as 1, 2, 3", SC'11): ten rounds of two 64x64->128 multiplies, the Weyl key
+// schedule added between rounds.
+// ---------------------------------------------------------------------------
+struct U64x4 {
+    uint64_t a, b, c, d;
+};
+
+__device__ __forceinline__ U64x4 philox4x64_10(U64x4 x, uint64_t k0, uint64_t k1)
+{
+    constexpr uint64_t kMulA = 0xD2E7470EE14C6C93ull;
+    constexpr uint64_t kMulB = 0xCA5A826395121157ull;
+    constexpr uint64_t kWeylA = 0x9E3779B97F4A7C15ull;
+    constexpr uint64_t kWeylB = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t pa_hi = __umul64hi(kMulA, x.a), pa_lo = kMulA * x.a;
+        const uint64_t pc_hi = __umul64hi(kMulB, x.c), pc_lo = kMulB * x.c;
+        x = U64x4{pc_hi ^ x.b ^ k0, pc_lo, pa_hi ^ x.d ^ k1, pa_lo};
+        k0 += kWeylA;
+        k1 += kWeylB;
+    }
+    return x;
+}
+
+// ---------------------------------------------------------------------------
+// Special-function-unit approximations (one MUFU instruction each).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Fire-and-forget global add (the result is not needed).
+__device__ __forceinline__ void red_add(uint32_t *p, uint32_t v)
+{
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Heading tables computed on the host (in double, rounded once to FP32).
+// ---------------------------------------------------------------------------
+struct HeadingTab {
+    float ux[kMaxK], uy[kMaxK]; // unit vector (cos, sin) of theta_k
+    float sx[kMaxK], sy[kMaxK]; // one Euler step v*dt*(cos, sin)
+    float tx[kMaxK], ty[kMaxK]; // 2*v*dt*(cos, sin)
+};
+
+// Arguments of the rollout kernel (Algorithm 1 + emplacement).
+struct RolloutArgs {
+    HeadingTab tab;
+    uint64_t enabled; // bit k: heading k may be drawn (k < K and not disabled)
+    float s2;         // (v*dt)^2
+    float w2_log2e;   // w2 * log2(e): beta*w2*log2(e) scales distance differences
+    int K, G, B;
+    const float *goals;
+    const float *beta;
+    const float *log_b;
+    float z0x, z0y;
+    int N, T;
+    float gx0, gy0, inv_res;
+    int W, H;
+    uint64_t seed;
+    uint32_t human;
+    uint32_t *counts;
+    uint32_t *oob;
+    int win_x0, win_y0;  // shared-memory window origin (grid cells)
+    int win_side;        // window width | height << 16 (cells, each <= 255); 0 = no window
+    int n_trace;
+    float *tr_states;
+    uint8_t *tr_head;
+    int32_t *tr_comp;
+};
+
+// Arguments of the belief-update kernel (Eq. 3 / Eq. 7).
+struct PosteriorArgs {
+    float ux[kMaxK], uy[kMaxK]; // unit heading vectors
+    uint64_t enabled;
+    float s, s2, two_s, w2;
+    int K, G, B;
+    const float *goals;
+    const float *beta;
+    const float *obs;
+    int n_obs;
+    float *log_b;
+};
+
+// Launch wrappers (defined next to their kernels).
+cudaError_t launch_rollout(const RolloutArgs &a, int threads, size_t dyn_smem, cudaStream_t s);
+size_t rollout_static_smem_estimate();
+cudaError_t launch_posterior(const PosteriorArgs &a, cudaStream_t s);
+cudaError_t launch_philox_blocks(uint64_t seed, uint32_t human, uint32_t purpose,
+                                 uint64_t particle0, uint64_t block, int n, uint64_t *out,
+                                 cudaStream_t s);
+cudaError_t launch_sfu_probe(int op, int blocks, int threads, int iters, float *sink,
+                             cudaStream_t s);
+int rollout_kt_for(int K); // template bucket for K (8, 16, 36 or 64)
+
+} // namespace pm

@@ -1,0 +1,349 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (stated once, used below):
+  posterior   |log b_gpu - log b_64| <= 1e-5 where b_64 >= 1e-8, b_gpu <= 1e-7
+              elsewhere, |sum b_gpu - 1| <= 1e-6;
+  trajectories identical heading sequences and (beta, g) draws under the
+              shared Philox streams except at most 1e-4 of the particles
+              (FP32 CDF boundaries); non-diverged particles have bit-identical
+              FP32 states;
+  histogram   bit-exact given identical FP32 states;
+  occupancy   per-step TV against exact propagation within the allowance of
+              test_oracle_rollout.tv_bound.
+"""
+import math
+import zlib
+
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from gpu_util import GpuHuman, dev, posterior, predict
+from test_oracle_rollout import lattice_k4, tv, tv_bound
+
+pytestmark = pytest.mark.gpu
+
+TRAJ_RATE = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2603_01122_gb300 as pm
+    pm.build()
+    c = pm.pm_create(0)
+    yield c
+    pm.pm_destroy(c)
+
+
+def assert_posterior_close(got, want):
+    got = np.asarray(got, np.float64)
+    want = np.asarray(want, np.float64)
+    big = np.exp(want) >= 1e-8
+    assert np.all(np.abs(got[big] - want[big]) <= 1e-5), np.max(np.abs(got[big] - want[big]))
+    assert np.all(np.exp(got[~big]) <= 1e-7)
+    assert abs(np.exp(got).sum() - 1.0) <= 1e-6
+
+
+def poisson_reject_at(N, rate=TRAJ_RATE, alpha=1e-6):
+    """Smallest d with P(Poisson(N*rate) >= d) < alpha."""
+    lam = N * rate
+    p, cdf, d = math.exp(-lam), 0.0, 0
+    while True:
+        cdf += p
+        d += 1
+        if 1.0 - cdf < alpha:
+            return d
+        p *= lam / d
+
+
+def compare_trajectories(got, ref):
+    """Particles whose draws differ anywhere; states must be bit-equal elsewhere."""
+    diff = np.any(got["headings"] != ref["headings"], axis=1) | (got["comp"] != ref["comp"])
+    same = ~diff
+    assert np.array_equal(got["states32"][same], ref["states32"][same])
+    return int(diff.sum())
+
+
+def _obs_and_post(orc, hu):
+    m = orc.Model(hu.K, hu.speed, hu.dt, hu.goals, hu.beta, w1=hu.w1, w2=hu.w2)
+    obs = orc.simulate(m, hu.true_j, hu.start, hu.n_obs, hu.obs_seed, hu.human_id).astype(np.float32)
+    post, _ = orc.update_posterior(m, obs.astype(np.float64), hu.uniform_log_prior())
+    return m, obs, post
+
+
+# --------------------------------------------------------------------- generator
+def test_philox_blocks_bit_exact(ctx, orc):
+    import paper_2603_01122_gb300 as pm
+    n = 4096
+    for seed, human, purpose, p0, block in [(0, 0, 1, 0, 0), (20260301, 7, 2, 123456, 3),
+                                            (2**64 - 1, 2**32 - 1, 2, 2**40, 2**50)]:
+        out = torch.empty((n, 4), dtype=torch.int64, device="cuda:0")
+        pm.pm_philox_blocks(ctx, seed, human, purpose, p0, block, n, out)
+        got = out.cpu().numpy().view(np.uint64)
+        for i in list(range(64)) + list(range(n - 64, n)):
+            want = orc.philox4x64([(p0 + i) % 2**64, block, purpose, 0], [seed, human])
+            np.testing.assert_array_equal(got[i], want)
+
+
+# --------------------------------------------------------------------- posterior
+@pytest.mark.parametrize("name", ["plain_small", "paper_scale"])
+def test_posterior_matches_oracle(ctx, orc, name):
+    hu = getattr(workloads, name)()
+    m, obs, want = _obs_and_post(orc, hu)
+    got = posterior(ctx, GpuHuman.of(hu), obs, hu.uniform_log_prior())
+    assert_posterior_close(got, want)
+
+
+def test_posterior_batched_workload_histories(ctx, orc):
+    """All 16 humans of the batched workload (G = 2..6, 50 steps each)."""
+    for hu in workloads.batched():
+        m, obs, want = _obs_and_post(orc, hu)
+        got = posterior(ctx, GpuHuman.of(hu), obs, hu.uniform_log_prior())
+        assert_posterior_close(got, want)
+
+
+def test_posterior_mask_stationary_and_weights(ctx, orc):
+    hu = workloads.paper_scale()
+    rng = np.random.default_rng(9)
+    mask = int(rng.integers(0, 2**36)) & ~1  # heading 0 stays enabled
+    m = orc.Model(hu.K, hu.speed, hu.dt, hu.goals, hu.beta, w1=0.3, w2=1.7, mask_off=mask)
+    obs = orc.simulate(orc.Model(hu.K, hu.speed, hu.dt, hu.goals, hu.beta), hu.true_j, hu.start, 30,
+                       hu.obs_seed, hu.human_id).astype(np.float32)
+    obs = np.concatenate([obs[:10], obs[9:10], obs[9:10], obs[10:]])  # two stationary steps
+    prior = np.log(rng.dirichlet(np.ones(hu.G * hu.B))).astype(np.float32)
+    want, skipped = orc.update_posterior(m, obs.astype(np.float64), prior)
+    assert skipped == 2
+    gh = GpuHuman(hu.K, hu.speed, hu.dt, hu.goals, hu.beta, w1=0.3, w2=1.7, heading_off=mask)
+    assert_posterior_close(posterior(ctx, gh, obs, prior), want)
+
+
+def test_posterior_one_step_calls_equal_one_call(ctx, orc):
+    """Serving form: 50 calls of one observed step each equal one 50-step call."""
+    hu = workloads.paper_scale()
+    m, obs, want = _obs_and_post(orc, hu)
+    gh = GpuHuman.of(hu)
+    import paper_2603_01122_gb300 as pm
+    obs_d = dev(obs)
+    lb = dev(hu.uniform_log_prior())
+    for t in range(hu.n_obs):
+        pm.pm_update_posterior(ctx, gh.model, obs_d[t:t + 2], 1, lb)
+    torch.cuda.synchronize()
+    assert_posterior_close(lb.cpu().numpy(), want)
+
+
+def test_posterior_large_history_max_components(ctx, orc):
+    """G*B = 256 components, 200 steps, K = 64."""
+    rng = np.random.default_rng(4)
+    goals = rng.uniform(0, 10, (16, 2)).astype(np.float32)
+    beta = workloads.beta_grid(-2.0, 2.0, 16)
+    m = orc.Model(64, 1.0, workloads.f32(0.05), goals, beta)
+    obs = orc.simulate(m, 37, np.float32([5.0, 5.0]), 200, 3, 3).astype(np.float32)
+    prior = np.full(256, -math.log(256), np.float32)
+    want, _ = orc.update_posterior(m, obs.astype(np.float64), prior)
+    got = posterior(ctx, GpuHuman(64, 1.0, workloads.f32(0.05), goals, beta), obs, prior)
+    assert_posterior_close(got, want)
+
+
+# -------------------------------------------------------------------- rollout
+def test_plain_small_trajectories_and_histogram(ctx, orc):
+    """Every particle of the plain_small workload traced: draws identical except
+    <= 1e-4 of particles, histogram bit-exact given the FP32 states."""
+    hu = workloads.plain_small()
+    m, obs, post = _obs_and_post(orc, hu)
+    gh = GpuHuman.of(hu)
+    lb = posterior(ctx, gh, obs, hu.uniform_log_prior())
+    z0 = obs[-1]
+    N, T = hu.n_particles, hu.horizon
+    got = predict(ctx, gh, lb, z0, N, T, hu.grid, hu.seed, hu.human_id, n_trace=N)
+    ref = orc.rollout(m, lb, z0, T, hu.seed, hu.human_id, 0, N, grid=hu.grid, want_headings=True,
+                      want_states32=True, want_comp=True)
+    d = compare_trajectories(got, ref)
+    assert d <= TRAJ_RATE * N, d
+    c, o = orc.bin_states(got["states32"], hu.grid)
+    np.testing.assert_array_equal(got["counts"], c)
+    np.testing.assert_array_equal(got["oob"], o)
+    if d == 0:
+        np.testing.assert_array_equal(got["counts"], ref["counts"])
+
+
+def test_plain_small_occupancy_vs_exact_propagation(ctx, orc):
+    hu = workloads.plain_small()
+    m, obs, post = _obs_and_post(orc, hu)
+    gh = GpuHuman.of(hu)
+    lb = posterior(ctx, gh, obs, hu.uniform_log_prior())
+    z0 = obs[-1]
+    got = predict(ctx, gh, lb, z0, hu.n_particles, hu.horizon, hu.grid, hu.seed, hu.human_id)
+    p, po, em = orc.exact_occupancy(m, lb.astype(np.float64), z0.astype(np.float64), hu.horizon, hu.grid)
+    for t in range(1, hu.horizon + 1):
+        d = tv(got["counts"][t - 1], got["oob"][t - 1], hu.n_particles, p[t - 1], po[t - 1])
+        assert d <= tv_bound(p[t - 1], po[t - 1], hu.n_particles) + em[t - 1], (t, d)
+
+
+def test_beta_zero_lattice_walk(ctx, orc):
+    T, N = 16, 100_000
+    dt = workloads.f32(0.1)
+    gh = GpuHuman(4, 1.0, dt, [[3.0, 1.0]], [0.0])
+    res = workloads.f32(0.1)
+    x0 = workloads.f32(-(T + 1.5) * 0.1)
+    grid = (x0, x0, res, 2 * T + 3, 2 * T + 3)
+    got = predict(ctx, gh, [0.0], (0.0, 0.0), N, T, grid, 5, 9)
+    c = T + 1
+    for t in range(1, T + 1):
+        p = np.zeros((2 * c + 1, 2 * c + 1))
+        for i in range(-t, t + 1):
+            for j in range(-t, t + 1):
+                p[c + j, c + i] = lattice_k4(t, i, j)
+        d = tv(got["counts"][t - 1], got["oob"][t - 1], N, p, 0.0)
+        assert d <= tv_bound(p, 0.0, N), (t, d)
+
+
+def test_large_beta_straight_line(ctx, orc):
+    hu = workloads.plain_small()
+    gh = GpuHuman(hu.K, hu.speed, hu.dt, [[4.0, 0.0]], [1e4])
+    got = predict(ctx, gh, [0.0], (0.0, 0.0), 3000, hu.horizon, hu.grid, 1, 0, n_trace=3000)
+    assert np.all(got["headings"] == 0)
+    assert np.all(got["states32"] == got["states32"][0])
+    for t in range(hu.horizon):
+        assert got["counts"][t].max() == 3000
+
+
+def test_paper_scale_sampled_particles_full_launch(ctx, orc):
+    """Full paper_scale launch (N = 100k, T = 150, the benchmark's configuration)
+    with the first 20000 particles traced and recomputed one by one."""
+    hu = workloads.paper_scale()
+    m, obs, post = _obs_and_post(orc, hu)
+    gh = GpuHuman.of(hu)
+    lb = posterior(ctx, gh, obs, hu.uniform_log_prior())
+    z0 = obs[-1]
+    N, T, n = hu.n_particles, hu.horizon, 20000
+    got = predict(ctx, gh, lb, z0, N, T, hu.grid, hu.seed, hu.human_id, n_trace=n)
+    ref = orc.rollout(m, lb, z0, T, hu.seed, hu.human_id, 0, n, want_counts=False,
+                      want_headings=True, want_states32=True, want_comp=True)
+    d = compare_trajectories(got, ref)
+    print(f"paper_scale: {d} of {n} sampled particles diverged")
+    assert d <= TRAJ_RATE * n, d
+    counts, oob = got["counts"], got["oob"]
+    assert np.all(counts.reshape(T, -1).sum(1).astype(np.int64) + oob == N)
+    # every count lies within reach of z0 after t steps (|z_t - z0| <= t v dt)
+    x0, y0, res, W, H = hu.grid
+    yy, xx = np.mgrid[0:H, 0:W]
+    cxz, cyz = (z0[0] - x0) / res, (z0[1] - y0) / res
+    dist = np.hypot(np.maximum(np.abs(xx + 0.5 - cxz) - 0.5, 0), np.maximum(np.abs(yy + 0.5 - cyz) - 0.5, 0)) * res
+    for t in (1, 10, 75, 150):
+        assert counts[t - 1][dist > t * hu.speed * hu.dt + 1e-4].sum() == 0
+    # the traced particles' own histogram is a lower bound of the full one
+    c_sub, _ = orc.bin_states(got["states32"], hu.grid)
+    assert np.all(c_sub <= counts)
+
+
+@pytest.mark.parametrize("case", ["ragged_N", "single", "T1", "corner", "outside", "K3", "K37_mask",
+                                  "K64", "J256", "tiny_grid"])
+def test_edge_cases_full_trace(ctx, orc, case):
+    hu = workloads.paper_scale()
+    K, goals, beta, heading_off = hu.K, hu.goals, hu.beta, 0
+    N, T, z0, grid = 3001, 40, np.float32([5.0, 5.0]), hu.grid
+    dt = hu.dt
+    rng = np.random.default_rng(zlib.crc32(case.encode()))
+    if case == "ragged_N":
+        N = 257 * 13 + 5
+    elif case == "single":
+        N = 1
+    elif case == "T1":
+        T = 1
+    elif case == "corner":
+        z0 = np.float32([0.02, 0.03])
+    elif case == "outside":
+        z0 = np.float32([-0.5, 10.2])
+    elif case == "K3":
+        K = 3
+    elif case == "K37_mask":
+        K, heading_off = 37, int(rng.integers(0, 2**37)) & ~0b111
+    elif case == "K64":
+        K = 64
+    elif case == "J256":
+        goals = rng.uniform(0, 10, (16, 2)).astype(np.float32)
+        beta = workloads.beta_grid(-2.0, 2.0, 16)
+    elif case == "tiny_grid":
+        grid = (workloads.f32(4.9), workloads.f32(4.95), workloads.f32(0.05), 3, 2)
+        dt = workloads.f32(0.05)
+    m = orc.Model(K, hu.speed, dt, goals, beta, mask_off=heading_off)
+    J = m.G * m.B
+    lb = np.log(rng.dirichlet(np.ones(J))).astype(np.float32)
+    gh = GpuHuman(K, hu.speed, dt, goals, beta, heading_off=heading_off)
+    got = predict(ctx, gh, lb, z0, N, T, grid, 77, 5, n_trace=N)
+    ref = orc.rollout(m, lb, z0, T, 77, 5, 0, N, grid=grid, want_headings=True, want_states32=True,
+                      want_comp=True)
+    d = compare_trajectories(got, ref)
+    assert d < poisson_reject_at(N), d
+    c, o = orc.bin_states(got["states32"], grid)
+    np.testing.assert_array_equal(got["counts"], c)
+    np.testing.assert_array_equal(got["oob"], o)
+    assert np.all(got["counts"].reshape(T, -1).sum(1).astype(np.int64) + got["oob"] == N)
+    if heading_off:
+        off = [k for k in range(K) if (heading_off >> k) & 1]
+        assert not np.isin(got["headings"], off).any()
+
+
+def test_determinism_and_streams(ctx, orc):
+    hu = workloads.plain_small()
+    gh = GpuHuman.of(hu)
+    lb = hu.uniform_log_prior()
+    a = predict(ctx, gh, lb, (0.0, 0.0), 20000, 20, hu.grid, 1, 2)
+    b = predict(ctx, gh, lb, (0.0, 0.0), 20000, 20, hu.grid, 1, 2)
+    np.testing.assert_array_equal(a["counts"], b["counts"])
+    c = predict(ctx, gh, lb, (0.0, 0.0), 20000, 20, hu.grid, 1, 3)
+    assert not np.array_equal(a["counts"], c["counts"])
+
+
+def test_host_api_matches_device_path(ctx, orc):
+    import paper_2603_01122_gb300 as pm
+    hu = workloads.paper_scale()
+    m, obs, post = _obs_and_post(orc, hu)
+    gh = GpuHuman.of(hu)
+    lb = posterior(ctx, gh, obs, hu.uniform_log_prior())
+    N, T = 20000, 60
+    want = predict(ctx, gh, lb, obs[-1], N, T, hu.grid, hu.seed, hu.human_id)
+    x0, y0, res, W, H = hu.grid
+    post_out = np.zeros(hu.G * hu.B, np.float32)
+    counts = np.zeros((T, H, W), np.uint32)
+    oob = np.zeros(T, np.uint32)
+    pm.pm_predict_host(ctx, gh.model, np.ascontiguousarray(hu.goals), np.ascontiguousarray(hu.beta),
+                       np.ascontiguousarray(obs), hu.n_obs, hu.uniform_log_prior(), N, T,
+                       pm.make_grid(x0, y0, res, W, H), hu.seed, hu.human_id, post_out, counts, oob)
+    np.testing.assert_array_equal(post_out, lb)
+    np.testing.assert_array_equal(counts, want["counts"])
+    np.testing.assert_array_equal(oob, want["oob"])
+
+
+def test_invalid_arguments_rejected(ctx):
+    import paper_2603_01122_gb300 as pm
+    hu = workloads.plain_small()
+    gh = GpuHuman.of(hu)
+    lb = dev(hu.uniform_log_prior())
+    counts = torch.zeros((4, 100, 100), dtype=torch.int32, device="cuda:0")
+    oob = torch.zeros(4, dtype=torch.int32, device="cuda:0")
+    g = pm.make_grid(*hu.grid)
+    bad = [
+        dict(n_particles=0), dict(horizon=0), dict(horizon=pm.PM_MAX_HORIZON + 1),
+        dict(z0x=float("nan")), dict(grid=pm.make_grid(0, 0, 0.0, 10, 10)),
+        dict(grid=pm.make_grid(0, 0, 0.1, 0, 10)),
+    ]
+    for kw in bad:
+        args = dict(n_particles=100, horizon=4, z0x=0.0, grid=g)
+        args.update(kw)
+        with pytest.raises(pm.PmError) as e:
+            pm.pm_predict_occupancy(ctx, gh.model, lb, args["z0x"], 0.0, args["n_particles"],
+                                    args["horizon"], args["grid"], 1, 1, counts, oob)
+        assert e.value.status == pm.PM_EINVAL
+    for field, val in [("K", 0), ("K", 65), ("G", 0), ("B", 300), ("dt", 0.0), ("speed", float("inf"))]:
+        mm = pm.make_model(hu.K, hu.speed, hu.dt, gh.goals, gh.beta)
+        setattr(mm, field, val)
+        with pytest.raises(pm.PmError):
+            pm.pm_predict_occupancy(ctx, mm, lb, 0.0, 0.0, 100, 4, g, 1, 1, counts, oob)
+    mm = pm.make_model(hu.K, hu.speed, hu.dt, gh.goals, gh.beta, heading_off=0xFF)
+    with pytest.raises(pm.PmError):
+        pm.pm_update_posterior(ctx, mm, dev(np.zeros((3, 2), np.float32)), 2, lb)
+    torch.cuda.synchronize()
+    assert counts.sum().item() == 0  # nothing was queued
