@@ -43,8 +43,8 @@ ROLLOUT_SOURCES = ["paper_2603_01122_gb300/csrc/pm_rollout.cu", "paper_2603_0112
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=20000, help="particles in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -81,7 +81,7 @@ def sources_hash(paths):
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -105,6 +105,10 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def mark(self, t0, t1):
+        """Keep only the samples stamped inside the wall-clock interval [t0, t1]."""
+        self.t0, self.t1 = t0, t1
+
     def __exit__(self, *exc):
         if self.proc:
             self.proc.terminate()
@@ -114,18 +118,23 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        import datetime
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        t0, t1 = getattr(self, "t0", None), getattr(self, "t1", None)
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                if t0 is not None and not (t0 - 0.05 <= ts <= t1 + 0.05):
+                    continue
+                sm.append(float(parts[2]))
+                mx.append(float(parts[3]))
             except ValueError:
                 continue
-            for n, v in zip(names, parts[5:9]):
+            for n, v in zip(names, parts[6:10]):
                 if v.lower() == "active":
                     reasons.add(n)
         if not sm:
@@ -256,6 +265,15 @@ def run_native(args):
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     phys = vis.split(",")[local] if vis and vis.split(",")[local].isdigit() else str(local)
     with ClockSampler(phys) as clk:
+        pre = 200 if args.steps >= 100 else 0  # keep the GPU busy while nvidia-smi starts
+        if pre:
+            time.sleep(1.0)
+        with torch.cuda.stream(stream):
+            for _ in range(pre):
+                flush.fill_(1.0)
+                step()
+        torch.cuda.synchronize()
+        wall_t0 = time.time()
         wall0 = time.perf_counter()
         with torch.cuda.stream(stream):
             for i in range(args.steps):
@@ -269,6 +287,9 @@ def run_native(args):
                 ev[i][2].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
+        clk.mark(wall_t0, time.time())
+        if pre:
+            time.sleep(0.3)
     if world > 1:
         tdist.barrier()
     step_ms = [a.elapsed_time(c) for a, b, c in ev]

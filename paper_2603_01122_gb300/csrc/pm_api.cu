@@ -22,6 +22,10 @@ struct pm_ctx {
     // device staging owned by the context (host-buffer call, probe sink)
     void *stage = nullptr;
     size_t stage_bytes = 0;
+    // scratch of the belief update: per-chunk accumulators and a ticket word
+    void *post_scratch = nullptr;
+    size_t post_scratch_bytes = 0;
+    unsigned *ticket = nullptr;
 };
 
 namespace {
@@ -180,6 +184,37 @@ void choose_window(const pm_model *m, const pm_grid *g, float z0x, float z0y, in
     }
 }
 
+// Block size of the rollout: one particle per thread, all CTAs resident in
+// one wave where possible, and the CTAs spread evenly over the SMs (the
+// kernel time follows the most loaded SM: ceil(blocks / SMs) CTAs of
+// `threads` particles each).
+int choose_rollout_threads(pm_ctx *ctx, const pm_model *model, const pm_grid *grid, pm::RolloutArgs &a,
+                           bool hist, size_t *dyn_out)
+{
+    static const int cand[] = {256, 224, 192, 160, 128};
+    double best_eff = -1.0;
+    int best_t = 256;
+    size_t best_dyn = 0;
+    pm::RolloutArgs trial = a;
+    for (int t : cand) {
+        size_t dyn = 0;
+        if (hist) choose_window(model, grid, a.z0x, a.z0y, a.T, t, 64 * 1024, trial, &dyn);
+        const int occ = pm::rollout_occupancy(trial, t, dyn);
+        if (occ < 1) continue;
+        const long long blocks = ((long long)a.N + t - 1) / t;
+        const long long per_sm = (blocks + ctx->sm_count - 1) / ctx->sm_count;
+        const double eff = (double)a.N / ((double)per_sm * t * ctx->sm_count) * (occ >= 2 ? 1.0 : 0.8);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best_t = t;
+            best_dyn = dyn;
+        }
+    }
+    if (hist) choose_window(model, grid, a.z0x, a.z0y, a.T, best_t, 64 * 1024, a, &best_dyn);
+    *dyn_out = best_dyn;
+    return best_t;
+}
+
 pm_status ensure_stage(pm_ctx *ctx, size_t bytes)
 {
     if (ctx->stage_bytes >= bytes) return PM_OK;
@@ -192,6 +227,30 @@ pm_status ensure_stage(pm_ctx *ctx, size_t bytes)
         return fail(PM_ENOMEM, "cudaMalloc(%zu) for context staging failed: %s", bytes, cudaGetErrorString(e));
     }
     ctx->stage_bytes = bytes;
+    return PM_OK;
+}
+
+pm_status ensure_posterior_scratch(pm_ctx *ctx, size_t bytes)
+{
+    if (!ctx->ticket) {
+        cudaError_t e = cudaMalloc((void **)&ctx->ticket, 256);
+        if (e == cudaSuccess) e = cudaMemset(ctx->ticket, 0, 256);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->ticket = nullptr;
+            return fail(PM_ENOMEM, "ticket allocation failed: %s", cudaGetErrorString(e));
+        }
+    }
+    if (ctx->post_scratch_bytes >= bytes) return PM_OK;
+    if (ctx->post_scratch) cudaFree(ctx->post_scratch);
+    ctx->post_scratch = nullptr;
+    ctx->post_scratch_bytes = 0;
+    cudaError_t e = cudaMalloc(&ctx->post_scratch, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PM_ENOMEM, "cudaMalloc(%zu) for belief-update scratch failed", bytes);
+    }
+    ctx->post_scratch_bytes = bytes;
     return PM_OK;
 }
 
@@ -233,8 +292,8 @@ pm_status predict_impl(pm_ctx *ctx, const pm_model *model, const float *log_beli
     a.tr_states = states;
     a.tr_head = headings;
     a.tr_comp = components;
-    const int threads = 256;
     size_t dyn = 0;
+    int threads = 256;
     if (hist) {
         a.gx0 = grid->x0;
         a.gy0 = grid->y0;
@@ -243,8 +302,6 @@ pm_status predict_impl(pm_ctx *ctx, const pm_model *model, const float *log_beli
         a.H = grid->H;
         a.counts = counts;
         a.oob = oob;
-        const size_t budget = 64 * 1024;
-        choose_window(model, grid, z0x, z0y, horizon, threads, budget, a, &dyn);
         const size_t plane = (size_t)grid->W * (size_t)grid->H;
         cudaError_t e = cudaMemsetAsync(counts, 0, plane * (size_t)horizon * sizeof(uint32_t), stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(oob, 0, (size_t)horizon * sizeof(uint32_t), stream);
@@ -253,6 +310,7 @@ pm_status predict_impl(pm_ctx *ctx, const pm_model *model, const float *log_beli
         a.W = a.H = 1;
         a.inv_res = 1.0f;
     }
+    threads = choose_rollout_threads(ctx, model, grid, a, hist, &dyn);
     cudaError_t e = pm::launch_rollout(a, threads, dyn, stream);
     if (e != cudaSuccess) return cuda_fail(e, "rollout launch");
     return PM_OK;
@@ -291,7 +349,12 @@ pm_status posterior_impl(pm_ctx *ctx, const pm_model *model, const float *obs_xy
     a.obs = obs_xy;
     a.n_obs = n_obs;
     a.log_b = log_belief;
-    cudaError_t e = pm::launch_posterior(a, stream);
+    const int n_chunks = pm::posterior_chunks(n_obs, &a.steps_per_chunk);
+    st = ensure_posterior_scratch(ctx, pm::posterior_scratch_bytes(n_chunks, model->G * model->B));
+    if (st != PM_OK) return st;
+    a.part = (float *)ctx->post_scratch;
+    a.ticket = ctx->ticket;
+    cudaError_t e = pm::launch_posterior(a, n_chunks, stream);
     if (e != cudaSuccess) return cuda_fail(e, "posterior launch");
     return PM_OK;
 }
@@ -326,9 +389,11 @@ pm_status pm_create(pm_ctx **out, int device)
 void pm_destroy(pm_ctx *ctx)
 {
     if (!ctx) return;
-    if (ctx->stage) {
+    {
         DeviceScope dev(ctx->device);
-        cudaFree(ctx->stage);
+        if (ctx->stage) cudaFree(ctx->stage);
+        if (ctx->post_scratch) cudaFree(ctx->post_scratch);
+        if (ctx->ticket) cudaFree(ctx->ticket);
     }
     delete ctx;
 }

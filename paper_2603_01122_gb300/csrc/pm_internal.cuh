@@ -115,13 +115,19 @@ struct PosteriorArgs {
     const float *beta;
     const float *obs;
     int n_obs;
+    int steps_per_chunk; // observed steps handled by one CTA
     float *log_b;
+    float *part;         // scratch: per (chunk, component) accumulators, then [J] doubles
+    unsigned *ticket;    // scratch: chunks finished so far (0 between calls)
 };
 
 // Launch wrappers (defined next to their kernels).
 cudaError_t launch_rollout(const RolloutArgs &a, int threads, size_t dyn_smem, cudaStream_t s);
 size_t rollout_static_smem_estimate();
-cudaError_t launch_posterior(const PosteriorArgs &a, cudaStream_t s);
+int rollout_occupancy(const RolloutArgs &a, int threads, size_t dyn_smem); // resident CTAs per SM
+cudaError_t launch_posterior(const PosteriorArgs &a, int n_chunks, cudaStream_t s);
+int posterior_chunks(int n_obs, int *steps_per_chunk);
+size_t posterior_scratch_bytes(int n_chunks, int J);
 cudaError_t launch_philox_blocks(uint64_t seed, uint32_t human, uint32_t purpose,
                                  uint64_t particle0, uint64_t block, int n, uint64_t *out,
                                  cudaStream_t s);

@@ -3,15 +3,22 @@
 //
 // The per-step log-likelihood of component j = (g, b) is
 //   l_t(j) = beta Q(z_t, theta_obs; g) - LSE_k beta Q(z_t, theta_k; g)
-//          = -LSE_k beta w2 (d_obs - d_k),
-// with d the distance from the next state to the goal. The differences are
-// formed without cancellation: d_obs - d_k = 2 s (e_obs - e_k).(z - g) /
-// (d_obs + d_k). One warp handles one component at a time with its lanes
-// over the headings (warp-shuffle max and sum); the log-likelihoods are
-// accumulated over the observed steps in FP64, and the LogSumExp
-// normalisation over (beta, g) is applied once in FP64 at the end, which is
-// the sequential Eq. 7 telescoped (the per-step normalisers are common to
-// every component and cancel).
+//          = -m_t(j) - log S_t(j),   S_t(j) = sum_k exp(a_k - m_t(j)),
+// with a_k = beta w2 (d_obs - d_k), d the distance from the next state to the
+// goal and m_t(j) = max_k a_k. The differences are formed without
+// cancellation: d_obs - d_k = 2 s (e_obs - e_k).(z - g) / (d_obs + d_k).
+//
+// Layout: the observed steps are split into chunks, one CTA per chunk (and
+// per human in the batched form); a warp handles one component at a time with
+// its lanes over the headings (warp-shuffle max and sum). The per-step terms
+// are accumulated without any per-step logarithm: sum_t m_t in double-float
+// and prod_t S_t as a double-float mantissa with an integer power-of-two
+// exponent, so the FP32 rounding of log(S_t) (2.4e-7 at S_t ~ 64, and
+// correlated over steps) never enters. The last CTA of a human to finish
+// (ticket counter, no waiting) folds the chunks in order, takes one logarithm
+// per component, adds the prior and applies the LogSumExp normalisation once
+// -- Eq. 7 telescoped over the steps, since its per-step normalisers are
+// common to every component -- and resets the ticket for the next call.
 #include <cuda_runtime.h>
 
 #include "pm_internal.cuh"
@@ -33,18 +40,61 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-__device__ __forceinline__ double warp_max_d(double v)
+// Double-float accumulators of one component over a run of steps.
+struct Acc {
+    float mh, ml; // sum of m_t (hi + lo)
+    float ph, pl; // product of S_t, mantissa in [1, 2) (hi + lo)
+    int e;        // product exponent
+};
+
+__device__ __forceinline__ void acc_init(Acc &a)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
+    a.mh = a.ml = 0.0f;
+    a.ph = 1.0f;
+    a.pl = 0.0f;
+    a.e = 0;
 }
 
-__device__ __forceinline__ double warp_sum_d(double v)
+__device__ __forceinline__ void acc_add(Acc &a, float m)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    const float s = a.mh + m;
+    const float bb = s - a.mh;
+    const float err = (a.mh - (s - bb)) + (m - bb);
+    a.mh = s;
+    a.ml += err;
+}
+
+// (ph, pl) *= (qh, ql), then scale the mantissa back into [1, 2).
+__device__ __forceinline__ void acc_mul(Acc &a, float qh, float ql, int qe)
+{
+    const float p = a.ph * qh;
+    const float err = fmaf(a.ph, qh, -p);
+    const float q = fmaf(a.ph, ql, fmaf(a.pl, qh, err));
+    float h = p + q;
+    float l = q - (h - p);
+    const int ex = ((__float_as_int(h) >> 23) & 0xFF) - 127; // h in [1, 2^8) here
+    const float sc = __int_as_float((127 - ex) << 23);      // 2^-ex, exact
+    a.ph = h * sc;
+    a.pl = l * sc;
+    a.e += ex + qe;
+}
+
+__device__ __forceinline__ void acc_merge(Acc &a, const Acc &b)
+{
+    acc_add(a, b.mh);
+    acc_add(a, b.ml);
+    acc_mul(a, b.ph, b.pl, b.e);
+}
+
+__device__ __forceinline__ Acc shfl_acc(const Acc &a, int o)
+{
+    Acc r;
+    r.mh = __shfl_xor_sync(0xffffffffu, a.mh, o);
+    r.ml = __shfl_xor_sync(0xffffffffu, a.ml, o);
+    r.ph = __shfl_xor_sync(0xffffffffu, a.ph, o);
+    r.pl = __shfl_xor_sync(0xffffffffu, a.pl, o);
+    r.e = __shfl_xor_sync(0xffffffffu, a.e, o);
+    return r;
 }
 
 // Logit of heading k relative to the observed heading, beta w2 (d_obs - d_k).
@@ -58,9 +108,12 @@ __device__ __forceinline__ float rel_logit(float bw, float two_s, float D, float
 
 __global__ void __launch_bounds__(1024) posterior_kernel(const __grid_constant__ PosteriorArgs a)
 {
-    __shared__ double acc[kMaxJ];
+    __shared__ int last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int J = a.G * a.B;
+    const int chunk = blockIdx.x, nchunk = gridDim.x;
+    const int t0 = chunk * a.steps_per_chunk;
+    const int t1 = min(a.n_obs, t0 + a.steps_per_chunk);
     const int k0 = lane, k1 = lane + 32;
     const bool on0 = k0 < a.K && ((a.enabled >> k0) & 1ull);
     const bool on1 = k1 < a.K && ((a.enabled >> k1) & 1ull);
@@ -71,8 +124,9 @@ __global__ void __launch_bounds__(1024) posterior_kernel(const __grid_constant__
         const int g = j / a.B, b = j - g * a.B;
         const float bw = a.beta[b] * a.w2;
         const float gx = a.goals[2 * g], gy = a.goals[2 * g + 1];
-        double sum = 0.0;
-        for (int t = 0; t < a.n_obs; ++t) {
+        Acc acc;
+        acc_init(acc);
+        for (int t = t0; t < t1; ++t) {
             const float zx = a.obs[2 * t], zy = a.obs[2 * t + 1];
             const float dx = a.obs[2 * t + 2] - zx, dy = a.obs[2 * t + 3] - zy;
             const float len = sqrtf(fmaf(dx, dx, dy * dy));
@@ -84,44 +138,90 @@ __global__ void __launch_bounds__(1024) posterior_kernel(const __grid_constant__
             const float l0 = on0 ? rel_logit(bw, a.two_s, D, px, py, ex, ey, d_o, ux0, uy0) : -INFINITY;
             const float l1 = on1 ? rel_logit(bw, a.two_s, D, px, py, ex, ey, d_o, ux1, uy1) : -INFINITY;
             const float m = warp_max(fmaxf(l0, l1));
-            const float se = warp_sum((on0 ? expf(l0 - m) : 0.0f) + (on1 ? expf(l1 - m) : 0.0f));
-            sum -= (double)m + (double)logf(se);
+            const float S = warp_sum((on0 ? expf(l0 - m) : 0.0f) + (on1 ? expf(l1 - m) : 0.0f));
+            acc_add(acc, m);
+            acc_mul(acc, S, 0.0f, 0);
         }
-        if (lane == 0) acc[j] = sum;
+        if (lane == 0) {
+            float *p = a.part + 5 * ((size_t)chunk * J + j);
+            p[0] = acc.mh;
+            p[1] = acc.ml;
+            p[2] = acc.ph;
+            p[3] = acc.pl;
+            p[4] = __int_as_float(acc.e);
+        }
+    }
+
+    // the last chunk to finish combines and normalises
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(a.ticket, 1u) == (unsigned)(nchunk - 1));
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+
+    double *L = reinterpret_cast<double *>(a.part + ((5 * (size_t)nchunk * J + 1) & ~(size_t)1)); // [J], 8-byte aligned
+    for (int j = warp; j < J; j += nwarp) {
+        Acc acc;
+        acc_init(acc);
+        for (int c = lane; c < nchunk; c += 32) {
+            const volatile float *p = a.part + 5 * ((size_t)c * J + j);
+            Acc q;
+            q.mh = p[0];
+            q.ml = p[1];
+            q.ph = p[2];
+            q.pl = p[3];
+            q.e = __float_as_int(p[4]);
+            acc_merge(acc, q);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const Acc q = shfl_acc(acc, o);
+            acc_merge(acc, q);
+        }
+        if (lane == 0) {
+            // sum_t l_t(j) = -(sum_t m_t) - log(prod_t S_t)
+            const double logS = (double)acc.e * 0.6931471805599453 + (double)log1pf(acc.ph - 1.0f) +
+                                (double)acc.pl / (double)acc.ph;
+            L[j] = (double)a.log_b[j] - ((double)acc.mh + (double)acc.ml) - logS;
+        }
     }
     __syncthreads();
     if (warp == 0) {
-        double L[kMaxJ / 32];
         double mx = -INFINITY;
+        for (int j = lane; j < J; j += 32) mx = fmax(mx, L[j]);
 #pragma unroll
-        for (int q = 0; q < kMaxJ / 32; ++q) {
-            const int j = lane + 32 * q;
-            L[q] = (j < J) ? (double)a.log_b[j] + acc[j] : -INFINITY;
-            mx = fmax(mx, L[q]);
-        }
-        mx = warp_max_d(mx);
-        double se = 0.0;
-#pragma unroll
-        for (int q = 0; q < kMaxJ / 32; ++q)
-            if (L[q] != -INFINITY) se += exp(L[q] - mx);
-        se = warp_sum_d(se);
-        const double lse = mx + log(se);
-#pragma unroll
-        for (int q = 0; q < kMaxJ / 32; ++q) {
-            const int j = lane + 32 * q;
-            if (j < J) a.log_b[j] = (float)(L[q] - lse);
-        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        float se = 0.0f;
+        for (int j = lane; j < J; j += 32)
+            if (L[j] != -INFINITY) se += expf((float)(L[j] - mx));
+        se = warp_sum(se);
+        const double lse = mx + log((double)se);
+        for (int j = lane; j < J; j += 32) a.log_b[j] = (float)(L[j] - lse);
+        if (lane == 0) *a.ticket = 0u;
     }
 }
 
 } // namespace
 
-cudaError_t launch_posterior(const PosteriorArgs &a, cudaStream_t s)
+size_t posterior_scratch_bytes(int n_chunks, int J)
+{
+    return ((5 * (size_t)n_chunks * J + 1) & ~(size_t)1) * sizeof(float) + (size_t)J * sizeof(double);
+}
+
+int posterior_chunks(int n_obs, int *steps_per_chunk)
+{
+    const int spc = (n_obs + 63) / 64;
+    *steps_per_chunk = spc < 1 ? 1 : spc;
+    return (n_obs + *steps_per_chunk - 1) / *steps_per_chunk;
+}
+
+cudaError_t launch_posterior(const PosteriorArgs &a, int n_chunks, cudaStream_t s)
 {
     const int J = a.G * a.B;
     int threads = 32 * J;
     if (threads > 1024) threads = 1024;
-    posterior_kernel<<<1, threads, 0, s>>>(a);
+    posterior_kernel<<<n_chunks, threads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -82,13 +82,28 @@ __device__ __forceinline__ int draw_heading(const RolloutArgs &a, float x, float
     const float hD = 0.5f * rsqrt_approx(D); // 1/(2 d), D >= s^2 > 0
     float dv[KT];
     float dref = 0.0f;
+    if (FULL && (KT % 2 == 0)) {
+        // e_{k+K/2} = -e_k exactly in the tables: one dot product serves both
 #pragma unroll
-    for (int k = 0; k < KT; ++k) {
-        const float p = fmaf(a.tab.tx[k], dx, a.tab.ty[k] * dy); // 2 s e_k.(z - g)
-        const float dk = sqrt_approx(fmaxf(D + p, 0.0f));
-        const float rk = fmaf(-dk, dk, D) + p;                  // residual D + p - dk^2
-        if (k == 0) dref = dk;
-        dv[k] = fmaf(rk, hD, dk - dref);                         // d_k - d_0, corrected
+        for (int k = 0; k < KT / 2; ++k) {
+            const float p = fmaf(a.tab.tx[k], dx, a.tab.ty[k] * dy); // 2 s e_k.(z - g)
+            const float dk = sqrt_approx(fmaxf(D + p, 0.0f));
+            const float dm = sqrt_approx(fmaxf(D - p, 0.0f));
+            const float rk = fmaf(-dk, dk, D) + p;                  // residual D + p - dk^2
+            const float rm = fmaf(-dm, dm, D) - p;
+            if (k == 0) dref = dk;
+            dv[k] = fmaf(rk, hD, dk - dref);                         // d_k - d_0, corrected
+            dv[k + KT / 2] = fmaf(rm, hD, dm - dref);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            const float p = fmaf(a.tab.tx[k], dx, a.tab.ty[k] * dy);
+            const float dk = sqrt_approx(fmaxf(D + p, 0.0f));
+            const float rk = fmaf(-dk, dk, D) + p;
+            if (k == 0) dref = dk;
+            dv[k] = fmaf(rk, hD, dk - dref);
+        }
     }
     float dmin = INFINITY;
 #pragma unroll
@@ -237,6 +252,15 @@ __global__ void __launch_bounds__(kRolloutThreads) rollout_kernel(const __grid_c
 }
 
 template <int KT>
+int occupancy_kt(bool full, int threads, size_t dyn_smem)
+{
+    int n = 0;
+    if (full) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_kernel<KT, true>, threads, dyn_smem);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_kernel<KT, false>, threads, dyn_smem);
+    return n;
+}
+
+template <int KT>
 cudaError_t launch_kt(const RolloutArgs &a, int threads, size_t dyn_smem, cudaStream_t s)
 {
     const uint64_t all = (KT >= 64) ? ~0ull : ((1ull << KT) - 1ull);
@@ -271,6 +295,28 @@ int rollout_kt_for(int K)
 }
 
 size_t rollout_static_smem_estimate() { return sizeof(RolloutShared); }
+
+int rollout_occupancy(const RolloutArgs &a, int threads, size_t dyn_smem)
+{
+    const int KT = rollout_kt_for(a.K);
+    const uint64_t all = (KT >= 64) ? ~0ull : ((1ull << KT) - 1ull);
+    const bool full = (a.K == KT) && ((a.enabled & all) == all);
+    if (dyn_smem > 48 * 1024) {
+        // the attribute must be raised before the occupancy query counts it
+        switch (KT) {
+        case 8: cudaFuncSetAttribute(full ? rollout_kernel<8, true> : rollout_kernel<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem); break;
+        case 16: cudaFuncSetAttribute(full ? rollout_kernel<16, true> : rollout_kernel<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem); break;
+        case 36: cudaFuncSetAttribute(full ? rollout_kernel<36, true> : rollout_kernel<36, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem); break;
+        default: cudaFuncSetAttribute(full ? rollout_kernel<64, true> : rollout_kernel<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem); break;
+        }
+    }
+    switch (KT) {
+    case 8: return occupancy_kt<8>(full, threads, dyn_smem);
+    case 16: return occupancy_kt<16>(full, threads, dyn_smem);
+    case 36: return occupancy_kt<36>(full, threads, dyn_smem);
+    default: return occupancy_kt<64>(full, threads, dyn_smem);
+    }
+}
 
 cudaError_t launch_rollout(const RolloutArgs &a, int threads, size_t dyn_smem, cudaStream_t s)
 {
