@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=20000, help="particles in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched / serving / adjoint sections")
+    ap.add_argument("--serving-seconds", type=float, default=0.0,
+                    help="also run the Poisson arrival process for this many simulated seconds")
+    ap.add_argument("--serving-frames", type=int, default=250, help="frames of the forced-64-live run")
     return ap.parse_args()
 
 
@@ -197,6 +201,215 @@ def load_profile_traffic(kernel_hash):
     if d.get("kernel_sources_hash") != kernel_hash:
         return None
     return d.get("dram_bytes_per_launch")
+
+
+def gpu_paths(pm, ctx, torch, dev, hu, n_steps, human_id, start=None):
+    """Observed trajectory drawn from the model on the GPU: one traced particle
+    whose belief is a point mass on the true component."""
+    goals = torch.tensor(hu.goals, device=dev)
+    beta = torch.tensor(hu.beta, device=dev)
+    model = pm.make_model(hu.K, hu.speed, hu.dt, goals, beta)
+    J = hu.G * hu.B
+    onehot = torch.full((J,), -float("inf"), device=dev)
+    onehot[hu.true_j] = 0.0
+    st = torch.empty((1, n_steps, 2), device=dev)
+    z = hu.start if start is None else start
+    pm.pm_predict_occupancy_traced(ctx, model, onehot, float(z[0]), float(z[1]), 1, n_steps, None,
+                                   hu.obs_seed, human_id, None, None, 1, st, None, None)
+    return torch.cat([torch.tensor(np.asarray(z, np.float32), device=dev).view(1, 2), st[0]], 0).contiguous()
+
+
+def time_events(torch, stream, fn, reps):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_extra(args, pm, ctx, torch, dev, stream):
+    """Batched, serving, differentiation and small-case numbers (secondary
+    workloads; each quoted with its own unit)."""
+    out = {}
+    # -- plain_small: latency of one prediction (1 human, K = 8, N = 10k, T = 20)
+    hu = workloads.plain_small()
+    g, b = torch.tensor(hu.goals, device=dev), torch.tensor(hu.beta, device=dev)
+    model = pm.make_model(hu.K, hu.speed, hu.dt, g, b)
+    obs = gpu_paths(pm, ctx, torch, dev, hu, hu.n_obs, hu.human_id)
+    z0 = obs[-1].cpu().numpy()
+    prior = torch.tensor(hu.uniform_log_prior(), device=dev)
+    lb = torch.empty_like(prior)
+    x0, y0, res, W, H = hu.grid
+    grid = pm.make_grid(x0, y0, res, W, H)
+    counts = torch.empty((hu.horizon, H, W), dtype=torch.int32, device=dev)
+    oob = torch.empty(hu.horizon, dtype=torch.int32, device=dev)
+
+    def small():
+        lb.copy_(prior)
+        pm.pm_update_posterior(ctx, model, obs, hu.n_obs, lb, stream)
+        pm.pm_predict_occupancy(ctx, model, lb, float(z0[0]), float(z0[1]), hu.n_particles, hu.horizon, grid,
+                                hu.seed, hu.human_id, counts, oob, stream)
+    ms = time_events(torch, stream, small, 200)
+    out["plain_small"] = {"ms_per_prediction": ms, "hz": 1e3 / ms,
+                          "particle_steps_per_s": hu.n_particles * hu.horizon / (ms * 1e-3),
+                          "config": "1 human, K=8, N=10k, T=20, 20 observed steps, 100x100 grid"}
+
+    # -- batched: 16 humans, one persistent launch in a CUDA graph vs the plain per-human path
+    hs = workloads.batched()
+    recs = []
+    for k, h in enumerate(hs):
+        gg, bb = torch.tensor(h.goals, device=dev), torch.tensor(h.beta, device=dev)
+        ob = gpu_paths(pm, ctx, torch, dev, h, h.n_obs, h.human_id)
+        x0, y0, res, W, H = h.grid
+        recs.append(dict(h=h, g=gg, b=bb, obs=ob, prior=torch.tensor(h.uniform_log_prior(), device=dev),
+                         lb=torch.tensor(h.uniform_log_prior(), device=dev), z0=ob[-1].clone(),
+                         grid=pm.make_grid(x0, y0, res, W, H),
+                         counts=torch.empty((h.horizon, H, W), dtype=torch.int32, device=dev),
+                         oob=torch.empty(h.horizon, dtype=torch.int32, device=dev),
+                         model=pm.make_model(h.K, h.speed, h.dt, gg, bb)))
+    steps = sum(r["h"].n_particles * r["h"].horizon for r in recs)
+
+    def plain_batched():
+        for r in recs:
+            r["lb"].copy_(r["prior"])
+            pm.pm_update_posterior(ctx, r["model"], r["obs"], r["h"].n_obs, r["lb"], stream)
+            z = r["z0h"]
+            pm.pm_predict_occupancy(ctx, r["model"], r["lb"], z[0], z[1], r["h"].n_particles, r["h"].horizon,
+                                    r["grid"], r["h"].seed, r["h"].human_id, r["counts"], r["oob"], stream)
+    for r in recs:
+        r["z0h"] = [float(v) for v in r["z0"].cpu().numpy()]
+    plain_ms = time_events(torch, stream, plain_batched, 5)
+    batch = pm.pm_batch_create(ctx, recs[0]["model"], len(recs))
+    humans = [pm.make_human(r["g"], r["b"], r["lb"], r["z0"], r["h"].n_particles, r["h"].horizon, r["grid"],
+                            r["h"].seed, r["h"].human_id, r["counts"], r["oob"], obs_xy=r["obs"],
+                            n_obs=r["h"].n_obs) for r in recs]
+    pm.pm_batch_set(batch, humans, stream)
+    t0 = time.perf_counter()
+    pm.pm_batch_autotune(batch, stream)
+    tune_s = time.perf_counter() - t0
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        for r in recs:
+            r["lb"].copy_(r["prior"])
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=stream):
+            for r in recs:
+                r["lb"].copy_(r["prior"])
+            pm.pm_batch_update_posterior(batch, stream)
+            pm.pm_batch_predict(batch, stream)
+    batch_ms = time_events(torch, stream, graph.replay, 10)
+    pm.pm_batch_destroy(batch)
+    out["batched"] = {"humans": len(recs), "particle_steps": steps,
+                      "batched_ms": batch_ms, "batched_particle_steps_per_s": steps / (batch_ms * 1e-3),
+                      "plain_ms": plain_ms, "plain_particle_steps_per_s": steps / (plain_ms * 1e-3),
+                      "speedup_vs_plain": plain_ms / batch_ms, "autotune_s": tune_s,
+                      "tuned": None,
+                      "config": "16 humans, G~U{2..6}, N~U[20k,200k], T~U{50..300}, K=36, 400x400 grid, "
+                                "graph of belief update + persistent rollout"}
+    del recs
+
+    # -- serving: 64 live humans forced, one frame per observation
+    from paper_2603_01122_gb300.serving import Server, run_arrivals
+    wl = workloads.serving()
+    arr = wl["arrivals"]
+    hu0 = arr[0].human
+    srv = Server(ctx, hu0.K, hu0.speed, hu0.dt, hu0.grid, max_live=64, n_particles=hu0.n_particles,
+                 horizon=hu0.horizon, window=hu0.window)
+    try:
+        live = []
+        paths = []
+        for i in range(64):
+            h = arr[i % len(arr)].human
+            p = gpu_paths(pm, ctx, torch, dev, h, args.serving_frames + 1, h.human_id + 100000 * (i // len(arr)))
+            paths.append(p.cpu().numpy())
+            s_ = srv.admit(i, h.goals, h.beta, paths[-1][0], h.seed, h.human_id + 100000 * (i // len(arr)))
+            live.append(s_)
+        lat = []
+        for f in range(args.serving_frames):
+            for i, s_ in enumerate(live):
+                if f >= 1:
+                    srv.observe(s_, paths[i][f])
+            lat.append(srv.frame())
+        lat = np.array(lat[5:])
+        ps = srv.particle_steps_per_frame()
+        # plain path for the same 64 humans: one belief update and one prediction per human
+        x0, y0, res, W, H = hu0.grid
+        win = hu0.window
+        plain_counts = torch.empty((hu0.horizon, win, win), dtype=torch.int32, device=dev)
+        plain_oob = torch.empty(hu0.horizon, dtype=torch.int32, device=dev)
+        models = []
+        for s_ in live:
+            m_ = srv.meta[s_]
+            models.append((pm.make_model(hu0.K, hu0.speed, hu0.dt, srv.goals[s_, :m_["G"]].contiguous(),
+                                         srv.beta[s_, :m_["B"]].contiguous()), s_, m_))
+        zh = srv.obs_dev[:, 1].cpu().numpy()
+
+        def plain_frame():
+            for model_, s_, m_ in models:
+                pm.pm_update_posterior(ctx, model_, srv.obs_dev[s_], 1, srv.log_b[s_], stream)
+                z = zh[s_]
+                gx0 = float(np.float32(x0 + (np.floor((z[0] - x0) / res) - (win - 1) // 2) * res))
+                gy0 = float(np.float32(y0 + (np.floor((z[1] - y0) / res) - (win - 1) // 2) * res))
+                pm.pm_predict_occupancy(ctx, model_, srv.log_b[s_], float(z[0]), float(z[1]), hu0.n_particles,
+                                        hu0.horizon, pm.make_grid(gx0, gy0, res, win, win), m_["seed"],
+                                        m_["human_id"], plain_counts, plain_oob, stream)
+        plain_ms = time_events(torch, stream, plain_frame, 3)
+        out["serving_forced_64"] = {
+            "live": 64, "frames": int(lat.size), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "max_ms": float(lat.max() * 1e3),
+            "particle_steps_per_frame": ps, "particle_steps_per_s": ps / float(np.median(lat)),
+            "plain_path_ms_per_frame": plain_ms, "speedup_vs_plain": plain_ms / float(np.median(lat) * 1e3),
+            "target": "p99 < 8 ms at 64 humans",
+            "config": "64 humans, K=36, N=50k, T=150, 121x121 window at 0.05 m, 1 observation/frame, graph replay"}
+        if args.serving_seconds > 0:
+            paths2 = []
+            for a in arr:
+                n = int((a.t_leave - a.t_arrive) * wl["frame_hz"]) + 2
+                paths2.append(gpu_paths(pm, ctx, torch, dev, a.human, min(n, 4096), a.human.human_id).cpu().numpy())
+            res2 = run_arrivals(srv_fresh := Server(ctx, hu0.K, hu0.speed, hu0.dt, hu0.grid, max_live=64,
+                                                    n_particles=hu0.n_particles, horizon=hu0.horizon,
+                                                    window=hu0.window),
+                                arr, paths2, frame_hz=wl["frame_hz"], duration_s=args.serving_seconds)
+            srv_fresh.close()
+            l2 = res2["latency_s"]
+            out["serving_poisson"] = {"seconds": args.serving_seconds, "frames": int(l2.size),
+                                      "p50_ms": float(np.percentile(l2, 50) * 1e3),
+                                      "p99_ms": float(np.percentile(l2, 99) * 1e3),
+                                      "mean_live": float(res2["live"].mean()), "max_live": int(res2["live"].max()),
+                                      "frames_waited": res2["frames_waited"]}
+    finally:
+        srv.close()
+
+    # -- differentiation: 256 trajectories, adjoint of the marginal log-likelihood
+    ts = workloads.differentiation()
+    trajs = []
+    for m in range(ts.M):
+        h = workloads.Human(K=ts.K, speed=ts.speed, dt=ts.dt, goals=ts.goals[ts.true_goal[m]:ts.true_goal[m] + 1],
+                            beta=ts.true_beta[m:m + 1], true_j=0, start=ts.starts[m], n_obs=0, n_particles=1,
+                            horizon=1, grid=(0, 0, 1, 1, 1), seed=0, human_id=m, obs_seed=ts.obs_seed)
+        trajs.append(gpu_paths(pm, ctx, torch, dev, h, int(ts.lengths[m]), m))
+    offsets = torch.tensor(np.cumsum([0] + [t.shape[0] for t in trajs]), dtype=torch.int32, device=dev)
+    traj = torch.cat(trajs, 0).contiguous()
+    gg, bb = torch.tensor(ts.goals, device=dev), torch.tensor(ts.beta, device=dev)
+    model = pm.make_model(ts.K, ts.speed, ts.dt, gg, bb)
+    lp = torch.full((40,), -float(np.log(40.0)), device=dev)
+    L = torch.empty(1, device=dev)
+    dg, dv, dw = torch.empty_like(gg), torch.empty(1, device=dev), torch.empty(2, device=dev)
+
+    def adj():
+        pm.pm_loglik_backward(ctx, model, ts.M, offsets, traj.shape[0], traj, lp, 1.0, L, dg, dv, dw, stream)
+    ms = time_events(torch, stream, adj, 20)
+    nsteps = int(traj.shape[0]) - ts.M
+    out["differentiation"] = {"ms_per_backward": ms, "trajectory_steps_per_s": nsteps / (ms * 1e-3),
+                              "q_evals_per_s": nsteps * 40 * (ts.K + 1) / (ms * 1e-3),
+                              "config": "256 trajectories, lengths U{50..200}, K=36, 4 goals x 10 beta, "
+                                        "loss + d/d(goals, speed, w1, w2)"}
+    return out
 
 
 def run_native(args):
@@ -362,6 +575,8 @@ def run_native(args):
                     "api": "pm_predict_host"},
             "paper_context": "125 Hz for 1 human, n=8192, T<=10, |U|=96 on an RTX 2080 Ti (Table 1); not this metric",
         }
+        if not args.no_extra:
+            line["extra"] = run_extra(args, pm, ctx, torch, dev, stream)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = oracle_sample(hu, args.cpu_sample)
         print(json.dumps(line), flush=True)

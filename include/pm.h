@@ -167,6 +167,117 @@ pm_status pm_predict_host(pm_ctx *ctx, const pm_model *model, const float *goals
                           float *posterior_out, uint32_t *counts_out, uint32_t *oob_out,
                           void *stream);
 
+/* ---- many humans in one launch -------------------------------------------- */
+
+/* One human of a batch. Device pointers unless stated.
+ *   goals [G][2], beta [B]      the human's goals and rationality grid
+ *   obs_xy [n_obs+1][2], n_obs  observed states for pm_batch_update_posterior
+ *                               (n_obs = 0: no update for this human)
+ *   log_belief [G*B]            in/out belief (read by pm_batch_predict)
+ *   z0_xy [2]                   start state of the rollout, read on the device
+ *                               at every pm_batch_predict (e.g. the last
+ *                               observed state, updated in place between runs)
+ *   n_particles, horizon        N and T
+ *   grid                        binning grid (x0, y0, res) and output size W x H
+ *   center                      1: the W x H output is the window of grid cells
+ *                               centred on z0's cell (W, H odd), recomputed on
+ *                               the device at every run; 0: output cell =
+ *                               grid cell - (cx_off, cy_off)
+ *   seed, human_id              Philox key (as pm_predict_occupancy)
+ *   counts [horizon][H][W], oob [horizon]  outputs, zeroed by pm_batch_predict;
+ *                               states outside the output count in oob. */
+typedef struct pm_human {
+    const float *goals;
+    const float *beta;
+    int32_t G;
+    int32_t B;
+    const float *obs_xy;
+    int32_t n_obs;
+    float *log_belief;
+    const float *z0_xy;
+    int32_t n_particles;
+    int32_t horizon;
+    pm_grid grid;
+    int32_t center;
+    int32_t cx_off;
+    int32_t cy_off;
+    uint64_t seed;
+    uint32_t human_id;
+    uint32_t *counts;
+    uint32_t *oob;
+} pm_human;
+
+/* Opaque batch plan: device descriptors, the tile work list, scratch for the
+ * batched belief update and the tuned launch shape. */
+typedef struct pm_batch pm_batch;
+
+/* Create a plan for up to max_humans humans sharing the model fields K,
+ * speed, dt, w1, w2 and heading_off of `shared` (its goals/beta/G/B are
+ * ignored). Allocates the plan's device and page-locked host buffers. */
+pm_status pm_batch_create(pm_ctx *ctx, const pm_model *shared, int32_t max_humans, pm_batch **out);
+
+/* Set the batch contents (host array of n_humans descriptors, copied):
+ * validates them, builds the work list of tiles sorted by horizon (longest
+ * first) and queues the upload on `stream`. A CUDA graph that captured
+ * pm_batch_update_posterior / pm_batch_predict stays valid across calls to
+ * pm_batch_set as long as the number of posterior chunks of the largest
+ * n_obs does not grow (the graphs read the descriptors from device memory). */
+pm_status pm_batch_set(pm_batch *b, const pm_human *humans, int32_t n_humans, void *stream);
+
+/* Belief update (Eq. 3 / Eq. 7) of every human with n_obs > 0, one launch. */
+pm_status pm_batch_update_posterior(pm_batch *b, void *stream);
+
+/* Zero every output, then one persistent launch of Algorithm 1 over all tiles
+ * of all humans. Each human's counts equal those of pm_predict_occupancy with
+ * the same inputs (bit-identical). Enqueues only a memset and two kernels:
+ * it may be captured in a CUDA graph. */
+pm_status pm_batch_predict(pm_batch *b, void *stream);
+
+/* Time candidate launch shapes (threads per CTA and shared-memory window
+ * size) on the current batch with CUDA events and keep the fastest; it runs
+ * pm_batch_predict several times (outputs are overwritten). Synchronous. */
+pm_status pm_batch_autotune(pm_batch *b, void *stream);
+
+/* Read or set the launch shape: threads per CTA (multiple of 32, <= 256),
+ * resident CTAs per SM used for the grid (0 = as many as fit) and the window
+ * budget in KiB of shared memory. pm_batch_set_config rebuilds the work list
+ * (queued on the legacy stream). */
+pm_status pm_batch_get_config(const pm_batch *b, int32_t *threads, int32_t *ctas_per_sm, int32_t *window_kib);
+pm_status pm_batch_set_config(pm_batch *b, int32_t threads, int32_t ctas_per_sm, int32_t window_kib);
+
+/* Release the plan (synchronises with its pending uploads). */
+void pm_batch_destroy(pm_batch *b);
+
+/* ---- differentiation ------------------------------------------------------ */
+
+/* Marginal log-likelihood of M observed trajectories under the model (built
+ * on Eq. 2 and the joint prior of Eq. 3):
+ *   L = sum_m log sum_j exp(log_prior_j + sum_t log pi_j(u_mt | z_mt)),
+ * the control u_mt recovered from (z_mt, z_m,t+1) as in pm_update_posterior.
+ *   offsets  [M+1] int32 (device): trajectory m is points offsets[m] ..
+ *            offsets[m+1]-1 of traj_xy; offsets are clamped to [0, n_points]
+ *   traj_xy  [n_points][2] FP32 (device)
+ *   log_prior [G*B] (device)
+ *   loglik   [1] FP32 (device) output
+ * Per-step log pi is computed in FP32 and summed over each trajectory in
+ * FP64. Uses context scratch (M*(2G+4) doubles): calls on one context must
+ * be ordered on one stream. */
+pm_status pm_loglik_forward(pm_ctx *ctx, const pm_model *model, int32_t M, const int32_t *offsets,
+                            int32_t n_points, const float *traj_xy, const float *log_prior,
+                            float *loglik, void *stream);
+
+/* L as above and grad_out * dL/d(parameter) for the goal coordinates
+ * d_goals [G][2], the speed d_speed [1] and the Q weights d_w [2] = (w1, w2)
+ * (all device, FP32). The adjoint of Eq. 2 is
+ *   d log pi_j / dp = beta (dQ(theta_obs)/dp - sum_k pi_k dQ(theta_k)/dp),
+ * weighted by each trajectory's posterior over (beta, g). dL/dw1 is zero in
+ * exact arithmetic (w1 shifts every Q of a step equally) and is returned as
+ * computed. Sums over trajectories run in a fixed order (deterministic). */
+pm_status pm_loglik_backward(pm_ctx *ctx, const pm_model *model, int32_t M, const int32_t *offsets,
+                             int32_t n_points, const float *traj_xy, const float *log_prior,
+                             float grad_out, float *loglik, float *d_goals, float *d_speed,
+                             float *d_w, void *stream);
+
 /* ---- checks and measurement ---------------------------------------------- */
 
 /* Raw Philox4x64-10 blocks for counters (particle0 + i, block, purpose, 0),

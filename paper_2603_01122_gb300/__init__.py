@@ -37,6 +37,14 @@ class pm_grid(C.Structure):
                 ("H", C.c_int32)]
 
 
+class pm_human(C.Structure):
+    _fields_ = [("goals", C.c_void_p), ("beta", C.c_void_p), ("G", C.c_int32), ("B", C.c_int32),
+                ("obs_xy", C.c_void_p), ("n_obs", C.c_int32), ("log_belief", C.c_void_p),
+                ("z0_xy", C.c_void_p), ("n_particles", C.c_int32), ("horizon", C.c_int32),
+                ("grid", pm_grid), ("center", C.c_int32), ("cx_off", C.c_int32), ("cy_off", C.c_int32),
+                ("seed", C.c_uint64), ("human_id", C.c_uint32), ("counts", C.c_void_p), ("oob", C.c_void_p)]
+
+
 _lib = None
 _vp = C.c_void_p
 
@@ -56,6 +64,17 @@ def _signatures(lib):
                                          C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
         "pm_predict_host": ([_vp, P(pm_model), _vp, _vp, _vp, C.c_int32, _vp, C.c_int32, C.c_int32,
                              P(pm_grid), C.c_uint64, C.c_uint32, _vp, _vp, _vp, _vp], C.c_int),
+        "pm_batch_create": ([_vp, P(pm_model), C.c_int32, P(_vp)], C.c_int),
+        "pm_batch_set": ([_vp, P(pm_human), C.c_int32, _vp], C.c_int),
+        "pm_batch_update_posterior": ([_vp, _vp], C.c_int),
+        "pm_batch_predict": ([_vp, _vp], C.c_int),
+        "pm_batch_autotune": ([_vp, _vp], C.c_int),
+        "pm_batch_get_config": ([_vp, P(C.c_int32), P(C.c_int32), P(C.c_int32)], C.c_int),
+        "pm_batch_set_config": ([_vp, C.c_int32, C.c_int32, C.c_int32], C.c_int),
+        "pm_batch_destroy": ([_vp], None),
+        "pm_loglik_forward": ([_vp, P(pm_model), C.c_int32, _vp, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
+        "pm_loglik_backward": ([_vp, P(pm_model), C.c_int32, _vp, C.c_int32, _vp, _vp, C.c_float, _vp, _vp,
+                                _vp, _vp, _vp], C.c_int),
         "pm_philox_blocks": ([_vp, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint64,
                               C.c_int32, _vp, _vp], C.c_int),
         "pm_probe_sfu": ([_vp, C.c_int, P(C.c_double)], C.c_int),
@@ -175,6 +194,65 @@ def pm_predict_host(ctx, model: pm_model, goals, beta, obs_xy, n_obs, log_prior,
                                      _hp(log_prior), int(n_particles), int(horizon), C.byref(grid),
                                      int(seed), int(human_id), _hp(posterior_out), _hp(counts_out),
                                      _hp(oob_out), _stream(stream)))
+
+
+def make_human(goals, beta, log_belief, z0_xy, n_particles, horizon, grid: pm_grid, seed, human_id,
+               counts, oob, obs_xy=None, n_obs=0, center=0, cx_off=0, cy_off=0) -> pm_human:
+    """pm_human over device tensors (the tensors are kept alive with the struct)."""
+    h = pm_human(_p(goals), _p(beta), int(goals.shape[0]), int(beta.shape[0]), _p(obs_xy), int(n_obs),
+                 _p(log_belief), _p(z0_xy), int(n_particles), int(horizon), grid, int(center), int(cx_off),
+                 int(cy_off), int(seed), int(human_id), _p(counts), _p(oob))
+    h._keep = (goals, beta, log_belief, z0_xy, counts, oob, obs_xy)
+    return h
+
+
+def pm_batch_create(ctx, shared: pm_model, max_humans) -> int:
+    h = _vp()
+    _check(library().pm_batch_create(ctx, C.byref(shared), int(max_humans), C.byref(h)))
+    return h.value
+
+
+def pm_batch_set(batch, humans, stream=None):
+    arr = (pm_human * max(1, len(humans)))(*humans)
+    _check(library().pm_batch_set(batch, arr, len(humans), _stream(stream)))
+
+
+def pm_batch_update_posterior(batch, stream=None):
+    _check(library().pm_batch_update_posterior(batch, _stream(stream)))
+
+
+def pm_batch_predict(batch, stream=None):
+    _check(library().pm_batch_predict(batch, _stream(stream)))
+
+
+def pm_batch_autotune(batch, stream=None):
+    _check(library().pm_batch_autotune(batch, _stream(stream)))
+
+
+def pm_batch_get_config(batch):
+    t, c, w = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(library().pm_batch_get_config(batch, C.byref(t), C.byref(c), C.byref(w)))
+    return {"threads": t.value, "ctas_per_sm": c.value, "window_kib": w.value}
+
+
+def pm_batch_set_config(batch, threads, ctas_per_sm, window_kib):
+    _check(library().pm_batch_set_config(batch, int(threads), int(ctas_per_sm), int(window_kib)))
+
+
+def pm_batch_destroy(batch):
+    library().pm_batch_destroy(batch)
+
+
+def pm_loglik_forward(ctx, model: pm_model, M, offsets, n_points, traj_xy, log_prior, loglik, stream=None):
+    _check(library().pm_loglik_forward(ctx, C.byref(model), int(M), _p(offsets), int(n_points), _p(traj_xy),
+                                       _p(log_prior), _p(loglik), _stream(stream)))
+
+
+def pm_loglik_backward(ctx, model: pm_model, M, offsets, n_points, traj_xy, log_prior, grad_out, loglik,
+                       d_goals, d_speed, d_w, stream=None):
+    _check(library().pm_loglik_backward(ctx, C.byref(model), int(M), _p(offsets), int(n_points), _p(traj_xy),
+                                        _p(log_prior), float(grad_out), _p(loglik), _p(d_goals), _p(d_speed),
+                                        _p(d_w), _stream(stream)))
 
 
 def pm_philox_blocks(ctx, seed, human_id, purpose, particle0, block, n, out, stream=None):

@@ -1,0 +1,264 @@
+// pm_adjoint.cu -- marginal log-likelihood of observed trajectories under the
+// Boltzmann model (Eq. 2) with the joint prior over (beta, g) of Eq. 3, and
+// its gradient with respect to the goal coordinates, the walking speed v and
+// the Q weights (w1, w2):
+//
+//   L = sum_m log sum_j exp(log prior_j + A_mj),  A_mj = sum_t log pi_j(u_mt | z_mt)
+//   dL/dp = sum_m sum_j w_mj sum_t d log pi_j / dp,  w_mj = softmax_j(log prior_j + A_mj)
+//   d log pi / dp = beta (dQ(theta_obs)/dp - sum_k pi_k dQ(theta_k)/dp)
+//   dQ/dg = w2 u, dQ/dv = -w1 dt - w2 dt e.u, dQ/dw1 = -v dt, dQ/dw2 = -d,
+//   with d = ||z + v dt e - g|| and u = (z + v dt e - g) / d.
+//
+// One CTA per trajectory; a warp per component (beta, g) with its lanes over
+// the trajectory's steps and the headings unrolled in registers. The
+// per-step log pi is FP32; its sum over a trajectory (up to hundreds of
+// steps of about -log K each) is accumulated in FP64, the one place where
+// FP32 would lose the differences between components. Per-trajectory
+// partials go to scratch; the last CTA to finish (ticket, no waiting) sums
+// them over trajectories in a fixed order and writes the outputs.
+#include <cuda_runtime.h>
+
+#include "pm_internal.cuh"
+
+namespace pm {
+namespace {
+
+constexpr int kAdjThreads = 256;
+
+__device__ __forceinline__ float wsum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double wsum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double wmax_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+struct StepGrad {
+    float logpi, gx, gy, gv, gw1, gw2;
+};
+
+// log pi_j(theta_obs | z) and its derivatives for one observed step.
+template <int KT>
+__device__ __forceinline__ StepGrad step_terms(const AdjointArgs &a, float zx, float zy, float ex, float ey,
+                                               float gx, float gy, float beta, bool grad)
+{
+    const float px = zx - gx, py = zy - gy;
+    const float D = fmaf(px, px, fmaf(py, py, a.s2));
+    const float xo = fmaxf(D + a.two_s * fmaf(ex, px, ey * py), 0.0f);
+    const float ro = rsqrtf(fmaxf(xo, 1e-30f));
+    const float d_o = xo * ro;
+    const float bw = beta * a.w2;
+    float lg[KT];
+    float m = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+        const bool on = k < a.K && ((a.enabled >> k) & 1ull);
+        const float xk = fmaxf(D + a.two_s * fmaf(a.ux[k], px, a.uy[k] * py), 0.0f);
+        const float dk = xk * rsqrtf(fmaxf(xk, 1e-30f));
+        // beta w2 (d_obs - d_k), formed as a difference of squares
+        const float num = a.two_s * fmaf(ex - a.ux[k], px, (ey - a.uy[k]) * py);
+        lg[k] = on ? bw * (num / fmaxf(d_o + dk, 1e-30f)) : -INFINITY;
+        m = fmaxf(m, lg[k]);
+    }
+    float S = 0.0f;
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+        lg[k] = (lg[k] == -INFINITY) ? 0.0f : expf(lg[k] - m);
+        S += lg[k];
+    }
+    StepGrad r;
+    r.logpi = -m - logf(S);
+    if (!grad) return r;
+    const float inv = 1.0f / S;
+    float sux = 0.f, suy = 0.f, seu = 0.f, sd = 0.f, sp = 0.f;
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+        const float pk = lg[k] * inv;
+        const float xk = fmaxf(D + a.two_s * fmaf(a.ux[k], px, a.uy[k] * py), 0.0f);
+        const float rk = rsqrtf(fmaxf(xk, 1e-30f));
+        const float dk = xk * rk;
+        const float qx = fmaf(a.s, a.ux[k], px), qy = fmaf(a.s, a.uy[k], py); // z + s e_k - g
+        const float uxk = qx * rk, uyk = qy * rk;
+        sux = fmaf(pk, uxk, sux);
+        suy = fmaf(pk, uyk, suy);
+        seu = fmaf(pk, fmaf(a.ux[k], uxk, a.uy[k] * uyk), seu);
+        sd = fmaf(pk, dk, sd);
+        sp += pk;
+    }
+    const float qox = fmaf(a.s, ex, px), qoy = fmaf(a.s, ey, py);
+    const float uox = qox * ro, uoy = qoy * ro;
+    r.gx = bw * (uox - sux);
+    r.gy = bw * (uoy - suy);
+    r.gv = bw * a.dt * (seu - fmaf(ex, uox, ey * uoy));
+    r.gw1 = beta * a.v * a.dt * (sp - 1.0f); // dQ/dw1 is the same for every heading
+    r.gw2 = beta * (sd - d_o);
+    return r;
+}
+
+template <int KT>
+__global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(const __grid_constant__ AdjointArgs a)
+{
+    __shared__ double A_s[kMaxJ];
+    __shared__ float G_s[kMaxJ][5];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int J = a.G * a.B;
+    const int m = blockIdx.x;
+    const int P = 2 * a.G + 4; // per-trajectory partials: L, d_goals[2G], d_v, d_w1, d_w2
+    const int p0 = min(max(a.offsets[m], 0), a.n_points);
+    const int p1 = min(max(a.offsets[m + 1], p0), a.n_points);
+    const int nsteps = max(p1 - p0 - 1, 0);
+    const bool grad = a.want_grad != 0;
+
+    for (int j = warp; j < J; j += nwarp) {
+        const int g = j / a.B, b = j - g * a.B;
+        const float beta = a.beta[b];
+        const float gx = a.goals[2 * g], gy = a.goals[2 * g + 1];
+        double A = 0.0;
+        float Gx = 0.f, Gy = 0.f, Gv = 0.f, Gw1 = 0.f, Gw2 = 0.f;
+        for (int t = lane; t < nsteps; t += 32) {
+            const float *z = a.traj + 2 * (size_t)(p0 + t);
+            const float zx = z[0], zy = z[1];
+            const float dx = z[2] - zx, dy = z[3] - zy;
+            const float len = sqrtf(fmaf(dx, dx, dy * dy));
+            if (!(len >= 1e-6f)) continue; // stationary step: no information
+            const StepGrad s = step_terms<KT>(a, zx, zy, dx / len, dy / len, gx, gy, beta, grad);
+            A += (double)s.logpi;
+            if (grad) {
+                Gx += s.gx;
+                Gy += s.gy;
+                Gv += s.gv;
+                Gw1 += s.gw1;
+                Gw2 += s.gw2;
+            }
+        }
+        A = wsum_d(A);
+        if (grad) {
+            Gx = wsum(Gx);
+            Gy = wsum(Gy);
+            Gv = wsum(Gv);
+            Gw1 = wsum(Gw1);
+            Gw2 = wsum(Gw2);
+        }
+        if (lane == 0) {
+            A_s[j] = A;
+            G_s[j][0] = Gx;
+            G_s[j][1] = Gy;
+            G_s[j][2] = Gv;
+            G_s[j][3] = Gw1;
+            G_s[j][4] = Gw2;
+        }
+    }
+    __syncthreads();
+
+    double *part = a.part + (size_t)m * P;
+    if (warp == 0) {
+        double mx = -INFINITY;
+        for (int j = lane; j < J; j += 32) mx = fmax(mx, (double)a.log_prior[j] + A_s[j]);
+        mx = wmax_d(mx);
+        float se = 0.0f;
+        for (int j = lane; j < J; j += 32) {
+            const double Lj = (double)a.log_prior[j] + A_s[j];
+            if (Lj != -INFINITY) se += expf((float)(Lj - mx));
+        }
+        se = wsum(se);
+        const double lse = mx + log((double)se);
+        if (lane == 0) part[0] = lse;
+        if (grad) {
+            // posterior weights of the components for this trajectory
+            for (int j = lane; j < J; j += 32) {
+                const double Lj = (double)a.log_prior[j] + A_s[j];
+                A_s[j] = (Lj == -INFINITY) ? 0.0 : (double)expf((float)(Lj - lse));
+            }
+            __syncwarp();
+            float v = 0.f, w1 = 0.f, w2 = 0.f;
+            for (int j = lane; j < J; j += 32) {
+                const float w = (float)A_s[j];
+                v = fmaf(w, G_s[j][2], v);
+                w1 = fmaf(w, G_s[j][3], w1);
+                w2 = fmaf(w, G_s[j][4], w2);
+            }
+            v = wsum(v);
+            w1 = wsum(w1);
+            w2 = wsum(w2);
+            for (int g = 0; g < a.G; ++g) {
+                float sx = 0.f, sy = 0.f;
+                for (int b = lane; b < a.B; b += 32) {
+                    const int j = g * a.B + b;
+                    const float w = (float)A_s[j];
+                    sx = fmaf(w, G_s[j][0], sx);
+                    sy = fmaf(w, G_s[j][1], sy);
+                }
+                sx = wsum(sx);
+                sy = wsum(sy);
+                if (lane == 0) {
+                    part[1 + 2 * g] = sx;
+                    part[2 + 2 * g] = sy;
+                }
+            }
+            if (lane == 0) {
+                part[1 + 2 * a.G] = v;
+                part[2 + 2 * a.G] = w1;
+                part[3 + 2 * a.G] = w2;
+            }
+        }
+    }
+
+    // the last trajectory to finish sums the partials in trajectory order
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(a.ticket, 1u) == (unsigned)(gridDim.x - 1));
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int nout = grad ? P : 1;
+    for (int q = warp; q < nout; q += nwarp) {
+        double s = 0.0;
+        for (int mm = lane; mm < a.M; mm += 32) s += ((volatile double *)a.part)[(size_t)mm * P + q];
+        s = wsum_d(s);
+        if (lane == 0) {
+            if (q == 0) {
+                *a.loglik = (float)s;
+            } else if (q <= 2 * a.G) {
+                a.d_goals[q - 1] = (float)(s * (double)a.grad_out);
+            } else if (q == 2 * a.G + 1) {
+                *a.d_speed = (float)(s * (double)a.grad_out);
+            } else {
+                a.d_w[q - 2 * a.G - 2] = (float)(s * (double)a.grad_out);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *a.ticket = 0u;
+}
+
+} // namespace
+
+size_t adjoint_scratch_bytes(int M, int G) { return (size_t)M * (2 * G + 4) * sizeof(double); }
+
+cudaError_t launch_adjoint(const AdjointArgs &a, cudaStream_t s)
+{
+    const int KT = rollout_kt_for(a.K);
+    switch (KT) {
+    case 8: adjoint_kernel<8><<<a.M, kAdjThreads, 0, s>>>(a); break;
+    case 16: adjoint_kernel<16><<<a.M, kAdjThreads, 0, s>>>(a); break;
+    case 36: adjoint_kernel<36><<<a.M, kAdjThreads, 0, s>>>(a); break;
+    default: adjoint_kernel<64><<<a.M, kAdjThreads, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+} // namespace pm

@@ -6,7 +6,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -26,6 +28,38 @@ struct pm_ctx {
     void *post_scratch = nullptr;
     size_t post_scratch_bytes = 0;
     unsigned *ticket = nullptr;
+    // scratch of the log-likelihood adjoint: per-trajectory partials
+    void *adj_scratch = nullptr;
+    size_t adj_scratch_bytes = 0;
+};
+
+struct pm_batch {
+    pm_ctx *ctx = nullptr;
+    pm_model shared{};
+    int max_humans = 0;
+    std::vector<pm_human> humans;
+    // device
+    pm::BatchHuman *d_humans = nullptr;
+    pm::PostHuman *d_post = nullptr;
+    int2 *d_items = nullptr;
+    size_t items_cap = 0;
+    int *d_meta = nullptr; // [0] tiles, [1] humans
+    unsigned *d_head = nullptr;
+    float *d_post_part = nullptr;
+    unsigned *d_post_ticket = nullptr;
+    size_t post_stride = 0; // floats of posterior scratch per human
+    // page-locked staging of the uploads
+    char *h_stage = nullptr;
+    size_t h_stage_bytes = 0;
+    cudaEvent_t staged = nullptr;
+    // launch shape
+    int threads = 256;
+    int ctas_per_sm = 0;
+    int window_kib = 48;
+    int n_items = 0;
+    int max_chunks = 0;
+    int max_J = 1;
+    int occ = 0; // resident CTAs per SM of the current shape (queried outside any capture)
 };
 
 namespace {
@@ -359,6 +393,242 @@ pm_status posterior_impl(pm_ctx *ctx, const pm_model *model, const float *obs_xy
     return PM_OK;
 }
 
+pm_status loglik_impl(pm_ctx *ctx, const pm_model *model, int32_t M, const int32_t *offsets, int32_t n_points,
+                      const float *traj_xy, const float *log_prior, bool want_grad, float grad_out, float *loglik,
+                      float *d_goals, float *d_speed, float *d_w, cudaStream_t stream)
+{
+    if (!ctx) return fail(PM_EINVAL, "ctx is NULL");
+    pm_status st = check_model(model);
+    if (st != PM_OK) return st;
+    if (M < 1) return fail(PM_EINVAL, "M=%d must be >= 1", M);
+    if (n_points < 0) return fail(PM_EINVAL, "n_points must be >= 0");
+    if (!offsets || !traj_xy || !log_prior || !loglik) return fail(PM_EINVAL, "a device pointer is NULL");
+    if (want_grad && (!d_goals || !d_speed || !d_w)) return fail(PM_EINVAL, "gradient outputs are NULL");
+    if (!std::isfinite(grad_out)) return fail(PM_EINVAL, "grad_out must be finite");
+    DeviceScope dev(ctx->device);
+    st = ensure_posterior_scratch(ctx, 0); // allocates the ticket word
+    if (st != PM_OK) return st;
+    const size_t bytes = pm::adjoint_scratch_bytes(M, model->G);
+    if (ctx->adj_scratch_bytes < bytes) {
+        if (ctx->adj_scratch) cudaFree(ctx->adj_scratch);
+        ctx->adj_scratch = nullptr;
+        ctx->adj_scratch_bytes = 0;
+        cudaError_t e = cudaMalloc(&ctx->adj_scratch, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PM_ENOMEM, "cudaMalloc(%zu) for adjoint scratch failed", bytes);
+        }
+        ctx->adj_scratch_bytes = bytes;
+    }
+    pm::AdjointArgs a;
+    std::memset(&a, 0, sizeof a);
+    const double s = (double)model->speed * (double)model->dt;
+    for (int k = 0; k < model->K; ++k) {
+        double c, sn;
+        unit_heading(model->K, k, &c, &sn);
+        a.ux[k] = (float)c;
+        a.uy[k] = (float)sn;
+    }
+    a.enabled = enabled_mask(model);
+    a.s = (float)s;
+    a.s2 = (float)(s * s);
+    a.two_s = (float)(2.0 * s);
+    a.w2 = model->w2;
+    a.dt = model->dt;
+    a.v = model->speed;
+    a.K = model->K;
+    a.G = model->G;
+    a.B = model->B;
+    a.goals = model->goals;
+    a.beta = model->beta;
+    a.M = M;
+    a.offsets = offsets;
+    a.n_points = n_points;
+    a.traj = traj_xy;
+    a.log_prior = log_prior;
+    a.want_grad = want_grad ? 1 : 0;
+    a.grad_out = grad_out;
+    a.part = (double *)ctx->adj_scratch;
+    a.ticket = ctx->ticket + 1; // its own word of the ticket block
+    a.loglik = loglik;
+    a.d_goals = d_goals;
+    a.d_speed = d_speed;
+    a.d_w = d_w;
+    cudaError_t e = pm::launch_adjoint(a, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+    return PM_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// batched prediction
+// ---------------------------------------------------------------------------
+pm_status check_human(const pm_human &h, int i)
+{
+    if (!h.goals || !h.beta || !h.log_belief || !h.z0_xy || !h.counts || !h.oob)
+        return fail(PM_EINVAL, "human %d: a device pointer is NULL", i);
+    if (h.G < 1 || h.G > PM_MAX_GOALS || h.B < 1 || (long long)h.G * h.B > PM_MAX_COMPONENTS)
+        return fail(PM_EINVAL, "human %d: G=%d B=%d out of range", i, h.G, h.B);
+    if (h.n_particles < 1) return fail(PM_EINVAL, "human %d: n_particles must be >= 1", i);
+    if (h.horizon < 1 || h.horizon > PM_MAX_HORIZON) return fail(PM_EINVAL, "human %d: horizon out of range", i);
+    if (h.n_obs < 0 || (h.n_obs > 0 && !h.obs_xy)) return fail(PM_EINVAL, "human %d: observations", i);
+    pm_status st = check_grid(&h.grid);
+    if (st != PM_OK) return fail(st, "human %d: %s", i, g_err.c_str());
+    if (h.center && (h.grid.W % 2 == 0 || h.grid.H % 2 == 0))
+        return fail(PM_EINVAL, "human %d: a centred output window needs odd W and H", i);
+    return PM_OK;
+}
+
+int batch_radius_cap(int window_kib, int threads)
+{
+    const long long cells = ((long long)window_kib * 1024 - (long long)threads * 2) / 2;
+    int r = 0;
+    while ((2LL * (r + 1) + 1) * (2LL * (r + 1) + 1) <= cells && 2 * (r + 1) + 1 <= 255) ++r;
+    return r;
+}
+
+size_t batch_dyn_smem(const pm_batch *b)
+{
+    const int r = batch_radius_cap(b->window_kib, b->threads);
+    const size_t cells = (size_t)(2 * r + 1) * (2 * r + 1);
+    return (((cells + 1) / 2) * 4 + 15) / 16 * 16 + (size_t)b->threads * 2;
+}
+
+pm_status batch_upload(pm_batch *b, cudaStream_t stream)
+{
+    const int n = (int)b->humans.size();
+    const double s = (double)b->shared.speed * (double)b->shared.dt;
+    std::vector<int2> items;
+    for (int h = 0; h < n; ++h)
+        for (int p0 = 0; p0 < b->humans[h].n_particles; p0 += b->threads) items.push_back(make_int2(h, p0));
+    std::stable_sort(items.begin(), items.end(), [&](const int2 &x, const int2 &y) {
+        return b->humans[x.x].horizon > b->humans[y.x].horizon;
+    });
+    std::vector<pm::BatchHuman> hd(n);
+    std::vector<pm::PostHuman> ph(n);
+    int max_chunks = 0, max_J = 1;
+    for (int h = 0; h < n; ++h) {
+        const pm_human &u = b->humans[h];
+        pm::BatchHuman &d = hd[h];
+        d.goals = u.goals;
+        d.beta = u.beta;
+        d.G = u.G;
+        d.B = u.B;
+        d.log_b = u.log_belief;
+        d.z0 = u.z0_xy;
+        d.N = u.n_particles;
+        d.T = u.horizon;
+        d.gx0 = u.grid.x0;
+        d.gy0 = u.grid.y0;
+        d.inv_res = 1.0f / u.grid.res;
+        d.W = u.grid.W;
+        d.H = u.grid.H;
+        d.center = u.center ? 1 : 0;
+        d.cx_off = u.cx_off;
+        d.cy_off = u.cy_off;
+        d.reach_cells = (int)std::fmin(std::ceil((double)u.horizon * s / (double)u.grid.res) + 1.0, 1 << 20);
+        d.seed = u.seed;
+        d.human = u.human_id;
+        d.counts = u.counts;
+        d.oob = u.oob;
+        pm::PostHuman &q = ph[h];
+        q.goals = u.goals;
+        q.beta = u.beta;
+        q.G = u.G;
+        q.B = u.B;
+        q.obs = u.obs_xy;
+        q.n_obs = u.n_obs;
+        int spc = 1;
+        const int nch = u.n_obs > 0 ? pm::posterior_chunks(u.n_obs, &spc) : 0;
+        q.steps_per_chunk = spc;
+        q.log_b = u.log_belief;
+        q.part = b->d_post_part + (size_t)h * b->post_stride;
+        q.ticket = b->d_post_ticket + h;
+        max_chunks = std::max(max_chunks, nch);
+        max_J = std::max(max_J, u.G * u.B);
+    }
+    if (items.size() > b->items_cap) {
+        cudaStreamSynchronize(stream);
+        if (b->d_items) cudaFree(b->d_items);
+        b->d_items = nullptr;
+        b->items_cap = 0;
+        cudaError_t e = cudaMalloc(&b->d_items, items.size() * sizeof(int2));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PM_ENOMEM, "cudaMalloc for %zu work items failed", items.size());
+        }
+        b->items_cap = items.size();
+    }
+    const size_t bh = (size_t)n * sizeof(pm::BatchHuman), bp = (size_t)n * sizeof(pm::PostHuman);
+    const size_t bi = items.size() * sizeof(int2);
+    const size_t need = bh + bp + 16 + bi + 64;
+    cudaError_t e = cudaEventSynchronize(b->staged); // the previous upload has left the staging buffer
+    if (e != cudaSuccess) return cuda_fail(e, "staging event");
+    if (need > b->h_stage_bytes) {
+        if (b->h_stage) cudaFreeHost(b->h_stage);
+        b->h_stage = nullptr;
+        b->h_stage_bytes = 0;
+        e = cudaMallocHost((void **)&b->h_stage, need * 2);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PM_ENOMEM, "page-locked staging of %zu bytes failed", need * 2);
+        }
+        b->h_stage_bytes = need * 2;
+    }
+    char *p = b->h_stage;
+    std::memcpy(p, hd.data(), bh);
+    std::memcpy(p + bh, ph.data(), bp);
+    int meta[2] = {(int)items.size(), n};
+    std::memcpy(p + bh + bp, meta, sizeof meta);
+    if (bi) std::memcpy(p + bh + bp + 16, items.data(), bi);
+    if (bh) e = cudaMemcpyAsync(b->d_humans, p, bh, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && bp) e = cudaMemcpyAsync(b->d_post, p + bh, bp, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_meta, p + bh + bp, sizeof meta, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && bi) e = cudaMemcpyAsync(b->d_items, p + bh + bp + 16, bi, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->staged, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch upload");
+    b->n_items = (int)items.size();
+    b->max_chunks = std::max(b->max_chunks, max_chunks);
+    b->max_J = std::max(b->max_J, max_J);
+    pm::RolloutArgs t;
+    std::memset(&t, 0, sizeof t);
+    fill_rollout_tables(&b->shared, t);
+    b->occ = pm::batch_rollout_occupancy(b->shared.K, t.enabled, b->threads, batch_dyn_smem(b));
+    cudaGetLastError();
+    return PM_OK;
+}
+
+pm_status batch_predict_impl(pm_batch *b, cudaStream_t stream)
+{
+    pm_ctx *ctx = b->ctx;
+    cudaError_t e = cudaMemsetAsync(b->d_head, 0, sizeof(unsigned), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "queue reset");
+    e = pm::launch_batch_zero(b->d_humans, b->d_meta + 1, b->max_humans, ctx->sm_count, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "zero launch");
+    pm::RolloutArgs t;
+    std::memset(&t, 0, sizeof t);
+    fill_rollout_tables(&b->shared, t);
+    pm::BatchArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.tab = t.tab;
+    a.enabled = t.enabled;
+    a.s2 = t.s2;
+    a.w2_log2e = t.w2_log2e;
+    a.K = b->shared.K;
+    a.humans = b->d_humans;
+    a.items = b->d_items;
+    a.n_items = b->d_meta;
+    a.head = b->d_head;
+    a.win_radius_cap = batch_radius_cap(b->window_kib, b->threads);
+    const size_t dyn = batch_dyn_smem(b);
+    int occ = b->occ;
+    if (occ < 1) return fail(PM_EINVAL, "launch shape (%d threads, %d KiB window) does not fit an SM", b->threads, b->window_kib);
+    if (b->ctas_per_sm > 0) occ = std::min(occ, b->ctas_per_sm);
+    e = pm::launch_batch_rollout(a, ctx->sm_count * occ, b->threads, dyn, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch rollout launch");
+    return PM_OK;
+}
+
 } // namespace
 
 extern "C" {
@@ -394,6 +664,7 @@ void pm_destroy(pm_ctx *ctx)
         if (ctx->stage) cudaFree(ctx->stage);
         if (ctx->post_scratch) cudaFree(ctx->post_scratch);
         if (ctx->ticket) cudaFree(ctx->ticket);
+        if (ctx->adj_scratch) cudaFree(ctx->adj_scratch);
     }
     delete ctx;
 }
@@ -480,6 +751,207 @@ pm_status pm_predict_host(pm_ctx *ctx, const pm_model *model, const float *goals
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
     return PM_OK;
+}
+
+
+pm_status pm_batch_create(pm_ctx *ctx, const pm_model *shared, int32_t max_humans, pm_batch **out)
+{
+    if (!ctx || !out) return fail(PM_EINVAL, "ctx/out is NULL");
+    *out = nullptr;
+    pm_status st = check_model(shared, false);
+    if (st != PM_OK) return st;
+    if (max_humans < 1 || max_humans > 65535) return fail(PM_EINVAL, "max_humans=%d out of range", max_humans);
+    DeviceScope dev(ctx->device);
+    pm_batch *b = new pm_batch();
+    b->ctx = ctx;
+    b->shared = *shared;
+    b->shared.goals = nullptr;
+    b->shared.beta = nullptr;
+    b->max_humans = max_humans;
+    b->post_stride = pm::posterior_scratch_bytes(64, PM_MAX_COMPONENTS) / sizeof(float);
+    b->items_cap = (size_t)max_humans * 2048;
+    cudaError_t e = cudaMalloc(&b->d_humans, (size_t)max_humans * sizeof(pm::BatchHuman));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_post, (size_t)max_humans * sizeof(pm::PostHuman));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, b->items_cap * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_meta, 256);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_head, 256);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_post_part, (size_t)max_humans * b->post_stride * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_post_ticket, (size_t)max_humans * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(b->d_post_ticket, 0, (size_t)max_humans * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(b->d_meta, 0, 256);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        pm_batch_destroy(b);
+        return fail(PM_ENOMEM, "batch allocation failed: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return PM_OK;
+}
+
+void pm_batch_destroy(pm_batch *b)
+{
+    if (!b) return;
+    DeviceScope dev(b->ctx->device);
+    if (b->staged) {
+        cudaEventSynchronize(b->staged);
+        cudaEventDestroy(b->staged);
+    }
+    cudaFree(b->d_humans);
+    cudaFree(b->d_post);
+    cudaFree(b->d_items);
+    cudaFree(b->d_meta);
+    cudaFree(b->d_head);
+    cudaFree(b->d_post_part);
+    cudaFree(b->d_post_ticket);
+    if (b->h_stage) cudaFreeHost(b->h_stage);
+    delete b;
+}
+
+pm_status pm_batch_set(pm_batch *b, const pm_human *humans, int32_t n_humans, void *stream)
+{
+    if (!b) return fail(PM_EINVAL, "batch is NULL");
+    if (n_humans < 0 || n_humans > b->max_humans) return fail(PM_EINVAL, "n_humans=%d outside [0, %d]", n_humans, b->max_humans);
+    if (n_humans > 0 && !humans) return fail(PM_EINVAL, "humans is NULL");
+    for (int i = 0; i < n_humans; ++i) {
+        pm_status st = check_human(humans[i], i);
+        if (st != PM_OK) return st;
+    }
+    DeviceScope dev(b->ctx->device);
+    b->humans.assign(humans, humans + n_humans);
+    return batch_upload(b, (cudaStream_t)stream);
+}
+
+pm_status pm_batch_update_posterior(pm_batch *b, void *stream)
+{
+    if (!b) return fail(PM_EINVAL, "batch is NULL");
+    if (b->max_chunks == 0) return PM_OK;
+    DeviceScope dev(b->ctx->device);
+    pm::PosteriorArgs a;
+    std::memset(&a, 0, sizeof a);
+    const double s = (double)b->shared.speed * (double)b->shared.dt;
+    for (int k = 0; k < b->shared.K; ++k) {
+        double c, sn;
+        unit_heading(b->shared.K, k, &c, &sn);
+        a.ux[k] = (float)c;
+        a.uy[k] = (float)sn;
+    }
+    a.enabled = enabled_mask(&b->shared);
+    a.s = (float)s;
+    a.s2 = (float)(s * s);
+    a.two_s = (float)(2.0 * s);
+    a.w2 = b->shared.w2;
+    a.K = b->shared.K;
+    cudaError_t e = pm::launch_posterior_batch(a, b->d_post, b->d_meta + 1, b->max_humans, b->max_chunks, b->max_J,
+                                               (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batched posterior launch");
+    return PM_OK;
+}
+
+pm_status pm_batch_predict(pm_batch *b, void *stream)
+{
+    if (!b) return fail(PM_EINVAL, "batch is NULL");
+    DeviceScope dev(b->ctx->device);
+    return batch_predict_impl(b, (cudaStream_t)stream);
+}
+
+pm_status pm_batch_get_config(const pm_batch *b, int32_t *threads, int32_t *ctas_per_sm, int32_t *window_kib)
+{
+    if (!b) return fail(PM_EINVAL, "batch is NULL");
+    if (threads) *threads = b->threads;
+    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+    if (window_kib) *window_kib = b->window_kib;
+    return PM_OK;
+}
+
+pm_status pm_batch_set_config(pm_batch *b, int32_t threads, int32_t ctas_per_sm, int32_t window_kib)
+{
+    if (!b) return fail(PM_EINVAL, "batch is NULL");
+    if (threads < 32 || threads > 256 || threads % 32) return fail(PM_EINVAL, "threads=%d must be 32..256, multiple of 32", threads);
+    if (ctas_per_sm < 0 || ctas_per_sm > 32) return fail(PM_EINVAL, "ctas_per_sm=%d out of range", ctas_per_sm);
+    if (window_kib < 1 || window_kib > 200) return fail(PM_EINVAL, "window_kib=%d out of range", window_kib);
+    DeviceScope dev(b->ctx->device);
+    const bool retile = threads != b->threads;
+    b->threads = threads;
+    b->ctas_per_sm = ctas_per_sm;
+    b->window_kib = window_kib;
+    if (retile && !b->humans.empty()) return batch_upload(b, nullptr);
+    pm::RolloutArgs t;
+    std::memset(&t, 0, sizeof t);
+    fill_rollout_tables(&b->shared, t);
+    b->occ = pm::batch_rollout_occupancy(b->shared.K, t.enabled, b->threads, batch_dyn_smem(b));
+    cudaGetLastError();
+    return PM_OK;
+}
+
+pm_status pm_batch_autotune(pm_batch *b, void *stream)
+{
+    if (!b) return fail(PM_EINVAL, "batch is NULL");
+    if (b->humans.empty()) return PM_OK;
+    DeviceScope dev(b->ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    static const int cand_threads[] = {128, 192, 224, 256};
+    static const int cand_window[] = {24, 48, 96};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bt = b->threads, bw = b->window_kib;
+    for (int t : cand_threads) {
+        for (int w : cand_window) {
+            b->threads = t;
+            b->window_kib = w;
+            b->ctas_per_sm = 0;
+            if (batch_upload(b, s) != PM_OK) continue;
+            if (batch_predict_impl(b, s) != PM_OK) { // warm-up; a shape that does not fit is skipped
+                cudaGetLastError();
+                continue;
+            }
+            float total = 0.0f;
+            bool ok = true;
+            for (int rep = 0; rep < 3 && ok; ++rep) {
+                cudaEventRecord(e0, s);
+                ok = batch_predict_impl(b, s) == PM_OK;
+                cudaEventRecord(e1, s);
+                float ms = 0.0f;
+                if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+                    total += ms;
+                else
+                    ok = false;
+            }
+            if (ok && total < best) {
+                best = total;
+                bt = t;
+                bw = w;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->threads = bt;
+    b->window_kib = bw;
+    b->ctas_per_sm = 0;
+    pm_status st = batch_upload(b, s);
+    if (st != PM_OK) return st;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    return PM_OK;
+}
+
+pm_status pm_loglik_forward(pm_ctx *ctx, const pm_model *model, int32_t M, const int32_t *offsets,
+                            int32_t n_points, const float *traj_xy, const float *log_prior, float *loglik,
+                            void *stream)
+{
+    return loglik_impl(ctx, model, M, offsets, n_points, traj_xy, log_prior, false, 1.0f, loglik, nullptr,
+                       nullptr, nullptr, (cudaStream_t)stream);
+}
+
+pm_status pm_loglik_backward(pm_ctx *ctx, const pm_model *model, int32_t M, const int32_t *offsets,
+                             int32_t n_points, const float *traj_xy, const float *log_prior, float grad_out,
+                             float *loglik, float *d_goals, float *d_speed, float *d_w, void *stream)
+{
+    return loglik_impl(ctx, model, M, offsets, n_points, traj_xy, log_prior, true, grad_out, loglik, d_goals,
+                       d_speed, d_w, (cudaStream_t)stream);
 }
 
 pm_status pm_philox_blocks(pm_ctx *ctx, uint64_t seed, uint32_t human_id, uint32_t purpose, uint64_t particle0,

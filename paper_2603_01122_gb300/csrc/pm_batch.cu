@@ -1,0 +1,199 @@
+// pm_batch.cu -- many humans in one persistent launch.
+//
+// The work list holds tiles (human, first particle) of blockDim particles,
+// sorted on the host by horizon (longest first). A grid of SMs x CTAs-per-SM
+// persistent CTAs takes tiles from a global counter (one atomicAdd per tile,
+// no waiting), loads the human's component table and belief CDF into shared
+// memory when the human changes, places the shared-memory histogram window
+// around the human's start cell and runs Algorithm 1 for the tile with the
+// same device code as the single-human kernel, so each human's histogram is
+// bit-identical alone and in the mix (its random numbers are keyed on
+// (seed, human_id, particle) only and the counts are integer sums).
+// Every human of a batch shares K, v, dt, w and the disabled headings (the
+// heading tables live in the kernel parameters); goals, beta grid, belief,
+// start, particles, horizon and output differ per human.
+#include <cuda_runtime.h>
+
+#include "pm_internal.cuh"
+#include "pm_rollout_dev.cuh"
+
+namespace pm {
+namespace {
+
+constexpr int kBatchMaxThreads = 256;
+
+template <int KT, bool FULL>
+__global__ void __launch_bounds__(kBatchMaxThreads) batch_rollout_kernel(const __grid_constant__ BatchArgs a)
+{
+    __shared__ RolloutShared sh;
+    __shared__ int s_item;
+    __shared__ int s_geom[6]; // cx_off, cy_off, win_x0, win_y0, ww, wh
+    __shared__ float s_z0[2];
+    extern __shared__ __align__(16) uint32_t dyn[];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int k = tid; k < KT; k += nthr) sh.step[k] = make_float2(a.tab.sx[k], a.tab.sy[k]);
+    const int n_items = *a.n_items;
+    int cur = -1;
+    for (;;) {
+        __syncthreads(); // the previous tile is done with shared memory
+        if (tid == 0) s_item = (int)atomicAdd(a.head, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const int2 item = a.items[it]; // (human, first particle)
+        const BatchHuman *h = a.humans + item.x;
+        const int J = h->G * h->B;
+        if (item.x != cur) {
+            for (int j = tid; j < J; j += nthr) {
+                const int g = j / h->B, b = j - g * h->B;
+                sh.comp[j] = make_float4(h->beta[b] * a.w2_log2e, h->goals[2 * g], h->goals[2 * g + 1], 0.0f);
+            }
+            if (tid < 32) belief_cdf(h->log_b, J, sh.cdf, tid);
+            cur = item.x;
+        }
+        if (tid == 0) {
+            const float zx = h->z0[0], zy = h->z0[1];
+            // start cell on the binning grid, with the same FP32 rule as the states
+            const int gcx = __float2int_rd(__fmul_rn(__fsub_rn(zx, h->gx0), h->inv_res));
+            const int gcy = __float2int_rd(__fmul_rn(__fsub_rn(zy, h->gy0), h->inv_res));
+            int cx_off = h->cx_off, cy_off = h->cy_off;
+            if (h->center) {
+                cx_off = gcx - (h->W - 1) / 2;
+                cy_off = gcy - (h->H - 1) / 2;
+            }
+            const int cxo = gcx - cx_off, cyo = gcy - cy_off;
+            int r = min(h->reach_cells, a.win_radius_cap);
+            int x_lo = max(cxo - r, 0), x_hi = min(cxo + r, h->W - 1);
+            int y_lo = max(cyo - r, 0), y_hi = min(cyo + r, h->H - 1);
+            int ww = x_hi - x_lo + 1, wh = y_hi - y_lo + 1;
+            if (ww <= 0 || wh <= 0) ww = wh = 0, x_lo = y_lo = 0;
+            s_geom[0] = cx_off;
+            s_geom[1] = cy_off;
+            s_geom[2] = x_lo;
+            s_geom[3] = y_lo;
+            s_geom[4] = ww;
+            s_geom[5] = wh;
+            s_z0[0] = zx;
+            s_z0[1] = zy;
+        }
+        if (tid < 2) {
+            sh.list_n[tid] = 0u;
+            sh.oob_n[tid] = 0u;
+        }
+        __syncthreads();
+        const int words = (s_geom[4] * s_geom[5] + 1) >> 1;
+        for (int w = tid; w < words; w += nthr) dyn[w] = 0u;
+        __syncthreads();
+        TileCtx c;
+        c.z0x = s_z0[0];
+        c.z0y = s_z0[1];
+        c.T = h->T;
+        c.i = (int64_t)item.y + tid;
+        c.active = c.i < h->N;
+        c.traced = false;
+        c.seed = h->seed;
+        c.human = h->human;
+        c.J = J;
+        c.hist = true;
+        c.gx0 = h->gx0;
+        c.gy0 = h->gy0;
+        c.inv_res = h->inv_res;
+        c.W = h->W;
+        c.H = h->H;
+        c.cx_off = s_geom[0];
+        c.cy_off = s_geom[1];
+        c.counts = h->counts;
+        c.oob = h->oob;
+        c.win_x0 = s_geom[2];
+        c.win_y0 = s_geom[3];
+        c.ww = s_geom[4];
+        c.wh = s_geom[5];
+        c.tr_states = nullptr;
+        c.tr_head = nullptr;
+        c.tr_comp = nullptr;
+        rollout_tile<KT, FULL>(a.tab, a.enabled, a.s2, c, sh, dyn);
+    }
+}
+
+// Zero every human's counts [T][H][W] and oob [T]: blockIdx.y strides over
+// humans, the x dimension over 16-byte words (scalar head and tail).
+__global__ void batch_zero_kernel(const BatchHuman *humans, const int *n_dev)
+{
+    const int n = *n_dev;
+    for (int hh = blockIdx.y; hh < n; hh += gridDim.y) {
+        const BatchHuman &h = humans[hh];
+        const size_t words = (size_t)h.T * h.H * h.W;
+        uint32_t *p = h.counts;
+        const size_t head = ((16 - ((uintptr_t)p & 15)) & 15) / 4;
+        const size_t lead = head < words ? head : words;
+        const size_t nvec = (words - lead) / 4;
+        const size_t tail0 = lead + nvec * 4;
+        const size_t stride = (size_t)gridDim.x * blockDim.x;
+        const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+        uint4 *v = reinterpret_cast<uint4 *>(p + lead);
+        for (size_t q = t0; q < nvec; q += stride) v[q] = make_uint4(0u, 0u, 0u, 0u);
+        if (t0 < lead) p[t0] = 0u;
+        if (t0 < words - tail0) p[tail0 + t0] = 0u;
+        for (size_t q = t0; q < (size_t)h.T; q += stride) h.oob[q] = 0u;
+    }
+}
+
+template <int KT>
+int batch_occupancy_kt(bool full, int threads, size_t dyn)
+{
+    int n = 0;
+    if (full) {
+        cudaFuncSetAttribute(batch_rollout_kernel<KT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_rollout_kernel<KT, true>, threads, dyn);
+    } else {
+        cudaFuncSetAttribute(batch_rollout_kernel<KT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_rollout_kernel<KT, false>, threads, dyn);
+    }
+    return n;
+}
+
+template <int KT>
+cudaError_t batch_launch_kt(const BatchArgs &a, bool full, int blocks, int threads, size_t dyn, cudaStream_t s)
+{
+    if (full) batch_rollout_kernel<KT, true><<<blocks, threads, dyn, s>>>(a);
+    else batch_rollout_kernel<KT, false><<<blocks, threads, dyn, s>>>(a);
+    return cudaGetLastError();
+}
+
+} // namespace
+
+int batch_rollout_occupancy(int K, uint64_t enabled, int threads, size_t dyn)
+{
+    const int KT = rollout_kt_for(K);
+    const uint64_t all = (KT >= 64) ? ~0ull : ((1ull << KT) - 1ull);
+    const bool full = (K == KT) && ((enabled & all) == all);
+    switch (KT) {
+    case 8: return batch_occupancy_kt<8>(full, threads, dyn);
+    case 16: return batch_occupancy_kt<16>(full, threads, dyn);
+    case 36: return batch_occupancy_kt<36>(full, threads, dyn);
+    default: return batch_occupancy_kt<64>(full, threads, dyn);
+    }
+}
+
+cudaError_t launch_batch_rollout(const BatchArgs &a, int blocks, int threads, size_t dyn, cudaStream_t s)
+{
+    const int KT = rollout_kt_for(a.K);
+    const uint64_t all = (KT >= 64) ? ~0ull : ((1ull << KT) - 1ull);
+    const bool full = (a.K == KT) && ((a.enabled & all) == all);
+    switch (KT) {
+    case 8: return batch_launch_kt<8>(a, full, blocks, threads, dyn, s);
+    case 16: return batch_launch_kt<16>(a, full, blocks, threads, dyn, s);
+    case 36: return batch_launch_kt<36>(a, full, blocks, threads, dyn, s);
+    default: return batch_launch_kt<64>(a, full, blocks, threads, dyn, s);
+    }
+}
+
+cudaError_t launch_batch_zero(const BatchHuman *humans, const int *n_dev, int max_rows, int sm_count, cudaStream_t s)
+{
+    if (max_rows <= 0) return cudaSuccess;
+    dim3 grid((unsigned)(sm_count * 2), (unsigned)(max_rows < 64 ? max_rows : 64));
+    batch_zero_kernel<<<grid, 256, 0, s>>>(humans, n_dev);
+    return cudaGetLastError();
+}
+
+} // namespace pm

@@ -121,12 +121,81 @@ struct PosteriorArgs {
     unsigned *ticket;    // scratch: chunks finished so far (0 between calls)
 };
 
+// Arguments of the log-likelihood / adjoint kernel.
+struct AdjointArgs {
+    float ux[kMaxK], uy[kMaxK]; // unit heading vectors
+    uint64_t enabled;
+    float s, s2, two_s, w2, dt, v;
+    int K, G, B;
+    const float *goals;
+    const float *beta;
+    int M;                 // trajectories
+    const int32_t *offsets; // [M+1] point offsets
+    int n_points;          // points in traj (offsets are clamped to it)
+    const float *traj;     // [n_points][2]
+    const float *log_prior; // [G*B]
+    int want_grad;
+    float grad_out;
+    double *part;          // scratch [M][2G+4]
+    unsigned *ticket;      // scratch ticket (0 between calls)
+    float *loglik;
+    float *d_goals;
+    float *d_speed;
+    float *d_w;
+};
+
+// One human of a batched belief update (device array).
+struct PostHuman {
+    const float *goals;
+    const float *beta;
+    int G, B;
+    const float *obs;
+    int n_obs;
+    int steps_per_chunk;
+    float *log_b;
+    float *part;
+    unsigned *ticket;
+};
+
+// One human of a batched rollout (device array).
+struct BatchHuman {
+    const float *goals;
+    const float *beta;
+    int G, B;
+    const float *log_b;
+    const float *z0;      // device [2]
+    int N, T;
+    float gx0, gy0, inv_res;
+    int W, H;             // output cells
+    int center;           // output window centred on the start cell
+    int cx_off, cy_off;   // output cell = grid cell - offset (center == 0)
+    int reach_cells;      // ceil(T v dt / res) + 1
+    uint64_t seed;
+    uint32_t human;
+    uint32_t *counts;
+    uint32_t *oob;
+};
+
+struct BatchArgs {
+    HeadingTab tab;
+    uint64_t enabled;
+    float s2, w2_log2e;
+    int K;
+    const BatchHuman *humans;
+    const int2 *items;   // (human, first particle), longest horizon first
+    const int *n_items;
+    unsigned *head;      // next tile (zeroed before every launch)
+    int win_radius_cap;  // (2r+1)^2 cells fit the dynamic shared memory
+};
+
 // Launch wrappers (defined next to their kernels).
 cudaError_t launch_rollout(const RolloutArgs &a, int threads, size_t dyn_smem, cudaStream_t s);
 size_t rollout_static_smem_estimate();
 int rollout_occupancy(const RolloutArgs &a, int threads, size_t dyn_smem); // resident CTAs per SM
 cudaError_t launch_posterior(const PosteriorArgs &a, int n_chunks, cudaStream_t s);
 int posterior_chunks(int n_obs, int *steps_per_chunk);
+cudaError_t launch_posterior_batch(const PosteriorArgs &a, const PostHuman *humans, const int *n_humans,
+                                   int max_rows, int max_chunks, int max_J, cudaStream_t s);
 size_t posterior_scratch_bytes(int n_chunks, int J);
 cudaError_t launch_philox_blocks(uint64_t seed, uint32_t human, uint32_t purpose,
                                  uint64_t particle0, uint64_t block, int n, uint64_t *out,
@@ -134,5 +203,10 @@ cudaError_t launch_philox_blocks(uint64_t seed, uint32_t human, uint32_t purpose
 cudaError_t launch_sfu_probe(int op, int blocks, int threads, int iters, float *sink,
                              cudaStream_t s);
 int rollout_kt_for(int K); // template bucket for K (8, 16, 36 or 64)
+cudaError_t launch_adjoint(const AdjointArgs &a, cudaStream_t s);
+int batch_rollout_occupancy(int K, uint64_t enabled, int threads, size_t dyn);
+cudaError_t launch_batch_rollout(const BatchArgs &a, int blocks, int threads, size_t dyn, cudaStream_t s);
+cudaError_t launch_batch_zero(const BatchHuman *humans, const int *n_dev, int max_rows, int sm_count, cudaStream_t s);
+size_t adjoint_scratch_bytes(int M, int G);
 
 } // namespace pm

@@ -106,14 +106,15 @@ __device__ __forceinline__ float rel_logit(float bw, float two_s, float D, float
     return bw * (num / fmaxf(d_o + dk, 1e-30f));
 }
 
-__global__ void __launch_bounds__(1024) posterior_kernel(const __grid_constant__ PosteriorArgs a)
+// One chunk of one human's observed steps; the last chunk of the human to
+// finish folds all chunks and writes the posterior.
+__device__ __forceinline__ void posterior_chunk(const PosteriorArgs &a, const PostHuman &h, int chunk, int nchunk)
 {
     __shared__ int last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int J = a.G * a.B;
-    const int chunk = blockIdx.x, nchunk = gridDim.x;
-    const int t0 = chunk * a.steps_per_chunk;
-    const int t1 = min(a.n_obs, t0 + a.steps_per_chunk);
+    const int J = h.G * h.B;
+    const int t0 = chunk * h.steps_per_chunk;
+    const int t1 = min(h.n_obs, t0 + h.steps_per_chunk);
     const int k0 = lane, k1 = lane + 32;
     const bool on0 = k0 < a.K && ((a.enabled >> k0) & 1ull);
     const bool on1 = k1 < a.K && ((a.enabled >> k1) & 1ull);
@@ -121,14 +122,14 @@ __global__ void __launch_bounds__(1024) posterior_kernel(const __grid_constant__
     const float ux1 = on1 ? a.ux[k1] : 0.0f, uy1 = on1 ? a.uy[k1] : 0.0f;
 
     for (int j = warp; j < J; j += nwarp) {
-        const int g = j / a.B, b = j - g * a.B;
-        const float bw = a.beta[b] * a.w2;
-        const float gx = a.goals[2 * g], gy = a.goals[2 * g + 1];
+        const int g = j / h.B, b = j - g * h.B;
+        const float bw = h.beta[b] * a.w2;
+        const float gx = h.goals[2 * g], gy = h.goals[2 * g + 1];
         Acc acc;
         acc_init(acc);
         for (int t = t0; t < t1; ++t) {
-            const float zx = a.obs[2 * t], zy = a.obs[2 * t + 1];
-            const float dx = a.obs[2 * t + 2] - zx, dy = a.obs[2 * t + 3] - zy;
+            const float zx = h.obs[2 * t], zy = h.obs[2 * t + 1];
+            const float dx = h.obs[2 * t + 2] - zx, dy = h.obs[2 * t + 3] - zy;
             const float len = sqrtf(fmaf(dx, dx, dy * dy));
             if (!(len >= 1e-6f)) continue; // stationary: the belief is unchanged
             const float ex = dx / len, ey = dy / len;
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(1024) posterior_kernel(const __grid_constant__
             acc_mul(acc, S, 0.0f, 0);
         }
         if (lane == 0) {
-            float *p = a.part + 5 * ((size_t)chunk * J + j);
+            float *p = h.part + 5 * ((size_t)chunk * J + j);
             p[0] = acc.mh;
             p[1] = acc.ml;
             p[2] = acc.ph;
@@ -155,17 +156,17 @@ __global__ void __launch_bounds__(1024) posterior_kernel(const __grid_constant__
     // the last chunk to finish combines and normalises
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(a.ticket, 1u) == (unsigned)(nchunk - 1));
+    if (threadIdx.x == 0) last = (atomicAdd(h.ticket, 1u) == (unsigned)(nchunk - 1));
     __syncthreads();
     if (!last) return;
     __threadfence();
 
-    double *L = reinterpret_cast<double *>(a.part + ((5 * (size_t)nchunk * J + 1) & ~(size_t)1)); // [J], 8-byte aligned
+    double *L = reinterpret_cast<double *>(h.part + ((5 * (size_t)nchunk * J + 1) & ~(size_t)1)); // [J], 8-byte aligned
     for (int j = warp; j < J; j += nwarp) {
         Acc acc;
         acc_init(acc);
         for (int c = lane; c < nchunk; c += 32) {
-            const volatile float *p = a.part + 5 * ((size_t)c * J + j);
+            const volatile float *p = h.part + 5 * ((size_t)c * J + j);
             Acc q;
             q.mh = p[0];
             q.ml = p[1];
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(1024) posterior_kernel(const __grid_constant__
             // sum_t l_t(j) = -(sum_t m_t) - log(prod_t S_t)
             const double logS = (double)acc.e * 0.6931471805599453 + (double)log1pf(acc.ph - 1.0f) +
                                 (double)acc.pl / (double)acc.ph;
-            L[j] = (double)a.log_b[j] - ((double)acc.mh + (double)acc.ml) - logS;
+            L[j] = (double)h.log_b[j] - ((double)acc.mh + (double)acc.ml) - logS;
         }
     }
     __syncthreads();
@@ -197,9 +198,38 @@ __global__ void __launch_bounds__(1024) posterior_kernel(const __grid_constant__
             if (L[j] != -INFINITY) se += expf((float)(L[j] - mx));
         se = warp_sum(se);
         const double lse = mx + log((double)se);
-        for (int j = lane; j < J; j += 32) a.log_b[j] = (float)(L[j] - lse);
-        if (lane == 0) *a.ticket = 0u;
+        for (int j = lane; j < J; j += 32) h.log_b[j] = (float)(L[j] - lse);
+        if (lane == 0) *h.ticket = 0u;
     }
+}
+
+__global__ void __launch_bounds__(1024) posterior_kernel(const __grid_constant__ PosteriorArgs a)
+{
+    PostHuman h;
+    h.goals = a.goals;
+    h.beta = a.beta;
+    h.G = a.G;
+    h.B = a.B;
+    h.obs = a.obs;
+    h.n_obs = a.n_obs;
+    h.steps_per_chunk = a.steps_per_chunk;
+    h.log_b = a.log_b;
+    h.part = a.part;
+    h.ticket = a.ticket;
+    posterior_chunk(a, h, blockIdx.x, gridDim.x);
+}
+
+// Batched form: blockIdx.y is the human, blockIdx.x the chunk; humans with
+// fewer chunks (or no observed steps) leave the extra CTAs idle.
+__global__ void __launch_bounds__(1024) posterior_batch_kernel(const __grid_constant__ PosteriorArgs a,
+                                                               const PostHuman *humans, const int *n_humans)
+{
+    if ((int)blockIdx.y >= *n_humans) return;
+    const PostHuman h = humans[blockIdx.y];
+    if (h.n_obs <= 0 || h.log_b == nullptr) return;
+    const int nchunk = (h.n_obs + h.steps_per_chunk - 1) / h.steps_per_chunk;
+    if ((int)blockIdx.x >= nchunk) return;
+    posterior_chunk(a, h, blockIdx.x, nchunk);
 }
 
 } // namespace
@@ -214,6 +244,16 @@ int posterior_chunks(int n_obs, int *steps_per_chunk)
     const int spc = (n_obs + 63) / 64;
     *steps_per_chunk = spc < 1 ? 1 : spc;
     return (n_obs + *steps_per_chunk - 1) / *steps_per_chunk;
+}
+
+cudaError_t launch_posterior_batch(const PosteriorArgs &a, const PostHuman *humans, const int *n_humans,
+                                   int max_rows, int max_chunks, int max_J, cudaStream_t s)
+{
+    int threads = 32 * max_J;
+    if (threads > 1024) threads = 1024;
+    if (max_rows <= 0 || max_chunks <= 0) return cudaSuccess;
+    posterior_batch_kernel<<<dim3(max_chunks, max_rows), threads, 0, s>>>(a, humans, n_humans);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_posterior(const PosteriorArgs &a, int n_chunks, cudaStream_t s)

@@ -1,0 +1,208 @@
+"""Batched persistent launch: every human's result equals its single-human
+result bit for bit (alone vs in the mix), for the belief update and the
+histogram, under retiling by the autotuner and under CUDA-graph replay."""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from gpu_util import GpuHuman, dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2603_01122_gb300 as pm
+    pm.build()
+    c = pm.pm_create(0)
+    yield c
+    pm.pm_destroy(c)
+
+
+def _setup(orc, humans, scale=1.0):
+    """Device inputs for each human: observed history from the oracle's model."""
+    import paper_2603_01122_gb300 as pm
+    out = []
+    for hu in humans:
+        m = orc.Model(hu.K, hu.speed, hu.dt, hu.goals, hu.beta)
+        obs = orc.simulate(m, hu.true_j, hu.start, max(hu.n_obs, 1), hu.obs_seed, hu.human_id).astype(np.float32)
+        gh = GpuHuman.of(hu)
+        N = max(1, int(hu.n_particles * scale))
+        T = hu.horizon
+        x0, y0, res, W, H = hu.grid
+        if hu.window:
+            W = H = hu.window
+        d = dict(hu=hu, gh=gh, obs=dev(obs), n_obs=obs.shape[0] - 1, N=N, T=T,
+                 lb=dev(hu.uniform_log_prior()), z0=dev(obs[-1]), grid=pm.make_grid(x0, y0, res, W, H),
+                 full_grid=pm.make_grid(x0, y0, res, hu.grid[3], hu.grid[4]),
+                 counts=torch.empty((T, H, W), dtype=torch.int32, device="cuda:0"),
+                 oob=torch.empty(T, dtype=torch.int32, device="cuda:0"))
+        out.append(d)
+    return out
+
+
+def _pm_humans(ds, center=0):
+    import paper_2603_01122_gb300 as pm
+    return [pm.make_human(d["gh"].goals, d["gh"].beta, d["lb"], d["z0"], d["N"], d["T"], d["grid"],
+                          d["hu"].seed, d["hu"].human_id, d["counts"], d["oob"], obs_xy=d["obs"],
+                          n_obs=d["n_obs"], center=center) for d in ds]
+
+
+def _single(ctx, d, lb):
+    import paper_2603_01122_gb300 as pm
+    T = d["T"]
+    g = d["full_grid"]
+    counts = torch.empty((T, g.H, g.W), dtype=torch.int32, device="cuda:0")
+    oob = torch.empty(T, dtype=torch.int32, device="cuda:0")
+    z0 = d["z0"].cpu().numpy()
+    pm.pm_predict_occupancy(ctx, d["gh"].model, lb, float(z0[0]), float(z0[1]), d["N"], T, g, d["hu"].seed,
+                            d["hu"].human_id, counts, oob)
+    return counts, oob
+
+
+def _shared_model(hu, gh):
+    import paper_2603_01122_gb300 as pm
+    return pm.make_model(hu.K, hu.speed, hu.dt, gh.goals, gh.beta)
+
+
+def test_batched_workload_alone_equals_in_mix(ctx, orc):
+    import paper_2603_01122_gb300 as pm
+    humans = workloads.batched()
+    ds = _setup(orc, humans)
+    b = pm.pm_batch_create(ctx, _shared_model(humans[0], ds[0]["gh"]), len(ds))
+    try:
+        pm.pm_batch_set(b, _pm_humans(ds))
+        # single-human posteriors first, from the same priors
+        singles = []
+        for d in ds:
+            lb = d["lb"].clone()
+            pm.pm_update_posterior(ctx, d["gh"].model, d["obs"], d["n_obs"], lb)
+            singles.append(lb)
+        pm.pm_batch_update_posterior(b)
+        pm.pm_batch_predict(b)
+        torch.cuda.synchronize()
+        for d, lb in zip(ds, singles):
+            assert torch.equal(d["lb"], lb)
+            c, o = _single(ctx, d, lb)
+            torch.cuda.synchronize()
+            assert torch.equal(d["counts"], c), d["hu"].human_id
+            assert torch.equal(d["oob"], o)
+            tot = d["counts"].view(d["T"], -1).sum(1, dtype=torch.int64) + d["oob"]
+            assert torch.all(tot == d["N"])
+    finally:
+        pm.pm_batch_destroy(b)
+
+
+def test_centred_windows_equal_cropped_full_grid(ctx, orc):
+    import paper_2603_01122_gb300 as pm
+    arr = workloads.serving()["arrivals"][:6]
+    ds = _setup(orc, [a.human for a in arr], scale=0.2)
+    b = pm.pm_batch_create(ctx, _shared_model(arr[0].human, ds[0]["gh"]), 8)
+    try:
+        pm.pm_batch_set(b, _pm_humans(ds, center=1))
+        pm.pm_batch_update_posterior(b)
+        pm.pm_batch_predict(b)
+        torch.cuda.synchronize()
+        for d in ds:
+            full, full_oob = _single(ctx, d, d["lb"])
+            torch.cuda.synchronize()
+            x0, y0, res, W, H = d["hu"].grid
+            z0 = d["z0"].cpu().numpy()
+            r = np.float32
+            cx = int(np.floor(r(r(r(z0[0]) - r(x0)) * (r(1.0) / r(res)))))
+            cy = int(np.floor(r(r(r(z0[1]) - r(y0)) * (r(1.0) / r(res)))))
+            w = d["hu"].window
+            ox, oy = cx - (w - 1) // 2, cy - (w - 1) // 2
+            f = full.cpu().numpy()
+            want = np.zeros((d["T"], w, w), np.int64)
+            xs, ys = max(ox, 0), max(oy, 0)
+            xe, ye = min(ox + w, W), min(oy + w, H)
+            want[:, ys - oy:ye - oy, xs - ox:xe - ox] = f[:, ys:ye, xs:xe]
+            got = d["counts"].cpu().numpy()
+            np.testing.assert_array_equal(got, want)
+            outside = f.reshape(d["T"], -1).sum(1) - want.reshape(d["T"], -1).sum(1)
+            np.testing.assert_array_equal(d["oob"].cpu().numpy(), full_oob.cpu().numpy() + outside)
+    finally:
+        pm.pm_batch_destroy(b)
+
+
+def test_autotune_and_graph_replay(ctx, orc):
+    import paper_2603_01122_gb300 as pm
+    humans = workloads.batched()[:6]
+    ds = _setup(orc, humans, scale=0.25)
+    b = pm.pm_batch_create(ctx, _shared_model(humans[0], ds[0]["gh"]), 8)
+    try:
+        pm.pm_batch_set(b, _pm_humans(ds))
+        pm.pm_batch_predict(b)
+        torch.cuda.synchronize()
+        ref = [d["counts"].clone() for d in ds]
+        pm.pm_batch_autotune(b)
+        cfg = pm.pm_batch_get_config(b)
+        assert cfg["threads"] in (128, 192, 224, 256)
+        pm.pm_batch_predict(b)
+        torch.cuda.synchronize()
+        for d, r in zip(ds, ref):
+            assert torch.equal(d["counts"], r)
+        for t, w in [(128, 24), (224, 96)]:
+            pm.pm_batch_set_config(b, t, 0, w)
+            pm.pm_batch_predict(b)
+            torch.cuda.synchronize()
+            for d, r in zip(ds, ref):
+                assert torch.equal(d["counts"], r)
+        # capture one frame (belief update + prediction) in a CUDA graph
+        s = torch.cuda.Stream()
+        lb0 = [d["lb"].clone() for d in ds]
+        with torch.cuda.stream(s):
+            pm.pm_batch_update_posterior(b, s)
+            pm.pm_batch_predict(b, s)
+        s.synchronize()
+        want = [d["counts"].clone() for d in ds]
+        want_lb = [d["lb"].clone() for d in ds]
+        g = torch.cuda.CUDAGraph()
+        for d, l in zip(ds, lb0):
+            d["lb"].copy_(l)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            pm.pm_batch_update_posterior(b, s)
+            pm.pm_batch_predict(b, s)
+        for d, l in zip(ds, lb0):
+            d["lb"].copy_(l)
+            d["counts"].fill_(7)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        for d, w, wl in zip(ds, want, want_lb):
+            assert torch.equal(d["counts"], w)
+            assert torch.equal(d["lb"], wl)
+        # the graph reads z0 from device memory: move one start and replay
+        ds[0]["z0"].add_(0.5)
+        for d, l in zip(ds, lb0):
+            d["lb"].copy_(l)
+        g.replay()
+        torch.cuda.synchronize()
+        c, o = _single(ctx, ds[0], ds[0]["lb"])
+        torch.cuda.synchronize()
+        assert torch.equal(ds[0]["counts"], c)
+    finally:
+        pm.pm_batch_destroy(b)
+
+
+def test_batch_rejects_mixed_or_invalid(ctx, orc):
+    import paper_2603_01122_gb300 as pm
+    humans = workloads.batched()[:2]
+    ds = _setup(orc, humans, scale=0.01)
+    b = pm.pm_batch_create(ctx, _shared_model(humans[0], ds[0]["gh"]), 1)
+    try:
+        with pytest.raises(pm.PmError):
+            pm.pm_batch_set(b, _pm_humans(ds))  # more than max_humans
+        hs = _pm_humans(ds[:1])
+        hs[0].horizon = 0
+        with pytest.raises(pm.PmError):
+            pm.pm_batch_set(b, hs)
+        hs = _pm_humans(ds[:1], center=1)
+        hs[0].grid = pm.make_grid(0, 0, 0.05, 120, 121)
+        with pytest.raises(pm.PmError):
+            pm.pm_batch_set(b, hs)
+    finally:
+        pm.pm_batch_destroy(b)
