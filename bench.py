@@ -37,7 +37,8 @@ sys.path.insert(0, ROOT)
 import workloads  # noqa: E402
 
 METRIC = "particle-steps/s"
-ROLLOUT_SOURCES = ["paper_2603_01122_gb300/csrc/pm_rollout.cu", "paper_2603_01122_gb300/csrc/pm_internal.cuh"]
+ROLLOUT_SOURCES = ["paper_2603_01122_gb300/csrc/pm_rollout.cu", "paper_2603_01122_gb300/csrc/pm_rollout_dev.cuh",
+                   "paper_2603_01122_gb300/csrc/pm_internal.cuh"]
 
 
 def parse():
