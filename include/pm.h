@@ -278,6 +278,26 @@ pm_status pm_loglik_backward(pm_ctx *ctx, const pm_model *model, int32_t M, cons
                              float grad_out, float *loglik, float *d_goals, float *d_speed,
                              float *d_w, void *stream);
 
+/* ---- for callers that cannot allocate ------------------------------------- */
+
+/* The paper has no counterpart to this call; it serves callers that must not
+ * allocate device memory: a real-time loop that forbids allocation once it
+ * runs, work enqueued during a stream capture whose mode rejects cudaMalloc,
+ * or an application whose device memory belongs to its own pool. It computes
+ * what pm_update_posterior computes (same arguments, same belief layout and
+ * validation) without a context, and allocates nothing: its scratch is a
+ * static device array of this library, 165,888 bytes, which every GPU that
+ * loads the library holds until the process exits. Limit: G*B <= 256 (larger
+ * models are rejected with PM_EINVAL); the observed steps are split over at
+ * most 32 CTAs. The first call on a device looks up the array's device
+ * address, so make that first call before any stream capture. Every call
+ * shares the array: calls whose work overlaps on the GPU (different streams,
+ * or several host threads) race on it and must be serialised by the caller.
+ * The belief may differ from pm_update_posterior's in the last bits (the
+ * steps are summed in other chunks). */
+pm_status pm_update_posterior_noalloc(const pm_model *model, const float *obs_xy, int32_t n_obs,
+                                      float *log_belief, void *stream);
+
 /* ---- checks and measurement ---------------------------------------------- */
 
 /* Raw Philox4x64-10 blocks for counters (particle0 + i, block, purpose, 0),

@@ -75,6 +75,7 @@ def _signatures(lib):
         "pm_loglik_forward": ([_vp, P(pm_model), C.c_int32, _vp, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
         "pm_loglik_backward": ([_vp, P(pm_model), C.c_int32, _vp, C.c_int32, _vp, _vp, C.c_float, _vp, _vp,
                                 _vp, _vp, _vp], C.c_int),
+        "pm_update_posterior_noalloc": ([P(pm_model), _vp, C.c_int32, _vp, _vp], C.c_int),
         "pm_philox_blocks": ([_vp, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint64,
                               C.c_int32, _vp, _vp], C.c_int),
         "pm_probe_sfu": ([_vp, C.c_int, P(C.c_double)], C.c_int),
@@ -253,6 +254,12 @@ def pm_loglik_backward(ctx, model: pm_model, M, offsets, n_points, traj_xy, log_
     _check(library().pm_loglik_backward(ctx, C.byref(model), int(M), _p(offsets), int(n_points), _p(traj_xy),
                                         _p(log_prior), float(grad_out), _p(loglik), _p(d_goals), _p(d_speed),
                                         _p(d_w), _stream(stream)))
+
+
+def pm_update_posterior_noalloc(model: pm_model, obs_xy, n_obs, log_belief, stream=None):
+    """Belief update that allocates nothing (no context; static device scratch)."""
+    _check(library().pm_update_posterior_noalloc(C.byref(model), _p(obs_xy), int(n_obs), _p(log_belief),
+                                                 _stream(stream)))
 
 
 def pm_philox_blocks(ctx, seed, human_id, purpose, particle0, block, n, out, stream=None):

@@ -631,6 +631,57 @@ pm_status batch_predict_impl(pm_batch *b, cudaStream_t stream)
 
 } // namespace
 
+// Belief update on caller-supplied scratch (used by the entry point that
+// allocates nothing): `part` holds the per-chunk accumulators and the [J]
+// doubles, `ticket` one zero word; at most `max_chunks` CTAs are used.
+pm_status pm_internal_error(pm_status st, const char *msg) { return fail(st, "%s", msg); }
+
+pm_status pm_internal_posterior_on_scratch(const pm_model *model, const float *obs_xy, int32_t n_obs,
+                                           float *log_belief, float *part, unsigned *ticket, size_t part_bytes,
+                                           int max_chunks, void *stream)
+{
+    pm_status st = check_model(model);
+    if (st != PM_OK) return st;
+    if (n_obs < 0) return fail(PM_EINVAL, "n_obs=%d must be >= 0", n_obs);
+    if (!log_belief) return fail(PM_EINVAL, "log_belief is NULL");
+    if (n_obs == 0) return PM_OK;
+    if (!obs_xy) return fail(PM_EINVAL, "obs_xy is NULL");
+    pm::PosteriorArgs a;
+    std::memset(&a, 0, sizeof a);
+    const double s = (double)model->speed * (double)model->dt;
+    for (int k = 0; k < model->K; ++k) {
+        double c, sn;
+        unit_heading(model->K, k, &c, &sn);
+        a.ux[k] = (float)c;
+        a.uy[k] = (float)sn;
+    }
+    a.enabled = enabled_mask(model);
+    a.s = (float)s;
+    a.s2 = (float)(s * s);
+    a.two_s = (float)(2.0 * s);
+    a.w2 = model->w2;
+    a.K = model->K;
+    a.G = model->G;
+    a.B = model->B;
+    a.goals = model->goals;
+    a.beta = model->beta;
+    a.obs = obs_xy;
+    a.n_obs = n_obs;
+    a.log_b = log_belief;
+    a.steps_per_chunk = (n_obs + max_chunks - 1) / max_chunks;
+    const int n_chunks = (n_obs + a.steps_per_chunk - 1) / a.steps_per_chunk;
+    if (pm::posterior_scratch_bytes(n_chunks, model->G * model->B) > part_bytes)
+        return fail(PM_EINVAL, "scratch of %zu bytes is too small for G*B=%d", part_bytes, model->G * model->B);
+    a.part = part;
+    a.ticket = ticket;
+    // the ticket must start at zero; a call that did not finish could have left it set
+    cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the ticket");
+    e = pm::launch_posterior(a, n_chunks, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "posterior launch");
+    return PM_OK;
+}
+
 extern "C" {
 
 pm_status pm_create(pm_ctx **out, int device)
