@@ -202,11 +202,13 @@ void choose_window(const pm_model *m, const pm_grid *g, float z0x, float z0y, in
         if (w <= 0 || h <= 0) { // z0 is far outside the grid: no window
             a.win_x0 = a.win_y0 = 0;
             a.win_side = 0;
-            *dyn_smem = list_bytes;
+            *dyn_smem = 2 * list_bytes;
             return;
         }
-        const size_t words = (size_t)((w * h + 1) / 2);
-        const size_t bytes = ((words * 4 + 15) & ~(size_t)15) + list_bytes;
+        // two windows (alternating by step parity) of 16-bit counts, each padded
+        // to 16 bytes, then two touched-cell lists
+        const size_t stride_words = (size_t)(((w * h + 1) / 2 + 3) & ~3LL);
+        const size_t bytes = 2 * stride_words * 4 + 2 * list_bytes;
         if (bytes <= smem_budget || r <= 4) {
             a.win_x0 = (int)x_lo;
             a.win_y0 = (int)y_lo;
@@ -245,6 +247,7 @@ int choose_rollout_threads(pm_ctx *ctx, const pm_model *model, const pm_grid *gr
         }
     }
     if (hist) choose_window(model, grid, a.z0x, a.z0y, a.T, best_t, 64 * 1024, a, &best_dyn);
+    cudaGetLastError(); // a shape the occupancy query rejected is simply not chosen
     *dyn_out = best_dyn;
     return best_t;
 }
@@ -346,7 +349,10 @@ pm_status predict_impl(pm_ctx *ctx, const pm_model *model, const float *log_beli
     }
     threads = choose_rollout_threads(ctx, model, grid, a, hist, &dyn);
     cudaError_t e = pm::launch_rollout(a, threads, dyn, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "rollout launch");
+    if (e != cudaSuccess) {
+        return fail(PM_ECUDA, "rollout launch (%d CTAs x %d threads, %zu B dynamic shared memory): %s",
+                    (a.N + threads - 1) / threads, threads, dyn, cudaGetErrorString(e));
+    }
     return PM_OK;
 }
 
@@ -481,7 +487,8 @@ pm_status check_human(const pm_human &h, int i)
 
 int batch_radius_cap(int window_kib, int threads)
 {
-    const long long cells = ((long long)window_kib * 1024 - (long long)threads * 2) / 2;
+    // two windows of 16-bit counts and two lists of `threads` entries
+    const long long cells = (((long long)window_kib * 1024 - (long long)threads * 4) / 2 - 32) / 2;
     int r = 0;
     while ((2LL * (r + 1) + 1) * (2LL * (r + 1) + 1) <= cells && 2 * (r + 1) + 1 <= 255) ++r;
     return r;
@@ -491,7 +498,8 @@ size_t batch_dyn_smem(const pm_batch *b)
 {
     const int r = batch_radius_cap(b->window_kib, b->threads);
     const size_t cells = (size_t)(2 * r + 1) * (2 * r + 1);
-    return (((cells + 1) / 2) * 4 + 15) / 16 * 16 + (size_t)b->threads * 2;
+    const size_t stride_words = (((cells + 1) / 2) + 3) & ~(size_t)3;
+    return 2 * stride_words * 4 + 2 * (size_t)b->threads * 2;
 }
 
 pm_status batch_upload(pm_batch *b, cudaStream_t stream)

@@ -76,12 +76,10 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_rollout_kernel(const _
             s_z0[0] = zx;
             s_z0[1] = zy;
         }
-        if (tid < 2) {
-            sh.list_n[tid] = 0u;
-            sh.oob_n[tid] = 0u;
-        }
+        if (tid < 3) sh.list_n[tid] = 0u;
+        if (tid < 2) sh.oob_n[tid] = 0u;
         __syncthreads();
-        const int words = (s_geom[4] * s_geom[5] + 1) >> 1;
+        const int words = 2 * window_stride_words(s_geom[4], s_geom[5]);
         for (int w = tid; w < words; w += nthr) dyn[w] = 0u;
         __syncthreads();
         TileCtx c;

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kRolloutThreads) rollout_kernel(const __grid_c
     const int J = a.G * a.B;
     const bool hist = a.counts != nullptr;
     const int ww = a.win_side & 0xFFFF, wh = a.win_side >> 16; // window width/height (cells)
-    const int win_words = (ww * wh + 1) >> 1;
+    const int win_words = 2 * window_stride_words(ww, wh);     // both windows
 
     for (int j = tid; j < J; j += nthr) {
         const int g = j / a.B, b = j - g * a.B;
@@ -47,10 +47,8 @@ __global__ void __launch_bounds__(kRolloutThreads) rollout_kernel(const __grid_c
     for (int k = tid; k < KT; k += nthr) sh.step[k] = make_float2(a.tab.sx[k], a.tab.sy[k]);
     if (hist)
         for (int w = tid; w < win_words; w += nthr) dyn[w] = 0u;
-    if (tid < 2) {
-        sh.list_n[tid] = 0u;
-        sh.oob_n[tid] = 0u;
-    }
+    if (tid < 3) sh.list_n[tid] = 0u;
+    if (tid < 2) sh.oob_n[tid] = 0u;
     if (tid < 32) belief_cdf(a.log_b, J, sh.cdf, tid);
     __syncthreads();
 
@@ -99,16 +97,18 @@ cudaError_t launch_kt(const RolloutArgs &a, int threads, size_t dyn_smem, cudaSt
     const uint64_t all = (KT >= 64) ? ~0ull : ((1ull << KT) - 1ull);
     const bool full = (a.K == KT) && ((a.enabled & all) == all);
     const unsigned blocks = (unsigned)((a.N + threads - 1) / threads);
+    cudaGetLastError(); // clear errors of earlier calls whose failure was handled
     if (full) {
         auto k = rollout_kernel<KT, true>;
-        if (dyn_smem > 48 * 1024) {
+        if (dyn_smem > 0) { // static + dynamic may pass the 48 KiB default
+
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
             if (e != cudaSuccess) return e;
         }
         k<<<blocks, threads, dyn_smem, s>>>(a);
     } else {
         auto k = rollout_kernel<KT, false>;
-        if (dyn_smem > 48 * 1024) {
+        if (dyn_smem > 0) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
             if (e != cudaSuccess) return e;
         }
@@ -134,8 +134,9 @@ int rollout_occupancy(const RolloutArgs &a, int threads, size_t dyn_smem)
     const int KT = rollout_kt_for(a.K);
     const uint64_t all = (KT >= 64) ? ~0ull : ((1ull << KT) - 1ull);
     const bool full = (a.K == KT) && ((a.enabled & all) == all);
-    if (dyn_smem > 48 * 1024) {
-        // the attribute must be raised before the occupancy query counts it
+    if (dyn_smem > 0) {
+        // static + dynamic may pass the 48 KiB default: raise the limit before
+        // the occupancy query counts it
         switch (KT) {
         case 8: cudaFuncSetAttribute(full ? rollout_kernel<8, true> : rollout_kernel<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem); break;
         case 16: cudaFuncSetAttribute(full ? rollout_kernel<16, true> : rollout_kernel<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem); break;

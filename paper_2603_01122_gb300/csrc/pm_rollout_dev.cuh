@@ -10,7 +10,7 @@ struct __align__(16) RolloutShared {
     float4 comp[kMaxJ]; // (beta_b * w2 * log2 e, g_x, g_y, 0) of component j = g*B + b
     uint32_t cdf[kMaxJ]; // inclusive fixed-point running sum of the belief
     float2 step[kMaxK];  // Euler step of heading k
-    uint32_t list_n[2];  // touched-cell list length, by step parity
+    uint32_t list_n[3];  // touched-cell list length, by step mod 3
     uint32_t oob_n[2];   // particles outside the grid, by step parity
 };
 
@@ -52,6 +52,16 @@ __device__ inline void belief_cdf(const float *log_b, int J, uint32_t *cdf, int 
 
 // One heading draw of Eq. 2 at state (x, y) for goal (gx, gy) and
 // cb = beta * w2 * log2(e). FULL: all KT headings enabled.
+//
+// d_k - d_0 is formed from the residual of the approximate square root, so
+// beta*w2*(d_j - d_k) keeps FP32 relative precision; the weights
+// exp(beta (Q_k - Q_max)) are rounded to 22-bit fixed point, so the running
+// sums C_k are exact and the draw (smallest k with C_k > (u24 * S) >> 24)
+// depends only on the rounded weights. For even KT with every heading
+// enabled the FP32 work runs on packed pairs of consecutive headings
+// (fma/add/sub/mul .f32x2: the same IEEE operations, half the instructions);
+// otherwise it runs scalar, skipping disabled headings. Both give identical
+// results.
 template <int KT, bool FULL>
 __device__ __forceinline__ int draw_heading(const HeadingTab &tab, uint64_t enabled, float s2, float x, float y,
                                             float gx, float gy, float cb, uint32_t word)
@@ -59,22 +69,57 @@ __device__ __forceinline__ int draw_heading(const HeadingTab &tab, uint64_t enab
     const float dx = x - gx, dy = y - gy;
     const float D = fmaf(dx, dx, fmaf(dy, dy, s2));
     const float hD = 0.5f * rsqrt_approx(D); // 1/(2 d), D >= s^2 > 0
-    float dv[KT];
-    float dref = 0.0f;
-    if (FULL && (KT % 2 == 0)) {
-        // e_{k+K/2} = -e_k exactly in the tables: one dot product serves both
+    if constexpr (FULL && (KT % 2 == 0)) {
+        const f32x2 DX = f2_pack(dx, dx), DY = f2_pack(dy, dy);
+        const f32x2 DD = f2_pack(D, D), NDD = f2_pack(-D, -D), HD = f2_pack(hD, hD);
+        const f32x2 *TX = reinterpret_cast<const f32x2 *>(tab.tx);
+        const f32x2 *TY = reinterpret_cast<const f32x2 *>(tab.ty);
+        f32x2 dv[KT / 2];
+        f32x2 DREF = 0ull;
+        float dmin = INFINITY;
 #pragma unroll
-        for (int k = 0; k < KT / 2; ++k) {
-            const float p = fmaf(tab.tx[k], dx, tab.ty[k] * dy); // 2 s e_k.(z - g)
-            const float dk = sqrt_approx(fmaxf(D + p, 0.0f));
-            const float dm = sqrt_approx(fmaxf(D - p, 0.0f));
-            const float rk = fmaf(-dk, dk, D) + p;                  // residual D + p - dk^2
-            const float rm = fmaf(-dm, dm, D) - p;
-            if (k == 0) dref = dk;
-            dv[k] = fmaf(rk, hD, dk - dref);                         // d_k - d_0, corrected
-            dv[k + KT / 2] = fmaf(rm, hD, dm - dref);
+        for (int q = 0; q < KT / 2; ++q) {
+            const f32x2 P = f2_fma(TX[q], DX, f2_mul(TY[q], DY)); // 2 s e_k.(z - g), k = 2q, 2q+1
+            float x0, x1;
+            f2_unpack(f2_add(DD, P), x0, x1);
+            const float d0 = sqrt_approx(fmaxf(x0, 0.0f)), d1 = sqrt_approx(fmaxf(x1, 0.0f));
+            const f32x2 DK = f2_pack(d0, d1);
+            if (q == 0) DREF = f2_pack(d0, d0);
+            const f32x2 R = f2_sub(P, f2_fma(DK, DK, NDD));       // D + p - dk^2
+            dv[q] = f2_fma(R, HD, f2_sub(DK, DREF));                // d_k - d_0, corrected
+            float v0, v1;
+            f2_unpack(dv[q], v0, v1);
+            dmin = fminf(dmin, fminf(v0, v1));
         }
+        const f32x2 NC = f2_pack(-cb, -cb);
+        const float base = dmin * cb;
+        const f32x2 BASE = f2_pack(base, base);
+        const f32x2 SC = f2_pack(4194304.0f, 4194304.0f), MG = f2_pack(12582912.0f, 12582912.0f);
+        uint32_t bits[KT];
+        uint32_t S = 0u;
+#pragma unroll
+        for (int q = 0; q < KT / 2; ++q) {
+            float a0, a1;
+            f2_unpack(f2_fma(dv[q], NC, BASE), a0, a1);             // log2 of exp(beta (Q_k - Q_max))
+            float w0, w1;
+            f2_unpack(f2_fma(f2_pack(ex2_approx(a0), ex2_approx(a1)), SC, MG), w0, w1);
+            bits[2 * q] = __float_as_uint(w0);                      // 0x4B400000 + round(e * 2^22)
+            bits[2 * q + 1] = __float_as_uint(w1);
+            S += bits[2 * q] + bits[2 * q + 1];
+        }
+        S -= (uint32_t)KT * 0x4B400000u;                            // total weight (exact integer)
+        const uint32_t thr = (uint32_t)(((uint64_t)(word >> 8) * (uint64_t)S) >> 24);
+        uint32_t acc = ~thr; // C_k - thr - 1 once E_k is added: negative iff C_k <= thr
+        int sel = 0;
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            acc += bits[k] - 0x4B400000u;
+            sel += (int)(acc >> 31);
+        }
+        return sel;
     } else {
+        float dv[KT];
+        float dref = 0.0f;
 #pragma unroll
         for (int k = 0; k < KT; ++k) {
             const float p = fmaf(tab.tx[k], dx, tab.ty[k] * dy);
@@ -83,30 +128,29 @@ __device__ __forceinline__ int draw_heading(const HeadingTab &tab, uint64_t enab
             if (k == 0) dref = dk;
             dv[k] = fmaf(rk, hD, dk - dref);
         }
+        float dmin = INFINITY;
+#pragma unroll
+        for (int k = 0; k < KT; ++k)
+            if (FULL || ((enabled >> k) & 1ull)) dmin = fminf(dmin, dv[k]);
+        const float base = dmin * cb;
+        const float nc = -cb;
+        uint32_t C[KT];
+        uint32_t S = 0;
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            const float e = ex2_approx(fmaf(dv[k], nc, base));
+            uint32_t E = __float_as_uint(fmaf(e, 4194304.0f, 12582912.0f)) - 0x4B400000u;
+            if (!FULL && !((enabled >> k) & 1ull)) E = 0u;
+            S += E;
+            C[k] = S;
+        }
+        const uint32_t thr = (uint32_t)(((uint64_t)(word >> 8) * (uint64_t)S) >> 24);
+        int sel = 0;
+#pragma unroll
+        for (int k = 0; k < KT; ++k) sel += (C[k] <= thr) ? 1 : 0;
+        return sel;
     }
-    float dmin = INFINITY;
-#pragma unroll
-    for (int k = 0; k < KT; ++k)
-        if (FULL || ((enabled >> k) & 1ull)) dmin = fminf(dmin, dv[k]);
-    const float base = dmin * cb;
-    const float nc = -cb;
-    uint32_t C[KT];
-    uint32_t S = 0;
-#pragma unroll
-    for (int k = 0; k < KT; ++k) {
-        const float e = ex2_approx(fmaf(dv[k], nc, base)); // exp(beta*(Q_k - Q_max))
-        uint32_t E = __float_as_uint(fmaf(e, 4194304.0f, 12582912.0f)) - 0x4B400000u;
-        if (!FULL && !((enabled >> k) & 1ull)) E = 0u;
-        S += E;
-        C[k] = S;
-    }
-    const uint32_t thr = (uint32_t)(((uint64_t)(word >> 8) * (uint64_t)S) >> 24);
-    int sel = 0;
-#pragma unroll
-    for (int k = 0; k < KT; ++k) sel += (C[k] <= thr) ? 1 : 0;
-    return sel;
 }
-
 
 // Per-tile state of one human for rollout_tile.
 struct TileCtx {
@@ -130,13 +174,23 @@ struct TileCtx {
     int32_t *tr_comp;
 };
 
+// Words of one shared-memory window of ww x wh 16-bit counts, padded to 16 B.
+__device__ __host__ __forceinline__ int window_stride_words(int ww, int wh)
+{
+    return (((ww * wh + 1) >> 1) + 3) & ~3;
+}
+
 // Algorithm 1 for one particle per thread of the CTA: the (beta, g) draw from
 // the belief table in shared memory, then T heading draws and Euler steps,
 // each step emplaced in the CTA's shared-memory window (first touch appends
-// the cell to a list; the list is flushed with one global reduction per
-// touched cell) or, outside the window, directly in global memory. `sh` must
-// hold the component table and belief CDF of the human, the window must be
-// zero and list_n / oob_n zero on entry; the window is zero again on exit.
+// the cell to the step's list; after one block barrier the list is flushed
+// with one global reduction per touched cell) or, outside the window,
+// directly in global memory. Two windows and two lists alternate by step
+// parity and three list counters rotate, so the flush of step t overlaps the
+// inserts of step t+1 and one barrier per step suffices. `sh` must hold the
+// component table and belief CDF of the human; both windows, list_n[0..2]
+// and oob_n[0..1] must be zero on entry; the windows are zero again on exit.
+// dyn layout: window 0 | window 1 (window_stride_words each) | list 0 | list 1.
 template <int KT, bool FULL>
 __device__ __forceinline__ void rollout_tile(const HeadingTab &tab, uint64_t enabled, float s2,
                                              const TileCtx &c, RolloutShared &sh, uint32_t *dyn)
@@ -144,10 +198,8 @@ __device__ __forceinline__ void rollout_tile(const HeadingTab &tab, uint64_t ena
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
     const int ww = c.ww, wh = c.wh;
-    const int win_words = (ww * wh + 1) >> 1;
-    uint32_t *win32 = dyn;
-    uint16_t *win16 = reinterpret_cast<uint16_t *>(dyn);
-    uint16_t *list = reinterpret_cast<uint16_t *>(dyn + win_words);
+    const int stride = window_stride_words(ww, wh);
+    uint16_t *list0 = reinterpret_cast<uint16_t *>(dyn + 2 * stride);
 
     float x = c.z0x, y = c.z0y, cb = 0.0f, gx = 0.0f, gy = 0.0f;
     const uint64_t i = (uint64_t)c.i;
@@ -169,6 +221,7 @@ __device__ __forceinline__ void rollout_tile(const HeadingTab &tab, uint64_t ena
 
     const size_t plane = (size_t)c.W * (size_t)c.H;
     uint32_t q0 = 0, q1 = 0, q2 = 0, q3 = 0, q4 = 0, q5 = 0, q6 = 0, q7 = 0;
+    int li = 1; // t mod 3: the list counter of step t
     for (int t = 1; t <= c.T; ++t) {
         int cx = 0, cy = 0;
         bool in_grid = false;
@@ -199,44 +252,49 @@ __device__ __forceinline__ void rollout_tile(const HeadingTab &tab, uint64_t ena
                 in_grid = (vx == vx) && (vy == vy) && cx >= 0 && cx < c.W && cy >= 0 && cy < c.H;
             }
         }
-        if (!c.hist) continue;
-        __syncthreads(); // the flush of step t-1 has cleared the window
-        if (tid == 0) sh.list_n[(t + 1) & 1] = 0u;
-        if (c.active) {
-            if (!in_grid) {
-                atomicAdd(&sh.oob_n[t & 1], 1u);
-            } else {
-                const int wx = cx - c.win_x0, wy = cy - c.win_y0;
-                if ((unsigned)wx < (unsigned)ww && (unsigned)wy < (unsigned)wh) {
-                    const int w = wy * ww + wx;
-                    const uint32_t sft = (uint32_t)(w & 1) << 4;
-                    const uint32_t old = atomicAdd(&win32[w >> 1], 1u << sft);
-                    if (((old >> sft) & 0xFFFFu) == 0u) {
-                        const uint32_t slot = atomicAdd(&sh.list_n[t & 1], 1u);
-                        list[slot] = (uint16_t)(wx | (wy << 8));
-                    }
+        if (c.hist) {
+            const int b = t & 1;
+            uint32_t *win32 = dyn + b * stride;
+            uint16_t *win16 = reinterpret_cast<uint16_t *>(win32);
+            uint16_t *list = list0 + b * nthr;
+            if (c.active) {
+                if (!in_grid) {
+                    atomicAdd(&sh.oob_n[b], 1u);
                 } else {
-                    red_add(c.counts + (size_t)(t - 1) * plane + (size_t)cy * c.W + cx, 1u);
+                    const int wx = cx - c.win_x0, wy = cy - c.win_y0;
+                    if ((unsigned)wx < (unsigned)ww && (unsigned)wy < (unsigned)wh) {
+                        const int w = wy * ww + wx;
+                        const uint32_t sft = (uint32_t)(w & 1) << 4;
+                        const uint32_t old = atomicAdd(&win32[w >> 1], 1u << sft);
+                        if (((old >> sft) & 0xFFFFu) == 0u) {
+                            const uint32_t slot = atomicAdd(&sh.list_n[li], 1u);
+                            list[slot] = (uint16_t)(wx | (wy << 8));
+                        }
+                    } else {
+                        red_add(c.counts + (size_t)(t - 1) * plane + (size_t)cy * c.W + cx, 1u);
+                    }
                 }
             }
+            __syncthreads(); // all of step t is in window b; step t-1's flush is done
+            const int lr = (li == 0) ? 2 : li - 1; // counter of step t-1: free from here on
+            if (tid == 0) sh.list_n[lr] = 0u;
+            const uint32_t n = sh.list_n[li];
+            uint32_t *crow = c.counts + (size_t)(t - 1) * plane;
+            for (uint32_t e = tid; e < n; e += nthr) {
+                const uint32_t pk = list[e];
+                const int wx = (int)(pk & 0xFFu), wy = (int)(pk >> 8);
+                const int w = wy * ww + wx;
+                const uint32_t v = win16[w];
+                win16[w] = 0;
+                red_add(crow + (size_t)(c.win_y0 + wy) * c.W + (c.win_x0 + wx), v);
+            }
+            if (tid == 0) {
+                const uint32_t o = sh.oob_n[b];
+                if (o) red_add(c.oob + (t - 1), o);
+                sh.oob_n[b] = 0u;
+            }
         }
-        __syncthreads(); // all of step t is in the window
-        const uint32_t n = sh.list_n[t & 1];
-        uint32_t *crow = c.counts + (size_t)(t - 1) * plane;
-        for (uint32_t e = tid; e < n; e += nthr) {
-            const uint32_t pk = list[e];
-            const int wx = (int)(pk & 0xFFu), wy = (int)(pk >> 8);
-            const int w = wy * ww + wx;
-            const uint32_t v = win16[w];
-            win16[w] = 0;
-            red_add(crow + (size_t)(c.win_y0 + wy) * c.W + (c.win_x0 + wx), v);
-        }
-        if (tid == 0) {
-            const uint32_t o = sh.oob_n[t & 1];
-            if (o) red_add(c.oob + (t - 1), o);
-            sh.oob_n[t & 1] = 0u;
-        }
+        li = (li == 2) ? 0 : li + 1;
     }
 }
-
 } // namespace pm
