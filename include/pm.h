@@ -233,17 +233,24 @@ pm_status pm_batch_update_posterior(pm_batch *b, void *stream);
  * it may be captured in a CUDA graph. */
 pm_status pm_batch_predict(pm_batch *b, void *stream);
 
-/* Time candidate launch shapes (threads per CTA and shared-memory window
- * size) on the current batch with CUDA events and keep the fastest; it runs
- * pm_batch_predict several times (outputs are overwritten). Synchronous. */
+/* Time candidate launch shapes (threads per CTA, particles per thread,
+ * emplacement mode and shared-memory window size) on the current batch with
+ * CUDA events and keep the fastest; it runs pm_batch_predict several times
+ * (outputs are overwritten). Synchronous. */
 pm_status pm_batch_autotune(pm_batch *b, void *stream);
 
 /* Read or set the launch shape: threads per CTA (multiple of 32, <= 256),
- * resident CTAs per SM used for the grid (0 = as many as fit) and the window
- * budget in KiB of shared memory. pm_batch_set_config rebuilds the work list
- * (queued on the legacy stream). */
-pm_status pm_batch_get_config(const pm_batch *b, int32_t *threads, int32_t *ctas_per_sm, int32_t *window_kib);
-pm_status pm_batch_set_config(pm_batch *b, int32_t threads, int32_t ctas_per_sm, int32_t window_kib);
+ * particles per thread (1 or 2), the emplacement mode (shared_window = 1: a
+ * per-CTA shared-memory window flushed once per touched cell, one particle
+ * per thread; 0: lanes of a warp in the same cell combined into one global
+ * reduction), resident CTAs per SM used for the grid (0 = as many as fit)
+ * and the window budget in KiB of shared memory. pm_batch_set_config
+ * rebuilds the work list when the tile size changes (queued on the legacy
+ * stream). Every shape gives the same counts. */
+pm_status pm_batch_get_config(const pm_batch *b, int32_t *threads, int32_t *particles_per_thread,
+                              int32_t *shared_window, int32_t *ctas_per_sm, int32_t *window_kib);
+pm_status pm_batch_set_config(pm_batch *b, int32_t threads, int32_t particles_per_thread,
+                              int32_t shared_window, int32_t ctas_per_sm, int32_t window_kib);
 
 /* Release the plan (synchronises with its pending uploads). */
 void pm_batch_destroy(pm_batch *b);

@@ -54,6 +54,8 @@ struct pm_batch {
     cudaEvent_t staged = nullptr;
     // launch shape
     int threads = 256;
+    int ppt = 1;            // particles per thread
+    bool warp_hist = true;  // warp-combined emplacement (else shared-memory window)
     int ctas_per_sm = 0;
     int window_kib = 48;
     int n_items = 0;
@@ -186,7 +188,7 @@ void fill_rollout_tables(const pm_model *m, pm::RolloutArgs &a)
 // Window of the shared-memory histogram: the cells within reach of z0 in T
 // steps (|z_t - z0| <= T v dt), clipped to the grid and to 255 x 255 cells and
 // to the shared-memory budget; particles outside it are counted directly.
-void choose_window(const pm_model *m, const pm_grid *g, float z0x, float z0y, int T, int threads,
+[[maybe_unused]] void choose_window(const pm_model *m, const pm_grid *g, float z0x, float z0y, int T, int threads,
                    size_t smem_budget, pm::RolloutArgs &a, size_t *dyn_smem)
 {
     const float inv_res = 1.0f / g->res;
@@ -220,36 +222,34 @@ void choose_window(const pm_model *m, const pm_grid *g, float z0x, float z0y, in
     }
 }
 
-// Block size of the rollout: one particle per thread, all CTAs resident in
-// one wave where possible, and the CTAs spread evenly over the SMs (the
-// kernel time follows the most loaded SM: ceil(blocks / SMs) CTAs of
-// `threads` particles each).
-int choose_rollout_threads(pm_ctx *ctx, const pm_model *model, const pm_grid *grid, pm::RolloutArgs &a,
-                           bool hist, size_t *dyn_out)
+// Launch shape of the single-human rollout: one particle per thread with
+// warp-combined emplacement (measured faster on GB300 than the shared-memory
+// window, whose block barriers and shared memory cost more than the global
+// reductions it saves), and a block size that spreads the CTAs evenly over
+// the SMs: the kernel time follows the most loaded SM, ceil(blocks / SMs)
+// CTAs of `threads` particles.
+pm::RolloutShape choose_rollout_shape(pm_ctx *ctx, pm::RolloutArgs &a, size_t *dyn_out)
 {
     static const int cand[] = {256, 224, 192, 160, 128};
     double best_eff = -1.0;
-    int best_t = 256;
-    size_t best_dyn = 0;
-    pm::RolloutArgs trial = a;
+    pm::RolloutShape best{256, 1, true};
     for (int t : cand) {
-        size_t dyn = 0;
-        if (hist) choose_window(model, grid, a.z0x, a.z0y, a.T, t, 64 * 1024, trial, &dyn);
-        const int occ = pm::rollout_occupancy(trial, t, dyn);
+        const pm::RolloutShape sh{t, 1, true};
+        const int occ = pm::rollout_occupancy(a, sh, 0);
         if (occ < 1) continue;
         const long long blocks = ((long long)a.N + t - 1) / t;
         const long long per_sm = (blocks + ctx->sm_count - 1) / ctx->sm_count;
         const double eff = (double)a.N / ((double)per_sm * t * ctx->sm_count) * (occ >= 2 ? 1.0 : 0.8);
         if (eff > best_eff + 1e-9) {
             best_eff = eff;
-            best_t = t;
-            best_dyn = dyn;
+            best = sh;
         }
     }
-    if (hist) choose_window(model, grid, a.z0x, a.z0y, a.T, best_t, 64 * 1024, a, &best_dyn);
     cudaGetLastError(); // a shape the occupancy query rejected is simply not chosen
-    *dyn_out = best_dyn;
-    return best_t;
+    a.win_x0 = a.win_y0 = 0;
+    a.win_side = 0;
+    *dyn_out = 0;
+    return best;
 }
 
 pm_status ensure_stage(pm_ctx *ctx, size_t bytes)
@@ -347,8 +347,9 @@ pm_status predict_impl(pm_ctx *ctx, const pm_model *model, const float *log_beli
         a.W = a.H = 1;
         a.inv_res = 1.0f;
     }
-    threads = choose_rollout_threads(ctx, model, grid, a, hist, &dyn);
-    cudaError_t e = pm::launch_rollout(a, threads, dyn, stream);
+    const pm::RolloutShape shape = choose_rollout_shape(ctx, a, &dyn);
+    threads = shape.threads;
+    cudaError_t e = pm::launch_rollout(a, shape, dyn, stream);
     if (e != cudaSuccess) {
         return fail(PM_ECUDA, "rollout launch (%d CTAs x %d threads, %zu B dynamic shared memory): %s",
                     (a.N + threads - 1) / threads, threads, dyn, cudaGetErrorString(e));
@@ -494,8 +495,11 @@ int batch_radius_cap(int window_kib, int threads)
     return r;
 }
 
+pm::RolloutShape batch_shape_of(const pm_batch *b) { return pm::RolloutShape{b->threads, b->ppt, b->warp_hist}; }
+
 size_t batch_dyn_smem(const pm_batch *b)
 {
+    if (b->warp_hist) return 0;
     const int r = batch_radius_cap(b->window_kib, b->threads);
     const size_t cells = (size_t)(2 * r + 1) * (2 * r + 1);
     const size_t stride_words = (((cells + 1) / 2) + 3) & ~(size_t)3;
@@ -508,7 +512,7 @@ pm_status batch_upload(pm_batch *b, cudaStream_t stream)
     const double s = (double)b->shared.speed * (double)b->shared.dt;
     std::vector<int2> items;
     for (int h = 0; h < n; ++h)
-        for (int p0 = 0; p0 < b->humans[h].n_particles; p0 += b->threads) items.push_back(make_int2(h, p0));
+        for (int p0 = 0; p0 < b->humans[h].n_particles; p0 += b->threads * b->ppt) items.push_back(make_int2(h, p0));
     std::stable_sort(items.begin(), items.end(), [&](const int2 &x, const int2 &y) {
         return b->humans[x.x].horizon > b->humans[y.x].horizon;
     });
@@ -601,7 +605,7 @@ pm_status batch_upload(pm_batch *b, cudaStream_t stream)
     pm::RolloutArgs t;
     std::memset(&t, 0, sizeof t);
     fill_rollout_tables(&b->shared, t);
-    b->occ = pm::batch_rollout_occupancy(b->shared.K, t.enabled, b->threads, batch_dyn_smem(b));
+    b->occ = pm::batch_rollout_occupancy(b->shared.K, t.enabled, batch_shape_of(b), batch_dyn_smem(b));
     cudaGetLastError();
     return PM_OK;
 }
@@ -630,9 +634,11 @@ pm_status batch_predict_impl(pm_batch *b, cudaStream_t stream)
     a.win_radius_cap = batch_radius_cap(b->window_kib, b->threads);
     const size_t dyn = batch_dyn_smem(b);
     int occ = b->occ;
-    if (occ < 1) return fail(PM_EINVAL, "launch shape (%d threads, %d KiB window) does not fit an SM", b->threads, b->window_kib);
+    if (occ < 1)
+        return fail(PM_EINVAL, "launch shape (%d threads, %d particles each, %s) does not fit an SM", b->threads, b->ppt,
+                    b->warp_hist ? "warp emplacement" : "shared window");
     if (b->ctas_per_sm > 0) occ = std::min(occ, b->ctas_per_sm);
-    e = pm::launch_batch_rollout(a, ctx->sm_count * occ, b->threads, dyn, stream);
+    e = pm::launch_batch_rollout(a, batch_shape_of(b), ctx->sm_count * occ, dyn, stream);
     if (e != cudaSuccess) return cuda_fail(e, "batch rollout launch");
     return PM_OK;
 }
@@ -914,31 +920,42 @@ pm_status pm_batch_predict(pm_batch *b, void *stream)
     return batch_predict_impl(b, (cudaStream_t)stream);
 }
 
-pm_status pm_batch_get_config(const pm_batch *b, int32_t *threads, int32_t *ctas_per_sm, int32_t *window_kib)
+pm_status pm_batch_get_config(const pm_batch *b, int32_t *threads, int32_t *particles_per_thread,
+                              int32_t *shared_window, int32_t *ctas_per_sm, int32_t *window_kib)
 {
     if (!b) return fail(PM_EINVAL, "batch is NULL");
     if (threads) *threads = b->threads;
+    if (particles_per_thread) *particles_per_thread = b->ppt;
+    if (shared_window) *shared_window = b->warp_hist ? 0 : 1;
     if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
     if (window_kib) *window_kib = b->window_kib;
     return PM_OK;
 }
 
-pm_status pm_batch_set_config(pm_batch *b, int32_t threads, int32_t ctas_per_sm, int32_t window_kib)
+pm_status pm_batch_set_config(pm_batch *b, int32_t threads, int32_t particles_per_thread, int32_t shared_window,
+                              int32_t ctas_per_sm, int32_t window_kib)
 {
     if (!b) return fail(PM_EINVAL, "batch is NULL");
+    if (particles_per_thread != 1 && particles_per_thread != 2)
+        return fail(PM_EINVAL, "particles_per_thread=%d must be 1 or 2", particles_per_thread);
+    if (shared_window != 0 && shared_window != 1) return fail(PM_EINVAL, "shared_window must be 0 or 1");
+    if (shared_window && particles_per_thread != 1)
+        return fail(PM_EINVAL, "the shared-window emplacement runs one particle per thread");
     if (threads < 32 || threads > 256 || threads % 32) return fail(PM_EINVAL, "threads=%d must be 32..256, multiple of 32", threads);
     if (ctas_per_sm < 0 || ctas_per_sm > 32) return fail(PM_EINVAL, "ctas_per_sm=%d out of range", ctas_per_sm);
     if (window_kib < 1 || window_kib > 200) return fail(PM_EINVAL, "window_kib=%d out of range", window_kib);
     DeviceScope dev(b->ctx->device);
-    const bool retile = threads != b->threads;
+    const bool retile = threads != b->threads || particles_per_thread != b->ppt;
     b->threads = threads;
+    b->ppt = particles_per_thread;
+    b->warp_hist = shared_window == 0;
     b->ctas_per_sm = ctas_per_sm;
     b->window_kib = window_kib;
     if (retile && !b->humans.empty()) return batch_upload(b, nullptr);
     pm::RolloutArgs t;
     std::memset(&t, 0, sizeof t);
     fill_rollout_tables(&b->shared, t);
-    b->occ = pm::batch_rollout_occupancy(b->shared.K, t.enabled, b->threads, batch_dyn_smem(b));
+    b->occ = pm::batch_rollout_occupancy(b->shared.K, t.enabled, batch_shape_of(b), batch_dyn_smem(b));
     cudaGetLastError();
     return PM_OK;
 }
@@ -949,46 +966,53 @@ pm_status pm_batch_autotune(pm_batch *b, void *stream)
     if (b->humans.empty()) return PM_OK;
     DeviceScope dev(b->ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
-    static const int cand_threads[] = {128, 192, 224, 256};
-    static const int cand_window[] = {24, 48, 96};
+    struct Cand {
+        int threads, ppt;
+        bool warp;
+        int window;
+    };
+    static const Cand cands[] = {{128, 1, true, 48}, {192, 1, true, 48}, {224, 1, true, 48}, {256, 1, true, 48},
+                                 {128, 2, true, 48}, {256, 2, true, 48}, {224, 1, false, 48}, {256, 1, false, 48},
+                                 {256, 1, false, 96}};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bt = b->threads, bw = b->window_kib;
-    for (int t : cand_threads) {
-        for (int w : cand_window) {
-            b->threads = t;
-            b->window_kib = w;
-            b->ctas_per_sm = 0;
-            if (batch_upload(b, s) != PM_OK) continue;
-            if (batch_predict_impl(b, s) != PM_OK) { // warm-up; a shape that does not fit is skipped
-                cudaGetLastError();
-                continue;
-            }
-            float total = 0.0f;
-            bool ok = true;
-            for (int rep = 0; rep < 3 && ok; ++rep) {
-                cudaEventRecord(e0, s);
-                ok = batch_predict_impl(b, s) == PM_OK;
-                cudaEventRecord(e1, s);
-                float ms = 0.0f;
-                if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
-                    total += ms;
-                else
-                    ok = false;
-            }
-            if (ok && total < best) {
-                best = total;
-                bt = t;
-                bw = w;
-            }
+    Cand bc{b->threads, b->ppt, b->warp_hist, b->window_kib};
+    for (const Cand &cd : cands) {
+        b->threads = cd.threads;
+        b->ppt = cd.ppt;
+        b->warp_hist = cd.warp;
+        b->window_kib = cd.window;
+        b->ctas_per_sm = 0;
+        if (batch_upload(b, s) != PM_OK) continue;
+        if (batch_predict_impl(b, s) != PM_OK) { // warm-up; a shape that does not fit is skipped
+            cudaGetLastError();
+            continue;
+        }
+        float total = 0.0f;
+        bool ok = true;
+        for (int rep = 0; rep < 3 && ok; ++rep) {
+            cudaEventRecord(e0, s);
+            ok = batch_predict_impl(b, s) == PM_OK;
+            cudaEventRecord(e1, s);
+            float ms = 0.0f;
+            if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+                total += ms;
+            else
+                ok = false;
+        }
+        if (ok && total < best) {
+            best = total;
+            bc = cd;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->threads = bt;
-    b->window_kib = bw;
+    b->threads = bc.threads;
+    b->ppt = bc.ppt;
+    b->warp_hist = bc.warp;
+    b->window_kib = bc.window;
     b->ctas_per_sm = 0;
     pm_status st = batch_upload(b, s);
     if (st != PM_OK) return st;

@@ -22,8 +22,15 @@ namespace {
 
 constexpr int kBatchMaxThreads = 256;
 
-template <int KT, bool FULL>
-__global__ void __launch_bounds__(kBatchMaxThreads) batch_rollout_kernel(const __grid_constant__ BatchArgs a)
+template <int PPT, bool WARP_HIST>
+constexpr int batch_min_blocks()
+{
+    return WARP_HIST ? (PPT == 1 ? 3 : 2) : 3;
+}
+
+template <int KT, bool FULL, int PPT, bool WARP_HIST>
+__global__ void __launch_bounds__(kBatchMaxThreads, (batch_min_blocks<PPT, WARP_HIST>()))
+    batch_rollout_kernel(const __grid_constant__ BatchArgs a)
 {
     __shared__ RolloutShared sh;
     __shared__ int s_item;
@@ -79,16 +86,18 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_rollout_kernel(const _
         if (tid < 3) sh.list_n[tid] = 0u;
         if (tid < 2) sh.oob_n[tid] = 0u;
         __syncthreads();
-        const int words = 2 * window_stride_words(s_geom[4], s_geom[5]);
-        for (int w = tid; w < words; w += nthr) dyn[w] = 0u;
+        if (!WARP_HIST) {
+            const int words = 2 * window_stride_words(s_geom[4], s_geom[5]);
+            for (int w = tid; w < words; w += nthr) dyn[w] = 0u;
+        }
         __syncthreads();
         TileCtx c;
         c.z0x = s_z0[0];
         c.z0y = s_z0[1];
         c.T = h->T;
         c.i = (int64_t)item.y + tid;
-        c.active = c.i < h->N;
-        c.traced = false;
+        c.N = h->N;
+        c.n_trace = 0;
         c.seed = h->seed;
         c.human = h->human;
         c.J = J;
@@ -109,7 +118,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_rollout_kernel(const _
         c.tr_states = nullptr;
         c.tr_head = nullptr;
         c.tr_comp = nullptr;
-        rollout_tile<KT, FULL>(a.tab, a.enabled, a.s2, c, sh, dyn);
+        rollout_tile<KT, FULL, PPT, WARP_HIST>(a.tab, a.enabled, a.s2, c, sh, dyn);
     }
 }
 
@@ -136,54 +145,61 @@ __global__ void batch_zero_kernel(const BatchHuman *humans, const int *n_dev)
     }
 }
 
-template <int KT>
-int batch_occupancy_kt(bool full, int threads, size_t dyn)
+template <int KT, bool FULL, int PPT, bool WH>
+cudaError_t batch_one(const BatchArgs &a, int blocks, int threads, size_t dyn, cudaStream_t s, int *occ)
 {
-    int n = 0;
-    if (full) {
-        cudaFuncSetAttribute(batch_rollout_kernel<KT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_rollout_kernel<KT, true>, threads, dyn);
-    } else {
-        cudaFuncSetAttribute(batch_rollout_kernel<KT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_rollout_kernel<KT, false>, threads, dyn);
+    auto k = batch_rollout_kernel<KT, FULL, PPT, WH>;
+    if (dyn > 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
     }
-    return n;
-}
-
-template <int KT>
-cudaError_t batch_launch_kt(const BatchArgs &a, bool full, int blocks, int threads, size_t dyn, cudaStream_t s)
-{
-    if (full) batch_rollout_kernel<KT, true><<<blocks, threads, dyn, s>>>(a);
-    else batch_rollout_kernel<KT, false><<<blocks, threads, dyn, s>>>(a);
+    if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, threads, dyn);
+    cudaGetLastError();
+    k<<<blocks, threads, dyn, s>>>(a);
     return cudaGetLastError();
 }
 
-} // namespace
-
-int batch_rollout_occupancy(int K, uint64_t enabled, int threads, size_t dyn)
+template <int KT, bool FULL>
+cudaError_t batch_shape(const BatchArgs &a, const RolloutShape &sh, int blocks, size_t dyn, cudaStream_t s, int *occ)
 {
-    const int KT = rollout_kt_for(K);
-    const uint64_t all = (KT >= 64) ? ~0ull : ((1ull << KT) - 1ull);
-    const bool full = (K == KT) && ((enabled & all) == all);
-    switch (KT) {
-    case 8: return batch_occupancy_kt<8>(full, threads, dyn);
-    case 16: return batch_occupancy_kt<16>(full, threads, dyn);
-    case 36: return batch_occupancy_kt<36>(full, threads, dyn);
-    default: return batch_occupancy_kt<64>(full, threads, dyn);
+    if (sh.warp_hist) {
+        if (sh.ppt == 2) return batch_one<KT, FULL, 2, true>(a, blocks, sh.threads, dyn, s, occ);
+        return batch_one<KT, FULL, 1, true>(a, blocks, sh.threads, dyn, s, occ);
     }
+    return batch_one<KT, FULL, 1, false>(a, blocks, sh.threads, dyn, s, occ);
 }
 
-cudaError_t launch_batch_rollout(const BatchArgs &a, int blocks, int threads, size_t dyn, cudaStream_t s)
+cudaError_t batch_dispatch(const BatchArgs &a, const RolloutShape &sh, int blocks, size_t dyn, cudaStream_t s, int *occ)
 {
     const int KT = rollout_kt_for(a.K);
     const uint64_t all = (KT >= 64) ? ~0ull : ((1ull << KT) - 1ull);
     const bool full = (a.K == KT) && ((a.enabled & all) == all);
     switch (KT) {
-    case 8: return batch_launch_kt<8>(a, full, blocks, threads, dyn, s);
-    case 16: return batch_launch_kt<16>(a, full, blocks, threads, dyn, s);
-    case 36: return batch_launch_kt<36>(a, full, blocks, threads, dyn, s);
-    default: return batch_launch_kt<64>(a, full, blocks, threads, dyn, s);
+    case 8: return full ? batch_shape<8, true>(a, sh, blocks, dyn, s, occ) : batch_shape<8, false>(a, sh, blocks, dyn, s, occ);
+    case 16: return full ? batch_shape<16, true>(a, sh, blocks, dyn, s, occ) : batch_shape<16, false>(a, sh, blocks, dyn, s, occ);
+    case 36: return full ? batch_shape<36, true>(a, sh, blocks, dyn, s, occ) : batch_shape<36, false>(a, sh, blocks, dyn, s, occ);
+    default: return full ? batch_shape<64, true>(a, sh, blocks, dyn, s, occ) : batch_shape<64, false>(a, sh, blocks, dyn, s, occ);
     }
+}
+
+} // namespace
+
+int batch_rollout_occupancy(int K, uint64_t enabled, const RolloutShape &shape, size_t dyn)
+{
+    BatchArgs a;
+    a.K = K;
+    a.enabled = enabled;
+    int n = 0;
+    if (batch_dispatch(a, shape, 0, dyn, nullptr, &n) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+cudaError_t launch_batch_rollout(const BatchArgs &a, const RolloutShape &shape, int blocks, size_t dyn, cudaStream_t s)
+{
+    return batch_dispatch(a, shape, blocks, dyn, s, nullptr);
 }
 
 cudaError_t launch_batch_zero(const BatchHuman *humans, const int *n_dev, int max_rows, int sm_count, cudaStream_t s)

@@ -233,10 +233,19 @@ struct BatchArgs {
     int win_radius_cap;  // (2r+1)^2 cells fit the dynamic shared memory
 };
 
+// Launch shape of the rollout: threads per CTA, particles per thread (1 or
+// 2) and the emplacement mode (warp-combined global reductions, or the
+// shared-memory window).
+struct RolloutShape {
+    int threads;
+    int ppt;
+    bool warp_hist;
+};
+
 // Launch wrappers (defined next to their kernels).
-cudaError_t launch_rollout(const RolloutArgs &a, int threads, size_t dyn_smem, cudaStream_t s);
+cudaError_t launch_rollout(const RolloutArgs &a, const RolloutShape &shape, size_t dyn_smem, cudaStream_t s);
 size_t rollout_static_smem_estimate();
-int rollout_occupancy(const RolloutArgs &a, int threads, size_t dyn_smem); // resident CTAs per SM
+int rollout_occupancy(const RolloutArgs &a, const RolloutShape &shape, size_t dyn_smem); // resident CTAs per SM
 cudaError_t launch_posterior(const PosteriorArgs &a, int n_chunks, cudaStream_t s);
 int posterior_chunks(int n_obs, int *steps_per_chunk);
 cudaError_t launch_posterior_batch(const PosteriorArgs &a, const PostHuman *humans, const int *n_humans,
@@ -249,8 +258,8 @@ cudaError_t launch_sfu_probe(int op, int blocks, int threads, int iters, float *
                              cudaStream_t s);
 int rollout_kt_for(int K); // template bucket for K (8, 16, 36 or 64)
 cudaError_t launch_adjoint(const AdjointArgs &a, cudaStream_t s);
-int batch_rollout_occupancy(int K, uint64_t enabled, int threads, size_t dyn);
-cudaError_t launch_batch_rollout(const BatchArgs &a, int blocks, int threads, size_t dyn, cudaStream_t s);
+int batch_rollout_occupancy(int K, uint64_t enabled, const RolloutShape &shape, size_t dyn);
+cudaError_t launch_batch_rollout(const BatchArgs &a, const RolloutShape &shape, int blocks, size_t dyn, cudaStream_t s);
 cudaError_t launch_batch_zero(const BatchHuman *humans, const int *n_dev, int max_rows, int sm_count, cudaStream_t s);
 size_t adjoint_scratch_bytes(int M, int G);
 

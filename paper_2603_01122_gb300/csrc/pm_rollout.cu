@@ -28,8 +28,17 @@ namespace {
 
 constexpr int kRolloutThreads = 256;
 
-template <int KT, bool FULL>
-__global__ void __launch_bounds__(kRolloutThreads) rollout_kernel(const __grid_constant__ RolloutArgs a)
+// Resident CTAs per SM the compiler is asked to fit: the warp-histogram forms
+// use almost no shared memory, so registers decide their occupancy.
+template <int PPT, bool WARP_HIST>
+constexpr int rollout_min_blocks()
+{
+    return WARP_HIST ? (PPT == 1 ? 3 : 2) : 3;
+}
+
+template <int KT, bool FULL, int PPT, bool WARP_HIST>
+__global__ void __launch_bounds__(kRolloutThreads, (rollout_min_blocks<PPT, WARP_HIST>()))
+    rollout_kernel(const __grid_constant__ RolloutArgs a)
 {
     __shared__ RolloutShared sh;
     extern __shared__ __align__(16) uint32_t dyn[];
@@ -38,15 +47,16 @@ __global__ void __launch_bounds__(kRolloutThreads) rollout_kernel(const __grid_c
     const int J = a.G * a.B;
     const bool hist = a.counts != nullptr;
     const int ww = a.win_side & 0xFFFF, wh = a.win_side >> 16; // window width/height (cells)
-    const int win_words = 2 * window_stride_words(ww, wh);     // both windows
 
     for (int j = tid; j < J; j += nthr) {
         const int g = j / a.B, b = j - g * a.B;
         sh.comp[j] = make_float4(a.beta[b] * a.w2_log2e, a.goals[2 * g], a.goals[2 * g + 1], 0.0f);
     }
     for (int k = tid; k < KT; k += nthr) sh.step[k] = make_float2(a.tab.sx[k], a.tab.sy[k]);
-    if (hist)
+    if (hist && !WARP_HIST) {
+        const int win_words = 2 * window_stride_words(ww, wh); // both windows
         for (int w = tid; w < win_words; w += nthr) dyn[w] = 0u;
+    }
     if (tid < 3) sh.list_n[tid] = 0u;
     if (tid < 2) sh.oob_n[tid] = 0u;
     if (tid < 32) belief_cdf(a.log_b, J, sh.cdf, tid);
@@ -56,9 +66,9 @@ __global__ void __launch_bounds__(kRolloutThreads) rollout_kernel(const __grid_c
     c.z0x = a.z0x;
     c.z0y = a.z0y;
     c.T = a.T;
-    c.i = (int64_t)blockIdx.x * nthr + tid;
-    c.active = c.i < a.N;
-    c.traced = c.i < a.n_trace;
+    c.i = (int64_t)blockIdx.x * nthr * PPT + tid;
+    c.N = a.N;
+    c.n_trace = a.n_trace;
     c.seed = a.seed;
     c.human = a.human;
     c.J = J;
@@ -79,42 +89,51 @@ __global__ void __launch_bounds__(kRolloutThreads) rollout_kernel(const __grid_c
     c.tr_states = a.tr_states;
     c.tr_head = a.tr_head;
     c.tr_comp = a.tr_comp;
-    rollout_tile<KT, FULL>(a.tab, a.enabled, a.s2, c, sh, dyn);
+    rollout_tile<KT, FULL, PPT, WARP_HIST>(a.tab, a.enabled, a.s2, c, sh, dyn);
 }
 
-template <int KT>
-int occupancy_kt(bool full, int threads, size_t dyn_smem)
+template <int KT, bool FULL, int PPT, bool WH>
+cudaError_t launch_one(const RolloutArgs &a, int threads, size_t dyn_smem, cudaStream_t s, int *occ)
 {
-    int n = 0;
-    if (full) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_kernel<KT, true>, threads, dyn_smem);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_kernel<KT, false>, threads, dyn_smem);
-    return n;
+    auto k = rollout_kernel<KT, FULL, PPT, WH>;
+    if (dyn_smem > 0) { // static + dynamic may pass the 48 KiB default
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, threads, dyn_smem);
+    const unsigned blocks = (unsigned)((a.N + (int64_t)threads * PPT - 1) / ((int64_t)threads * PPT));
+    cudaGetLastError(); // clear errors of earlier calls whose failure was handled
+    k<<<blocks, threads, dyn_smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int KT, bool FULL>
+cudaError_t launch_shape(const RolloutArgs &a, const RolloutShape &sh, size_t dyn, cudaStream_t s, int *occ)
+{
+    if (sh.warp_hist) {
+        if (sh.ppt == 2) return launch_one<KT, FULL, 2, true>(a, sh.threads, dyn, s, occ);
+        return launch_one<KT, FULL, 1, true>(a, sh.threads, dyn, s, occ);
+    }
+    return launch_one<KT, FULL, 1, false>(a, sh.threads, dyn, s, occ);
 }
 
 template <int KT>
-cudaError_t launch_kt(const RolloutArgs &a, int threads, size_t dyn_smem, cudaStream_t s)
+cudaError_t launch_kt(const RolloutArgs &a, const RolloutShape &sh, size_t dyn, cudaStream_t s, int *occ)
 {
     const uint64_t all = (KT >= 64) ? ~0ull : ((1ull << KT) - 1ull);
     const bool full = (a.K == KT) && ((a.enabled & all) == all);
-    const unsigned blocks = (unsigned)((a.N + threads - 1) / threads);
-    cudaGetLastError(); // clear errors of earlier calls whose failure was handled
-    if (full) {
-        auto k = rollout_kernel<KT, true>;
-        if (dyn_smem > 0) { // static + dynamic may pass the 48 KiB default
+    if (full) return launch_shape<KT, true>(a, sh, dyn, s, occ);
+    return launch_shape<KT, false>(a, sh, dyn, s, occ);
+}
 
-            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
-            if (e != cudaSuccess) return e;
-        }
-        k<<<blocks, threads, dyn_smem, s>>>(a);
-    } else {
-        auto k = rollout_kernel<KT, false>;
-        if (dyn_smem > 0) {
-            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
-            if (e != cudaSuccess) return e;
-        }
-        k<<<blocks, threads, dyn_smem, s>>>(a);
+cudaError_t dispatch(const RolloutArgs &a, const RolloutShape &sh, size_t dyn, cudaStream_t s, int *occ)
+{
+    switch (rollout_kt_for(a.K)) {
+    case 8: return launch_kt<8>(a, sh, dyn, s, occ);
+    case 16: return launch_kt<16>(a, sh, dyn, s, occ);
+    case 36: return launch_kt<36>(a, sh, dyn, s, occ);
+    default: return launch_kt<64>(a, sh, dyn, s, occ);
     }
-    return cudaGetLastError();
 }
 
 } // namespace
@@ -129,38 +148,19 @@ int rollout_kt_for(int K)
 
 size_t rollout_static_smem_estimate() { return sizeof(RolloutShared); }
 
-int rollout_occupancy(const RolloutArgs &a, int threads, size_t dyn_smem)
+int rollout_occupancy(const RolloutArgs &a, const RolloutShape &shape, size_t dyn_smem)
 {
-    const int KT = rollout_kt_for(a.K);
-    const uint64_t all = (KT >= 64) ? ~0ull : ((1ull << KT) - 1ull);
-    const bool full = (a.K == KT) && ((a.enabled & all) == all);
-    if (dyn_smem > 0) {
-        // static + dynamic may pass the 48 KiB default: raise the limit before
-        // the occupancy query counts it
-        switch (KT) {
-        case 8: cudaFuncSetAttribute(full ? rollout_kernel<8, true> : rollout_kernel<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem); break;
-        case 16: cudaFuncSetAttribute(full ? rollout_kernel<16, true> : rollout_kernel<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem); break;
-        case 36: cudaFuncSetAttribute(full ? rollout_kernel<36, true> : rollout_kernel<36, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem); break;
-        default: cudaFuncSetAttribute(full ? rollout_kernel<64, true> : rollout_kernel<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem); break;
-        }
+    int n = 0;
+    if (dispatch(a, shape, dyn_smem, nullptr, &n) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
     }
-    switch (KT) {
-    case 8: return occupancy_kt<8>(full, threads, dyn_smem);
-    case 16: return occupancy_kt<16>(full, threads, dyn_smem);
-    case 36: return occupancy_kt<36>(full, threads, dyn_smem);
-    default: return occupancy_kt<64>(full, threads, dyn_smem);
-    }
+    return n;
 }
 
-cudaError_t launch_rollout(const RolloutArgs &a, int threads, size_t dyn_smem, cudaStream_t s)
+cudaError_t launch_rollout(const RolloutArgs &a, const RolloutShape &shape, size_t dyn_smem, cudaStream_t s)
 {
-    if (threads <= 0) threads = kRolloutThreads;
-    switch (rollout_kt_for(a.K)) {
-    case 8: return launch_kt<8>(a, threads, dyn_smem, s);
-    case 16: return launch_kt<16>(a, threads, dyn_smem, s);
-    case 36: return launch_kt<36>(a, threads, dyn_smem, s);
-    default: return launch_kt<64>(a, threads, dyn_smem, s);
-    }
+    return dispatch(a, shape, dyn_smem, s, nullptr);
 }
 
 } // namespace pm

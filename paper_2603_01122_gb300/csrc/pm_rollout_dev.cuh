@@ -76,27 +76,30 @@ __device__ __forceinline__ int draw_heading(const HeadingTab &tab, uint64_t enab
         const f32x2 *TY = reinterpret_cast<const f32x2 *>(tab.ty);
         f32x2 dv[KT / 2];
         f32x2 DREF = 0ull;
-        float dmin = INFINITY;
+        float dmin[4] = {INFINITY, INFINITY, INFINITY, INFINITY}; // independent partial minima
 #pragma unroll
         for (int q = 0; q < KT / 2; ++q) {
             const f32x2 P = f2_fma(TX[q], DX, f2_mul(TY[q], DY)); // 2 s e_k.(z - g), k = 2q, 2q+1
             float x0, x1;
             f2_unpack(f2_add(DD, P), x0, x1);
-            const float d0 = sqrt_approx(fmaxf(x0, 0.0f)), d1 = sqrt_approx(fmaxf(x1, 0.0f));
+            // |x| only differs from max(x, 0) when rounding made a (near-zero) square negative
+            const float d0 = sqrt_approx(fabsf(x0)), d1 = sqrt_approx(fabsf(x1));
             const f32x2 DK = f2_pack(d0, d1);
             if (q == 0) DREF = f2_pack(d0, d0);
             const f32x2 R = f2_sub(P, f2_fma(DK, DK, NDD));       // D + p - dk^2
             dv[q] = f2_fma(R, HD, f2_sub(DK, DREF));                // d_k - d_0, corrected
             float v0, v1;
             f2_unpack(dv[q], v0, v1);
-            dmin = fminf(dmin, fminf(v0, v1));
+            dmin[q & 3] = fminf(dmin[q & 3], fminf(v0, v1));
         }
+        const float dm = fminf(fminf(dmin[0], dmin[1]), fminf(dmin[2], dmin[3]));
         const f32x2 NC = f2_pack(-cb, -cb);
-        const float base = dmin * cb;
+        const float base = dm * cb;
         const f32x2 BASE = f2_pack(base, base);
         const f32x2 SC = f2_pack(4194304.0f, 4194304.0f), MG = f2_pack(12582912.0f, 12582912.0f);
+        constexpr int H2 = KT / 2; // the running sums restart at the half: two independent chains
         uint32_t bits[KT];
-        uint32_t S = 0u;
+        uint32_t S0 = 0u, S1 = 0u;
 #pragma unroll
         for (int q = 0; q < KT / 2; ++q) {
             float a0, a1;
@@ -105,18 +108,24 @@ __device__ __forceinline__ int draw_heading(const HeadingTab &tab, uint64_t enab
             f2_unpack(f2_fma(f2_pack(ex2_approx(a0), ex2_approx(a1)), SC, MG), w0, w1);
             bits[2 * q] = __float_as_uint(w0);                      // 0x4B400000 + round(e * 2^22)
             bits[2 * q + 1] = __float_as_uint(w1);
-            S += bits[2 * q] + bits[2 * q + 1];
+            if (2 * q < H2) S0 += bits[2 * q]; else S1 += bits[2 * q];
+            if (2 * q + 1 < H2) S0 += bits[2 * q + 1]; else S1 += bits[2 * q + 1];
         }
-        S -= (uint32_t)KT * 0x4B400000u;                            // total weight (exact integer)
+        S0 -= (uint32_t)H2 * 0x4B400000u;                           // weight of headings [0, K/2)
+        S1 -= (uint32_t)(KT - H2) * 0x4B400000u;                    // weight of headings [K/2, K)
+        const uint32_t S = S0 + S1;                                 // total weight (exact integer)
         const uint32_t thr = (uint32_t)(((uint64_t)(word >> 8) * (uint64_t)S) >> 24);
-        uint32_t acc = ~thr; // C_k - thr - 1 once E_k is added: negative iff C_k <= thr
-        int sel = 0;
+        // C_k - thr - 1 once E_k is added: negative iff C_k <= thr
+        uint32_t acc0 = ~thr, acc1 = ~thr + S0;
+        int sel0 = 0, sel1 = 0;
 #pragma unroll
-        for (int k = 0; k < KT; ++k) {
-            acc += bits[k] - 0x4B400000u;
-            sel += (int)(acc >> 31);
+        for (int k = 0; k < H2; ++k) {
+            acc0 += bits[k] - 0x4B400000u;
+            sel0 += (int)(acc0 >> 31);
+            acc1 += bits[H2 + k] - 0x4B400000u;
+            sel1 += (int)(acc1 >> 31);
         }
-        return sel;
+        return sel0 + sel1;
     } else {
         float dv[KT];
         float dref = 0.0f;
@@ -156,9 +165,9 @@ __device__ __forceinline__ int draw_heading(const HeadingTab &tab, uint64_t enab
 struct TileCtx {
     float z0x, z0y;
     int T;
-    int64_t i;      // this thread's particle index (within its human)
-    bool active;    // i < particles of the human
-    bool traced;    // record the trajectory of this particle
+    int64_t i;       // the first particle of this thread (the others follow at +blockDim)
+    int64_t N;       // particles of the human: indices >= N are idle
+    int64_t n_trace; // particles below this index record their trajectory
     uint64_t seed;
     uint32_t human;
     int J;
@@ -168,7 +177,7 @@ struct TileCtx {
     int cx_off, cy_off;      // output cell = grid cell - offset
     uint32_t *counts;
     uint32_t *oob;
-    int win_x0, win_y0, ww, wh; // shared-memory window, output cells
+    int win_x0, win_y0, ww, wh; // shared-memory window, output cells (window mode)
     float *tr_states;
     uint8_t *tr_head;
     int32_t *tr_comp;
@@ -180,18 +189,24 @@ __device__ __host__ __forceinline__ int window_stride_words(int ww, int wh)
     return (((ww * wh + 1) >> 1) + 3) & ~3;
 }
 
-// Algorithm 1 for one particle per thread of the CTA: the (beta, g) draw from
-// the belief table in shared memory, then T heading draws and Euler steps,
-// each step emplaced in the CTA's shared-memory window (first touch appends
-// the cell to the step's list; after one block barrier the list is flushed
-// with one global reduction per touched cell) or, outside the window,
-// directly in global memory. Two windows and two lists alternate by step
-// parity and three list counters rotate, so the flush of step t overlaps the
-// inserts of step t+1 and one barrier per step suffices. `sh` must hold the
-// component table and belief CDF of the human; both windows, list_n[0..2]
-// and oob_n[0..1] must be zero on entry; the windows are zero again on exit.
-// dyn layout: window 0 | window 1 (window_stride_words each) | list 0 | list 1.
-template <int KT, bool FULL>
+// Algorithm 1 for PPT particles per thread of the CTA (particles i, i+blockDim,
+// ...; independent chains the scheduler interleaves): the (beta, g) draw from
+// the belief table in shared memory, then T heading draws and Euler steps.
+//
+// Emplacement, two modes:
+//  - WARP_HIST: the lanes of a warp that fall in the same cell at step t are
+//    combined (match.any) and their leader adds the count to global memory
+//    with one reduction; no shared window, no block barrier.
+//  - window: each step is counted in the CTA's shared-memory window (first
+//    touch appends the cell to the step's list; after one block barrier the
+//    list is flushed with one global reduction per touched cell); cells
+//    outside the window go straight to global memory. Two windows and two
+//    lists alternate by step parity and three list counters rotate, so the
+//    flush of step t overlaps the inserts of step t+1. `sh` must hold the
+//    human's tables; both windows, list_n[0..2] and oob_n[0..1] must be zero
+//    on entry; the windows are zero again on exit. dyn layout: window 0 |
+//    window 1 (window_stride_words each) | list 0 | list 1 (PPT*blockDim each).
+template <int KT, bool FULL, int PPT, bool WARP_HIST>
 __device__ __forceinline__ void rollout_tile(const HeadingTab &tab, uint64_t enabled, float s2,
                                              const TileCtx &c, RolloutShared &sh, uint32_t *dyn)
 {
@@ -200,68 +215,103 @@ __device__ __forceinline__ void rollout_tile(const HeadingTab &tab, uint64_t ena
     const int ww = c.ww, wh = c.wh;
     const int stride = window_stride_words(ww, wh);
     uint16_t *list0 = reinterpret_cast<uint16_t *>(dyn + 2 * stride);
+    const int list_cap = PPT * nthr;
 
-    float x = c.z0x, y = c.z0y, cb = 0.0f, gx = 0.0f, gy = 0.0f;
-    const uint64_t i = (uint64_t)c.i;
-    if (c.active) {
-        const U64x4 r = philox4x64_10(U64x4{i, 0ull, kPurposeSelect, 0ull}, c.seed, c.human);
-        const uint32_t thr = (uint32_t)(((uint64_t)((uint32_t)r.a >> 8) * (uint64_t)sh.cdf[c.J - 1]) >> 24);
-        int lo = 0, hi = c.J - 1; // smallest j with cdf[j] > thr
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (sh.cdf[mid] > thr) hi = mid;
-            else lo = mid + 1;
+    float x[PPT], y[PPT], cb[PPT], gx[PPT], gy[PPT];
+    uint64_t ip[PPT];
+    bool act[PPT], trc[PPT];
+    uint32_t q[PPT][8];
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        ip[p] = (uint64_t)c.i + (uint64_t)p * nthr;
+        act[p] = (int64_t)ip[p] < c.N;
+        trc[p] = (int64_t)ip[p] < c.n_trace;
+        x[p] = c.z0x;
+        y[p] = c.z0y;
+        cb[p] = gx[p] = gy[p] = 0.0f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) q[p][w] = 0u;
+        if (act[p]) {
+            const U64x4 r = philox4x64_10(U64x4{ip[p], 0ull, kPurposeSelect, 0ull}, c.seed, c.human);
+            const uint32_t thr = (uint32_t)(((uint64_t)((uint32_t)r.a >> 8) * (uint64_t)sh.cdf[c.J - 1]) >> 24);
+            int lo = 0, hi = c.J - 1; // smallest j with cdf[j] > thr
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (sh.cdf[mid] > thr) hi = mid;
+                else lo = mid + 1;
+            }
+            const float4 cc = sh.comp[lo];
+            cb[p] = cc.x;
+            gx[p] = cc.y;
+            gy[p] = cc.z;
+            if (trc[p] && c.tr_comp) c.tr_comp[ip[p]] = lo;
         }
-        const float4 cc = sh.comp[lo];
-        cb = cc.x;
-        gx = cc.y;
-        gy = cc.z;
-        if (c.traced && c.tr_comp) c.tr_comp[i] = lo;
     }
 
     const size_t plane = (size_t)c.W * (size_t)c.H;
-    uint32_t q0 = 0, q1 = 0, q2 = 0, q3 = 0, q4 = 0, q5 = 0, q6 = 0, q7 = 0;
-    int li = 1; // t mod 3: the list counter of step t
+    int li = 1; // t mod 3: the list counter of step t (window mode)
     for (int t = 1; t <= c.T; ++t) {
-        int cx = 0, cy = 0;
-        bool in_grid = false;
-        if (c.active) {
-            if (((t - 1) & 7) == 0) {
-                const U64x4 r = philox4x64_10(U64x4{i, (uint64_t)((t - 1) >> 3), kPurposeStep, 0ull}, c.seed, c.human);
-                q0 = (uint32_t)r.a; q1 = (uint32_t)(r.a >> 32);
-                q2 = (uint32_t)r.b; q3 = (uint32_t)(r.b >> 32);
-                q4 = (uint32_t)r.c; q5 = (uint32_t)(r.c >> 32);
-                q6 = (uint32_t)r.d; q7 = (uint32_t)(r.d >> 32);
-            }
-            const uint32_t word = q0;
-            q0 = q1; q1 = q2; q2 = q3; q3 = q4; q4 = q5; q5 = q6; q6 = q7;
-            const int k = draw_heading<KT, FULL>(tab, enabled, s2, x, y, gx, gy, cb, word);
-            const float2 st = sh.step[k];
-            x = __fadd_rn(x, st.x);
-            y = __fadd_rn(y, st.y);
-            if (c.traced) {
-                const size_t o = (size_t)i * c.T + (t - 1);
-                if (c.tr_states) reinterpret_cast<float2 *>(c.tr_states)[o] = make_float2(x, y);
-                if (c.tr_head) c.tr_head[o] = (uint8_t)k;
-            }
-            if (c.hist) {
-                const float vx = __fmul_rn(__fsub_rn(x, c.gx0), c.inv_res);
-                const float vy = __fmul_rn(__fsub_rn(y, c.gy0), c.inv_res);
-                cx = __float2int_rd(vx) - c.cx_off;
-                cy = __float2int_rd(vy) - c.cy_off;
-                in_grid = (vx == vx) && (vy == vy) && cx >= 0 && cx < c.W && cy >= 0 && cy < c.H;
+        int cx[PPT], cy[PPT];
+        bool ing[PPT];
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            cx[p] = cy[p] = 0;
+            ing[p] = false;
+            if (act[p]) {
+                if (((t - 1) & 7) == 0) {
+                    const U64x4 r = philox4x64_10(U64x4{ip[p], (uint64_t)((t - 1) >> 3), kPurposeStep, 0ull},
+                                                  c.seed, c.human);
+                    q[p][0] = (uint32_t)r.a; q[p][1] = (uint32_t)(r.a >> 32);
+                    q[p][2] = (uint32_t)r.b; q[p][3] = (uint32_t)(r.b >> 32);
+                    q[p][4] = (uint32_t)r.c; q[p][5] = (uint32_t)(r.c >> 32);
+                    q[p][6] = (uint32_t)r.d; q[p][7] = (uint32_t)(r.d >> 32);
+                }
+                const uint32_t word = q[p][0];
+#pragma unroll
+                for (int w = 0; w < 7; ++w) q[p][w] = q[p][w + 1];
+                const int k = draw_heading<KT, FULL>(tab, enabled, s2, x[p], y[p], gx[p], gy[p], cb[p], word);
+                const float2 st = sh.step[k];
+                x[p] = __fadd_rn(x[p], st.x);
+                y[p] = __fadd_rn(y[p], st.y);
+                if (trc[p]) {
+                    const size_t o = (size_t)ip[p] * c.T + (t - 1);
+                    if (c.tr_states) reinterpret_cast<float2 *>(c.tr_states)[o] = make_float2(x[p], y[p]);
+                    if (c.tr_head) c.tr_head[o] = (uint8_t)k;
+                }
+                if (c.hist) {
+                    const float vx = __fmul_rn(__fsub_rn(x[p], c.gx0), c.inv_res);
+                    const float vy = __fmul_rn(__fsub_rn(y[p], c.gy0), c.inv_res);
+                    cx[p] = __float2int_rd(vx) - c.cx_off;
+                    cy[p] = __float2int_rd(vy) - c.cy_off;
+                    ing[p] = (vx == vx) && (vy == vy) && cx[p] >= 0 && cx[p] < c.W && cy[p] >= 0 && cy[p] < c.H;
+                }
             }
         }
         if (c.hist) {
-            const int b = t & 1;
-            uint32_t *win32 = dyn + b * stride;
-            uint16_t *win16 = reinterpret_cast<uint16_t *>(win32);
-            uint16_t *list = list0 + b * nthr;
-            if (c.active) {
-                if (!in_grid) {
-                    atomicAdd(&sh.oob_n[b], 1u);
-                } else {
-                    const int wx = cx - c.win_x0, wy = cy - c.win_y0;
+            if constexpr (WARP_HIST) {
+                const int lane = tid & 31;
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) {
+                    const uint32_t key = !act[p] ? 0xFFFFFFFFu : (ing[p] ? (uint32_t)(cy[p] * c.W + cx[p]) : 0xFFFFFFFEu);
+                    const uint32_t peers = __match_any_sync(0xffffffffu, key);
+                    if (key != 0xFFFFFFFFu && (__ffs(peers) - 1) == lane) {
+                        if (key == 0xFFFFFFFEu) red_add(c.oob + (t - 1), (uint32_t)__popc(peers));
+                        else red_add(c.counts + (size_t)(t - 1) * plane + key, (uint32_t)__popc(peers));
+                    }
+                }
+            } else {
+                const int b = t & 1;
+                uint32_t *win32 = dyn + b * stride;
+                uint16_t *win16 = reinterpret_cast<uint16_t *>(win32);
+                uint16_t *list = list0 + b * list_cap;
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) {
+                    if (!act[p]) continue;
+                    if (!ing[p]) {
+                        atomicAdd(&sh.oob_n[b], 1u);
+                        continue;
+                    }
+                    const int wx = cx[p] - c.win_x0, wy = cy[p] - c.win_y0;
                     if ((unsigned)wx < (unsigned)ww && (unsigned)wy < (unsigned)wh) {
                         const int w = wy * ww + wx;
                         const uint32_t sft = (uint32_t)(w & 1) << 4;
@@ -271,27 +321,27 @@ __device__ __forceinline__ void rollout_tile(const HeadingTab &tab, uint64_t ena
                             list[slot] = (uint16_t)(wx | (wy << 8));
                         }
                     } else {
-                        red_add(c.counts + (size_t)(t - 1) * plane + (size_t)cy * c.W + cx, 1u);
+                        red_add(c.counts + (size_t)(t - 1) * plane + (size_t)cy[p] * c.W + cx[p], 1u);
                     }
                 }
-            }
-            __syncthreads(); // all of step t is in window b; step t-1's flush is done
-            const int lr = (li == 0) ? 2 : li - 1; // counter of step t-1: free from here on
-            if (tid == 0) sh.list_n[lr] = 0u;
-            const uint32_t n = sh.list_n[li];
-            uint32_t *crow = c.counts + (size_t)(t - 1) * plane;
-            for (uint32_t e = tid; e < n; e += nthr) {
-                const uint32_t pk = list[e];
-                const int wx = (int)(pk & 0xFFu), wy = (int)(pk >> 8);
-                const int w = wy * ww + wx;
-                const uint32_t v = win16[w];
-                win16[w] = 0;
-                red_add(crow + (size_t)(c.win_y0 + wy) * c.W + (c.win_x0 + wx), v);
-            }
-            if (tid == 0) {
-                const uint32_t o = sh.oob_n[b];
-                if (o) red_add(c.oob + (t - 1), o);
-                sh.oob_n[b] = 0u;
+                __syncthreads(); // all of step t is in window b; step t-1's flush is done
+                const int lr = (li == 0) ? 2 : li - 1; // counter of step t-1: free from here on
+                if (tid == 0) sh.list_n[lr] = 0u;
+                const uint32_t n = sh.list_n[li];
+                uint32_t *crow = c.counts + (size_t)(t - 1) * plane;
+                for (uint32_t e = tid; e < n; e += nthr) {
+                    const uint32_t pk = list[e];
+                    const int wx = (int)(pk & 0xFFu), wy = (int)(pk >> 8);
+                    const int w = wy * ww + wx;
+                    const uint32_t v = win16[w];
+                    win16[w] = 0;
+                    red_add(crow + (size_t)(c.win_y0 + wy) * c.W + (c.win_x0 + wx), v);
+                }
+                if (tid == 0) {
+                    const uint32_t o = sh.oob_n[b];
+                    if (o) red_add(c.oob + (t - 1), o);
+                    sh.oob_n[b] = 0u;
+                }
             }
         }
         li = (li == 2) ? 0 : li + 1;

@@ -144,8 +144,8 @@ def test_autotune_and_graph_replay(ctx, orc):
         torch.cuda.synchronize()
         for d, r in zip(ds, ref):
             assert torch.equal(d["counts"], r)
-        for t, w in [(128, 24), (224, 96)]:
-            pm.pm_batch_set_config(b, t, 0, w)
+        for t, ppt, sw, w in [(128, 1, 0, 48), (256, 2, 0, 48), (224, 1, 1, 24), (256, 1, 1, 96)]:
+            pm.pm_batch_set_config(b, t, ppt, sw, 0, w)
             pm.pm_batch_predict(b)
             torch.cuda.synchronize()
             for d, r in zip(ds, ref):
