@@ -219,9 +219,11 @@ pm_status pm_batch_create(pm_ctx *ctx, const pm_model *shared, int32_t max_human
 /* Set the batch contents (host array of n_humans descriptors, copied):
  * validates them, builds the work list of tiles sorted by horizon (longest
  * first) and queues the upload on `stream`. A CUDA graph that captured
- * pm_batch_update_posterior / pm_batch_predict stays valid across calls to
- * pm_batch_set as long as the number of posterior chunks of the largest
- * n_obs does not grow (the graphs read the descriptors from device memory). */
+ * pm_batch_update_posterior / pm_batch_predict reads the descriptors, the
+ * tile list and the counts from device memory and stays valid across calls
+ * to pm_batch_set while the tile list fits the capacity reached before the
+ * capture (max_humans * 2048 tiles at creation; a larger batch reallocates
+ * the list, after which the graph must be captured again). */
 pm_status pm_batch_set(pm_batch *b, const pm_human *humans, int32_t n_humans, void *stream);
 
 /* Belief update (Eq. 3 / Eq. 7) of every human with n_obs > 0, one launch. */
@@ -233,24 +235,25 @@ pm_status pm_batch_update_posterior(pm_batch *b, void *stream);
  * it may be captured in a CUDA graph. */
 pm_status pm_batch_predict(pm_batch *b, void *stream);
 
-/* Time candidate launch shapes (threads per CTA, particles per thread,
- * emplacement mode and shared-memory window size) on the current batch with
- * CUDA events and keep the fastest; it runs pm_batch_predict several times
- * (outputs are overwritten). Synchronous. */
+/* Time candidate launch shapes (emplacement mode, threads per CTA and
+ * shared-memory window size) on the current batch with CUDA events and keep
+ * the fastest; it runs pm_batch_predict several times (outputs are
+ * overwritten). Synchronous. */
 pm_status pm_batch_autotune(pm_batch *b, void *stream);
 
 /* Read or set the launch shape: threads per CTA (multiple of 32, <= 256),
- * particles per thread (1 or 2), the emplacement mode (shared_window = 1: a
- * per-CTA shared-memory window flushed once per touched cell, one particle
- * per thread; 0: lanes of a warp in the same cell combined into one global
- * reduction), resident CTAs per SM used for the grid (0 = as many as fit)
- * and the window budget in KiB of shared memory. pm_batch_set_config
- * rebuilds the work list when the tile size changes (queued on the legacy
- * stream). Every shape gives the same counts. */
-pm_status pm_batch_get_config(const pm_batch *b, int32_t *threads, int32_t *particles_per_thread,
-                              int32_t *shared_window, int32_t *ctas_per_sm, int32_t *window_kib);
-pm_status pm_batch_set_config(pm_batch *b, int32_t threads, int32_t particles_per_thread,
-                              int32_t shared_window, int32_t ctas_per_sm, int32_t window_kib);
+ * the emplacement mode, resident CTAs per SM used for the grid (0 = as many
+ * as fit) and the window budget in KiB of shared memory. shared_window = 0:
+ * persistent warps take 32-particle tiles and combine the lanes of a warp
+ * that land in the same cell into one global reduction; 1: a CTA takes a
+ * tile of `threads` particles and counts each step in its shared-memory
+ * window, flushed once per touched cell. pm_batch_set_config rebuilds the
+ * work list when the tile size changes (queued on the legacy stream). Every
+ * shape gives the same counts. */
+pm_status pm_batch_get_config(const pm_batch *b, int32_t *threads, int32_t *shared_window, int32_t *ctas_per_sm,
+                              int32_t *window_kib);
+pm_status pm_batch_set_config(pm_batch *b, int32_t threads, int32_t shared_window, int32_t ctas_per_sm,
+                              int32_t window_kib);
 
 /* Release the plan (synchronises with its pending uploads). */
 void pm_batch_destroy(pm_batch *b);

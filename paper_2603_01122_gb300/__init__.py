@@ -69,8 +69,8 @@ def _signatures(lib):
         "pm_batch_update_posterior": ([_vp, _vp], C.c_int),
         "pm_batch_predict": ([_vp, _vp], C.c_int),
         "pm_batch_autotune": ([_vp, _vp], C.c_int),
-        "pm_batch_get_config": ([_vp] + [P(C.c_int32)] * 5, C.c_int),
-        "pm_batch_set_config": ([_vp] + [C.c_int32] * 5, C.c_int),
+        "pm_batch_get_config": ([_vp] + [P(C.c_int32)] * 4, C.c_int),
+        "pm_batch_set_config": ([_vp] + [C.c_int32] * 4, C.c_int),
         "pm_batch_destroy": ([_vp], None),
         "pm_loglik_forward": ([_vp, P(pm_model), C.c_int32, _vp, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
         "pm_loglik_backward": ([_vp, P(pm_model), C.c_int32, _vp, C.c_int32, _vp, _vp, C.c_float, _vp, _vp,
@@ -231,15 +231,14 @@ def pm_batch_autotune(batch, stream=None):
 
 
 def pm_batch_get_config(batch):
-    t, p, sw, c, w = (C.c_int32() for _ in range(5))
-    _check(library().pm_batch_get_config(batch, C.byref(t), C.byref(p), C.byref(sw), C.byref(c), C.byref(w)))
-    return {"threads": t.value, "particles_per_thread": p.value, "shared_window": sw.value,
-            "ctas_per_sm": c.value, "window_kib": w.value}
+    t, sw, c, w = (C.c_int32() for _ in range(4))
+    _check(library().pm_batch_get_config(batch, C.byref(t), C.byref(sw), C.byref(c), C.byref(w)))
+    return {"threads": t.value, "shared_window": sw.value, "ctas_per_sm": c.value, "window_kib": w.value}
 
 
-def pm_batch_set_config(batch, threads, particles_per_thread, shared_window, ctas_per_sm, window_kib):
-    _check(library().pm_batch_set_config(batch, int(threads), int(particles_per_thread), int(shared_window),
-                                         int(ctas_per_sm), int(window_kib)))
+def pm_batch_set_config(batch, threads, shared_window, ctas_per_sm, window_kib):
+    _check(library().pm_batch_set_config(batch, int(threads), int(shared_window), int(ctas_per_sm),
+                                         int(window_kib)))
 
 
 def pm_batch_destroy(batch):

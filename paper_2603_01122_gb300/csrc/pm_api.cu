@@ -54,8 +54,7 @@ struct pm_batch {
     cudaEvent_t staged = nullptr;
     // launch shape
     int threads = 256;
-    int ppt = 1;            // particles per thread
-    bool warp_hist = true;  // warp-combined emplacement (else shared-memory window)
+    bool warp_hist = true;  // warp-combined emplacement, persistent warps (else shared-memory window)
     int ctas_per_sm = 0;
     int window_kib = 48;
     int n_items = 0;
@@ -185,73 +184,6 @@ void fill_rollout_tables(const pm_model *m, pm::RolloutArgs &a)
     a.beta = m->beta;
 }
 
-// Window of the shared-memory histogram: the cells within reach of z0 in T
-// steps (|z_t - z0| <= T v dt), clipped to the grid and to 255 x 255 cells and
-// to the shared-memory budget; particles outside it are counted directly.
-[[maybe_unused]] void choose_window(const pm_model *m, const pm_grid *g, float z0x, float z0y, int T, int threads,
-                   size_t smem_budget, pm::RolloutArgs &a, size_t *dyn_smem)
-{
-    const float inv_res = 1.0f / g->res;
-    const double cx0 = std::floor((double)((z0x - g->x0) * inv_res));
-    const double cy0 = std::floor((double)((z0y - g->y0) * inv_res));
-    const double reach = std::ceil((double)T * (double)m->speed * (double)m->dt / (double)g->res) + 1.0;
-    const size_t list_bytes = (size_t)threads * sizeof(uint16_t);
-    long long r = (long long)std::fmin(reach, 127.0);
-    for (;;) {
-        long long x_lo = (long long)std::fmax(cx0 - r, 0.0), x_hi = (long long)std::fmin(cx0 + r, (double)g->W - 1);
-        long long y_lo = (long long)std::fmax(cy0 - r, 0.0), y_hi = (long long)std::fmin(cy0 + r, (double)g->H - 1);
-        long long w = x_hi - x_lo + 1, h = y_hi - y_lo + 1;
-        if (w <= 0 || h <= 0) { // z0 is far outside the grid: no window
-            a.win_x0 = a.win_y0 = 0;
-            a.win_side = 0;
-            *dyn_smem = 2 * list_bytes;
-            return;
-        }
-        // two windows (alternating by step parity) of 16-bit counts, each padded
-        // to 16 bytes, then two touched-cell lists
-        const size_t stride_words = (size_t)(((w * h + 1) / 2 + 3) & ~3LL);
-        const size_t bytes = 2 * stride_words * 4 + 2 * list_bytes;
-        if (bytes <= smem_budget || r <= 4) {
-            a.win_x0 = (int)x_lo;
-            a.win_y0 = (int)y_lo;
-            a.win_side = (int)(w | (h << 16));
-            *dyn_smem = bytes;
-            return;
-        }
-        r = (r * 7) / 8;
-    }
-}
-
-// Launch shape of the single-human rollout: one particle per thread with
-// warp-combined emplacement (measured faster on GB300 than the shared-memory
-// window, whose block barriers and shared memory cost more than the global
-// reductions it saves), and a block size that spreads the CTAs evenly over
-// the SMs: the kernel time follows the most loaded SM, ceil(blocks / SMs)
-// CTAs of `threads` particles.
-pm::RolloutShape choose_rollout_shape(pm_ctx *ctx, pm::RolloutArgs &a, size_t *dyn_out)
-{
-    static const int cand[] = {256, 224, 192, 160, 128};
-    double best_eff = -1.0;
-    pm::RolloutShape best{256, 1, true};
-    for (int t : cand) {
-        const pm::RolloutShape sh{t, 1, true};
-        const int occ = pm::rollout_occupancy(a, sh, 0);
-        if (occ < 1) continue;
-        const long long blocks = ((long long)a.N + t - 1) / t;
-        const long long per_sm = (blocks + ctx->sm_count - 1) / ctx->sm_count;
-        const double eff = (double)a.N / ((double)per_sm * t * ctx->sm_count) * (occ >= 2 ? 1.0 : 0.8);
-        if (eff > best_eff + 1e-9) {
-            best_eff = eff;
-            best = sh;
-        }
-    }
-    cudaGetLastError(); // a shape the occupancy query rejected is simply not chosen
-    a.win_x0 = a.win_y0 = 0;
-    a.win_side = 0;
-    *dyn_out = 0;
-    return best;
-}
-
 pm_status ensure_stage(pm_ctx *ctx, size_t bytes)
 {
     if (ctx->stage_bytes >= bytes) return PM_OK;
@@ -329,8 +261,6 @@ pm_status predict_impl(pm_ctx *ctx, const pm_model *model, const float *log_beli
     a.tr_states = states;
     a.tr_head = headings;
     a.tr_comp = components;
-    size_t dyn = 0;
-    int threads = 256;
     if (hist) {
         a.gx0 = grid->x0;
         a.gy0 = grid->y0;
@@ -347,13 +277,14 @@ pm_status predict_impl(pm_ctx *ctx, const pm_model *model, const float *log_beli
         a.W = a.H = 1;
         a.inv_res = 1.0f;
     }
-    const pm::RolloutShape shape = choose_rollout_shape(ctx, a, &dyn);
-    threads = shape.threads;
-    cudaError_t e = pm::launch_rollout(a, shape, dyn, stream);
-    if (e != cudaSuccess) {
-        return fail(PM_ECUDA, "rollout launch (%d CTAs x %d threads, %zu B dynamic shared memory): %s",
-                    (a.N + threads - 1) / threads, threads, dyn, cudaGetErrorString(e));
-    }
+    // persistent warps take 32-particle chunks from a context-owned counter
+    st = ensure_posterior_scratch(ctx, 0);
+    if (st != PM_OK) return st;
+    unsigned *head = ctx->ticket + 2;
+    cudaError_t ez = cudaMemsetAsync(head, 0, sizeof(unsigned), stream);
+    if (ez != cudaSuccess) return cuda_fail(ez, "chunk counter");
+    cudaError_t e = pm::launch_rollout(a, head, ctx->sm_count, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "rollout launch");
     return PM_OK;
 }
 
@@ -495,11 +426,11 @@ int batch_radius_cap(int window_kib, int threads)
     return r;
 }
 
-pm::RolloutShape batch_shape_of(const pm_batch *b) { return pm::RolloutShape{b->threads, b->ppt, b->warp_hist}; }
+pm::RolloutShape batch_shape_of(const pm_batch *b) { return pm::RolloutShape{b->threads, 1, b->warp_hist}; }
 
 size_t batch_dyn_smem(const pm_batch *b)
 {
-    if (b->warp_hist) return 0;
+    if (b->warp_hist) return pm::batch_warp_tables_bytes(b->threads);
     const int r = batch_radius_cap(b->window_kib, b->threads);
     const size_t cells = (size_t)(2 * r + 1) * (2 * r + 1);
     const size_t stride_words = (((cells + 1) / 2) + 3) & ~(size_t)3;
@@ -512,7 +443,8 @@ pm_status batch_upload(pm_batch *b, cudaStream_t stream)
     const double s = (double)b->shared.speed * (double)b->shared.dt;
     std::vector<int2> items;
     for (int h = 0; h < n; ++h)
-        for (int p0 = 0; p0 < b->humans[h].n_particles; p0 += b->threads * b->ppt) items.push_back(make_int2(h, p0));
+        for (int p0 = 0; p0 < b->humans[h].n_particles; p0 += (b->warp_hist ? 32 : b->threads))
+            items.push_back(make_int2(h, p0));
     std::stable_sort(items.begin(), items.end(), [&](const int2 &x, const int2 &y) {
         return b->humans[x.x].horizon > b->humans[y.x].horizon;
     });
@@ -635,7 +567,7 @@ pm_status batch_predict_impl(pm_batch *b, cudaStream_t stream)
     const size_t dyn = batch_dyn_smem(b);
     int occ = b->occ;
     if (occ < 1)
-        return fail(PM_EINVAL, "launch shape (%d threads, %d particles each, %s) does not fit an SM", b->threads, b->ppt,
+        return fail(PM_EINVAL, "launch shape (%d threads, %s) does not fit an SM", b->threads,
                     b->warp_hist ? "warp emplacement" : "shared window");
     if (b->ctas_per_sm > 0) occ = std::min(occ, b->ctas_per_sm);
     e = pm::launch_batch_rollout(a, batch_shape_of(b), ctx->sm_count * occ, dyn, stream);
@@ -890,7 +822,6 @@ pm_status pm_batch_set(pm_batch *b, const pm_human *humans, int32_t n_humans, vo
 pm_status pm_batch_update_posterior(pm_batch *b, void *stream)
 {
     if (!b) return fail(PM_EINVAL, "batch is NULL");
-    if (b->max_chunks == 0) return PM_OK;
     DeviceScope dev(b->ctx->device);
     pm::PosteriorArgs a;
     std::memset(&a, 0, sizeof a);
@@ -920,34 +851,28 @@ pm_status pm_batch_predict(pm_batch *b, void *stream)
     return batch_predict_impl(b, (cudaStream_t)stream);
 }
 
-pm_status pm_batch_get_config(const pm_batch *b, int32_t *threads, int32_t *particles_per_thread,
-                              int32_t *shared_window, int32_t *ctas_per_sm, int32_t *window_kib)
+pm_status pm_batch_get_config(const pm_batch *b, int32_t *threads, int32_t *shared_window, int32_t *ctas_per_sm,
+                              int32_t *window_kib)
 {
     if (!b) return fail(PM_EINVAL, "batch is NULL");
     if (threads) *threads = b->threads;
-    if (particles_per_thread) *particles_per_thread = b->ppt;
     if (shared_window) *shared_window = b->warp_hist ? 0 : 1;
     if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
     if (window_kib) *window_kib = b->window_kib;
     return PM_OK;
 }
 
-pm_status pm_batch_set_config(pm_batch *b, int32_t threads, int32_t particles_per_thread, int32_t shared_window,
-                              int32_t ctas_per_sm, int32_t window_kib)
+pm_status pm_batch_set_config(pm_batch *b, int32_t threads, int32_t shared_window, int32_t ctas_per_sm,
+                              int32_t window_kib)
 {
     if (!b) return fail(PM_EINVAL, "batch is NULL");
-    if (particles_per_thread != 1 && particles_per_thread != 2)
-        return fail(PM_EINVAL, "particles_per_thread=%d must be 1 or 2", particles_per_thread);
     if (shared_window != 0 && shared_window != 1) return fail(PM_EINVAL, "shared_window must be 0 or 1");
-    if (shared_window && particles_per_thread != 1)
-        return fail(PM_EINVAL, "the shared-window emplacement runs one particle per thread");
     if (threads < 32 || threads > 256 || threads % 32) return fail(PM_EINVAL, "threads=%d must be 32..256, multiple of 32", threads);
     if (ctas_per_sm < 0 || ctas_per_sm > 32) return fail(PM_EINVAL, "ctas_per_sm=%d out of range", ctas_per_sm);
     if (window_kib < 1 || window_kib > 200) return fail(PM_EINVAL, "window_kib=%d out of range", window_kib);
     DeviceScope dev(b->ctx->device);
-    const bool retile = threads != b->threads || particles_per_thread != b->ppt;
+    const bool retile = threads != b->threads || (shared_window == 0) != b->warp_hist;
     b->threads = threads;
-    b->ppt = particles_per_thread;
     b->warp_hist = shared_window == 0;
     b->ctas_per_sm = ctas_per_sm;
     b->window_kib = window_kib;
@@ -967,21 +892,19 @@ pm_status pm_batch_autotune(pm_batch *b, void *stream)
     DeviceScope dev(b->ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     struct Cand {
-        int threads, ppt;
+        int threads;
         bool warp;
         int window;
     };
-    static const Cand cands[] = {{128, 1, true, 48}, {192, 1, true, 48}, {224, 1, true, 48}, {256, 1, true, 48},
-                                 {128, 2, true, 48}, {256, 2, true, 48}, {224, 1, false, 48}, {256, 1, false, 48},
-                                 {256, 1, false, 96}};
+    static const Cand cands[] = {{256, true, 48}, {128, true, 48}, {224, false, 48}, {256, false, 48},
+                                 {256, false, 96}};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    Cand bc{b->threads, b->ppt, b->warp_hist, b->window_kib};
+    Cand bc{b->threads, b->warp_hist, b->window_kib};
     for (const Cand &cd : cands) {
         b->threads = cd.threads;
-        b->ppt = cd.ppt;
         b->warp_hist = cd.warp;
         b->window_kib = cd.window;
         b->ctas_per_sm = 0;
@@ -1010,7 +933,6 @@ pm_status pm_batch_autotune(pm_batch *b, void *stream)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->threads = bc.threads;
-    b->ppt = bc.ppt;
     b->warp_hist = bc.warp;
     b->window_kib = bc.window;
     b->ctas_per_sm = 0;

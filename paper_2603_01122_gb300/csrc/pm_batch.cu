@@ -22,15 +22,10 @@ namespace {
 
 constexpr int kBatchMaxThreads = 256;
 
-template <int PPT, bool WARP_HIST>
-constexpr int batch_min_blocks()
-{
-    return WARP_HIST ? (PPT == 1 ? 3 : 2) : 3;
-}
-
-template <int KT, bool FULL, int PPT, bool WARP_HIST>
-__global__ void __launch_bounds__(kBatchMaxThreads, (batch_min_blocks<PPT, WARP_HIST>()))
-    batch_rollout_kernel(const __grid_constant__ BatchArgs a)
+// Window form: a CTA takes a tile of blockDim particles and counts each step
+// in its shared-memory window (rollout_tile), one particle per thread.
+template <int KT, bool FULL>
+__global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_rollout_kernel(const __grid_constant__ BatchArgs a)
 {
     __shared__ RolloutShared sh;
     __shared__ int s_item;
@@ -86,7 +81,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, (batch_min_blocks<PPT, WARP_
         if (tid < 3) sh.list_n[tid] = 0u;
         if (tid < 2) sh.oob_n[tid] = 0u;
         __syncthreads();
-        if (!WARP_HIST) {
+        {
             const int words = 2 * window_stride_words(s_geom[4], s_geom[5]);
             for (int w = tid; w < words; w += nthr) dyn[w] = 0u;
         }
@@ -118,7 +113,85 @@ __global__ void __launch_bounds__(kBatchMaxThreads, (batch_min_blocks<PPT, WARP_
         c.tr_states = nullptr;
         c.tr_head = nullptr;
         c.tr_comp = nullptr;
-        rollout_tile<KT, FULL, PPT, WARP_HIST>(a.tab, a.enabled, a.s2, c, sh, dyn);
+        rollout_tile<KT, FULL, 1, false>(a.tab, a.enabled, a.s2, c, sh, dyn);
+    }
+}
+
+// Bytes of one warp's tables in dynamic shared memory: comp[kMaxJ] (16 B
+// each) then cdf[kMaxJ] (4 B each). Sized for the library's largest G*B, not
+// for the current batch, so that a CUDA graph captured on one batch stays
+// valid when humans with more components join later.
+constexpr size_t kWarpTableBytes = (size_t)kMaxJ * 20;
+
+// Persistent warps over all humans: each warp takes a 32-particle tile
+// (human, first particle) from the global counter, loads that human's
+// component table and belief CDF into its own slice of shared memory when
+// the human changes, and runs the tile with the warp-combined emplacement.
+// No block barrier after the start, so tiles of different humans and
+// horizons mix freely on every scheduler.
+template <int KT, bool FULL>
+__global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_warp_kernel(const __grid_constant__ BatchArgs a)
+{
+    __shared__ float2 step[kMaxK];
+    extern __shared__ __align__(16) uint32_t dyn[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int k = tid; k < KT; k += blockDim.x) step[k] = make_float2(a.tab.sx[k], a.tab.sy[k]);
+    __syncthreads();
+    char *slab = reinterpret_cast<char *>(dyn) + (size_t)warp * kWarpTableBytes;
+    float4 *comp = reinterpret_cast<float4 *>(slab);
+    uint32_t *cdf = reinterpret_cast<uint32_t *>(slab + (size_t)kMaxJ * 16);
+    const int n_items = *a.n_items;
+    int cur = -1;
+    for (;;) {
+        unsigned it = 0;
+        if (lane == 0) it = atomicAdd(a.head, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if ((int)it >= n_items) break;
+        const int2 item = a.items[it]; // (human, first particle)
+        const BatchHuman *h = a.humans + item.x;
+        const int J = min(h->G * h->B, kMaxJ); // the host rejects larger models
+        if (item.x != cur) {
+            __syncwarp();
+            for (int j = lane; j < J; j += 32) {
+                const int g = j / h->B, b = j - g * h->B;
+                comp[j] = make_float4(h->beta[b] * a.w2_log2e, h->goals[2 * g], h->goals[2 * g + 1], 0.0f);
+            }
+            belief_cdf(h->log_b, J, cdf, lane);
+            __syncwarp();
+            cur = item.x;
+        }
+        const float zx = h->z0[0], zy = h->z0[1];
+        int cx_off = h->cx_off, cy_off = h->cy_off;
+        if (h->center) {
+            // the output window is centred on the start cell (same FP32 rule as the states)
+            cx_off = __float2int_rd(__fmul_rn(__fsub_rn(zx, h->gx0), h->inv_res)) - (h->W - 1) / 2;
+            cy_off = __float2int_rd(__fmul_rn(__fsub_rn(zy, h->gy0), h->inv_res)) - (h->H - 1) / 2;
+        }
+        TileCtx c;
+        c.z0x = zx;
+        c.z0y = zy;
+        c.T = h->T;
+        c.i = (int64_t)item.y + lane;
+        c.N = h->N;
+        c.n_trace = 0;
+        c.seed = h->seed;
+        c.human = h->human;
+        c.J = J;
+        c.hist = true;
+        c.gx0 = h->gx0;
+        c.gy0 = h->gy0;
+        c.inv_res = h->inv_res;
+        c.W = h->W;
+        c.H = h->H;
+        c.cx_off = cx_off;
+        c.cy_off = cy_off;
+        c.counts = h->counts;
+        c.oob = h->oob;
+        c.win_x0 = c.win_y0 = c.ww = c.wh = 0;
+        c.tr_states = nullptr;
+        c.tr_head = nullptr;
+        c.tr_comp = nullptr;
+        rollout_lane<KT, FULL>(a.tab, a.enabled, a.s2, c, comp, cdf, step);
     }
 }
 
@@ -145,10 +218,9 @@ __global__ void batch_zero_kernel(const BatchHuman *humans, const int *n_dev)
     }
 }
 
-template <int KT, bool FULL, int PPT, bool WH>
-cudaError_t batch_one(const BatchArgs &a, int blocks, int threads, size_t dyn, cudaStream_t s, int *occ)
+template <typename Kern>
+cudaError_t launch_or_query(Kern k, const BatchArgs &a, int blocks, int threads, size_t dyn, cudaStream_t s, int *occ)
 {
-    auto k = batch_rollout_kernel<KT, FULL, PPT, WH>;
     if (dyn > 0) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;
@@ -162,11 +234,8 @@ cudaError_t batch_one(const BatchArgs &a, int blocks, int threads, size_t dyn, c
 template <int KT, bool FULL>
 cudaError_t batch_shape(const BatchArgs &a, const RolloutShape &sh, int blocks, size_t dyn, cudaStream_t s, int *occ)
 {
-    if (sh.warp_hist) {
-        if (sh.ppt == 2) return batch_one<KT, FULL, 2, true>(a, blocks, sh.threads, dyn, s, occ);
-        return batch_one<KT, FULL, 1, true>(a, blocks, sh.threads, dyn, s, occ);
-    }
-    return batch_one<KT, FULL, 1, false>(a, blocks, sh.threads, dyn, s, occ);
+    if (sh.warp_hist) return launch_or_query(batch_warp_kernel<KT, FULL>, a, blocks, sh.threads, dyn, s, occ);
+    return launch_or_query(batch_rollout_kernel<KT, FULL>, a, blocks, sh.threads, dyn, s, occ);
 }
 
 cudaError_t batch_dispatch(const BatchArgs &a, const RolloutShape &sh, int blocks, size_t dyn, cudaStream_t s, int *occ)
@@ -183,6 +252,8 @@ cudaError_t batch_dispatch(const BatchArgs &a, const RolloutShape &sh, int block
 }
 
 } // namespace
+
+size_t batch_warp_tables_bytes(int threads) { return (size_t)(threads / 32) * kWarpTableBytes; }
 
 int batch_rollout_occupancy(int K, uint64_t enabled, const RolloutShape &shape, size_t dyn)
 {

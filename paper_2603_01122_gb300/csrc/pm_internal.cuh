@@ -243,9 +243,9 @@ struct RolloutShape {
 };
 
 // Launch wrappers (defined next to their kernels).
-cudaError_t launch_rollout(const RolloutArgs &a, const RolloutShape &shape, size_t dyn_smem, cudaStream_t s);
+// `head` is a zeroed device counter of 32-particle chunks.
+cudaError_t launch_rollout(const RolloutArgs &a, unsigned *head, int sm_count, cudaStream_t s);
 size_t rollout_static_smem_estimate();
-int rollout_occupancy(const RolloutArgs &a, const RolloutShape &shape, size_t dyn_smem); // resident CTAs per SM
 cudaError_t launch_posterior(const PosteriorArgs &a, int n_chunks, cudaStream_t s);
 int posterior_chunks(int n_obs, int *steps_per_chunk);
 cudaError_t launch_posterior_batch(const PosteriorArgs &a, const PostHuman *humans, const int *n_humans,
@@ -259,6 +259,7 @@ cudaError_t launch_sfu_probe(int op, int blocks, int threads, int iters, float *
 int rollout_kt_for(int K); // template bucket for K (8, 16, 36 or 64)
 cudaError_t launch_adjoint(const AdjointArgs &a, cudaStream_t s);
 int batch_rollout_occupancy(int K, uint64_t enabled, const RolloutShape &shape, size_t dyn);
+size_t batch_warp_tables_bytes(int threads); // dynamic shared memory of the warp form
 cudaError_t launch_batch_rollout(const BatchArgs &a, const RolloutShape &shape, int blocks, size_t dyn, cudaStream_t s);
 cudaError_t launch_batch_zero(const BatchHuman *humans, const int *n_dev, int max_rows, int sm_count, cudaStream_t s);
 size_t adjoint_scratch_bytes(int M, int G);

@@ -219,8 +219,9 @@ __global__ void __launch_bounds__(1024) posterior_kernel(const __grid_constant__
     posterior_chunk(a, h, blockIdx.x, gridDim.x);
 }
 
-// Batched form: blockIdx.y is the human, blockIdx.x the chunk; humans with
-// fewer chunks (or no observed steps) leave the extra CTAs idle.
+// Batched form: blockIdx.y is the human; the CTAs of a row stride over its
+// chunks, so any number of observed steps fits a fixed grid (as a captured
+// CUDA graph requires); humans with no observed steps leave their row idle.
 __global__ void __launch_bounds__(1024) posterior_batch_kernel(const __grid_constant__ PosteriorArgs a,
                                                                const PostHuman *humans, const int *n_humans)
 {
@@ -228,8 +229,7 @@ __global__ void __launch_bounds__(1024) posterior_batch_kernel(const __grid_cons
     const PostHuman h = humans[blockIdx.y];
     if (h.n_obs <= 0 || h.log_b == nullptr) return;
     const int nchunk = (h.n_obs + h.steps_per_chunk - 1) / h.steps_per_chunk;
-    if ((int)blockIdx.x >= nchunk) return;
-    posterior_chunk(a, h, blockIdx.x, nchunk);
+    for (int ch = blockIdx.x; ch < nchunk; ch += gridDim.x) posterior_chunk(a, h, ch, nchunk);
 }
 
 } // namespace
@@ -251,8 +251,8 @@ cudaError_t launch_posterior_batch(const PosteriorArgs &a, const PostHuman *huma
 {
     int threads = 32 * max_J;
     if (threads > 1024) threads = 1024;
-    if (max_rows <= 0 || max_chunks <= 0) return cudaSuccess;
-    posterior_batch_kernel<<<dim3(max_chunks, max_rows), threads, 0, s>>>(a, humans, n_humans);
+    if (max_rows <= 0) return cudaSuccess;
+    posterior_batch_kernel<<<dim3(max_chunks > 0 ? max_chunks : 1, max_rows), threads, 0, s>>>(a, humans, n_humans);
     return cudaGetLastError();
 }
 

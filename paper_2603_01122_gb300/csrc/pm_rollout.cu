@@ -26,53 +26,42 @@
 namespace pm {
 namespace {
 
-constexpr int kRolloutThreads = 256;
 
-// Resident CTAs per SM the compiler is asked to fit: the warp-histogram forms
-// use almost no shared memory, so registers decide their occupancy.
-template <int PPT, bool WARP_HIST>
-constexpr int rollout_min_blocks()
-{
-    return WARP_HIST ? (PPT == 1 ? 3 : 2) : 3;
-}
+constexpr int kWarpCtaThreads = 256; // 8 warps: two per SM sub-partition
+constexpr int kWarpCtaMinBlocks = 3;
 
-template <int KT, bool FULL, int PPT, bool WARP_HIST>
-__global__ void __launch_bounds__(kRolloutThreads, (rollout_min_blocks<PPT, WARP_HIST>()))
-    rollout_kernel(const __grid_constant__ RolloutArgs a)
+// Persistent warps over one human: the CTA loads the component table, the
+// belief CDF and the Euler steps into shared memory once, then each warp
+// takes chunks of 32 particles (one per lane) from a global counter until the
+// particles are exhausted, so the work spreads evenly over the schedulers and
+// SMs whatever the particle count.
+template <int KT, bool FULL>
+__global__ void __launch_bounds__(kWarpCtaThreads, kWarpCtaMinBlocks)
+    rollout_warp_kernel(const __grid_constant__ RolloutArgs a, unsigned *head)
 {
-    __shared__ RolloutShared sh;
-    extern __shared__ __align__(16) uint32_t dyn[];
-    const int tid = threadIdx.x;
-    const int nthr = blockDim.x;
+    __shared__ float4 comp[kMaxJ];
+    __shared__ uint32_t cdf[kMaxJ];
+    __shared__ float2 step[kMaxK];
+    const int tid = threadIdx.x, lane = tid & 31;
     const int J = a.G * a.B;
-    const bool hist = a.counts != nullptr;
-    const int ww = a.win_side & 0xFFFF, wh = a.win_side >> 16; // window width/height (cells)
-
-    for (int j = tid; j < J; j += nthr) {
+    for (int j = tid; j < J; j += blockDim.x) {
         const int g = j / a.B, b = j - g * a.B;
-        sh.comp[j] = make_float4(a.beta[b] * a.w2_log2e, a.goals[2 * g], a.goals[2 * g + 1], 0.0f);
+        comp[j] = make_float4(a.beta[b] * a.w2_log2e, a.goals[2 * g], a.goals[2 * g + 1], 0.0f);
     }
-    for (int k = tid; k < KT; k += nthr) sh.step[k] = make_float2(a.tab.sx[k], a.tab.sy[k]);
-    if (hist && !WARP_HIST) {
-        const int win_words = 2 * window_stride_words(ww, wh); // both windows
-        for (int w = tid; w < win_words; w += nthr) dyn[w] = 0u;
-    }
-    if (tid < 3) sh.list_n[tid] = 0u;
-    if (tid < 2) sh.oob_n[tid] = 0u;
-    if (tid < 32) belief_cdf(a.log_b, J, sh.cdf, tid);
+    for (int k = tid; k < KT; k += blockDim.x) step[k] = make_float2(a.tab.sx[k], a.tab.sy[k]);
+    if (tid < 32) belief_cdf(a.log_b, J, cdf, tid);
     __syncthreads();
 
     TileCtx c;
     c.z0x = a.z0x;
     c.z0y = a.z0y;
     c.T = a.T;
-    c.i = (int64_t)blockIdx.x * nthr * PPT + tid;
     c.N = a.N;
     c.n_trace = a.n_trace;
     c.seed = a.seed;
     c.human = a.human;
     c.J = J;
-    c.hist = hist;
+    c.hist = a.counts != nullptr;
     c.gx0 = a.gx0;
     c.gy0 = a.gy0;
     c.inv_res = a.inv_res;
@@ -82,57 +71,50 @@ __global__ void __launch_bounds__(kRolloutThreads, (rollout_min_blocks<PPT, WARP
     c.cy_off = 0;
     c.counts = a.counts;
     c.oob = a.oob;
-    c.win_x0 = a.win_x0;
-    c.win_y0 = a.win_y0;
-    c.ww = ww;
-    c.wh = wh;
+    c.win_x0 = c.win_y0 = c.ww = c.wh = 0;
     c.tr_states = a.tr_states;
     c.tr_head = a.tr_head;
     c.tr_comp = a.tr_comp;
-    rollout_tile<KT, FULL, PPT, WARP_HIST>(a.tab, a.enabled, a.s2, c, sh, dyn);
-}
-
-template <int KT, bool FULL, int PPT, bool WH>
-cudaError_t launch_one(const RolloutArgs &a, int threads, size_t dyn_smem, cudaStream_t s, int *occ)
-{
-    auto k = rollout_kernel<KT, FULL, PPT, WH>;
-    if (dyn_smem > 0) { // static + dynamic may pass the 48 KiB default
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
-        if (e != cudaSuccess) return e;
+    for (;;) {
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(head, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        const int64_t i0 = (int64_t)item * 32;
+        if (i0 >= a.N) break;
+        c.i = i0 + lane;
+        rollout_lane<KT, FULL>(a.tab, a.enabled, a.s2, c, comp, cdf, step);
     }
-    if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, threads, dyn_smem);
-    const unsigned blocks = (unsigned)((a.N + (int64_t)threads * PPT - 1) / ((int64_t)threads * PPT));
-    cudaGetLastError(); // clear errors of earlier calls whose failure was handled
-    k<<<blocks, threads, dyn_smem, s>>>(a);
-    return cudaGetLastError();
-}
-
-template <int KT, bool FULL>
-cudaError_t launch_shape(const RolloutArgs &a, const RolloutShape &sh, size_t dyn, cudaStream_t s, int *occ)
-{
-    if (sh.warp_hist) {
-        if (sh.ppt == 2) return launch_one<KT, FULL, 2, true>(a, sh.threads, dyn, s, occ);
-        return launch_one<KT, FULL, 1, true>(a, sh.threads, dyn, s, occ);
-    }
-    return launch_one<KT, FULL, 1, false>(a, sh.threads, dyn, s, occ);
 }
 
 template <int KT>
-cudaError_t launch_kt(const RolloutArgs &a, const RolloutShape &sh, size_t dyn, cudaStream_t s, int *occ)
+cudaError_t launch_kt(const RolloutArgs &a, unsigned *head, int sm_count, cudaStream_t s, int *occ)
 {
     const uint64_t all = (KT >= 64) ? ~0ull : ((1ull << KT) - 1ull);
     const bool full = (a.K == KT) && ((a.enabled & all) == all);
-    if (full) return launch_shape<KT, true>(a, sh, dyn, s, occ);
-    return launch_shape<KT, false>(a, sh, dyn, s, occ);
+    auto k = full ? rollout_warp_kernel<KT, true> : rollout_warp_kernel<KT, false>;
+    int n = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kWarpCtaThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (occ) {
+        *occ = n;
+        return cudaSuccess;
+    }
+    const int64_t chunks = ((int64_t)a.N + 31) / 32;
+    const int64_t need = (chunks + kWarpCtaThreads / 32 - 1) / (kWarpCtaThreads / 32);
+    int64_t blocks = (int64_t)sm_count * (n > 0 ? n : 1);
+    if (need < blocks) blocks = need;
+    cudaGetLastError(); // clear errors of earlier calls whose failure was handled
+    k<<<(unsigned)blocks, kWarpCtaThreads, 0, s>>>(a, head);
+    return cudaGetLastError();
 }
 
-cudaError_t dispatch(const RolloutArgs &a, const RolloutShape &sh, size_t dyn, cudaStream_t s, int *occ)
+cudaError_t dispatch(const RolloutArgs &a, unsigned *head, int sm_count, cudaStream_t s, int *occ)
 {
     switch (rollout_kt_for(a.K)) {
-    case 8: return launch_kt<8>(a, sh, dyn, s, occ);
-    case 16: return launch_kt<16>(a, sh, dyn, s, occ);
-    case 36: return launch_kt<36>(a, sh, dyn, s, occ);
-    default: return launch_kt<64>(a, sh, dyn, s, occ);
+    case 8: return launch_kt<8>(a, head, sm_count, s, occ);
+    case 16: return launch_kt<16>(a, head, sm_count, s, occ);
+    case 36: return launch_kt<36>(a, head, sm_count, s, occ);
+    default: return launch_kt<64>(a, head, sm_count, s, occ);
     }
 }
 
@@ -148,19 +130,9 @@ int rollout_kt_for(int K)
 
 size_t rollout_static_smem_estimate() { return sizeof(RolloutShared); }
 
-int rollout_occupancy(const RolloutArgs &a, const RolloutShape &shape, size_t dyn_smem)
+cudaError_t launch_rollout(const RolloutArgs &a, unsigned *head, int sm_count, cudaStream_t s)
 {
-    int n = 0;
-    if (dispatch(a, shape, dyn_smem, nullptr, &n) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    return n;
-}
-
-cudaError_t launch_rollout(const RolloutArgs &a, const RolloutShape &shape, size_t dyn_smem, cudaStream_t s)
-{
-    return dispatch(a, shape, dyn_smem, s, nullptr);
+    return dispatch(a, head, sm_count, s, nullptr);
 }
 
 } // namespace pm

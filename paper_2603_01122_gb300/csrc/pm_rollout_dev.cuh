@@ -347,4 +347,75 @@ __device__ __forceinline__ void rollout_tile(const HeadingTab &tab, uint64_t ena
         li = (li == 2) ? 0 : li + 1;
     }
 }
+// Algorithm 1 for the particle of one lane: the (beta, g) draw from the
+// belief table (comp, cdf), then T heading draws and Euler steps, each step
+// emplaced with the lanes of the warp that land in the same cell combined
+// (match.any) into one global reduction. Every lane of the warp must call
+// it with the same c.T (idle lanes pass c.i >= c.N). No block barrier.
+template <int KT, bool FULL>
+__device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t enabled, float s2, const TileCtx &c,
+                                             const float4 *comp, const uint32_t *cdf, const float2 *step)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t i = (uint64_t)c.i;
+    const bool act = c.i < c.N;
+    const bool trc = c.i < c.n_trace;
+    float x = c.z0x, y = c.z0y, cb = 0.0f, gx = 0.0f, gy = 0.0f;
+    if (act) {
+        const U64x4 r = philox4x64_10(U64x4{i, 0ull, kPurposeSelect, 0ull}, c.seed, c.human);
+        const uint32_t thr = (uint32_t)(((uint64_t)((uint32_t)r.a >> 8) * (uint64_t)cdf[c.J - 1]) >> 24);
+        int lo = 0, hi = c.J - 1; // smallest j with cdf[j] > thr
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (cdf[mid] > thr) hi = mid;
+            else lo = mid + 1;
+        }
+        const float4 cc = comp[lo];
+        cb = cc.x;
+        gx = cc.y;
+        gy = cc.z;
+        if (trc && c.tr_comp) c.tr_comp[i] = lo;
+    }
+    const size_t plane = (size_t)c.W * (size_t)c.H;
+    uint32_t q0 = 0, q1 = 0, q2 = 0, q3 = 0, q4 = 0, q5 = 0, q6 = 0, q7 = 0;
+    for (int t = 1; t <= c.T; ++t) {
+        uint32_t key = 0xFFFFFFFFu; // idle lane
+        if (act) {
+            if (((t - 1) & 7) == 0) {
+                const U64x4 r = philox4x64_10(U64x4{i, (uint64_t)((t - 1) >> 3), kPurposeStep, 0ull}, c.seed, c.human);
+                q0 = (uint32_t)r.a; q1 = (uint32_t)(r.a >> 32);
+                q2 = (uint32_t)r.b; q3 = (uint32_t)(r.b >> 32);
+                q4 = (uint32_t)r.c; q5 = (uint32_t)(r.c >> 32);
+                q6 = (uint32_t)r.d; q7 = (uint32_t)(r.d >> 32);
+            }
+            const uint32_t word = q0;
+            q0 = q1; q1 = q2; q2 = q3; q3 = q4; q4 = q5; q5 = q6; q6 = q7;
+            const int k = draw_heading<KT, FULL>(tab, enabled, s2, x, y, gx, gy, cb, word);
+            const float2 st = step[k];
+            x = __fadd_rn(x, st.x);
+            y = __fadd_rn(y, st.y);
+            if (trc) {
+                const size_t o = (size_t)i * c.T + (t - 1);
+                if (c.tr_states) reinterpret_cast<float2 *>(c.tr_states)[o] = make_float2(x, y);
+                if (c.tr_head) c.tr_head[o] = (uint8_t)k;
+            }
+            if (c.hist) {
+                const float vx = __fmul_rn(__fsub_rn(x, c.gx0), c.inv_res);
+                const float vy = __fmul_rn(__fsub_rn(y, c.gy0), c.inv_res);
+                const int cx = __float2int_rd(vx) - c.cx_off;
+                const int cy = __float2int_rd(vy) - c.cy_off;
+                const bool in = (vx == vx) && (vy == vy) && cx >= 0 && cx < c.W && cy >= 0 && cy < c.H;
+                key = in ? (uint32_t)(cy * c.W + cx) : 0xFFFFFFFEu;
+            }
+        }
+        if (c.hist) {
+            const uint32_t peers = __match_any_sync(0xffffffffu, key);
+            if (key != 0xFFFFFFFFu && (__ffs(peers) - 1) == lane) {
+                if (key == 0xFFFFFFFEu) red_add(c.oob + (t - 1), (uint32_t)__popc(peers));
+                else red_add(c.counts + (size_t)(t - 1) * plane + key, (uint32_t)__popc(peers));
+            }
+        }
+    }
+}
+
 } // namespace pm
