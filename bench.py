@@ -63,6 +63,28 @@ def dist_env():
     return rank, world, local
 
 
+def rank_human_id(base_id, rank):
+    """Each rank predicts its own human (its own Philox key): the ranks share
+    no data and exchange nothing on the data path."""
+    return base_id + 1000 * rank
+
+
+def max_over_ranks(x, world, tdist=None, device=None):
+    """The largest of the ranks' values of x (the slowest rank's time)."""
+    if world == 1:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, seconds):
+    """Whole-job units per second: every rank's units over the slowest time."""
+    return world * units_per_rank / seconds
+
+
 def workload_config(hu):
     x0, y0, res, W, H = hu.grid
     return {
@@ -429,7 +451,7 @@ def run_native(args):
     stream = torch.cuda.Stream(device=dev)
 
     hu = workloads.paper_scale()
-    human_id = hu.human_id + 1000 * rank
+    human_id = rank_human_id(hu.human_id, rank)
     K, N, T = hu.K, hu.n_particles, hu.horizon
     x0, y0, res, W, H = hu.grid
     goals = torch.tensor(hu.goals, device=dev)
@@ -509,13 +531,9 @@ def run_native(args):
     step_ms = [a.elapsed_time(c) for a, b, c in ev]
     roll_ms = [b.elapsed_time(c) for a, b, c in ev]
     post_ms = [a.elapsed_time(b) for a, b, c in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, tdist, dev)
     ms_per_step = total_ms / args.steps
-    value = world * N * T / (ms_per_step * 1e-3)
+    value = job_throughput(world, N * T, ms_per_step * 1e-3)
 
     # roofline of the dominant kernel (the rollout): algorithmic SFU results
     # per launch (K exp + K sqrt per particle-step) / its event-timed duration
@@ -547,11 +565,7 @@ def run_native(args):
     e2e_s = (time.perf_counter() - e0) / e2e_steps
     h2d = (goals_h.numel() + beta_h.numel() + obs_h.numel() + prior_h.numel()) * 4
     d2h = (post_h.numel() + counts_h.numel() + oob_h.numel()) * 4
-    e2e_value = N * T / e2e_s
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        e2e_value = world * N * T / float(t.item())
+    e2e_value = job_throughput(world, N * T, max_over_ranks(e2e_s, world, tdist, dev))
 
     if rank == 0:
         line = {
