@@ -175,6 +175,8 @@ void fill_rollout_tables(const pm_model *m, pm::RolloutArgs &a)
         a.tab.ty[k] = (float)(2.0 * s * sn);
     }
     a.enabled = enabled_mask(m);
+    a.tab.s = (float)s;
+    a.tab.lb_gap = (float)(2.0 * s * std::sin(3.14159265358979323846 / (2.0 * m->K)));
     a.s2 = (float)(s * s);
     a.w2_log2e = (float)((double)m->w2 * 1.4426950408889634);
     a.K = m->K;

@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_rollout_kernel(cons
         if (item.x != cur) {
             for (int j = tid; j < J; j += nthr) {
                 const int g = j / h->B, b = j - g * h->B;
-                sh.comp[j] = make_float4(h->beta[b] * a.w2_log2e, h->goals[2 * g], h->goals[2 * g + 1], 0.0f);
+                const float cbj = h->beta[b] * a.w2_log2e;
+                sh.comp[j] = make_float4(cbj, h->goals[2 * g], h->goals[2 * g + 1], lb_flag(a.tab, cbj));
             }
             if (tid < 32) belief_cdf(h->log_b, J, sh.cdf, tid);
             cur = item.x;
@@ -154,7 +155,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_warp_kernel(const _
             __syncwarp();
             for (int j = lane; j < J; j += 32) {
                 const int g = j / h->B, b = j - g * h->B;
-                comp[j] = make_float4(h->beta[b] * a.w2_log2e, h->goals[2 * g], h->goals[2 * g + 1], 0.0f);
+                const float cbj = h->beta[b] * a.w2_log2e;
+                comp[j] = make_float4(cbj, h->goals[2 * g], h->goals[2 * g + 1], lb_flag(a.tab, cbj));
             }
             belief_cdf(h->log_b, J, cdf, lane);
             __syncwarp();

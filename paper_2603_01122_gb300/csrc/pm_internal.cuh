@@ -122,6 +122,12 @@ struct HeadingTab {
     float ux[kMaxK], uy[kMaxK]; // unit vector (cos, sin) of theta_k
     float sx[kMaxK], sy[kMaxK]; // one Euler step v*dt*(cos, sin)
     float tx[kMaxK], ty[kMaxK]; // 2*v*dt*(cos, sin)
+    float s;                    // step length v*dt
+    // 2 s sin(pi / 2K): with all K equally spaced headings enabled, the
+    // nearest one to any direction is within pi/K, so min_k d_k exceeds the
+    // triangle bound |r - s| by at most this much (zero when the headings are
+    // not all enabled: the bound is then not used)
+    float lb_gap;
 };
 
 // Arguments of the rollout kernel (Algorithm 1 + emplacement).

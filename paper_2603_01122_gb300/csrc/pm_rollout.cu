@@ -46,7 +46,8 @@ __global__ void __launch_bounds__(kWarpCtaThreads, kWarpCtaMinBlocks)
     const int J = a.G * a.B;
     for (int j = tid; j < J; j += blockDim.x) {
         const int g = j / a.B, b = j - g * a.B;
-        comp[j] = make_float4(a.beta[b] * a.w2_log2e, a.goals[2 * g], a.goals[2 * g + 1], 0.0f);
+        const float cbj = a.beta[b] * a.w2_log2e;
+        comp[j] = make_float4(cbj, a.goals[2 * g], a.goals[2 * g + 1], lb_flag(a.tab, cbj));
     }
     for (int k = tid; k < KT; k += blockDim.x) step[k] = make_float2(a.tab.sx[k], a.tab.sy[k]);
     if (tid < 32) belief_cdf(a.log_b, J, cdf, tid);

@@ -161,6 +161,89 @@ __device__ __forceinline__ int draw_heading(const HeadingTab &tab, uint64_t enab
     }
 }
 
+// The same draw for even KT with all KT equally spaced headings enabled, the
+// weights normalised by a bound of the distances instead of their exact
+// extreme, which fuses the distance, exponential and summation passes into one.
+// By the triangle inequality every d_k lies in [|r - s|, r + s] (r = ||z - g||,
+// s = v dt), and the heading nearest the extreme direction lies within pi/K of
+// it, so the extreme d_k is within lb_gap = 2 s sin(pi/2K) of the bound. The
+// reference ref is the lower bound for beta >= 0 and the upper bound for
+// beta < 0, pushed outwards by a few ulps of r + s so that every exponent
+// -cb (d_k - ref) is <= 0 after rounding; the largest weight is then at least
+// 2^(-|cb| lb_gap) (callers use this form only where that is >= 1/2). A
+// common shift of all logits leaves the distribution of Eq. 2 unchanged.
+template <int KT>
+__device__ __forceinline__ int draw_heading_lb(const HeadingTab &tab, float s2, float x, float y, float gx, float gy,
+                                               float cb, uint32_t word)
+{
+    static_assert(KT % 4 == 0, "pairs of headings must not straddle the two summation chains");
+    const float dx = x - gx, dy = y - gy;
+    const float D = fmaf(dx, dx, fmaf(dy, dy, s2));
+    const float hD = 0.5f * rsqrt_approx(D);
+    const float r = sqrt_approx(fmaf(dx, dx, dy * dy));
+    const float margin = (r + tab.s) * 0x1p-20f;
+    const float ref = (cb >= 0.0f) ? fabsf(r - tab.s) - margin : r + tab.s + margin;
+    const f32x2 DX = f2_pack(dx, dx), DY = f2_pack(dy, dy);
+    const f32x2 DD = f2_pack(D, D), NDD = f2_pack(-D, -D), HD = f2_pack(hD, hD);
+    const f32x2 REF = f2_pack(ref, ref), NC = f2_pack(-cb, -cb);
+    const f32x2 SC = f2_pack(4194304.0f, 4194304.0f), MG = f2_pack(12582912.0f, 12582912.0f);
+    const f32x2 *TX = reinterpret_cast<const f32x2 *>(tab.tx);
+    const f32x2 *TY = reinterpret_cast<const f32x2 *>(tab.ty);
+    constexpr int H2 = KT / 2;
+    uint32_t bits[KT];
+    uint32_t S0 = 0u, S1 = 0u;
+#pragma unroll
+    for (int q = 0; q < KT / 2; ++q) {
+        const f32x2 P = f2_fma(TX[q], DX, f2_mul(TY[q], DY)); // 2 s e_k.(z - g), k = 2q, 2q+1
+        float x0, x1;
+        f2_unpack(f2_add(DD, P), x0, x1);
+        const float d0 = sqrt_approx(fabsf(x0)), d1 = sqrt_approx(fabsf(x1));
+        const f32x2 DK = f2_pack(d0, d1);
+        const f32x2 R = f2_sub(P, f2_fma(DK, DK, NDD));           // D + p - dk^2
+        const f32x2 U = f2_fma(R, HD, f2_sub(DK, REF));            // d_k - ref, corrected
+        float a0, a1;
+        f2_unpack(f2_mul(U, NC), a0, a1);                           // log2 weight, <= 0
+        float w0, w1;
+        f2_unpack(f2_fma(f2_pack(ex2_approx(a0), ex2_approx(a1)), SC, MG), w0, w1);
+        bits[2 * q] = __float_as_uint(w0);                          // 0x4B400000 + round(e * 2^22)
+        bits[2 * q + 1] = __float_as_uint(w1);
+        if (2 * q < H2) S0 += bits[2 * q] + bits[2 * q + 1];
+        else S1 += bits[2 * q] + bits[2 * q + 1];
+    }
+    S0 -= (uint32_t)H2 * 0x4B400000u;
+    S1 -= (uint32_t)(KT - H2) * 0x4B400000u;
+    const uint32_t S = S0 + S1;
+    const uint32_t thr = (uint32_t)(((uint64_t)(word >> 8) * (uint64_t)S) >> 24);
+    uint32_t acc0 = ~thr, acc1 = ~thr + S0;
+    int sel0 = 0, sel1 = 0;
+#pragma unroll
+    for (int k = 0; k < H2; ++k) {
+        acc0 += bits[k] - 0x4B400000u;
+        sel0 += (int)(acc0 >> 31);
+        acc1 += bits[H2 + k] - 0x4B400000u;
+        sel1 += (int)(acc1 >> 31);
+    }
+    return sel0 + sel1;
+}
+
+// Component flag of the belief table: the bound-normalised draw keeps the
+// largest weight >= 1/2 (22-bit weights keep >= 21 significant bits).
+__device__ __forceinline__ float lb_flag(const HeadingTab &tab, float cb)
+{
+    return (fabsf(cb) * tab.lb_gap <= 1.0f) ? 1.0f : 0.0f;
+}
+
+// The heading draw of one particle: the fused bound form where it applies.
+template <int KT, bool FULL>
+__device__ __forceinline__ int draw(const HeadingTab &tab, uint64_t enabled, float s2, float x, float y, float gx,
+                                    float gy, float cb, bool lb, uint32_t word)
+{
+    if constexpr (FULL && (KT % 4 == 0)) {
+        if (lb) return draw_heading_lb<KT>(tab, s2, x, y, gx, gy, cb, word);
+    }
+    return draw_heading<KT, FULL>(tab, enabled, s2, x, y, gx, gy, cb, word);
+}
+
 // Per-tile state of one human for rollout_tile.
 struct TileCtx {
     float z0x, z0y;
@@ -219,7 +302,7 @@ __device__ __forceinline__ void rollout_tile(const HeadingTab &tab, uint64_t ena
 
     float x[PPT], y[PPT], cb[PPT], gx[PPT], gy[PPT];
     uint64_t ip[PPT];
-    bool act[PPT], trc[PPT];
+    bool act[PPT], trc[PPT], lb[PPT];
     uint32_t q[PPT][8];
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
@@ -229,6 +312,7 @@ __device__ __forceinline__ void rollout_tile(const HeadingTab &tab, uint64_t ena
         x[p] = c.z0x;
         y[p] = c.z0y;
         cb[p] = gx[p] = gy[p] = 0.0f;
+        lb[p] = false;
 #pragma unroll
         for (int w = 0; w < 8; ++w) q[p][w] = 0u;
         if (act[p]) {
@@ -244,6 +328,7 @@ __device__ __forceinline__ void rollout_tile(const HeadingTab &tab, uint64_t ena
             cb[p] = cc.x;
             gx[p] = cc.y;
             gy[p] = cc.z;
+            lb[p] = cc.w != 0.0f;
             if (trc[p] && c.tr_comp) c.tr_comp[ip[p]] = lo;
         }
     }
@@ -269,7 +354,7 @@ __device__ __forceinline__ void rollout_tile(const HeadingTab &tab, uint64_t ena
                 const uint32_t word = q[p][0];
 #pragma unroll
                 for (int w = 0; w < 7; ++w) q[p][w] = q[p][w + 1];
-                const int k = draw_heading<KT, FULL>(tab, enabled, s2, x[p], y[p], gx[p], gy[p], cb[p], word);
+                const int k = draw<KT, FULL>(tab, enabled, s2, x[p], y[p], gx[p], gy[p], cb[p], lb[p], word);
                 const float2 st = sh.step[k];
                 x[p] = __fadd_rn(x[p], st.x);
                 y[p] = __fadd_rn(y[p], st.y);
@@ -361,6 +446,7 @@ __device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t ena
     const bool act = c.i < c.N;
     const bool trc = c.i < c.n_trace;
     float x = c.z0x, y = c.z0y, cb = 0.0f, gx = 0.0f, gy = 0.0f;
+    bool lb = false;
     if (act) {
         const U64x4 r = philox4x64_10(U64x4{i, 0ull, kPurposeSelect, 0ull}, c.seed, c.human);
         const uint32_t thr = (uint32_t)(((uint64_t)((uint32_t)r.a >> 8) * (uint64_t)cdf[c.J - 1]) >> 24);
@@ -374,6 +460,7 @@ __device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t ena
         cb = cc.x;
         gx = cc.y;
         gy = cc.z;
+        lb = cc.w != 0.0f;
         if (trc && c.tr_comp) c.tr_comp[i] = lo;
     }
     const size_t plane = (size_t)c.W * (size_t)c.H;
@@ -390,7 +477,7 @@ __device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t ena
             }
             const uint32_t word = q0;
             q0 = q1; q1 = q2; q2 = q3; q3 = q4; q4 = q5; q5 = q6; q6 = q7;
-            const int k = draw_heading<KT, FULL>(tab, enabled, s2, x, y, gx, gy, cb, word);
+            const int k = draw<KT, FULL>(tab, enabled, s2, x, y, gx, gy, cb, lb, word);
             const float2 st = step[k];
             x = __fadd_rn(x, st.x);
             y = __fadd_rn(y, st.y);
