@@ -316,9 +316,14 @@ pm_status pm_philox_blocks(pm_ctx *ctx, uint64_t seed, uint32_t human_id, uint32
                            uint64_t particle0, uint64_t block, int32_t n, uint64_t *out,
                            void *stream);
 
-/* Throughput of the special-function unit measured on this device, in
- * results per second: op 0 = ex2.approx.f32, 1 = sqrt.approx.f32,
- * 2 = rsqrt.approx.f32. Synchronous (times its own launch with events). */
+/* Throughput of one arithmetic operation measured on this device, in
+ * results per second (eight independent chains per thread, 8 CTAs of 256
+ * threads per SM): op 0 = ex2.approx.f32, 1 = sqrt.approx.f32,
+ * 2 = rsqrt.approx.f32 (special-function unit), 3 = fma.rn.f32,
+ * 4 = fma.rn.f32x2 (two results per instruction), 5 = add.u32.
+ * PM_EINVAL for another op. Synchronous (times its own launch with events).
+ * Ops 0-2 give the roofline of the rollout; 3-5 the FP32 and integer pipes
+ * that its heading loop also loads. */
 pm_status pm_probe_sfu(pm_ctx *ctx, int op, double *results_per_s);
 
 /* Device properties the roofline uses: SM count, SM clock (kHz), and the

@@ -976,7 +976,7 @@ pm_status pm_philox_blocks(pm_ctx *ctx, uint64_t seed, uint32_t human_id, uint32
 pm_status pm_probe_sfu(pm_ctx *ctx, int op, double *results_per_s)
 {
     if (!ctx || !results_per_s) return fail(PM_EINVAL, "ctx/results is NULL");
-    if (op < 0 || op > 2) return fail(PM_EINVAL, "op %d outside [0, 2]", op);
+    if (op < 0 || op > 5) return fail(PM_EINVAL, "op %d outside [0, 5]", op);
     DeviceScope dev(ctx->device);
     const int threads = 256, blocks = ctx->sm_count * 8, iters = 4096;
     pm_status st = ensure_stage(ctx, (size_t)blocks * threads * sizeof(float));
@@ -1001,7 +1001,8 @@ pm_status pm_probe_sfu(pm_ctx *ctx, int op, double *results_per_s)
     cudaEventDestroy(e1);
     cudaStreamDestroy(s);
     if (e != cudaSuccess) return cuda_fail(e, "sfu probe");
-    *results_per_s = (double)blocks * threads * iters * 8.0 / (best_ms * 1e-3);
+    const double per_instr = (op == 4) ? 2.0 : 1.0; // the packed FMA yields two results
+    *results_per_s = (double)blocks * threads * iters * 8.0 * per_instr / (best_ms * 1e-3);
     return PM_OK;
 }
 

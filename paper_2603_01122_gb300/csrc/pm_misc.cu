@@ -20,24 +20,41 @@ __global__ void philox_blocks_kernel(uint64_t seed, uint32_t human, uint32_t pur
     out[4 * (size_t)i + 3] = r.d;
 }
 
-// Eight independent dependency chains per thread of one SFU operation.
+// Eight independent dependency chains per thread of one operation: the SFU
+// (0 ex2, 1 sqrt, 2 rsqrt), the FP32 pipe (3 scalar FMA, 4 packed FMA on
+// pairs) or the integer pipe (5 add).
 template <int OP>
 __global__ void sfu_probe_kernel(int iters, float *sink)
 {
     float v[8];
+    f32x2 p[8];
+    uint32_t u[8];
+    const uint32_t inc = threadIdx.x | 1u;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) v[c] = 0.5f + 0.01f * (float)(threadIdx.x & 7) + 0.001f * (float)c;
+    for (int c = 0; c < 8; ++c) {
+        v[c] = 0.5f + 0.01f * (float)(threadIdx.x & 7) + 0.001f * (float)c;
+        p[c] = f2_pack(v[c], v[c] + 0.25f);
+        u[c] = threadIdx.x * 8u + (uint32_t)c;
+    }
+    const f32x2 M = f2_pack(0.999f, 0.998f), A = f2_pack(0.001f, 0.002f);
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             if (OP == 0) v[c] = ex2_approx(-v[c]);
             else if (OP == 1) v[c] = sqrt_approx(v[c]);
-            else v[c] = rsqrt_approx(v[c]);
+            else if (OP == 2) v[c] = rsqrt_approx(v[c]);
+            else if (OP == 3) v[c] = fmaf(v[c], 0.999f, 0.001f);
+            else if (OP == 4) p[c] = f2_fma(p[c], M, A);
+            else u[c] += inc;
         }
     }
     float s = 0.0f;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) s += v[c];
+    for (int c = 0; c < 8; ++c) {
+        float lo, hi;
+        f2_unpack(p[c], lo, hi);
+        s += v[c] + lo + hi + (float)u[c];
+    }
     sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
@@ -52,9 +69,14 @@ cudaError_t launch_philox_blocks(uint64_t seed, uint32_t human, uint32_t purpose
 
 cudaError_t launch_sfu_probe(int op, int blocks, int threads, int iters, float *sink, cudaStream_t s)
 {
-    if (op == 0) sfu_probe_kernel<0><<<blocks, threads, 0, s>>>(iters, sink);
-    else if (op == 1) sfu_probe_kernel<1><<<blocks, threads, 0, s>>>(iters, sink);
-    else sfu_probe_kernel<2><<<blocks, threads, 0, s>>>(iters, sink);
+    switch (op) {
+    case 0: sfu_probe_kernel<0><<<blocks, threads, 0, s>>>(iters, sink); break;
+    case 1: sfu_probe_kernel<1><<<blocks, threads, 0, s>>>(iters, sink); break;
+    case 2: sfu_probe_kernel<2><<<blocks, threads, 0, s>>>(iters, sink); break;
+    case 3: sfu_probe_kernel<3><<<blocks, threads, 0, s>>>(iters, sink); break;
+    case 4: sfu_probe_kernel<4><<<blocks, threads, 0, s>>>(iters, sink); break;
+    default: sfu_probe_kernel<5><<<blocks, threads, 0, s>>>(iters, sink); break;
+    }
     return cudaGetLastError();
 }
 

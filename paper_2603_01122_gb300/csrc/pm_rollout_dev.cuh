@@ -172,48 +172,38 @@ __device__ __forceinline__ int draw_heading(const HeadingTab &tab, uint64_t enab
 // -cb (d_k - ref) is <= 0 after rounding; the largest weight is then at least
 // 2^(-|cb| lb_gap) (callers use this form only where that is >= 1/2). A
 // common shift of all logits leaves the distribution of Eq. 2 unchanged.
-template <int KT>
-__device__ __forceinline__ int draw_heading_lb(const HeadingTab &tab, float s2, float x, float y, float gx, float gy,
-                                               float cb, uint32_t word)
+struct LbStep {
+    float dx, dy; // z - g
+    float D;      // ||z - g||^2 + s^2
+    float r;      // ||z - g||
+    float ref;    // reference distance (see above)
+};
+
+__device__ __forceinline__ LbStep lb_step(const HeadingTab &tab, float s2, float x, float y, float gx, float gy,
+                                          float cb)
 {
-    static_assert(KT % 4 == 0, "pairs of headings must not straddle the two summation chains");
-    const float dx = x - gx, dy = y - gy;
-    const float D = fmaf(dx, dx, fmaf(dy, dy, s2));
-    const float hD = 0.5f * rsqrt_approx(D);
-    const float r = sqrt_approx(fmaf(dx, dx, dy * dy));
-    const float margin = (r + tab.s) * 0x1p-20f;
-    const float ref = (cb >= 0.0f) ? fabsf(r - tab.s) - margin : r + tab.s + margin;
-    const f32x2 DX = f2_pack(dx, dx), DY = f2_pack(dy, dy);
-    const f32x2 DD = f2_pack(D, D), NDD = f2_pack(-D, -D), HD = f2_pack(hD, hD);
-    const f32x2 REF = f2_pack(ref, ref), NC = f2_pack(-cb, -cb);
-    const f32x2 SC = f2_pack(4194304.0f, 4194304.0f), MG = f2_pack(12582912.0f, 12582912.0f);
-    const f32x2 *TX = reinterpret_cast<const f32x2 *>(tab.tx);
-    const f32x2 *TY = reinterpret_cast<const f32x2 *>(tab.ty);
+    LbStep q;
+    q.dx = x - gx;
+    q.dy = y - gy;
+    q.D = fmaf(q.dx, q.dx, fmaf(q.dy, q.dy, s2));
+    q.r = sqrt_approx(fmaf(q.dx, q.dx, q.dy * q.dy));
+    const float margin = (q.r + tab.s) * 0x1p-20f;
+    q.ref = (cb >= 0.0f) ? fabsf(q.r - tab.s) - margin : q.r + tab.s + margin;
+    return q;
+}
+
+// Inverse CDF over the 22-bit fixed-point weights (bits = 0x4B400000 + w_k):
+// the smallest k with C_k > (u24 * S) >> 24, from two independent running
+// sums (headings [0, K/2) and [K/2, K)) whose totals are S0 and S1.
+template <int KT>
+__device__ __forceinline__ int select_fixed(const uint32_t (&bits)[KT], uint32_t S0, uint32_t S1, uint32_t word)
+{
     constexpr int H2 = KT / 2;
-    uint32_t bits[KT];
-    uint32_t S0 = 0u, S1 = 0u;
-#pragma unroll
-    for (int q = 0; q < KT / 2; ++q) {
-        const f32x2 P = f2_fma(TX[q], DX, f2_mul(TY[q], DY)); // 2 s e_k.(z - g), k = 2q, 2q+1
-        float x0, x1;
-        f2_unpack(f2_add(DD, P), x0, x1);
-        const float d0 = sqrt_approx(fabsf(x0)), d1 = sqrt_approx(fabsf(x1));
-        const f32x2 DK = f2_pack(d0, d1);
-        const f32x2 R = f2_sub(P, f2_fma(DK, DK, NDD));           // D + p - dk^2
-        const f32x2 U = f2_fma(R, HD, f2_sub(DK, REF));            // d_k - ref, corrected
-        float a0, a1;
-        f2_unpack(f2_mul(U, NC), a0, a1);                           // log2 weight, <= 0
-        float w0, w1;
-        f2_unpack(f2_fma(f2_pack(ex2_approx(a0), ex2_approx(a1)), SC, MG), w0, w1);
-        bits[2 * q] = __float_as_uint(w0);                          // 0x4B400000 + round(e * 2^22)
-        bits[2 * q + 1] = __float_as_uint(w1);
-        if (2 * q < H2) S0 += bits[2 * q] + bits[2 * q + 1];
-        else S1 += bits[2 * q] + bits[2 * q + 1];
-    }
     S0 -= (uint32_t)H2 * 0x4B400000u;
     S1 -= (uint32_t)(KT - H2) * 0x4B400000u;
     const uint32_t S = S0 + S1;
     const uint32_t thr = (uint32_t)(((uint64_t)(word >> 8) * (uint64_t)S) >> 24);
+    // C_k - thr - 1 once w_k is added: negative iff C_k <= thr
     uint32_t acc0 = ~thr, acc1 = ~thr + S0;
     int sel0 = 0, sel1 = 0;
 #pragma unroll
@@ -224,6 +214,53 @@ __device__ __forceinline__ int draw_heading_lb(const HeadingTab &tab, float s2, 
         sel1 += (int)(acc1 >> 31);
     }
     return sel0 + sel1;
+}
+
+// Bound-normalised draw with the distances from the approximate square root
+// and one Newton correction: with p_k = 2 s e_k.(z - g), d_k^2 = D + p_k and
+// the residual R_k = D + p_k - dk^2 of the approximation dk,
+//   -cb (d_k - ref) = R_k (-cb / 2d) + (dk (-cb) + cb ref).
+// K is a multiple of 4 and the headings are equally spaced, so heading
+// k + K/2 is -e_k exactly (the table is built by quarter turns) and shares
+// p_k with the opposite sign: one p serves two pairs of headings, whose
+// weights go to the two summation chains.
+template <int KT>
+__device__ __forceinline__ int draw_heading_lb(const HeadingTab &tab, const LbStep &q, float cb, uint32_t word)
+{
+    static_assert(KT % 4 == 0, "pairs of headings must not straddle the two summation chains");
+    const float hD = 0.5f * rsqrt_approx(q.D); // 1/(2 d), D >= s^2 > 0
+    const f32x2 DX = f2_pack(q.dx, q.dx), DY = f2_pack(q.dy, q.dy);
+    const f32x2 DD = f2_pack(q.D, q.D), NDD = f2_pack(-q.D, -q.D);
+    const f32x2 SC = f2_pack(4194304.0f, 4194304.0f), MG = f2_pack(12582912.0f, 12582912.0f);
+    const f32x2 *TX = reinterpret_cast<const f32x2 *>(tab.tx);
+    const f32x2 *TY = reinterpret_cast<const f32x2 *>(tab.ty);
+    constexpr int H2 = KT / 2;
+    uint32_t bits[KT];
+    uint32_t S0 = 0u, S1 = 0u;
+    const f32x2 HDNC = f2_pack(-cb * hD, -cb * hD), NHDNC = f2_pack(cb * hD, cb * hD);
+    const f32x2 NC = f2_pack(-cb, -cb), RC = f2_pack(cb * q.ref, cb * q.ref);
+#pragma unroll
+    for (int k2 = 0; k2 < KT / 4; ++k2) {
+        const f32x2 P = f2_fma(TX[k2], DX, f2_mul(TY[k2], DY)); // heading k; k + K/2 has -P
+        float x0, x1, y0, y1;
+        f2_unpack(f2_add(DD, P), x0, x1);
+        f2_unpack(f2_sub(DD, P), y0, y1);
+        const f32x2 DA = f2_pack(sqrt_approx(fabsf(x0)), sqrt_approx(fabsf(x1)));
+        const f32x2 DB = f2_pack(sqrt_approx(fabsf(y0)), sqrt_approx(fabsf(y1)));
+        float a0, a1, b0, b1;
+        f2_unpack(f2_fma(f2_sub(P, f2_fma(DA, DA, NDD)), HDNC, f2_fma(DA, NC, RC)), a0, a1);
+        f2_unpack(f2_fma(f2_add(P, f2_fma(DB, DB, NDD)), NHDNC, f2_fma(DB, NC, RC)), b0, b1);
+        float w0, w1, v0, v1;
+        f2_unpack(f2_fma(f2_pack(ex2_approx(a0), ex2_approx(a1)), SC, MG), w0, w1);
+        f2_unpack(f2_fma(f2_pack(ex2_approx(b0), ex2_approx(b1)), SC, MG), v0, v1);
+        bits[2 * k2] = __float_as_uint(w0);
+        bits[2 * k2 + 1] = __float_as_uint(w1);
+        bits[H2 + 2 * k2] = __float_as_uint(v0);
+        bits[H2 + 2 * k2 + 1] = __float_as_uint(v1);
+        S0 += bits[2 * k2] + bits[2 * k2 + 1];
+        S1 += bits[H2 + 2 * k2] + bits[H2 + 2 * k2 + 1];
+    }
+    return select_fixed<KT>(bits, S0, S1, word);
 }
 
 // Component flag of the belief table: the bound-normalised draw keeps the
@@ -239,7 +276,9 @@ __device__ __forceinline__ int draw(const HeadingTab &tab, uint64_t enabled, flo
                                     float gy, float cb, bool lb, uint32_t word)
 {
     if constexpr (FULL && (KT % 4 == 0)) {
-        if (lb) return draw_heading_lb<KT>(tab, s2, x, y, gx, gy, cb, word);
+        if (lb) {
+            return draw_heading_lb<KT>(tab, lb_step(tab, s2, x, y, gx, gy, cb), cb, word);
+        }
     }
     return draw_heading<KT, FULL>(tab, enabled, s2, x, y, gx, gy, cb, word);
 }
