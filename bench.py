@@ -577,7 +577,7 @@ def run_native(args):
             "gpu_launches": 2 * args.steps,
             "wall_s": wall,
             "breakdown_ms": {"posterior": statistics.mean(post_ms), "rollout": statistics.mean(roll_ms)},
-            "roofline": {"bound": "alu", "kernel": "rollout_kernel<36>", "achieved": achieved,
+            "roofline": {"bound": "alu", "kernel": "rollout_warp_kernel<36,true>", "achieved": achieved,
                          "peak": peak, "unit": "G SFU results/s", "frac": achieved / peak,
                          "traffic": traffic,
                          "peak_source": "measured by pm_probe_sfu (ex2/sqrt 1:1 harmonic mean); "

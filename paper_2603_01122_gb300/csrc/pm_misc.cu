@@ -22,14 +22,13 @@ __global__ void philox_blocks_kernel(uint64_t seed, uint32_t human, uint32_t pur
 
 // Eight independent dependency chains per thread of one operation: the SFU
 // (0 ex2, 1 sqrt, 2 rsqrt), the FP32 pipe (3 scalar FMA, 4 packed FMA on
-// pairs) or the integer pipe (5 add).
+// pairs) or the integer pipe (5 add; chains in dependent pairs).
 template <int OP>
 __global__ void sfu_probe_kernel(int iters, float *sink)
 {
     float v[8];
     f32x2 p[8];
     uint32_t u[8];
-    const uint32_t inc = threadIdx.x | 1u;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         v[c] = 0.5f + 0.01f * (float)(threadIdx.x & 7) + 0.001f * (float)c;
@@ -45,7 +44,7 @@ __global__ void sfu_probe_kernel(int iters, float *sink)
             else if (OP == 2) v[c] = rsqrt_approx(v[c]);
             else if (OP == 3) v[c] = fmaf(v[c], 0.999f, 0.001f);
             else if (OP == 4) p[c] = f2_fma(p[c], M, A);
-            else u[c] += inc;
+            else u[c] += u[c ^ 1]; // four chains of dependent pairs (no closed form)
         }
     }
     float s = 0.0f;

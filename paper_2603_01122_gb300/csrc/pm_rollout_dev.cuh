@@ -192,28 +192,53 @@ __device__ __forceinline__ LbStep lb_step(const HeadingTab &tab, float s2, float
     return q;
 }
 
-// Inverse CDF over the 22-bit fixed-point weights (bits = 0x4B400000 + w_k):
-// the smallest k with C_k > (u24 * S) >> 24, from two independent running
-// sums (headings [0, K/2) and [K/2, K)) whose totals are S0 and S1.
+// Segments of the running sums of the inverse CDF: KT/G segments of G
+// headings (G even, so a pair of headings never straddles two), each an
+// independent chain of additions.
 template <int KT>
-__device__ __forceinline__ int select_fixed(const uint32_t (&bits)[KT], uint32_t S0, uint32_t S1, uint32_t word)
+struct CdfSegs {
+    static constexpr int G = (KT == 8) ? 4 : (KT == 16) ? 4 : (KT == 36) ? 6 : 8;
+    static constexpr int N = KT / G;
+    static_assert(KT % G == 0 && G % 2 == 0, "segments hold whole pairs");
+};
+
+// Inverse CDF over the 22-bit fixed-point weights (bits = 0x4B400000 + w_k):
+// the smallest k with C_k > (u24 * S) >> 24. Seg[q] is the raw sum of the
+// bits of segment q; each segment scans its own headings from the running
+// sum at its start, so the scan is KT/G short chains instead of one long one.
+template <int KT>
+__device__ __forceinline__ int select_fixed(const uint32_t (&bits)[KT], const uint32_t (&seg)[CdfSegs<KT>::N],
+                                            uint32_t word)
 {
-    constexpr int H2 = KT / 2;
-    S0 -= (uint32_t)H2 * 0x4B400000u;
-    S1 -= (uint32_t)(KT - H2) * 0x4B400000u;
-    const uint32_t S = S0 + S1;
+    constexpr int G = CdfSegs<KT>::G, NS = CdfSegs<KT>::N;
+    uint32_t start[NS]; // C at the start of each segment
+    uint32_t S = 0u;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+        start[q] = S;
+        S += seg[q] - (uint32_t)G * 0x4B400000u;
+    }
     const uint32_t thr = (uint32_t)(((uint64_t)(word >> 8) * (uint64_t)S) >> 24);
     // C_k - thr - 1 once w_k is added: negative iff C_k <= thr
-    uint32_t acc0 = ~thr, acc1 = ~thr + S0;
-    int sel0 = 0, sel1 = 0;
+    int sel[NS];
+    uint32_t acc[NS];
 #pragma unroll
-    for (int k = 0; k < H2; ++k) {
-        acc0 += bits[k] - 0x4B400000u;
-        sel0 += (int)(acc0 >> 31);
-        acc1 += bits[H2 + k] - 0x4B400000u;
-        sel1 += (int)(acc1 >> 31);
+    for (int q = 0; q < NS; ++q) {
+        acc[q] = start[q] + ~thr;
+        sel[q] = 0;
     }
-    return sel0 + sel1;
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            acc[q] += bits[q * G + k] - 0x4B400000u;
+            sel[q] += (int)(acc[q] >> 31);
+        }
+    }
+    int total = 0;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) total += sel[q];
+    return total;
 }
 
 // Bound-normalised draw with the distances from the approximate square root
@@ -235,8 +260,11 @@ __device__ __forceinline__ int draw_heading_lb(const HeadingTab &tab, const LbSt
     const f32x2 *TX = reinterpret_cast<const f32x2 *>(tab.tx);
     const f32x2 *TY = reinterpret_cast<const f32x2 *>(tab.ty);
     constexpr int H2 = KT / 2;
+    constexpr int G = CdfSegs<KT>::G;
     uint32_t bits[KT];
-    uint32_t S0 = 0u, S1 = 0u;
+    uint32_t seg[CdfSegs<KT>::N];
+#pragma unroll
+    for (int q = 0; q < CdfSegs<KT>::N; ++q) seg[q] = 0u;
     const f32x2 HDNC = f2_pack(-cb * hD, -cb * hD), NHDNC = f2_pack(cb * hD, cb * hD);
     const f32x2 NC = f2_pack(-cb, -cb), RC = f2_pack(cb * q.ref, cb * q.ref);
 #pragma unroll
@@ -257,10 +285,10 @@ __device__ __forceinline__ int draw_heading_lb(const HeadingTab &tab, const LbSt
         bits[2 * k2 + 1] = __float_as_uint(w1);
         bits[H2 + 2 * k2] = __float_as_uint(v0);
         bits[H2 + 2 * k2 + 1] = __float_as_uint(v1);
-        S0 += bits[2 * k2] + bits[2 * k2 + 1];
-        S1 += bits[H2 + 2 * k2] + bits[H2 + 2 * k2 + 1];
+        seg[(2 * k2) / G] += bits[2 * k2] + bits[2 * k2 + 1];
+        seg[(H2 + 2 * k2) / G] += bits[H2 + 2 * k2] + bits[H2 + 2 * k2 + 1];
     }
-    return select_fixed<KT>(bits, S0, S1, word);
+    return select_fixed<KT>(bits, seg, word);
 }
 
 // Component flag of the belief table: the bound-normalised draw keeps the
