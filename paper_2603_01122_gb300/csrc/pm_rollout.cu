@@ -1,23 +1,24 @@
 // pm_rollout.cu -- Algorithm 1 (hardware-accelerated human prediction) with the
 // bootstrapped belief of Sec. III-B and the per-step emplacement onto an
-// occupancy grid, as one fused kernel: one thread per particle.
+// occupancy grid, as one fused kernel: one lane per particle, persistent
+// warps.
 //
 // Per particle and step (the hot loop), for every heading k:
 //   distance from the next state to the goal, d_k = sqrt(D + 2 s e_k.(z - g))
-//   with D = ||z - g||^2 + s^2, computed as a difference to a reference
-//   distance plus one Newton correction, so that beta*w2*(d_j - d_k) keeps FP32
-//   relative precision even when ||z - g|| >> s (a plain FP32 distance of a
-//   5 m vector carries 5e-7 m of rounding, i.e. 5e-5 of logit at beta = 100);
-//   logits beta*Q_k up to a common shift are -beta*w2*d_k (w1 cancels, Eq. 2);
-//   the largest logit is found first, then ex2.approx on the SFU;
+//   with D = ||z - g||^2 + s^2, taken from the approximate square root plus
+//   one Newton correction from its residual, so that beta*w2*(d_j - d_k)
+//   keeps FP32 relative precision even when ||z - g|| >> s (a plain FP32
+//   distance of a 5 m vector carries 5e-7 m of rounding, i.e. 5e-5 of logit at
+//   beta = 100); logits beta*Q_k up to a common shift are -beta*w2*d_k (w1
+//   cancels, Eq. 2), shifted by a bound of the extreme distance (or the exact
+//   extreme) so that every exponent is <= 0, then ex2.approx on the SFU;
 //   weights are rounded to 22-bit fixed point so that the running sums C_k of
 //   the inverse CDF are exact integers (the sampling decision then depends
 //   only on the rounded weights, not on summation order).
 // The drawn heading moves the FP32 state by one Euler step (Eq. 1); the state
-// is binned with FP32 operations (x - x0) * inv_res and counted in a
-// per-CTA shared-memory window (16-bit counts packed two per word) whose
-// touched cells are listed on first touch and flushed with one global
-// reduction per touched cell at the end of the step.
+// is binned with FP32 operations (x - x0) * inv_res and the lanes of the warp
+// that land in the same cell are combined (match.any) into one global
+// reduction per cell and step.
 #include <cuda_runtime.h>
 
 #include "pm_internal.cuh"

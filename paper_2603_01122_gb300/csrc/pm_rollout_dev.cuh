@@ -303,12 +303,16 @@ template <int KT, bool FULL>
 __device__ __forceinline__ int draw(const HeadingTab &tab, uint64_t enabled, float s2, float x, float y, float gx,
                                     float gy, float cb, bool lb, uint32_t word)
 {
+    int k;
     if constexpr (FULL && (KT % 4 == 0)) {
-        if (lb) {
-            return draw_heading_lb<KT>(tab, lb_step(tab, s2, x, y, gx, gy, cb), cb, word);
-        }
+        if (lb) k = draw_heading_lb<KT>(tab, lb_step(tab, s2, x, y, gx, gy, cb), cb, word);
+        else k = draw_heading<KT, FULL>(tab, enabled, s2, x, y, gx, gy, cb, word);
+    } else {
+        k = draw_heading<KT, FULL>(tab, enabled, s2, x, y, gx, gy, cb, word);
     }
-    return draw_heading<KT, FULL>(tab, enabled, s2, x, y, gx, gy, cb, word);
+    // k < K whenever the total weight S > 0, which finite inputs guarantee;
+    // the clamp keeps the step-table read in bounds for any input
+    return min(k, KT - 1);
 }
 
 // Per-tile state of one human for rollout_tile.
