@@ -315,6 +315,7 @@ def run_extra(args, pm, ctx, torch, dev, stream):
     t0 = time.perf_counter()
     pm.pm_batch_autotune(batch, stream)
     tune_s = time.perf_counter() - t0
+    tuned = pm.pm_batch_get_config(batch)
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.stream(stream):
         for r in recs:
@@ -331,7 +332,8 @@ def run_extra(args, pm, ctx, torch, dev, stream):
                       "batched_ms": batch_ms, "batched_particle_steps_per_s": steps / (batch_ms * 1e-3),
                       "plain_ms": plain_ms, "plain_particle_steps_per_s": steps / (plain_ms * 1e-3),
                       "speedup_vs_plain": plain_ms / batch_ms, "autotune_s": tune_s,
-                      "tuned": None,
+                      "tuned": tuned,
+                      "rate_vs_plain_small": steps / (batch_ms * 1e-3) / out["plain_small"]["particle_steps_per_s"],
                       "config": "16 humans, G~U{2..6}, N~U[20k,200k], T~U{50..300}, K=36, 400x400 grid, "
                                 "graph of belief update + persistent rollout"}
     del recs
@@ -387,6 +389,7 @@ def run_extra(args, pm, ctx, torch, dev, stream):
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "max_ms": float(lat.max() * 1e3),
             "particle_steps_per_frame": ps, "particle_steps_per_s": ps / float(np.median(lat)),
             "plain_path_ms_per_frame": plain_ms, "speedup_vs_plain": plain_ms / float(np.median(lat) * 1e3),
+            "rate_vs_plain_small": ps / float(np.median(lat)) / out["plain_small"]["particle_steps_per_s"],
             "target": "p99 < 8 ms at 64 humans",
             "config": "64 humans, K=36, N=50k, T=150, 121x121 window at 0.05 m, 1 observation/frame, graph replay"}
         if args.serving_seconds > 0:
