@@ -26,6 +26,10 @@
 namespace pm {
 namespace {
 
+// ln 2 split so that a product with a small integer keeps its error term
+constexpr float kLn2Hi = 0.693147182464599609375f;   // nearest float to ln 2
+constexpr float kLn2Lo = -1.904654323148236e-09f;    // ln 2 - kLn2Hi
+
 __device__ __forceinline__ float warp_max(float v)
 {
 #pragma unroll
@@ -111,15 +115,22 @@ __device__ __forceinline__ float rel_logit(float bw, float two_s, float D, float
 __device__ __forceinline__ void posterior_chunk(const PosteriorArgs &a, const PostHuman &h, int chunk, int nchunk)
 {
     __shared__ int last;
+    __shared__ float2 su[kMaxK]; // unit heading vectors
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int J = h.G * h.B;
     const int t0 = chunk * h.steps_per_chunk;
     const int t1 = min(h.n_obs, t0 + h.steps_per_chunk);
+    // the table goes through shared memory once per CTA: lanes reading
+    // different entries of the kernel parameters would be served one address
+    // at a time by the constant cache
+    __syncthreads(); // the previous chunk of this CTA (batched form) is done with su
+    for (int k = threadIdx.x; k < kMaxK; k += blockDim.x) su[k] = make_float2(a.ux[k], a.uy[k]);
+    __syncthreads();
     const int k0 = lane, k1 = lane + 32;
     const bool on0 = k0 < a.K && ((a.enabled >> k0) & 1ull);
     const bool on1 = k1 < a.K && ((a.enabled >> k1) & 1ull);
-    const float ux0 = on0 ? a.ux[k0] : 0.0f, uy0 = on0 ? a.uy[k0] : 0.0f;
-    const float ux1 = on1 ? a.ux[k1] : 0.0f, uy1 = on1 ? a.uy[k1] : 0.0f;
+    const float ux0 = on0 ? su[k0].x : 0.0f, uy0 = on0 ? su[k0].y : 0.0f;
+    const float ux1 = on1 ? su[k1].x : 0.0f, uy1 = on1 ? su[k1].y : 0.0f;
 
     for (int j = warp; j < J; j += nwarp) {
         const int g = j / h.B, b = j - g * h.B;
@@ -150,18 +161,21 @@ __device__ __forceinline__ void posterior_chunk(const PosteriorArgs &a, const Po
             p[2] = acc.ph;
             p[3] = acc.pl;
             p[4] = __int_as_float(acc.e);
+            __threadfence(); // the partials are visible before this CTA takes its ticket
         }
     }
 
     // the last chunk to finish combines and normalises
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = (atomicAdd(h.ticket, 1u) == (unsigned)(nchunk - 1));
     __syncthreads();
     if (!last) return;
     __threadfence();
 
-    double *L = reinterpret_cast<double *>(h.part + ((5 * (size_t)nchunk * J + 1) & ~(size_t)1)); // [J], 8-byte aligned
+    // L_j = log b_j + sum_t l_t(j) as a double-float pair (hi, lo) in shared
+    // memory; the fold and the normalisation stay in FP32 arithmetic (this
+    // GPU's FP64 unit retires about two lanes per clock per SM)
+    __shared__ float2 L[kMaxJ];
     for (int j = warp; j < J; j += nwarp) {
         Acc acc;
         acc_init(acc);
@@ -181,24 +195,38 @@ __device__ __forceinline__ void posterior_chunk(const PosteriorArgs &a, const Po
             acc_merge(acc, q);
         }
         if (lane == 0) {
-            // sum_t l_t(j) = -(sum_t m_t) - log(prod_t S_t)
-            const double logS = (double)acc.e * 0.6931471805599453 + (double)log1pf(acc.ph - 1.0f) +
-                                (double)acc.pl / (double)acc.ph;
-            L[j] = (double)h.log_b[j] - ((double)acc.mh + (double)acc.ml) - logS;
+            const float lb = h.log_b[j];
+            if (lb == -INFINITY) {
+                L[j] = make_float2(-INFINITY, 0.0f);
+            } else {
+                // sum_t l_t(j) = -(sum_t m_t) - log(prod_t S_t),
+                // log(prod_t S_t) = e ln2 + log1p(ph - 1) + pl / ph
+                const float ef = (float)acc.e;
+                const float p = ef * kLn2Hi;
+                const float perr = fmaf(ef, kLn2Hi, -p) + ef * kLn2Lo; // e ln2 = p + perr
+                Acc r;
+                r.mh = lb;
+                r.ml = 0.0f;
+                acc_add(r, -acc.mh);
+                acc_add(r, -acc.ml);
+                acc_add(r, -p);
+                acc_add(r, -(perr + log1pf(acc.ph - 1.0f) + acc.pl / acc.ph));
+                L[j] = make_float2(r.mh, r.ml);
+            }
         }
     }
     __syncthreads();
     if (warp == 0) {
-        double mx = -INFINITY;
-        for (int j = lane; j < J; j += 32) mx = fmax(mx, L[j]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        float mx = -INFINITY;
+        for (int j = lane; j < J; j += 32) mx = fmaxf(mx, L[j].x);
+        mx = warp_max(mx);
         float se = 0.0f;
         for (int j = lane; j < J; j += 32)
-            if (L[j] != -INFINITY) se += expf((float)(L[j] - mx));
+            if (L[j].x != -INFINITY) se += expf((L[j].x - mx) + L[j].y);
         se = warp_sum(se);
-        const double lse = mx + log((double)se);
-        for (int j = lane; j < J; j += 32) h.log_b[j] = (float)(L[j] - lse);
+        const float lse = logf(se); // se in [1, J]
+        for (int j = lane; j < J; j += 32)
+            h.log_b[j] = (L[j].x == -INFINITY || mx == -INFINITY) ? -INFINITY : ((L[j].x - mx) + L[j].y) - lse;
         if (lane == 0) *h.ticket = 0u;
     }
 }
@@ -236,7 +264,7 @@ __global__ void __launch_bounds__(1024) posterior_batch_kernel(const __grid_cons
 
 size_t posterior_scratch_bytes(int n_chunks, int J)
 {
-    return ((5 * (size_t)n_chunks * J + 1) & ~(size_t)1) * sizeof(float) + (size_t)J * sizeof(double);
+    return (5 * (size_t)n_chunks * J) * sizeof(float);
 }
 
 int posterior_chunks(int n_obs, int *steps_per_chunk)
