@@ -72,7 +72,11 @@ typedef struct pm_model {
 
 /* Occupancy grid: cell (cx, cy) covers [x0 + cx*res, x0 + (cx+1)*res) x
  * [y0 + cy*res, y0 + (cy+1)*res), 0 <= cx < W, 0 <= cy < H. A state is binned
- * with FP32 operations: cx = floor((x - x0) * inv_res), inv_res = 1.0f/res. */
+ * with FP32 operations: cx = floor((x - x0) * inv_res), inv_res = 1.0f/res.
+ * W and H are at most 2^22 (PM_EINVAL otherwise), and a state more than 2^22
+ * cells from (x0, y0) along either axis counts as outside every grid (this
+ * also bounds the windows of the batched form: a centred window is useful
+ * only for humans within 2^22 cells of the origin, e.g. 209 km at 5 cm). */
 typedef struct pm_grid {
     float x0;
     float y0;

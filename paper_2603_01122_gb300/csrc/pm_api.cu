@@ -155,7 +155,7 @@ pm_status check_grid(const pm_grid *g)
     if (!g) return fail(PM_EINVAL, "grid is NULL");
     if (!finite_pos(g->res) || !std::isfinite(g->x0) || !std::isfinite(g->y0))
         return fail(PM_EINVAL, "grid origin must be finite and res > 0");
-    if (g->W < 1 || g->H < 1 || (long long)g->W * g->H > (1LL << 31))
+    if (g->W < 1 || g->H < 1 || g->W > (1 << 22) || g->H > (1 << 22) || (long long)g->W * g->H > (1LL << 31))
         return fail(PM_EINVAL, "grid W=%d H=%d out of range", g->W, g->H);
     return PM_OK;
 }
@@ -416,6 +416,9 @@ pm_status check_human(const pm_human &h, int i)
     if (st != PM_OK) return fail(st, "human %d: %s", i, g_err.c_str());
     if (h.center && (h.grid.W % 2 == 0 || h.grid.H % 2 == 0))
         return fail(PM_EINVAL, "human %d: a centred output window needs odd W and H", i);
+    if (!h.center && (std::abs((long long)h.cx_off) + h.grid.W > (1LL << 22) ||
+                      std::abs((long long)h.cy_off) + h.grid.H > (1LL << 22)))
+        return fail(PM_EINVAL, "human %d: window offset more than 2^22 cells from the grid origin", i);
     return PM_OK;
 }
 

@@ -560,15 +560,20 @@ __device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t ena
             if (c.hist) {
                 const float vx = __fmul_rn(__fsub_rn(x, c.gx0), c.inv_res);
                 const float vy = __fmul_rn(__fsub_rn(y, c.gy0), c.inv_res);
-                const int cx = __float2int_rd(vx) - c.cx_off;
-                const int cy = __float2int_rd(vy) - c.cy_off;
-                const bool in = (vx == vx) && (vy == vy) && cx >= 0 && cx < c.W && cy >= 0 && cy < c.H;
+                // floor(v) for |v| < 2^22 on the FP32 pipe: v + 1.5 * 2^23 rounded
+                // down is exact and holds floor(v) in its low mantissa bits;
+                // larger |v| and NaN are outside every grid (W, H <= 2^22)
+                const int cx = (__float_as_int(__fadd_rd(vx, 12582912.0f)) - 0x4B400000) - c.cx_off;
+                const int cy = (__float_as_int(__fadd_rd(vy, 12582912.0f)) - 0x4B400000) - c.cy_off;
+                const bool in = fabsf(vx) < 4194304.0f && fabsf(vy) < 4194304.0f && cx >= 0 && cx < c.W &&
+                                cy >= 0 && cy < c.H;
                 key = in ? (uint32_t)(cy * c.W + cx) : 0xFFFFFFFEu;
             }
         }
         if (c.hist) {
             const uint32_t peers = __match_any_sync(0xffffffffu, key);
-            if (key != 0xFFFFFFFFu && (__ffs(peers) - 1) == lane) {
+            // the lowest lane of each group of equal keys adds the group's size
+            if (key != 0xFFFFFFFFu && (peers & ((1u << lane) - 1u)) == 0u) {
                 if (key == 0xFFFFFFFEu) red_add(c.oob + (t - 1), (uint32_t)__popc(peers));
                 else red_add(c.counts + (size_t)(t - 1) * plane + key, (uint32_t)__popc(peers));
             }

@@ -328,7 +328,7 @@ def test_invalid_arguments_rejected(ctx):
     bad = [
         dict(n_particles=0), dict(horizon=0), dict(horizon=pm.PM_MAX_HORIZON + 1),
         dict(z0x=float("nan")), dict(grid=pm.make_grid(0, 0, 0.0, 10, 10)),
-        dict(grid=pm.make_grid(0, 0, 0.1, 0, 10)),
+        dict(grid=pm.make_grid(0, 0, 0.1, 0, 10)), dict(grid=pm.make_grid(0, 0, 0.1, (1 << 22) + 1, 1)),
     ]
     for kw in bad:
         args = dict(n_particles=100, horizon=4, z0x=0.0, grid=g)
