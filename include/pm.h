@@ -312,6 +312,34 @@ pm_status pm_loglik_backward(pm_ctx *ctx, const pm_model *model, int32_t M, cons
 pm_status pm_update_posterior_noalloc(const pm_model *model, const float *obs_xy, int32_t n_obs,
                                       float *log_belief, void *stream);
 
+/* ---- grid epilogue: smoothing and multi-human union ---------------------- */
+
+/* Gaussian convolution of one human's occupancy (Sec. III-B; the particles'
+ * point masses are spread around their cells before the planner reads the
+ * grid). prob[t][y][x] = sum_{i,j} w_i w_j counts[t][y+i][x+j] / n_particles
+ * over the grid (cells off the grid count 0: mass blurred past the edge is
+ * dropped), w_{-R..R} = exp(-i^2 / (2 sigma^2)) normalised to sum 1, R =
+ * ceil(3 sigma) computed in double from the float sigma_cells, which must
+ * satisfy 0 <= 3 sigma <= 16 (so R <= 16 cells; 0 = normalisation only). counts: device [horizon][grid->H][grid->W] (as written by
+ * pm_predict_occupancy); prob: device float [horizon][grid->H][grid->W],
+ * written entirely. Stream-ordered; PM_EINVAL for bad sizes or sigma. */
+pm_status pm_smooth_occupancy(pm_ctx *ctx, const uint32_t *counts, int32_t n_particles, int32_t horizon,
+                              const pm_grid *grid, float sigma_cells, float *prob, void *stream);
+
+/* Multi-human prediction on one shared grid (Sec. IV-B): every human of the
+ * batch contributes its occupancy, blurred as pm_smooth_occupancy does (its
+ * window widened by R cells, so mass blurred past the window is kept), at its
+ * window's cell offset (cx_off, cy_off, or centred on its start cell), and
+ * prob[t][y][x] is the pointwise maximum over the humans whose horizon
+ * exceeds t (0 where none reaches). grid: the shared grid; every human's
+ * grid must have the same origin and resolution. prob: device float
+ * [horizon][grid->H][grid->W], written entirely. Reads the batch's device
+ * descriptors, so it may be captured in the same CUDA graph as
+ * pm_batch_predict (after it on the stream). PM_EINVAL for mismatched grids,
+ * bad sizes or sigma. */
+pm_status pm_batch_union(pm_batch *b, float sigma_cells, int32_t horizon, const pm_grid *grid, float *prob,
+                         void *stream);
+
 /* ---- checks and measurement ---------------------------------------------- */
 
 /* Raw Philox4x64-10 blocks for counters (particle0 + i, block, purpose, 0),

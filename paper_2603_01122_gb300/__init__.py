@@ -72,6 +72,8 @@ def _signatures(lib):
         "pm_batch_get_config": ([_vp] + [P(C.c_int32)] * 4, C.c_int),
         "pm_batch_set_config": ([_vp] + [C.c_int32] * 4, C.c_int),
         "pm_batch_destroy": ([_vp], None),
+        "pm_smooth_occupancy": ([_vp, _vp, C.c_int32, C.c_int32, P(pm_grid), C.c_float, _vp, _vp], C.c_int),
+        "pm_batch_union": ([_vp, C.c_float, C.c_int32, P(pm_grid), _vp, _vp], C.c_int),
         "pm_loglik_forward": ([_vp, P(pm_model), C.c_int32, _vp, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
         "pm_loglik_backward": ([_vp, P(pm_model), C.c_int32, _vp, C.c_int32, _vp, _vp, C.c_float, _vp, _vp,
                                 _vp, _vp, _vp], C.c_int),
@@ -224,6 +226,16 @@ def pm_batch_update_posterior(batch, stream=None):
 
 def pm_batch_predict(batch, stream=None):
     _check(library().pm_batch_predict(batch, _stream(stream)))
+
+
+def pm_smooth_occupancy(ctx, counts, n_particles, horizon, grid, sigma_cells, prob, stream=None):
+    _check(library().pm_smooth_occupancy(ctx, _p(counts), int(n_particles), int(horizon), C.byref(grid),
+                                         float(sigma_cells), _p(prob), _stream(stream)))
+
+
+def pm_batch_union(batch, sigma_cells, horizon, grid, prob, stream=None):
+    _check(library().pm_batch_union(batch, float(sigma_cells), int(horizon), C.byref(grid), _p(prob),
+                                    _stream(stream)))
 
 
 def pm_batch_autotune(batch, stream=None):

@@ -856,6 +856,85 @@ pm_status pm_batch_predict(pm_batch *b, void *stream)
     return batch_predict_impl(b, (cudaStream_t)stream);
 }
 
+namespace {
+
+// Blur taps w_{-R..R} of the truncated, normalised Gaussian (computed in double).
+pm_status smooth_taps(float sigma, pm::SmoothArgs &a)
+{
+    if (!(sigma >= 0.0f) || !(3.0 * (double)sigma <= (double)pm::kMaxSmoothR))
+        return fail(PM_EINVAL, "sigma_cells=%g: need 0 <= ceil(3 sigma) <= %d", (double)sigma, pm::kMaxSmoothR);
+    if (sigma == 0.0f) {
+        a.R = 0;
+        a.w[0] = 1.0f;
+        return PM_OK;
+    }
+    const int R = (int)std::ceil(3.0 * (double)sigma); // <= kMaxSmoothR by the check above
+    double w[2 * pm::kMaxSmoothR + 1], sum = 0.0;
+    for (int i = -R; i <= R; ++i) sum += (w[i + R] = std::exp(-(double)i * i / (2.0 * (double)sigma * sigma)));
+    for (int i = 0; i <= 2 * R; ++i) a.w[i] = (float)(w[i] / sum);
+    a.R = R;
+    return PM_OK;
+}
+
+} // namespace
+
+pm_status pm_smooth_occupancy(pm_ctx *ctx, const uint32_t *counts, int32_t n_particles, int32_t horizon,
+                              const pm_grid *grid, float sigma_cells, float *prob, void *stream)
+{
+    if (!ctx || !counts || !prob) return fail(PM_EINVAL, "ctx/counts/prob is NULL");
+    if (n_particles < 1) return fail(PM_EINVAL, "n_particles=%d must be >= 1", n_particles);
+    if (horizon < 1 || horizon > PM_MAX_HORIZON) return fail(PM_EINVAL, "horizon=%d out of range", horizon);
+    pm_status st = check_grid(grid);
+    if (st != PM_OK) return st;
+    pm::SmoothArgs a;
+    std::memset(&a, 0, sizeof a);
+    st = smooth_taps(sigma_cells, a);
+    if (st != PM_OK) return st;
+    a.single.counts = counts;
+    a.single.inv_n = 1.0f / (float)n_particles;
+    a.single.T = horizon;
+    a.single.W = grid->W;
+    a.single.H = grid->H;
+    a.out = prob;
+    a.T = horizon;
+    a.W = grid->W;
+    a.H = grid->H;
+    DeviceScope dev(ctx->device);
+    cudaGetLastError();
+    cudaError_t e = pm::launch_smooth_union(a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "smoothing launch");
+    return PM_OK;
+}
+
+pm_status pm_batch_union(pm_batch *b, float sigma_cells, int32_t horizon, const pm_grid *grid, float *prob,
+                         void *stream)
+{
+    if (!b || !prob) return fail(PM_EINVAL, "batch/prob is NULL");
+    if (horizon < 1 || horizon > PM_MAX_HORIZON) return fail(PM_EINVAL, "horizon=%d out of range", horizon);
+    pm_status st = check_grid(grid);
+    if (st != PM_OK) return st;
+    for (size_t i = 0; i < b->humans.size(); ++i) {
+        const pm_grid &g = b->humans[i].grid;
+        if (g.x0 != grid->x0 || g.y0 != grid->y0 || g.res != grid->res)
+            return fail(PM_EINVAL, "human %zu: grid origin/resolution differ from the shared grid", i);
+    }
+    pm::SmoothArgs a;
+    std::memset(&a, 0, sizeof a);
+    st = smooth_taps(sigma_cells, a);
+    if (st != PM_OK) return st;
+    a.humans = b->d_humans;
+    a.n_humans = b->d_meta + 1;
+    a.out = prob;
+    a.T = horizon;
+    a.W = grid->W;
+    a.H = grid->H;
+    DeviceScope dev(b->ctx->device);
+    cudaGetLastError();
+    cudaError_t e = pm::launch_smooth_union(a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "union launch");
+    return PM_OK;
+}
+
 pm_status pm_batch_get_config(const pm_batch *b, int32_t *threads, int32_t *shared_window, int32_t *ctas_per_sm,
                               int32_t *window_kib)
 {

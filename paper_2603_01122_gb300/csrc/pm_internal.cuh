@@ -168,7 +168,7 @@ struct PosteriorArgs {
     int n_obs;
     int steps_per_chunk; // observed steps handled by one CTA
     float *log_b;
-    float *part;         // scratch: per (chunk, component) accumulators, then [J] doubles
+    float *part;         // scratch: per (chunk, component) accumulators
     unsigned *ticket;    // scratch: chunks finished so far (0 between calls)
 };
 
@@ -227,6 +227,26 @@ struct BatchHuman {
     uint32_t *oob;
 };
 
+// Grid epilogue (Gaussian smoothing, Sec. III-B; max-union, Sec. IV-B).
+constexpr int kMaxSmoothR = 16; // blur radius ceil(3 sigma) in cells
+
+struct SmoothSrc {
+    const uint32_t *counts; // [T][H][W]
+    float inv_n;            // 1 / particles
+    int T, W, H;
+    int ox, oy;             // window cell (x, y) = shared cell (x + ox, y + oy)
+};
+
+struct SmoothArgs {
+    const BatchHuman *humans; // batched source (device), or nullptr: `single`
+    const int *n_humans;      // device: live humans of the batch
+    SmoothSrc single;
+    float w[2 * kMaxSmoothR + 1]; // normalised taps w_{-R..R}
+    int R;
+    float *out; // shared grid [T][H][W]
+    int T, W, H;
+};
+
 struct BatchArgs {
     HeadingTab tab;
     uint64_t enabled;
@@ -251,6 +271,7 @@ struct RolloutShape {
 // Launch wrappers (defined next to their kernels).
 // `head` is a zeroed device counter of 32-particle chunks.
 cudaError_t launch_rollout(const RolloutArgs &a, unsigned *head, int sm_count, cudaStream_t s);
+cudaError_t launch_smooth_union(const SmoothArgs &a, cudaStream_t s);
 size_t rollout_static_smem_estimate();
 cudaError_t launch_posterior(const PosteriorArgs &a, int n_chunks, cudaStream_t s);
 int posterior_chunks(int n_obs, int *steps_per_chunk);
