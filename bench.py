@@ -37,6 +37,19 @@ sys.path.insert(0, ROOT)
 import workloads  # noqa: E402
 
 METRIC = "particle-steps/s"
+
+
+def _measured_peak(key, default):
+    """A measured peak of this GPU type from MEASURED_PEAKS.json at the
+    repository root (copy bandwidth, bf16 GEMM), else the given value."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key])
+    except (OSError, ValueError, KeyError, TypeError):
+        return default
+
+
+HBM_PEAK_GBS = _measured_peak("hbm_gbs", 6794.5)
 ROLLOUT_SOURCES = ["paper_2603_01122_gb300/csrc/pm_rollout.cu", "paper_2603_01122_gb300/csrc/pm_rollout_dev.cuh",
                    "paper_2603_01122_gb300/csrc/pm_internal.cuh"]
 
@@ -279,7 +292,7 @@ def time_events(torch, stream, fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def run_extra(args, pm, ctx, torch, dev, stream):
+def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
     """Batched, serving, differentiation and small-case numbers (secondary
     workloads; each quoted with its own unit)."""
     out = {}
@@ -351,6 +364,17 @@ def run_extra(args, pm, ctx, torch, dev, stream):
             pm.pm_batch_update_posterior(batch, stream)
             pm.pm_batch_predict(batch, stream)
     batch_ms = time_events(torch, stream, graph.replay, 10)
+    # grid epilogue: every human's counts blurred (sigma 1.5 cells) and
+    # max-united on the shared 400 x 400 grid
+    x0, y0, res, W, H = recs[0]["h"].grid
+    T_max = max(r["h"].horizon for r in recs)
+    union = torch.empty((T_max, H, W), device=dev)
+    ugrid = pm.make_grid(x0, y0, res, W, H)
+
+    def do_union():
+        pm.pm_batch_union(batch, 1.5, T_max, ugrid, union, stream)
+    union_ms = time_events(torch, stream, do_union, 10)
+    union_bytes = sum(r["h"].horizon for r in recs) * H * W * 4 + T_max * H * W * 4
     pm.pm_batch_destroy(batch)
     out["batched"] = {"humans": len(recs), "particle_steps": steps,
                       "batched_ms": batch_ms, "batched_particle_steps_per_s": steps / (batch_ms * 1e-3),
@@ -358,6 +382,12 @@ def run_extra(args, pm, ctx, torch, dev, stream):
                       "speedup_vs_plain": plain_ms / batch_ms, "autotune_s": tune_s,
                       "tuned": tuned,
                       "rate_vs_plain_small": steps / (batch_ms * 1e-3) / out["plain_small"]["particle_steps_per_s"],
+                      "sfu_roofline_frac": steps / (batch_ms * 1e-3) * 2 * 36 / sfu_peak,
+                      "union": {"ms": union_ms, "sigma_cells": 1.5, "bytes": union_bytes,
+                                "GB_per_s": union_bytes / (union_ms * 1e-3) / 1e9,
+                                "hbm_frac": union_bytes / (union_ms * 1e-3) / 1e9 / HBM_PEAK_GBS,
+                                "config": f"16 humans' counts [T_h][400][400] -> union [{T_max}][400][400], "
+                                          "blur R = 5"},
                       "config": "16 humans, G~U{2..6}, N~U[20k,200k], T~U{50..300}, K=36, 400x400 grid, "
                                 "graph of belief update + persistent rollout"}
     del recs
@@ -414,8 +444,31 @@ def run_extra(args, pm, ctx, torch, dev, stream):
             "particle_steps_per_frame": ps, "particle_steps_per_s": ps / float(np.median(lat)),
             "plain_path_ms_per_frame": plain_ms, "speedup_vs_plain": plain_ms / float(np.median(lat) * 1e3),
             "rate_vs_plain_small": ps / float(np.median(lat)) / out["plain_small"]["particle_steps_per_s"],
+            "sfu_roofline_frac": ps / float(np.median(lat)) * 2 * 36 / sfu_peak,
             "target": "p99 < 8 ms at 64 humans",
             "config": "64 humans, K=36, N=50k, T=150, 121x121 window at 0.05 m, 1 observation/frame, graph replay"}
+        # the same frames with the grid epilogue (blur + max-union on the room grid) in the graph
+        srv_u = Server(ctx, hu0.K, hu0.speed, hu0.dt, hu0.grid, max_live=64, n_particles=hu0.n_particles,
+                       horizon=hu0.horizon, window=hu0.window, union_sigma=1.5)
+        try:
+            live_u = []
+            for i in range(64):
+                h = arr[i % len(arr)].human
+                live_u.append(srv_u.admit(i, h.goals, h.beta, paths[i][0], h.seed,
+                                          h.human_id + 100000 * (i // len(arr))))
+            lat_u = []
+            for f in range(min(args.serving_frames, 120)):
+                for i, s_ in enumerate(live_u):
+                    if f >= 1:
+                        srv_u.observe(s_, paths[i][f])
+                lat_u.append(srv_u.frame())
+            lat_u = np.array(lat_u[5:])
+            out["serving_forced_64"]["with_union"] = {
+                "frames": int(lat_u.size), "p50_ms": float(np.percentile(lat_u, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat_u, 99) * 1e3), "sigma_cells": 1.5,
+                "union_grid": f"[{hu0.horizon}][{hu0.grid[4]}][{hu0.grid[3]}]"}
+        finally:
+            srv_u.close()
         if args.serving_seconds > 0:
             paths2 = []
             for a in arr:
@@ -618,7 +671,7 @@ def run_native(args):
             "paper_context": "125 Hz for 1 human, n=8192, T<=10, |U|=96 on an RTX 2080 Ti (Table 1); not this metric",
         }
         if not args.no_extra:
-            line["extra"] = run_extra(args, pm, ctx, torch, dev, stream)
+            line["extra"] = run_extra(args, pm, ctx, torch, dev, stream, peak * 1e9)
         if not args.no_cpu_baseline:
             threads = host_threads()
             cb = oracle_sample(hu, args.cpu_sample * max(1, threads // 4), threads=threads)

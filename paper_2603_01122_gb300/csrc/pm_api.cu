@@ -47,6 +47,7 @@ struct pm_batch {
     unsigned *d_head = nullptr;
     float *d_post_part = nullptr;
     unsigned *d_post_ticket = nullptr;
+    pm::SmoothSrc *d_srcs = nullptr; // union source records, one per human
     size_t post_stride = 0; // floats of posterior scratch per human
     // page-locked staging of the uploads
     char *h_stage = nullptr;
@@ -776,6 +777,7 @@ pm_status pm_batch_create(pm_ctx *ctx, const pm_model *shared, int32_t max_human
     if (e == cudaSuccess) e = cudaMalloc(&b->d_post, (size_t)max_humans * sizeof(pm::PostHuman));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items, b->items_cap * sizeof(int2));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_meta, 256);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_srcs, (size_t)max_humans * sizeof(pm::SmoothSrc));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_head, 256);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_post_part, (size_t)max_humans * b->post_stride * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_post_ticket, (size_t)max_humans * sizeof(unsigned));
@@ -803,6 +805,7 @@ void pm_batch_destroy(pm_batch *b)
     cudaFree(b->d_post);
     cudaFree(b->d_items);
     cudaFree(b->d_meta);
+    cudaFree(b->d_srcs);
     cudaFree(b->d_head);
     cudaFree(b->d_post_part);
     cudaFree(b->d_post_ticket);
@@ -922,15 +925,17 @@ pm_status pm_batch_union(pm_batch *b, float sigma_cells, int32_t horizon, const 
     std::memset(&a, 0, sizeof a);
     st = smooth_taps(sigma_cells, a);
     if (st != PM_OK) return st;
-    a.humans = b->d_humans;
-    a.n_humans = b->d_meta + 1;
+    a.srcs = b->d_srcs;
+    a.n_srcs = b->d_meta + 1;
     a.out = prob;
     a.T = horizon;
     a.W = grid->W;
     a.H = grid->H;
     DeviceScope dev(b->ctx->device);
     cudaGetLastError();
-    cudaError_t e = pm::launch_smooth_union(a, (cudaStream_t)stream);
+    cudaError_t e = pm::launch_union_sources(b->d_humans, b->d_meta + 1, b->max_humans, b->d_srcs,
+                                             (cudaStream_t)stream);
+    if (e == cudaSuccess) e = pm::launch_smooth_union(a, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "union launch");
     return PM_OK;
 }

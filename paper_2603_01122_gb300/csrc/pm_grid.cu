@@ -6,13 +6,20 @@
 //     placed at its cell offset on one shared grid, which takes the pointwise
 //     maximum over humans.
 //
-// One CTA produces a 64 x 16 tile of the shared grid at one step. For each
-// human whose window (widened by the blur radius R) meets the tile, it stages
-// the human's counts over the tile plus an R-cell halo in shared memory
-// (coalesced rows, scaled by 1/N), blurs along x into a second buffer, blurs
-// along y into registers and folds the result into the running maximum; the
-// tile is written once. The work is a stream over the count planes: bound by
-// HBM bandwidth (each count read once, plus halo re-reads that L2 absorbs).
+// A first kernel reduces each human of a batch to a compact source record
+// (counts, 1/N, horizon, window size and cell offset; a centred window's
+// offset from the human's start cell, by the rollout's own formula). The
+// union kernel then produces a 64 x 16 tile of the shared grid at one step
+// per CTA: it loads the source records into shared memory, and for each
+// source whose window (widened by the blur radius R) meets the tile it stages
+// the counts of the tile plus an R-cell halo in shared memory (coalesced
+// rows, scaled by 1/N), blurs along x into a second buffer with each thread
+// sliding a register window over four outputs, blurs along y the same way,
+// and folds the result into the running maximum; the tile is written once.
+// The work streams over the count planes: HBM-bound when the windows cover
+// the grid, shared-memory-bound for small windows.
+#include <utility>
+
 #include <cuda_runtime.h>
 
 #include "pm_internal.cuh"
@@ -21,109 +28,155 @@ namespace pm {
 namespace {
 
 constexpr int kTileX = 64, kTileY = 16, kGridThreads = 256;
-constexpr int kCellsPerThread = kTileX * kTileY / kGridThreads; // 4
+constexpr int kSrcChunk = 128; // source records staged in shared memory at a time
 
-// Window offset of human h on the shared grid (the rollout's own formula for
-// a centred window).
-__device__ __forceinline__ void window_offset(const BatchHuman &h, int &ox, int &oy)
+__global__ void union_sources_kernel(const BatchHuman *humans, const int *n_humans, SmoothSrc *srcs)
 {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *n_humans) return;
+    const BatchHuman h = humans[i];
+    SmoothSrc s;
+    s.counts = h.counts;
+    s.inv_n = 1.0f / (float)h.N;
+    s.T = h.T;
+    s.W = h.W;
+    s.H = h.H;
     if (h.center) {
-        const int gcx = __float2int_rd(__fmul_rn(__fsub_rn(h.z0[0], h.gx0), h.inv_res));
-        const int gcy = __float2int_rd(__fmul_rn(__fsub_rn(h.z0[1], h.gy0), h.inv_res));
-        ox = gcx - (h.W - 1) / 2;
-        oy = gcy - (h.H - 1) / 2;
+        s.ox = __float2int_rd(__fmul_rn(__fsub_rn(h.z0[0], h.gx0), h.inv_res)) - (h.W - 1) / 2;
+        s.oy = __float2int_rd(__fmul_rn(__fsub_rn(h.z0[1], h.gy0), h.inv_res)) - (h.H - 1) / 2;
     } else {
-        ox = h.cx_off;
-        oy = h.cy_off;
+        s.ox = h.cx_off;
+        s.oy = h.cy_off;
+    }
+    srcs[i] = s;
+}
+
+// RB: the blur radius R as a compile-time constant, so that the sliding
+// windows of both passes live in registers and every tap is one FMA.
+template <int RB>
+__global__ void __launch_bounds__(kGridThreads) smooth_union_kernel(const __grid_constant__ SmoothArgs a)
+{
+    constexpr int AW = kTileX + 2 * RB, AH = kTileY + 2 * RB;
+    constexpr int NW = 2 * RB + 4; // window of four outputs
+    // row stride: a multiple of 4 floats (16-byte vector loads) covering the
+    // last vector load of the widest window, columns up to 60 + 4 ceil(NW/4) - 1
+    constexpr int AS = 60 + 4 * ((NW + 3) / 4);
+    static_assert(AS >= AW && AS % 4 == 0, "row stride");
+    __shared__ __align__(16) float A[AH][AS];
+    __shared__ __align__(16) float Bx[AH][kTileX];
+    __shared__ SmoothSrc S[kSrcChunk];
+    const int tid = threadIdx.x;
+    const int X0 = blockIdx.x * kTileX, Y0 = blockIdx.y * kTileY, t = blockIdx.z;
+    // horizontal pass: thread -> (row hy0 + 16 j, columns 4 hx .. 4 hx + 3)
+    const int hx = tid & 15, hy0 = tid >> 4;
+    // vertical pass and output: thread -> (column vx, rows 4 vg .. 4 vg + 3)
+    const int vx = tid & 63, vg = tid >> 6;
+    float w[2 * RB + 1];
+#pragma unroll
+    for (int k = 0; k <= 2 * RB; ++k) w[k] = a.w[k];
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+
+    const int n = a.srcs ? *a.n_srcs : 1;
+    for (int c0 = 0; c0 < n; c0 += kSrcChunk) {
+        const int nc = min(kSrcChunk, n - c0);
+        __syncthreads(); // the previous chunk's records are no longer read
+        if (tid < nc) S[tid] = a.srcs ? a.srcs[c0 + tid] : a.single;
+        __syncthreads();
+        for (int si = 0; si < nc; ++si) {
+            const SmoothSrc s = S[si];
+            // the source reaches this tile only if its widened window meets it
+            if (t >= s.T || s.ox - RB >= X0 + kTileX || s.ox + s.W + RB <= X0 || s.oy - RB >= Y0 + kTileY ||
+                s.oy + s.H + RB <= Y0)
+                continue;
+            const uint32_t *plane = s.counts + (size_t)t * s.W * s.H;
+            const int wx0 = X0 - RB - s.ox, wy0 = Y0 - RB - s.oy; // window cell of A[0][0]
+            for (int ry = tid >> 6; ry < AH; ry += kGridThreads / 64) {
+                const int wy = wy0 + ry;
+                const bool row_in = wy >= 0 && wy < s.H;
+                const uint32_t *row = plane + (size_t)wy * s.W;
+                for (int rx = tid & 63; rx < AW; rx += 64) {
+                    const int wx = wx0 + rx;
+                    float v = 0.0f;
+                    if (row_in && wx >= 0 && wx < s.W) v = (float)row[wx] * s.inv_n;
+                    A[ry][rx] = v;
+                }
+            }
+            __syncthreads();
+            if constexpr (RB == 0) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[j] = fmaxf(acc[j], A[4 * vg + j][vx]);
+            } else {
+                for (int y = hy0; y < AH; y += kGridThreads / 16) {
+                    float v[NW];
+#pragma unroll
+                    for (int k = 0; k < NW; k += 4) {
+                        // 16-byte load; the last one may read the row's padding (never used)
+                        const float4 q = *reinterpret_cast<const float4 *>(&A[y][4 * hx + k]);
+                        v[k] = q.x;
+                        if (k + 1 < NW) v[k + 1] = q.y;
+                        if (k + 2 < NW) v[k + 2] = q.z;
+                        if (k + 3 < NW) v[k + 3] = q.w;
+                    }
+                    float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+#pragma unroll
+                        for (int k = 0; k <= 2 * RB; ++k) o[j] = fmaf(w[k], v[j + k], o[j]);
+                    *reinterpret_cast<float4 *>(&Bx[y][4 * hx]) = make_float4(o[0], o[1], o[2], o[3]);
+                }
+                __syncthreads();
+                float v[NW];
+#pragma unroll
+                for (int k = 0; k < NW; ++k) v[k] = Bx[4 * vg + k][vx];
+                float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int k = 0; k <= 2 * RB; ++k) o[j] = fmaf(w[k], v[j + k], o[j]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[j] = fmaxf(acc[j], o[j]);
+            }
+            __syncthreads(); // A and Bx are refilled for the next source
+        }
+    }
+    const int X = X0 + vx;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int Y = Y0 + 4 * vg + j;
+        if (X < a.W && Y < a.H) a.out[((size_t)t * a.H + Y) * a.W + X] = acc[j];
     }
 }
 
-__global__ void __launch_bounds__(kGridThreads) smooth_union_kernel(const __grid_constant__ SmoothArgs a)
+template <int RB>
+void launch_rb(const SmoothArgs &a, dim3 grid, cudaStream_t s)
 {
-    __shared__ float A[kTileY + 2 * kMaxSmoothR][kTileX + 2 * kMaxSmoothR];
-    __shared__ float Bx[kTileY + 2 * kMaxSmoothR][kTileX];
-    const int tid = threadIdx.x;
-    const int R = a.R;
-    if (R < 0 || R > kMaxSmoothR) return; // the host validates R; never index past the tiles
-    const int X0 = blockIdx.x * kTileX, Y0 = blockIdx.y * kTileY, t = blockIdx.z;
-    const int AW = kTileX + 2 * R, AH = kTileY + 2 * R;
-    float acc[kCellsPerThread];
-#pragma unroll
-    for (int q = 0; q < kCellsPerThread; ++q) acc[q] = 0.0f;
+    smooth_union_kernel<RB><<<grid, kGridThreads, 0, s>>>(a);
+}
 
-    const int n = a.humans ? *a.n_humans : 1;
-    for (int hi = 0; hi < n; ++hi) {
-        const uint32_t *counts;
-        float inv_n;
-        int Th, Wh, Hh, ox, oy;
-        if (a.humans) {
-            const BatchHuman &h = a.humans[hi];
-            counts = h.counts;
-            inv_n = 1.0f / (float)h.N;
-            Th = h.T;
-            Wh = h.W;
-            Hh = h.H;
-            window_offset(h, ox, oy);
-        } else {
-            counts = a.single.counts;
-            inv_n = a.single.inv_n;
-            Th = a.single.T;
-            Wh = a.single.W;
-            Hh = a.single.H;
-            ox = a.single.ox;
-            oy = a.single.oy;
-        }
-        // the human reaches this tile only if its widened window meets it
-        if (t >= Th || ox - R >= X0 + kTileX || ox + Wh + R <= X0 || oy - R >= Y0 + kTileY || oy + Hh + R <= Y0)
-            continue;
-        const uint32_t *plane = counts + (size_t)t * Wh * Hh;
-        for (int e = tid; e < AW * AH; e += kGridThreads) {
-            const int ry = e / AW, rx = e - ry * AW;
-            const int wx = X0 - R + rx - ox, wy = Y0 - R + ry - oy; // window cell
-            float v = 0.0f;
-            if (wx >= 0 && wx < Wh && wy >= 0 && wy < Hh) v = (float)plane[(size_t)wy * Wh + wx] * inv_n;
-            A[ry][rx] = v;
-        }
-        __syncthreads();
-        if (R == 0) {
-#pragma unroll
-            for (int q = 0; q < kCellsPerThread; ++q) {
-                const int c = tid + q * kGridThreads, y = c / kTileX, x = c - y * kTileX;
-                acc[q] = fmaxf(acc[q], A[y][x]);
-            }
-        } else {
-            for (int e = tid; e < AH * kTileX; e += kGridThreads) {
-                const int y = e / kTileX, x = e - y * kTileX;
-                float s = 0.0f;
-                for (int k = 0; k <= 2 * R; ++k) s = fmaf(a.w[k], A[y][x + k], s);
-                Bx[y][x] = s;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < kCellsPerThread; ++q) {
-                const int c = tid + q * kGridThreads, y = c / kTileX, x = c - y * kTileX;
-                float s = 0.0f;
-                for (int k = 0; k <= 2 * R; ++k) s = fmaf(a.w[k], Bx[y + k][x], s);
-                acc[q] = fmaxf(acc[q], s);
-            }
-        }
-        __syncthreads(); // A and Bx are refilled for the next human
-    }
-#pragma unroll
-    for (int q = 0; q < kCellsPerThread; ++q) {
-        const int c = tid + q * kGridThreads, y = c / kTileX, x = c - y * kTileX;
-        const int X = X0 + x, Y = Y0 + y;
-        if (X < a.W && Y < a.H) a.out[((size_t)t * a.H + Y) * a.W + X] = acc[q];
-    }
+template <int... Rs>
+bool dispatch_rb(int R, const SmoothArgs &a, dim3 grid, cudaStream_t s, std::integer_sequence<int, Rs...>)
+{
+    bool done = false;
+    ((R == Rs ? (launch_rb<Rs>(a, grid, s), done = true) : false), ...);
+    return done;
 }
 
 } // namespace
+
+cudaError_t launch_union_sources(const BatchHuman *humans, const int *n_humans, int max_humans, SmoothSrc *srcs,
+                                 cudaStream_t s)
+{
+    if (max_humans <= 0) return cudaSuccess;
+    union_sources_kernel<<<(max_humans + 127) / 128, 128, 0, s>>>(humans, n_humans, srcs);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_smooth_union(const SmoothArgs &a, cudaStream_t s)
 {
     if (a.T <= 0 || a.W <= 0 || a.H <= 0) return cudaSuccess;
     const dim3 grid((a.W + kTileX - 1) / kTileX, (a.H + kTileY - 1) / kTileY, a.T);
-    smooth_union_kernel<<<grid, kGridThreads, 0, s>>>(a);
+    if (!dispatch_rb(a.R, a, grid, s, std::make_integer_sequence<int, kMaxSmoothR + 1>{}))
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -238,8 +238,8 @@ struct SmoothSrc {
 };
 
 struct SmoothArgs {
-    const BatchHuman *humans; // batched source (device), or nullptr: `single`
-    const int *n_humans;      // device: live humans of the batch
+    const SmoothSrc *srcs; // device source records, or nullptr: `single`
+    const int *n_srcs;     // device: number of records
     SmoothSrc single;
     float w[2 * kMaxSmoothR + 1]; // normalised taps w_{-R..R}
     int R;
@@ -272,6 +272,9 @@ struct RolloutShape {
 // `head` is a zeroed device counter of 32-particle chunks.
 cudaError_t launch_rollout(const RolloutArgs &a, unsigned *head, int sm_count, cudaStream_t s);
 cudaError_t launch_smooth_union(const SmoothArgs &a, cudaStream_t s);
+// One SmoothSrc per live human of a batch (window offsets resolved on the device).
+cudaError_t launch_union_sources(const BatchHuman *humans, const int *n_humans, int max_humans, SmoothSrc *srcs,
+                                 cudaStream_t s);
 size_t rollout_static_smem_estimate();
 cudaError_t launch_posterior(const PosteriorArgs &a, int n_chunks, cudaStream_t s);
 int posterior_chunks(int n_obs, int *steps_per_chunk);

@@ -14,6 +14,9 @@ room grid centred on the human's cell (Algorithm 1, bootstrapped belief).
   device), the batched belief update and the batched persistent rollout,
   replayed as one captured CUDA graph. Membership changes re-upload the
   batch descriptors only; the graph reads them from device memory.
+* Optionally (``union_sigma``) the frame also blurs every live human's window
+  and max-unites them on the shared room grid (Sec. III-B, Sec. IV-B): the
+  planner's input, in the same graph.
 * Latency = host wall time from the start of the frame (observations in host
   memory) to the occupancy being ready on the device (event synchronised).
 
@@ -28,7 +31,7 @@ from typing import Dict, List, Optional
 import numpy as np
 
 from . import (make_grid, make_human, make_model, pm_batch_create, pm_batch_destroy,
-               pm_batch_predict, pm_batch_set, pm_batch_update_posterior)
+               pm_batch_predict, pm_batch_set, pm_batch_union, pm_batch_update_posterior)
 
 
 @dataclasses.dataclass
@@ -69,7 +72,7 @@ class Server:
 
     def __init__(self, ctx, K, speed, dt, room_grid, *, max_live=64, budget_bytes=4 << 30,
                  n_particles=50_000, horizon=150, window=121, g_max=6, b_max=10, w1=1.0, w2=1.0,
-                 use_graph=True, device="cuda:0"):
+                 use_graph=True, device="cuda:0", union_sigma=None):
         import torch
 
         self.torch = torch
@@ -98,6 +101,12 @@ class Server:
         shared_beta = torch.ones(1, device=self.dev)
         self._shared = make_model(K, speed, dt, shared_goals, shared_beta, w1=w1, w2=w2)
         self.batch = pm_batch_create(ctx, self._shared, cap)
+        self.union_sigma = union_sigma
+        self.union = None
+        if union_sigma is not None:
+            _, _, _, RW, RH = room_grid
+            self.union_grid = make_grid(x0, y0, res, RW, RH)
+            self.union = torch.zeros((horizon, RH, RW), dtype=torch.float32, device=self.dev)
         self.use_graph = use_graph
         self.graph = None
         self.dirty = True
@@ -160,6 +169,8 @@ class Server:
         self.obs_dev.copy_(self.obs_host, non_blocking=True)
         pm_batch_update_posterior(self.batch, self.stream)
         pm_batch_predict(self.batch, self.stream)
+        if self.union is not None:
+            pm_batch_union(self.batch, self.union_sigma, self.T, self.union_grid, self.union, self.stream)
 
     def frame(self) -> float:
         """Run one frame for every live human; returns its latency in seconds."""

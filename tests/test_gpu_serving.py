@@ -74,3 +74,36 @@ def test_serving_frames_match_single_path(ctx, orc):
     assert out["frames_waited"] > 0             # arrivals queued for a slot
     assert live[-1] < live.max() or live.min() < live.max()  # departures freed slots
     assert np.all(out["latency_s"] > 0)
+
+
+def test_serving_frame_union_matches_oracle(ctx, orc):
+    """With the grid epilogue on, a frame also leaves the blurred max-union of
+    the live humans' windows on the room grid (the planner's input)."""
+    from oracle import grid_ops as G
+    from paper_2603_01122_gb300.serving import Server
+    wl = workloads.serving(duration_s=6.0, rate_hz=3.0)
+    arr = wl["arrivals"][:3]
+    hu0 = arr[0].human
+    N, T, win, sigma = 2000, 24, 31, 1.0
+    srv = Server(ctx, hu0.K, hu0.speed, hu0.dt, hu0.grid, max_live=4, n_particles=N, horizon=T, window=win,
+                 union_sigma=sigma)
+    try:
+        slots = []
+        for i, a in enumerate(arr):
+            hu = a.human
+            slots.append(srv.admit(i, hu.goals, hu.beta, hu.start, hu.seed, hu.human_id))
+        for _ in range(3):
+            srv.frame()
+        torch.cuda.synchronize()
+        x0, y0, res, W, H = hu0.grid
+        hs = []
+        for s in slots:
+            z0 = srv.obs_dev[s, 1].cpu().numpy()
+            hs.append(dict(counts=srv.counts[s].cpu().numpy().view(np.uint32).astype(np.int64), n=N,
+                           offset=G.window_offset(z0, hu0.grid, win, win)))
+        want = G.union(hs, T, H, W, sigma)
+        got = srv.union.cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(got - want) <= 1e-5 * want + 1e-12)
+        assert got.max() > 0.0
+    finally:
+        srv.close()
