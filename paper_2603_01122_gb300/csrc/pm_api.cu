@@ -895,6 +895,7 @@ pm_status pm_smooth_occupancy(pm_ctx *ctx, const uint32_t *counts, int32_t n_par
     if (st != PM_OK) return st;
     a.single.counts = counts;
     a.single.inv_n = 1.0f / (float)n_particles;
+    a.single.small = n_particles < (1 << 23);
     a.single.T = horizon;
     a.single.W = grid->W;
     a.single.H = grid->H;

@@ -9,7 +9,7 @@
 // A first kernel reduces each human of a batch to a compact source record
 // (counts, 1/N, horizon, window size and cell offset; a centred window's
 // offset from the human's start cell, by the rollout's own formula). The
-// union kernel then produces a 64 x 16 tile of the shared grid at one step
+// union kernel then produces a 64 x 32 tile of the shared grid at one step
 // per CTA: it loads the source records into shared memory, and for each
 // source whose window (widened by the blur radius R) meets the tile it stages
 // the counts of the tile plus an R-cell halo in shared memory (coalesced
@@ -27,7 +27,8 @@
 namespace pm {
 namespace {
 
-constexpr int kTileX = 64, kTileY = 16, kGridThreads = 256;
+constexpr int kTileX = 64, kTileY = 32, kGridThreads = 256;
+constexpr int kRowsPerThread = kTileX * kTileY / kGridThreads; // 8 (vertical pass)
 constexpr int kSrcChunk = 128; // source records staged in shared memory at a time
 
 __global__ void union_sources_kernel(const BatchHuman *humans, const int *n_humans, SmoothSrc *srcs)
@@ -38,6 +39,7 @@ __global__ void union_sources_kernel(const BatchHuman *humans, const int *n_huma
     SmoothSrc s;
     s.counts = h.counts;
     s.inv_n = 1.0f / (float)h.N;
+    s.small = h.N < (1 << 23);
     s.T = h.T;
     s.W = h.W;
     s.H = h.H;
@@ -69,12 +71,16 @@ __global__ void __launch_bounds__(kGridThreads) smooth_union_kernel(const __grid
     const int X0 = blockIdx.x * kTileX, Y0 = blockIdx.y * kTileY, t = blockIdx.z;
     // horizontal pass: thread -> (row hy0 + 16 j, columns 4 hx .. 4 hx + 3)
     const int hx = tid & 15, hy0 = tid >> 4;
-    // vertical pass and output: thread -> (column vx, rows 4 vg .. 4 vg + 3)
+    // vertical pass and output: thread -> (column vx, rows 8 vg .. 8 vg + 7)
     const int vx = tid & 63, vg = tid >> 6;
+    constexpr int RT = kRowsPerThread, NV = 2 * RB + RT;
+    constexpr int kStageIters = (AW * AH + kGridThreads - 1) / kGridThreads;
     float w[2 * RB + 1];
 #pragma unroll
     for (int k = 0; k <= 2 * RB; ++k) w[k] = a.w[k];
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float acc[RT];
+#pragma unroll
+    for (int j = 0; j < RT; ++j) acc[j] = 0.0f;
 
     const int n = a.srcs ? *a.n_srcs : 1;
     for (int c0 = 0; c0 < n; c0 += kSrcChunk) {
@@ -90,21 +96,50 @@ __global__ void __launch_bounds__(kGridThreads) smooth_union_kernel(const __grid
                 continue;
             const uint32_t *plane = s.counts + (size_t)t * s.W * s.H;
             const int wx0 = X0 - RB - s.ox, wy0 = Y0 - RB - s.oy; // window cell of A[0][0]
-            for (int ry = tid >> 6; ry < AH; ry += kGridThreads / 64) {
-                const int wy = wy0 + ry;
-                const bool row_in = wy >= 0 && wy < s.H;
-                const uint32_t *row = plane + (size_t)wy * s.W;
-                for (int rx = tid & 63; rx < AW; rx += 64) {
-                    const int wx = wx0 + rx;
-                    float v = 0.0f;
-                    if (row_in && wx >= 0 && wx < s.W) v = (float)row[wx] * s.inv_n;
-                    A[ry][rx] = v;
+            // counts stay raw (exact in FP32 below 2^23, converted on the FP32
+            // pipe); the 1/N scale is applied once per output at the end
+            const bool inside = wx0 >= 0 && wx0 + AW <= s.W && wy0 >= 0 && wy0 + AH <= s.H;
+            if (inside && s.small) {
+                // whole region inside the window: all loads first, then the stores
+                uint32_t c[kStageIters];
+#pragma unroll
+                for (int i = 0; i < kStageIters; ++i) {
+                    const int e = tid + i * kGridThreads;
+                    const int ry = e / AW, rx = e - ry * AW;
+                    c[i] = (e < AW * AH) ? plane[(size_t)(wy0 + ry) * s.W + (wx0 + rx)] : 0u;
+                }
+#pragma unroll
+                for (int i = 0; i < kStageIters; ++i) {
+                    const int e = tid + i * kGridThreads;
+                    const int ry = e / AW, rx = e - ry * AW;
+                    if (e < AW * AH) A[ry][rx] = __int_as_float((int)(c[i] | 0x4B000000u)) - 8388608.0f;
+                }
+            } else {
+                // region partly outside the window (or counts >= 2^23): the
+                // same two phases, each element checked against the window
+                uint32_t c[kStageIters];
+#pragma unroll
+                for (int i = 0; i < kStageIters; ++i) {
+                    const int e = tid + i * kGridThreads;
+                    const int ry = e / AW, rx = e - ry * AW;
+                    const int wy = wy0 + ry, wx = wx0 + rx;
+                    const bool in = e < AW * AH && wy >= 0 && wy < s.H && wx >= 0 && wx < s.W;
+                    c[i] = in ? plane[(size_t)wy * s.W + wx] : 0u;
+                }
+#pragma unroll
+                for (int i = 0; i < kStageIters; ++i) {
+                    const int e = tid + i * kGridThreads;
+                    const int ry = e / AW, rx = e - ry * AW;
+                    // exact integer-to-float below 2^23 on the FP32 pipe
+                    const float v = c[i] < 0x800000u ? __int_as_float((int)(c[i] | 0x4B000000u)) - 8388608.0f
+                                                     : (float)c[i];
+                    if (e < AW * AH) A[ry][rx] = v;
                 }
             }
             __syncthreads();
             if constexpr (RB == 0) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[j] = fmaxf(acc[j], A[4 * vg + j][vx]);
+                for (int j = 0; j < RT; ++j) acc[j] = fmaxf(acc[j], A[RT * vg + j][vx] * s.inv_n);
             } else {
                 for (int y = hy0; y < AH; y += kGridThreads / 16) {
                     float v[NW];
@@ -125,24 +160,24 @@ __global__ void __launch_bounds__(kGridThreads) smooth_union_kernel(const __grid
                     *reinterpret_cast<float4 *>(&Bx[y][4 * hx]) = make_float4(o[0], o[1], o[2], o[3]);
                 }
                 __syncthreads();
-                float v[NW];
+                float v[NV];
 #pragma unroll
-                for (int k = 0; k < NW; ++k) v[k] = Bx[4 * vg + k][vx];
-                float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                for (int k = 0; k < NV; ++k) v[k] = Bx[RT * vg + k][vx];
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
+                for (int j = 0; j < RT; ++j) {
+                    float o = 0.0f;
 #pragma unroll
-                    for (int k = 0; k <= 2 * RB; ++k) o[j] = fmaf(w[k], v[j + k], o[j]);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[j] = fmaxf(acc[j], o[j]);
+                    for (int k = 0; k <= 2 * RB; ++k) o = fmaf(w[k], v[j + k], o);
+                    acc[j] = fmaxf(acc[j], o * s.inv_n);
+                }
             }
             __syncthreads(); // A and Bx are refilled for the next source
         }
     }
     const int X = X0 + vx;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int Y = Y0 + 4 * vg + j;
+    for (int j = 0; j < RT; ++j) {
+        const int Y = Y0 + RT * vg + j;
         if (X < a.W && Y < a.H) a.out[((size_t)t * a.H + Y) * a.W + X] = acc[j];
     }
 }

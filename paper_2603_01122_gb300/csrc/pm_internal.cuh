@@ -235,6 +235,7 @@ struct SmoothSrc {
     float inv_n;            // 1 / particles
     int T, W, H;
     int ox, oy;             // window cell (x, y) = shared cell (x + ox, y + oy)
+    int small;              // every count < 2^23 (N < 2^23): exact FP32 conversion by the mantissa
 };
 
 struct SmoothArgs {
