@@ -340,6 +340,43 @@ pm_status pm_smooth_occupancy(pm_ctx *ctx, const uint32_t *counts, int32_t n_par
 pm_status pm_batch_union(pm_batch *b, float sigma_cells, int32_t horizon, const pm_grid *grid, float *prob,
                          void *stream);
 
+/* ---- local planner on the predictions ------------------------------------- */
+
+/* MPPI (model predictive path integral) control of the robot of Eq. 8 against
+ * the predicted occupancy, the local planner of Sec. III-C. Robot state
+ * z = [x, y, v, theta], control u = [a, omega]; explicit Euler over dt:
+ * x += v cos(theta) dt, y += v sin(theta) dt, v += a dt, theta += omega dt.
+ * Sample i applies u_ref[t] + delta[t][i], t = 0..T-1; after step t it pays
+ * (z - goal)^T diag(q) (z - goal) + u^T diag(r) u + step_cost, plus coll_cost
+ * when the occupancy at the robot's cell (FP32 binning as the emplacement
+ * step) at prediction step (t+1)*pred_stride - 1 is >= coll_threshold (no
+ * cost outside the grid or past prob_T); the terminal cost is
+ * (z_T - goal)^T diag(q_final) (z_T - goal). The update uses the
+ * cost-to-go from each step: u_opt[t] = u_ref[t] + sum_i w_i delta[t][i] /
+ * sum_i w_i, w_i = exp(-(S_i(t) - min_i S_i(t)) / temperature). */
+typedef struct pm_mppi {
+    int32_t n_samples;   /* N >= 1 */
+    int32_t horizon;     /* T >= 1 MPPI steps */
+    float dt;            /* seconds per MPPI step, > 0 */
+    int32_t pred_stride; /* prediction steps per MPPI step, >= 1 */
+    float q[4];          /* state weights (x, y, v, theta) */
+    float q_final[4];    /* terminal state weights */
+    float r[2];          /* control weights (a, omega) */
+    float goal[4];       /* robot goal state */
+    float coll_threshold, coll_cost, step_cost;
+    float temperature;   /* tau > 0 */
+} pm_mppi;
+
+/* z0: robot state (host, 4 floats). u_ref: device [T][2]; delta: device
+ * [T][N][2] (sample-minor, the caller draws it); prob: device [prob_T][H][W]
+ * predicted occupancy on `grid` (e.g. pm_batch_union's output), or NULL for
+ * no collision cost. Outputs (device, caller-owned): cost_to_go [T][N]
+ * (S_i(t); S_i(0) is sample i's total cost) and u_opt [T][2]. Two kernels,
+ * stream-ordered, no allocation; PM_EINVAL for bad sizes or weights. */
+pm_status pm_mppi_solve(pm_ctx *ctx, const pm_mppi *params, const float *z0, const float *u_ref,
+                        const float *delta, const float *prob, int32_t prob_T, const pm_grid *grid,
+                        float *cost_to_go, float *u_opt, void *stream);
+
 /* ---- checks and measurement ---------------------------------------------- */
 
 /* Raw Philox4x64-10 blocks for counters (particle0 + i, block, purpose, 0),

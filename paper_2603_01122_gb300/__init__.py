@@ -32,6 +32,20 @@ class pm_model(C.Structure):
                 ("beta", C.c_void_p), ("heading_off", C.c_uint64)]
 
 
+class pm_mppi(C.Structure):
+    _fields_ = [("n_samples", C.c_int32), ("horizon", C.c_int32), ("dt", C.c_float), ("pred_stride", C.c_int32),
+                ("q", C.c_float * 4), ("q_final", C.c_float * 4), ("r", C.c_float * 2), ("goal", C.c_float * 4),
+                ("coll_threshold", C.c_float), ("coll_cost", C.c_float), ("step_cost", C.c_float),
+                ("temperature", C.c_float)]
+
+
+def make_mppi(n_samples, horizon, dt, pred_stride, q, q_final, r, goal, coll_threshold=0.1, coll_cost=1000.0,
+              step_cost=0.0, temperature=1.0) -> pm_mppi:
+    return pm_mppi(int(n_samples), int(horizon), float(dt), int(pred_stride), (C.c_float * 4)(*q),
+                   (C.c_float * 4)(*q_final), (C.c_float * 2)(*r), (C.c_float * 4)(*goal), float(coll_threshold),
+                   float(coll_cost), float(step_cost), float(temperature))
+
+
 class pm_grid(C.Structure):
     _fields_ = [("x0", C.c_float), ("y0", C.c_float), ("res", C.c_float), ("W", C.c_int32),
                 ("H", C.c_int32)]
@@ -74,6 +88,8 @@ def _signatures(lib):
         "pm_batch_destroy": ([_vp], None),
         "pm_smooth_occupancy": ([_vp, _vp, C.c_int32, C.c_int32, P(pm_grid), C.c_float, _vp, _vp], C.c_int),
         "pm_batch_union": ([_vp, C.c_float, C.c_int32, P(pm_grid), _vp, _vp], C.c_int),
+        "pm_mppi_solve": ([_vp, P(pm_mppi), P(C.c_float), _vp, _vp, _vp, C.c_int32, P(pm_grid), _vp, _vp, _vp],
+                          C.c_int),
         "pm_loglik_forward": ([_vp, P(pm_model), C.c_int32, _vp, C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
         "pm_loglik_backward": ([_vp, P(pm_model), C.c_int32, _vp, C.c_int32, _vp, _vp, C.c_float, _vp, _vp,
                                 _vp, _vp, _vp], C.c_int),
@@ -236,6 +252,13 @@ def pm_smooth_occupancy(ctx, counts, n_particles, horizon, grid, sigma_cells, pr
 def pm_batch_union(batch, sigma_cells, horizon, grid, prob, stream=None):
     _check(library().pm_batch_union(batch, float(sigma_cells), int(horizon), C.byref(grid), _p(prob),
                                     _stream(stream)))
+
+
+def pm_mppi_solve(ctx, params: pm_mppi, z0, u_ref, delta, prob, prob_T, grid, cost_to_go, u_opt, stream=None):
+    z = (C.c_float * 4)(*[float(v) for v in z0])
+    _check(library().pm_mppi_solve(ctx, C.byref(params), z, _p(u_ref), _p(delta), _p(prob), int(prob_T),
+                                   C.byref(grid) if grid is not None else None, _p(cost_to_go), _p(u_opt),
+                                   _stream(stream)))
 
 
 def pm_batch_autotune(batch, stream=None):

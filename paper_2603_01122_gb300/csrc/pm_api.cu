@@ -1061,6 +1061,65 @@ pm_status pm_philox_blocks(pm_ctx *ctx, uint64_t seed, uint32_t human_id, uint32
     return PM_OK;
 }
 
+pm_status pm_mppi_solve(pm_ctx *ctx, const pm_mppi *p, const float *z0, const float *u_ref, const float *delta,
+                        const float *prob, int32_t prob_T, const pm_grid *grid, float *cost_to_go, float *u_opt,
+                        void *stream)
+{
+    if (!ctx || !p || !z0 || !u_ref || !delta || !cost_to_go || !u_opt)
+        return fail(PM_EINVAL, "ctx/params/z0/u_ref/delta/cost_to_go/u_opt is NULL");
+    if (p->n_samples < 1 || p->horizon < 1 || p->pred_stride < 1)
+        return fail(PM_EINVAL, "n_samples=%d horizon=%d pred_stride=%d must be >= 1", p->n_samples, p->horizon,
+                    p->pred_stride);
+    if ((long long)p->n_samples * p->horizon > (1LL << 31)) return fail(PM_EINVAL, "n_samples x horizon too large");
+    if (!finite_pos(p->dt) || !finite_pos(p->temperature)) return fail(PM_EINVAL, "dt and temperature must be > 0");
+    for (int k = 0; k < 4; ++k)
+        if (!std::isfinite(p->q[k]) || !std::isfinite(p->q_final[k]) || !std::isfinite(p->goal[k]) ||
+            !std::isfinite(z0[k]))
+            return fail(PM_EINVAL, "weights, goal and z0 must be finite");
+    if (!std::isfinite(p->r[0]) || !std::isfinite(p->r[1]) || !std::isfinite(p->coll_threshold) ||
+        !std::isfinite(p->coll_cost) || !std::isfinite(p->step_cost))
+        return fail(PM_EINVAL, "costs must be finite");
+    pm::MppiArgs a;
+    std::memset(&a, 0, sizeof a);
+    if (prob) {
+        pm_status st = check_grid(grid);
+        if (st != PM_OK) return st;
+        if (prob_T < 1) return fail(PM_EINVAL, "prob_T=%d must be >= 1", prob_T);
+        a.prob = prob;
+        a.prob_T = prob_T;
+        a.W = grid->W;
+        a.H = grid->H;
+        a.gx0 = grid->x0;
+        a.gy0 = grid->y0;
+        a.inv_res = 1.0f / grid->res;
+    }
+    a.N = p->n_samples;
+    a.T = p->horizon;
+    a.pred_stride = p->pred_stride;
+    a.dt = p->dt;
+    for (int k = 0; k < 4; ++k) {
+        a.z0[k] = z0[k];
+        a.q[k] = p->q[k];
+        a.q_final[k] = p->q_final[k];
+        a.goal[k] = p->goal[k];
+    }
+    a.r[0] = p->r[0];
+    a.r[1] = p->r[1];
+    a.coll_threshold = p->coll_threshold;
+    a.coll_cost = p->coll_cost;
+    a.step_cost = p->step_cost;
+    a.temperature = p->temperature;
+    a.u_ref = u_ref;
+    a.delta = delta;
+    a.ctg = cost_to_go;
+    a.u_opt = u_opt;
+    DeviceScope dev(ctx->device);
+    cudaGetLastError();
+    cudaError_t e = pm::launch_mppi(a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mppi launch");
+    return PM_OK;
+}
+
 pm_status pm_probe_sfu(pm_ctx *ctx, int op, double *results_per_s)
 {
     if (!ctx || !results_per_s) return fail(PM_EINVAL, "ctx/results is NULL");

@@ -248,6 +248,22 @@ struct SmoothArgs {
     int T, W, H;
 };
 
+// MPPI local planner on the predicted occupancy (Sec. III-C, Eq. 8).
+struct MppiArgs {
+    int N, T, pred_stride;
+    float dt;
+    float z0[4]; // x, y, v, theta
+    float q[4], q_final[4], r[2], goal[4];
+    float coll_threshold, coll_cost, step_cost, temperature;
+    const float *u_ref; // [T][2]
+    const float *delta; // [T][N][2]
+    const float *prob;  // [prob_T][H][W] or nullptr
+    int prob_T, W, H;
+    float gx0, gy0, inv_res;
+    float *ctg;   // [T][N] cost-to-go (out)
+    float *u_opt; // [T][2] (out)
+};
+
 struct BatchArgs {
     HeadingTab tab;
     uint64_t enabled;
@@ -273,6 +289,7 @@ struct RolloutShape {
 // `head` is a zeroed device counter of 32-particle chunks.
 cudaError_t launch_rollout(const RolloutArgs &a, unsigned *head, int sm_count, cudaStream_t s);
 cudaError_t launch_smooth_union(const SmoothArgs &a, cudaStream_t s);
+cudaError_t launch_mppi(const MppiArgs &a, cudaStream_t s);
 // One SmoothSrc per live human of a batch (window offsets resolved on the device).
 cudaError_t launch_union_sources(const BatchHuman *humans, const int *n_humans, int max_humans, SmoothSrc *srcs,
                                  cudaStream_t s);
