@@ -467,6 +467,27 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
                 "frames": int(lat_u.size), "p50_ms": float(np.percentile(lat_u, 50) * 1e3),
                 "p99_ms": float(np.percentile(lat_u, 99) * 1e3), "sigma_cells": 1.5,
                 "union_grid": f"[{hu0.horizon}][{hu0.grid[4]}][{hu0.grid[3]}]"}
+            # MPPI local planner on that union grid: 8192 perturbed sequences of
+            # 30 steps of 0.1 s (every 5th prediction step)
+            Nm, Tm = 8192, 30
+            rng = np.random.default_rng([workloads.MASTER_SEED, 9])
+            mp = pm.make_mppi(Nm, Tm, 0.1, 5, [3.0, 3.0, 10.0, 0.0], [0.6, 0.6, 2.0, 0.0], [2.0, 1.0],
+                              [15.0, 15.0, 0.5, 0.0], 0.1, 1000.0, 0.1, 2.0)
+            u_ref = torch.zeros((Tm, 2), device=dev)
+            delta = torch.tensor((rng.normal(size=(Tm, Nm, 2)) * [0.6, 0.5]).astype(np.float32), device=dev)
+            ctg = torch.empty((Tm, Nm), device=dev)
+            u_opt = torch.empty((Tm, 2), device=dev)
+            x0, y0, res, W, H = hu0.grid
+            rg = pm.make_grid(x0, y0, res, W, H)
+
+            def mppi():
+                pm.pm_mppi_solve(ctx, mp, [5.0, 5.0, 0.5, 0.6], u_ref, delta, srv_u.union, hu0.horizon, rg, ctg,
+                                 u_opt, stream)
+            mppi_ms = time_events(torch, stream, mppi, 20)
+            out["mppi"] = {"ms_per_solve": mppi_ms, "samples": Nm, "steps": Tm,
+                           "sample_steps_per_s": Nm * Tm / (mppi_ms * 1e-3),
+                           "config": "robot of Eq. 8, 8192 samples x 30 steps of 0.1 s, collision cost from the "
+                                     "64-human union grid [150][400][400]"}
         finally:
             srv_u.close()
         if args.serving_seconds > 0:
