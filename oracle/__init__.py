@@ -66,7 +66,8 @@ _u64p = C.POINTER(C.c_uint64)
 _i32p = C.POINTER(C.c_int32)
 _u8p = C.POINTER(C.c_uint8)
 
-_MODEL = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_uint64]
+_MODEL = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_uint64, C.c_int,
+          C.POINTER(C.c_double), C.c_uint32]
 
 
 def _declare(lib):
@@ -115,13 +116,16 @@ def _ptr(a, typ):
 class Model:
     """Parameters of the human model (Sec. III-A).
 
-    K headings theta_k = 2*pi*k/K at one speed ``v``; step ``dt``;
-    Q = -w1*v*dt - w2*||z + v*dt*e_theta - g||; ``goals`` [G, 2]; ``beta`` [B];
-    ``mask_off`` bit k set disables heading k (Q = -inf, Sec. IV-B).
+    K headings theta_k = 2*pi*k/K; the controls are those headings at the
+    speeds ``v * speeds[s]`` (default one speed, multiplier 1), control index
+    u = s*K + k; step ``dt``;
+    Q_u = -w1*v*m_s*dt - w2*||z + v*m_s*dt*e_theta - g||; ``goals`` [G, 2];
+    ``beta`` [B]; ``mask_off`` bit k disables heading k and ``speed_off`` bit s
+    disables speed s (Q = -inf: the stationary masking of Sec. IV-B).
     Float inputs are kept exactly as given (FP32 inputs stay FP32-valued).
     """
 
-    def __init__(self, K, v, dt, goals, beta, w1=1.0, w2=1.0, mask_off=0):
+    def __init__(self, K, v, dt, goals, beta, w1=1.0, w2=1.0, mask_off=0, speeds=(1.0,), speed_off=0):
         self.K = int(K)
         self.v = float(v)
         self.dt = float(dt)
@@ -130,6 +134,16 @@ class Model:
         self.goals = np.ascontiguousarray(np.asarray(goals, dtype=np.float64).reshape(-1, 2))
         self.beta = np.ascontiguousarray(np.asarray(beta, dtype=np.float64).reshape(-1))
         self.mask_off = int(mask_off)
+        self.speeds = np.ascontiguousarray(np.asarray(speeds, dtype=np.float64).reshape(-1))
+        self.speed_off = int(speed_off)
+
+    @property
+    def S(self):
+        return self.speeds.shape[0]
+
+    @property
+    def U(self):
+        return self.S * self.K
 
     @property
     def G(self):
@@ -140,7 +154,8 @@ class Model:
         return self.beta.shape[0]
 
     def _args(self):
-        return [self.K, self.v, self.dt, self.w1, self.w2, C.c_uint64(self.mask_off)]
+        return [self.K, self.v, self.dt, self.w1, self.w2, C.c_uint64(self.mask_off), self.S,
+                _ptr(self.speeds, _dp), C.c_uint32(self.speed_off)]
 
 
 def philox4x64(ctr, key):
@@ -162,9 +177,9 @@ def uniform_step(seed, human, i, t):
 
 
 def log_policy(model: Model, z, beta, goal):
-    """log pi(theta_k | z; beta, g) for k = 0..K-1 (Eq. 2)."""
+    """log pi(u | z; beta, g) for the controls u = s*K + k (Eq. 2)."""
     lib = _load()
-    out = np.zeros(model.K, dtype=np.float64)
+    out = np.zeros(model.U, dtype=np.float64)
     lib.orc_log_policy(*model._args(), float(z[0]), float(z[1]), float(beta), float(goal[0]),
                        float(goal[1]), _ptr(out, _dp))
     return out
@@ -214,7 +229,8 @@ def bin_point(x, y, grid):
 
 def rollout(model: Model, log_b, z0, T, seed, human, i0, i1, grid=None, want_counts=True,
             want_headings=False, want_states32=False, want_states64=False, want_comp=False):
-    """Algorithm 1 for particles [i0, i1) of stream (seed, human).
+    """Algorithm 1 for particles [i0, i1) of stream (seed, human); ``headings``
+    holds the drawn control index u = s*K + k.
 
     ``z0`` is taken as FP32 (the observed state handed to the GPU); ``log_b``
     is the belief b^{t'} (FP32 values from the GPU side are exact in FP64).

@@ -22,7 +22,11 @@
  * Readings of points the paper leaves open (each listed in the design doc):
  *   - Q(z, theta; g) = -w1*v*dt - w2*|| z + v*dt*(cos theta, sin theta) - g ||,
  *     evaluated at the next state (the running example's Q is heading-free).
- *   - K headings theta_k = 2*pi*k/K, counter-clockwise from +x, one speed v.
+ *   - K headings theta_k = 2*pi*k/K, counter-clockwise from +x; the controls
+ *     are those headings at speeds v*mult[s] (one speed, mult = {1}, unless
+ *     given), index u = s*K + k; a disabled heading or speed has Q = -inf.
+ *   - the observed control: the continuous heading of the displacement and the
+ *     enabled speed whose multiplier is nearest to its length / (v*dt).
  *   - the observed control is the continuous heading atan2(dy, dx) of the
  *     displacement; Q is evaluated there and normalised over the K headings;
  *     a displacement shorter than 1e-6 m leaves the belief unchanged.
@@ -110,6 +114,9 @@ typedef struct {
     const double *goals; /* [G][2] */
     const double *beta;  /* [B] */
     uint64_t mask_off;   /* bit k set: heading k disabled, Q = -inf */
+    int S;               /* speeds: control u = s*K + k moves v*mult[s]*dt along theta_k */
+    const double *mult;  /* [S] speed multipliers (> 0) */
+    uint32_t speed_off;  /* bit s set: speed s disabled, Q = -inf (stationary masking) */
 } orc_model;
 
 /* Unit vector of heading k, theta_k = 2*pi*k/K. Quarter turns are exact. */
@@ -129,18 +136,34 @@ static void orc_heading(int K, int k, double *c, double *s)
     *s = sin(th);
 }
 
-static int orc_disabled(const orc_model *m, int k)
+static int orc_disabled(const orc_model *m, int u)
 {
-    return (k < 64) && ((m->mask_off >> k) & 1u);
+    int k = u % m->K, sp = u / m->K;
+    return ((k < 64) && ((m->mask_off >> k) & 1u)) || ((m->speed_off >> sp) & 1u);
 }
 
-/* Q(z, theta; g) = -w1*v*dt - w2*||z + v*dt*(cos, sin) - g||. */
-static double orc_Q(const orc_model *m, double zx, double zy, double c, double s,
+/* Q(z, u; g) = -w1*v*m_s*dt - w2*||z + v*m_s*dt*(cos, sin) - g|| for the
+ * control of speed multiplier ms and heading (c, s). */
+static double orc_Q(const orc_model *m, double zx, double zy, double c, double s, double ms,
                     double gx, double gy)
 {
-    double st = m->v * m->dt;
+    double st = m->v * ms * m->dt;
     double dx = zx + st * c - gx, dy = zy + st * s - gy;
-    return -m->w1 * m->v * m->dt - m->w2 * sqrt(dx * dx + dy * dy);
+    return -m->w1 * m->v * ms * m->dt - m->w2 * sqrt(dx * dx + dy * dy);
+}
+
+/* The enabled speed whose multiplier is nearest to len / (v*dt) (lower index
+ * on a tie): the speed of an observed displacement of length len. */
+static int orc_snap_speed(const orc_model *m, double len)
+{
+    double r = len / (m->v * m->dt), best = INFINITY;
+    int sb = 0;
+    for (int sp = 0; sp < m->S; ++sp) {
+        if ((m->speed_off >> sp) & 1u) continue;
+        double d = fabs(m->mult[sp] - r);
+        if (d < best) { best = d; sb = sp; }
+    }
+    return sb;
 }
 
 /* log pi(k | z; beta, g) for every heading k (Eq. 2); disabled headings get
@@ -148,36 +171,43 @@ static double orc_Q(const orc_model *m, double zx, double zy, double c, double s
 double orc_log_policy_raw(const orc_model *m, double zx, double zy, double beta,
                           double gx, double gy, double *logpi)
 {
+    int U = m->S * m->K;
     double mx = -INFINITY;
-    for (int k = 0; k < m->K; ++k) {
+    for (int u = 0; u < U; ++u) {
         double c, s;
-        orc_heading(m->K, k, &c, &s);
-        logpi[k] = orc_disabled(m, k) ? -INFINITY : beta * orc_Q(m, zx, zy, c, s, gx, gy);
-        if (logpi[k] > mx) mx = logpi[k];
+        orc_heading(m->K, u % m->K, &c, &s);
+        logpi[u] = orc_disabled(m, u) ? -INFINITY : beta * orc_Q(m, zx, zy, c, s, m->mult[u / m->K], gx, gy);
+        if (logpi[u] > mx) mx = logpi[u];
     }
     double sum = 0.0;
-    for (int k = 0; k < m->K; ++k)
-        if (logpi[k] > -INFINITY) sum += exp(logpi[k] - mx);
+    for (int u = 0; u < U; ++u)
+        if (logpi[u] > -INFINITY) sum += exp(logpi[u] - mx);
     double lse = mx + log(sum);
-    for (int k = 0; k < m->K; ++k) logpi[k] = logpi[k] - lse;
+    for (int u = 0; u < U; ++u) logpi[u] = logpi[u] - lse;
     return lse;
 }
 
-/* Flat-argument form of orc_log_policy_raw for the Python wrapper. */
-void orc_log_policy(int K, double v, double dt, double w1, double w2, uint64_t mask_off,
-                    double zx, double zy, double beta, double gx, double gy, double *logpi)
+#define ORC_MODEL_ARGS int K, double v, double dt, double w1, double w2, uint64_t mask_off, \
+                       int S, const double *mult, uint32_t speed_off
+#define ORC_MODEL(G_, goals_, B_, beta_) {K, v, dt, w1, w2, G_, B_, goals_, beta_, mask_off, S, mult, speed_off}
+
+/* Flat-argument form of orc_log_policy_raw for the Python wrapper
+ * (logpi [S*K], control u = s*K + k). */
+void orc_log_policy(ORC_MODEL_ARGS, double zx, double zy, double beta, double gx, double gy, double *logpi)
 {
-    orc_model m = {K, v, dt, w1, w2, 1, 1, NULL, NULL, mask_off};
+    orc_model m = ORC_MODEL(1, NULL, 1, NULL);
     orc_log_policy_raw(&m, zx, zy, beta, gx, gy, logpi);
 }
 
-/* log pi(theta_obs | z; beta, g) for a continuous observed heading
- * (differential flatness: the control is recovered from two states). */
-static double orc_log_policy_obs(const orc_model *m, double zx, double zy, double th,
+/* log pi(u_obs | z; beta, g) for the observed control recovered from two
+ * states (differential flatness): the continuous heading th and the enabled
+ * speed nearest to the displacement length len. */
+static double orc_log_policy_obs(const orc_model *m, double zx, double zy, double th, double len,
                                  double beta, double gx, double gy, double *scratch)
 {
     double lse = orc_log_policy_raw(m, zx, zy, beta, gx, gy, scratch);
-    return beta * orc_Q(m, zx, zy, cos(th), sin(th), gx, gy) - lse;
+    double ms = m->mult[orc_snap_speed(m, len)];
+    return beta * orc_Q(m, zx, zy, cos(th), sin(th), ms, gx, gy) - lse;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -196,22 +226,22 @@ static double orc_lse(const double *x, int n)
 
 /* obs: [n_obs+1][2]; log_b: [G*B] in/out, index j = g*B + b.
  * Returns the number of steps skipped as stationary. */
-int orc_update_posterior(int K, double v, double dt, double w1, double w2, uint64_t mask_off,
-                         int G, const double *goals, int B, const double *beta,
+int orc_update_posterior(ORC_MODEL_ARGS, int G, const double *goals, int B, const double *beta,
                          const double *obs, int n_obs, double *log_b)
 {
-    orc_model m = {K, v, dt, w1, w2, G, B, goals, beta, mask_off};
+    orc_model m = ORC_MODEL(G, goals, B, beta);
     int J = G * B, skipped = 0;
-    double *scratch = (double *)malloc(sizeof(double) * (size_t)(K > 0 ? K : 1));
+    double *scratch = (double *)malloc(sizeof(double) * (size_t)(S * K > 0 ? S * K : 1));
     double *l = (double *)malloc(sizeof(double) * (size_t)J);
     for (int t = 0; t < n_obs; ++t) {
         double zx = obs[2 * t], zy = obs[2 * t + 1];
         double dx = obs[2 * t + 2] - zx, dy = obs[2 * t + 3] - zy;
-        if (sqrt(dx * dx + dy * dy) < 1e-6) { ++skipped; continue; }
+        double len = sqrt(dx * dx + dy * dy);
+        if (len < 1e-6) { ++skipped; continue; }
         double th = atan2(dy, dx);
         for (int j = 0; j < J; ++j) {
             int g = j / B, b = j % B;
-            double lp = orc_log_policy_obs(&m, zx, zy, th, beta[b], goals[2 * g], goals[2 * g + 1], scratch);
+            double lp = orc_log_policy_obs(&m, zx, zy, th, len, beta[b], goals[2 * g], goals[2 * g + 1], scratch);
             l[j] = lp + log_b[j];          /* log pi + log b^t              */
         }
         double lse = orc_lse(l, J);          /* log sum_{b',g'} pi * b^t      */
@@ -286,27 +316,30 @@ float orc_inv_res(float res)
 /* The policy is evaluated at the FP64 particle state; a shadow FP32 state   */
 /* takes the same FP32 steps (float)(v*dt*cos theta_k) and is what is binned. */
 /* ------------------------------------------------------------------------ */
-void orc_rollout(int K, double v, double dt, double w1, double w2, uint64_t mask_off,
-                 int G, const double *goals, int B, const double *beta,
+void orc_rollout(ORC_MODEL_ARGS, int G, const double *goals, int B, const double *beta,
                  const double *log_b, float z0x, float z0y, int T,
                  uint64_t seed, uint32_t human, int64_t i0, int64_t i1,
                  float gx0, float gy0, float res, int W, int H,
                  uint32_t *counts, uint32_t *oob, uint8_t *headings,
                  float *states32, double *states64, int32_t *comp)
 {
-    orc_model m = {K, v, dt, w1, w2, G, B, goals, beta, mask_off};
-    int J = G * B;
-    double st = v * dt;
-    double *hc = (double *)malloc(sizeof(double) * (size_t)K);
-    double *hs = (double *)malloc(sizeof(double) * (size_t)K);
-    float *fx = (float *)malloc(sizeof(float) * (size_t)K);
-    float *fy = (float *)malloc(sizeof(float) * (size_t)K);
-    double *logpi = (double *)malloc(sizeof(double) * (size_t)K);
-    double *e = (double *)malloc(sizeof(double) * (size_t)K);
-    for (int k = 0; k < K; ++k) {
-        orc_heading(K, k, &hc[k], &hs[k]);
-        fx[k] = (float)(st * hc[k]);
-        fy[k] = (float)(st * hs[k]);
+    orc_model m = ORC_MODEL(G, goals, B, beta);
+    int J = G * B, U = S * K;
+    /* control u = s*K + k moves (v*mult[s]*dt) * (cos, sin)(theta_k); the FP32
+     * shadow state moves by that product rounded once to FP32 */
+    double *hc = (double *)malloc(sizeof(double) * (size_t)U);
+    double *hs = (double *)malloc(sizeof(double) * (size_t)U);
+    float *fx = (float *)malloc(sizeof(float) * (size_t)U);
+    float *fy = (float *)malloc(sizeof(float) * (size_t)U);
+    double *logpi = (double *)malloc(sizeof(double) * (size_t)U);
+    double *e = (double *)malloc(sizeof(double) * (size_t)U);
+    for (int u = 0; u < U; ++u) {
+        double c, sn, st = v * mult[u / K] * dt;
+        orc_heading(K, u % K, &c, &sn);
+        hc[u] = st * c;
+        hs[u] = st * sn;
+        fx[u] = (float)(st * c);
+        fy[u] = (float)(st * sn);
     }
     float inv_res = orc_inv_res(res);
     for (int64_t i = i0; i < i1; ++i) {
@@ -319,10 +352,10 @@ void orc_rollout(int K, double v, double dt, double w1, double w2, uint64_t mask
         float sx = z0x, sy = z0y;
         for (int t = 1; t <= T; ++t) {
             orc_log_policy_raw(&m, zx, zy, bt, gx, gy, logpi);
-            for (int k = 0; k < K; ++k) e[k] = exp(logpi[k]);
-            int k = orc_inverse_cdf(e, K, orc_uniform_step(seed, human, (uint64_t)i, t));
-            zx += st * hc[k];
-            zy += st * hs[k];
+            for (int u = 0; u < U; ++u) e[u] = exp(logpi[u]);
+            int k = orc_inverse_cdf(e, U, orc_uniform_step(seed, human, (uint64_t)i, t));
+            zx += hc[k];
+            zy += hs[k];
             volatile float nx = sx + fx[k];
             volatile float ny = sy + fy[k];
             sx = nx;
@@ -369,14 +402,13 @@ void orc_bin_states(const float *states, int64_t n, int T, float x0, float y0, f
 /* edge_mass[T]: mass of states within edge_tol of a cell edge.               */
 /* Returns 0 on success, -1 if K is unsupported or memory is short.          */
 /* ------------------------------------------------------------------------ */
-int orc_exact_occupancy(int K, double v, double dt, double w1, double w2, uint64_t mask_off,
-                        int G, const double *goals, int B, const double *beta,
+int orc_exact_occupancy(ORC_MODEL_ARGS, int G, const double *goals, int B, const double *beta,
                         const double *log_b, double z0x, double z0y, int T,
                         double x0, double y0, double res, int W, int H, double edge_tol,
                         double *p, double *p_oob, double *edge_mass)
 {
-    if (K % 2 != 0 || K < 2 || K > 8) return -1;
-    orc_model m = {K, v, dt, w1, w2, G, B, goals, beta, mask_off};
+    if (K % 2 != 0 || K < 2 || K > 8 || S != 1 || mult[0] != 1.0) return -1; /* one speed: a lattice */
+    orc_model m = ORC_MODEL(G, goals, B, beta);
     int D = K / 2, side = 2 * T + 1;
     size_t nstate = 1;
     for (int d = 0; d < D; ++d) nstate *= (size_t)side;
@@ -484,38 +516,37 @@ int orc_exact_occupancy(int K, double v, double dt, double w1, double w2, uint64
 /* ------------------------------------------------------------------------ */
 typedef struct { double q, dgx, dgy, dv, dw1, dw2; } orc_qgrad;
 
-static orc_qgrad orc_Q_and_grad(const orc_model *m, double zx, double zy, double c, double s,
+static orc_qgrad orc_Q_and_grad(const orc_model *m, double zx, double zy, double c, double s, double ms,
                                 double gx, double gy)
 {
     orc_qgrad r;
-    double st = m->v * m->dt;
+    double st = m->v * ms * m->dt;
     double dx = zx + st * c - gx, dy = zy + st * s - gy;
     double dist = sqrt(dx * dx + dy * dy);
     double ux = 0.0, uy = 0.0;
     if (dist >= 1e-9) { ux = dx / dist; uy = dy / dist; }
-    r.q = -m->w1 * m->v * m->dt - m->w2 * dist;
+    r.q = -m->w1 * m->v * ms * m->dt - m->w2 * dist;
     r.dgx = m->w2 * ux;                 /* dQ/dg = w2 (z' - g)/||z' - g|| */
     r.dgy = m->w2 * uy;
-    r.dv = -m->w1 * m->dt - m->w2 * m->dt * (c * ux + s * uy);
-    r.dw1 = -m->v * m->dt;
+    r.dv = -m->w1 * ms * m->dt - m->w2 * ms * m->dt * (c * ux + s * uy);
+    r.dw1 = -m->v * ms * m->dt;
     r.dw2 = -dist;
     return r;
 }
 
-int orc_loglik_grad(int K, double v, double dt, double w1, double w2, uint64_t mask_off,
-                    int G, const double *goals, int B, const double *beta,
+int orc_loglik_grad(ORC_MODEL_ARGS, int G, const double *goals, int B, const double *beta,
                     int M, const int32_t *offsets, const double *traj, const double *log_prior,
                     double *L_out, double *d_goals, double *d_v, double *d_w)
 {
-    if (G > 64 || K < 1) return -1;
-    orc_model m = {K, v, dt, w1, w2, G, B, goals, beta, mask_off};
-    int J = G * B;
+    if (G > 64 || K < 1 || S < 1) return -1;
+    orc_model m = ORC_MODEL(G, goals, B, beta);
+    int J = G * B, U = S * K;
     double *A = (double *)malloc(sizeof(double) * (size_t)J);
     double *gr = (double *)malloc(sizeof(double) * (size_t)J * 5); /* dgx dgy dv dw1 dw2 */
-    orc_qgrad *qk = (orc_qgrad *)malloc(sizeof(orc_qgrad) * (size_t)(K > 0 ? K : 1));
+    orc_qgrad *qk = (orc_qgrad *)malloc(sizeof(orc_qgrad) * (size_t)U);
     double *hc = (double *)malloc(sizeof(double) * (size_t)K);
     double *hs = (double *)malloc(sizeof(double) * (size_t)K);
-    double *pk = (double *)malloc(sizeof(double) * (size_t)K);
+    double *pk = (double *)malloc(sizeof(double) * (size_t)U);
     for (int k = 0; k < K; ++k) orc_heading(K, k, &hc[k], &hs[k]);
     double Lsum = 0.0;
     double acc_g[2 * 64 + 8];
@@ -529,25 +560,27 @@ int orc_loglik_grad(int K, double v, double dt, double w1, double w2, uint64_t m
         for (int pt = offsets[mm]; pt + 1 < offsets[mm + 1]; ++pt) {
             double zx = traj[2 * pt], zy = traj[2 * pt + 1];
             double dx = traj[2 * pt + 2] - zx, dy = traj[2 * pt + 3] - zy;
-            if (sqrt(dx * dx + dy * dy) < 1e-6) continue;
+            double len = sqrt(dx * dx + dy * dy);
+            if (len < 1e-6) continue;
             double th = atan2(dy, dx), co = cos(th), so = sin(th);
+            double mo = mult[orc_snap_speed(&m, len)]; /* the observed control's speed */
             for (int j = 0; j < J; ++j) {
                 int g = j / B, b = j % B;
                 double bt = beta[b], gx = goals[2 * g], gy = goals[2 * g + 1];
                 double mx = -INFINITY;
-                for (int k = 0; k < K; ++k) {
-                    qk[k] = orc_Q_and_grad(&m, zx, zy, hc[k], hs[k], gx, gy);
+                for (int k = 0; k < U; ++k) {
+                    qk[k] = orc_Q_and_grad(&m, zx, zy, hc[k % K], hs[k % K], mult[k / K], gx, gy);
                     pk[k] = orc_disabled(&m, k) ? -INFINITY : bt * qk[k].q;
                     if (pk[k] > mx) mx = pk[k];
                 }
-                double S = 0.0;
-                for (int k = 0; k < K; ++k) { pk[k] = (pk[k] == -INFINITY) ? 0.0 : exp(pk[k] - mx); S += pk[k]; }
-                double lse = mx + log(S);
-                orc_qgrad qo = orc_Q_and_grad(&m, zx, zy, co, so, gx, gy);
+                double Ssum = 0.0;
+                for (int k = 0; k < U; ++k) { pk[k] = (pk[k] == -INFINITY) ? 0.0 : exp(pk[k] - mx); Ssum += pk[k]; }
+                double lse = mx + log(Ssum);
+                orc_qgrad qo = orc_Q_and_grad(&m, zx, zy, co, so, mo, gx, gy);
                 A[j] += bt * qo.q - lse;
                 double e_gx = 0, e_gy = 0, e_v = 0, e_w1 = 0, e_w2 = 0;
-                for (int k = 0; k < K; ++k) {
-                    double pi = pk[k] / S;
+                for (int k = 0; k < U; ++k) {
+                    double pi = pk[k] / Ssum;
                     e_gx += pi * qk[k].dgx; e_gy += pi * qk[k].dgy; e_v += pi * qk[k].dv;
                     e_w1 += pi * qk[k].dw1; e_w2 += pi * qk[k].dw2;
                 }
