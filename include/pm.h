@@ -54,9 +54,22 @@ typedef enum pm_status {
  * launch parameters. Not thread-safe; use one context per host thread. */
 typedef struct pm_ctx pm_ctx;
 
+#define PM_MAX_SPEEDS 4        /* speeds of the control set          */
+
 /* Human model. `goals` and `beta` are device pointers ([G][2] and [B]).
  * `heading_off` bit k set disables heading k (Q = -inf, so pi = 0), the
- * control masking of Sec. IV-B. beta values must be >= 0. */
+ * control masking of Sec. IV-B. beta values must be >= 0.
+ *
+ * Controls: with n_speeds = 0 (or 1 with speed_mult[0] = 1) the K headings at
+ * the one speed v. With n_speeds = S in [1, PM_MAX_SPEEDS], the S*K controls
+ * u = s*K + k move v*speed_mult[s]*dt along theta_k, with
+ * Q_u = -w1*v*speed_mult[s]*dt - w2*||z + v*speed_mult[s]*dt*e_k - g||, and
+ * `speed_off` bit s disables speed s (the stationary masking of Sec. IV-B:
+ * the high-speed controls of a human seen standing still). Several speeds
+ * need K a multiple of 4 with no heading disabled, S*K <= 256, and
+ * multipliers > 0; the observed control of a displacement is its continuous
+ * heading at the enabled speed whose multiplier is nearest to its length /
+ * (v*dt). Traced heading indices are control indices u. */
 typedef struct pm_model {
     int32_t K;
     float speed; /* v  [m/s]            */
@@ -68,6 +81,9 @@ typedef struct pm_model {
     const float *goals;
     const float *beta;
     uint64_t heading_off;
+    int32_t n_speeds;                 /* 0: one speed, multiplier 1      */
+    float speed_mult[PM_MAX_SPEEDS];  /* speed s is v * speed_mult[s]    */
+    uint32_t speed_off;               /* bit s set: speed s disabled     */
 } pm_model;
 
 /* Occupancy grid: cell (cx, cy) covers [x0 + cx*res, x0 + (cx+1)*res) x

@@ -7,7 +7,9 @@
 //   dL/dp = sum_m sum_j w_mj sum_t d log pi_j / dp,  w_mj = softmax_j(log prior_j + A_mj)
 //   d log pi / dp = beta (dQ(theta_obs)/dp - sum_k pi_k dQ(theta_k)/dp)
 //   dQ/dg = w2 u, dQ/dv = -w1 dt - w2 dt e.u, dQ/dw1 = -v dt, dQ/dw2 = -d,
-//   with d = ||z + v dt e - g|| and u = (z + v dt e - g) / d.
+//   with d = ||z + v dt e - g|| and u = (z + v dt e - g) / d; with several
+//   speeds (Sec. IV-B) each control carries its multiplier m_q in the step
+//   and in these derivatives, which makes dL/dw1 nonzero.
 //
 // One CTA per trajectory; a warp per component (beta, g) with its lanes over
 // the trajectory's steps and the headings unrolled in registers. The
@@ -108,12 +110,97 @@ __device__ __forceinline__ StepGrad step_terms(const AdjointArgs &a, float zx, f
     return r;
 }
 
-template <int KT>
+// Several speeds (control u = speed q x heading k moving sl_q = v m_q dt):
+// Q_u = -w1 v m_q dt - w2 d_u, so
+//   dQ_u/dg = w2 u_u, dQ_u/dv = -m_q dt (w1 + w2 e_k.u_u), dQ_u/dw1 = -v m_q dt,
+//   dQ_u/dw2 = -d_u,
+// and the observed control is the observed direction at the enabled speed
+// nearest to the step's length. cu[u] = (cos, sin of theta_k, sl_q, m_q or 0
+// when speed q is disabled); the controls are visited in three passes
+// (maximum, sum, expectations) instead of being held in registers.
+__device__ __forceinline__ StepGrad step_terms_ms(const AdjointArgs &a, const float4 *cu, int U, float zx, float zy,
+                                                  float ex, float ey, float len, float gx, float gy, float beta,
+                                                  bool grad)
+{
+    int q0 = 0;
+    float best = INFINITY;
+    const float r = len / a.s;
+    for (int q = 0; q < a.sp.S; ++q) {
+        const float d = fabsf(a.sp.mult[q] - r);
+        if (((a.sp.speed_on >> q) & 1u) && d < best) {
+            best = d;
+            q0 = q;
+        }
+    }
+    const float so = a.sp.sl[q0], mo = a.sp.mult[q0];
+    const float px = zx - gx, py = zy - gy;
+    const float P = fmaf(px, px, py * py);
+    const float xo = fmaxf(fmaf(so, so, P) + 2.0f * so * fmaf(ex, px, ey * py), 0.0f);
+    const float ro = rsqrtf(fmaxf(xo, 1e-30f));
+    const float d_o = xo * ro;
+    const float bw1 = beta * a.sp.w1, bw2 = beta * a.w2;
+    auto logit = [&](const float4 &c, float &du, float &rk) {
+        const float xk = fmaxf(fmaf(c.z, c.z, P) + 2.0f * c.z * fmaf(c.x, px, c.y * py), 0.0f);
+        rk = rsqrtf(fmaxf(xk, 1e-30f));
+        du = xk * rk;
+        const float num = fmaf(so - c.z, so + c.z, 2.0f * fmaf(fmaf(so, ex, -c.z * c.x), px, fmaf(so, ey, -c.z * c.y) * py));
+        return fmaf(bw1, so - c.z, bw2 * (num / fmaxf(d_o + du, 1e-30f)));
+    };
+    float m = -INFINITY;
+    for (int u = 0; u < U; ++u) {
+        const float4 c = cu[u];
+        if (c.w == 0.0f) continue;
+        float du, rk;
+        m = fmaxf(m, logit(c, du, rk));
+    }
+    float S = 0.0f;
+    for (int u = 0; u < U; ++u) {
+        const float4 c = cu[u];
+        if (c.w == 0.0f) continue;
+        float du, rk;
+        S += expf(logit(c, du, rk) - m);
+    }
+    StepGrad res;
+    res.logpi = -m - logf(S);
+    if (!grad) return res;
+    const float inv = 1.0f / S;
+    float sux = 0.f, suy = 0.f, smeu = 0.f, sm = 0.f, sd = 0.f;
+    for (int u = 0; u < U; ++u) {
+        const float4 c = cu[u];
+        if (c.w == 0.0f) continue;
+        float du, rk;
+        const float pk = expf(logit(c, du, rk) - m) * inv;
+        const float uxk = fmaf(c.z, c.x, px) * rk, uyk = fmaf(c.z, c.y, py) * rk; // (z + sl e_k - g) / d_u
+        sux = fmaf(pk, uxk, sux);
+        suy = fmaf(pk, uyk, suy);
+        smeu = fmaf(pk * c.w, fmaf(c.x, uxk, c.y * uyk), smeu);
+        sm = fmaf(pk, c.w, sm);
+        sd = fmaf(pk, du, sd);
+    }
+    const float uox = fmaf(so, ex, px) * ro, uoy = fmaf(so, ey, py) * ro;
+    res.gx = bw2 * (uox - sux);
+    res.gy = bw2 * (uoy - suy);
+    res.gv = beta * a.dt * fmaf(a.sp.w1, sm - mo, a.w2 * (smeu - mo * fmaf(ex, uox, ey * uoy)));
+    res.gw1 = beta * a.v * a.dt * (sm - mo);
+    res.gw2 = beta * (sd - d_o);
+    return res;
+}
+
+template <int KT, bool MS = false>
 __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(const __grid_constant__ AdjointArgs a)
 {
     __shared__ double A_s[kMaxJ];
     __shared__ float G_s[kMaxJ][5];
     __shared__ int last;
+    __shared__ float4 cu[MS ? PM_MAX_SPEEDS * kMaxK : 1];
+    const int U = MS ? a.sp.S * a.K : 0;
+    if constexpr (MS) {
+        for (int u = threadIdx.x; u < U; u += blockDim.x) {
+            const int q = u / a.K, k = u - q * a.K;
+            cu[u] = make_float4(a.ux[k], a.uy[k], a.sp.sl[q], ((a.sp.speed_on >> q) & 1u) ? a.sp.mult[q] : 0.0f);
+        }
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int J = a.G * a.B;
     const int m = blockIdx.x;
@@ -135,7 +222,8 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(const __grid_const
             const float dx = z[2] - zx, dy = z[3] - zy;
             const float len = sqrtf(fmaf(dx, dx, dy * dy));
             if (!(len >= 1e-6f)) continue; // stationary step: no information
-            const StepGrad s = step_terms<KT>(a, zx, zy, dx / len, dy / len, gx, gy, beta, grad);
+            const StepGrad s = MS ? step_terms_ms(a, cu, U, zx, zy, dx / len, dy / len, len, gx, gy, beta, grad)
+                                  : step_terms<KT>(a, zx, zy, dx / len, dy / len, gx, gy, beta, grad);
             A += (double)s.logpi;
             if (grad) {
                 Gx += s.gx;
@@ -251,6 +339,10 @@ size_t adjoint_scratch_bytes(int M, int G) { return (size_t)M * (2 * G + 4) * si
 
 cudaError_t launch_adjoint(const AdjointArgs &a, cudaStream_t s)
 {
+    if (a.sp.S > 0) {
+        adjoint_kernel<8, true><<<a.M, kAdjThreads, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     const int KT = rollout_kt_for(a.K);
     switch (KT) {
     case 8: adjoint_kernel<8><<<a.M, kAdjThreads, 0, s>>>(a); break;

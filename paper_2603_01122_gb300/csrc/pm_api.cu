@@ -127,6 +127,12 @@ void unit_heading(int K, int k, double *c, double *s)
     }
 }
 
+// The control set has several speeds, or one speed with a multiplier != 1.
+bool multi_speed(const pm_model *m)
+{
+    return m->n_speeds >= 2 || (m->n_speeds == 1 && m->speed_mult[0] != 1.0f);
+}
+
 uint64_t enabled_mask(const pm_model *m)
 {
     const uint64_t allK = (m->K >= 64) ? ~0ull : ((1ull << m->K) - 1ull);
@@ -148,6 +154,18 @@ pm_status check_model(const pm_model *m, bool need_tables = true)
     if (enabled_mask(m) == 0) return fail(PM_EINVAL, "every heading is disabled");
     const double s = (double)m->speed * (double)m->dt;
     if (!(s * s > 1e-30) || !std::isfinite(s)) return fail(PM_EINVAL, "step v*dt out of range");
+    if (m->n_speeds < 0 || m->n_speeds > PM_MAX_SPEEDS)
+        return fail(PM_EINVAL, "n_speeds=%d outside [0, %d]", m->n_speeds, PM_MAX_SPEEDS);
+    for (int sp = 0; sp < m->n_speeds; ++sp)
+        if (!finite_pos(m->speed_mult[sp]) || !(s * m->speed_mult[sp] * s * m->speed_mult[sp] > 1e-30))
+            return fail(PM_EINVAL, "speed_mult[%d] must be finite and > 0", sp);
+    if (m->n_speeds > 0 && (m->speed_off & ((1u << m->n_speeds) - 1u)) == ((1u << m->n_speeds) - 1u))
+        return fail(PM_EINVAL, "every speed is disabled");
+    if (multi_speed(m)) {
+        if (m->K % 4 != 0 || enabled_mask(m) != ((m->K >= 64) ? ~0ull : ((1ull << m->K) - 1ull)))
+            return fail(PM_EINVAL, "several speeds need K a multiple of 4 with every heading enabled");
+        if (m->n_speeds * m->K > 256) return fail(PM_EINVAL, "n_speeds*K=%d above 256", m->n_speeds * m->K);
+    }
     return PM_OK;
 }
 
@@ -180,11 +198,72 @@ void fill_rollout_tables(const pm_model *m, pm::RolloutArgs &a)
     a.tab.lb_gap = (float)(2.0 * s * std::sin(3.14159265358979323846 / (2.0 * m->K)));
     a.s2 = (float)(s * s);
     a.w2_log2e = (float)((double)m->w2 * 1.4426950408889634);
+    a.w1_vdt_log2e = (float)((double)m->w1 * s * 1.4426950408889634);
+    a.tab.S = 0; // one speed: the heading kernels
+    if (multi_speed(m)) {
+        a.tab.S = m->n_speeds;
+        double smax = 0.0;
+        for (int sp = 0; sp < m->n_speeds; ++sp) {
+            const double sl = (double)m->speed * (double)m->speed_mult[sp] * (double)m->dt;
+            a.tab.mult[sp] = m->speed_mult[sp];
+            a.tab.sl[sp] = (float)sl;
+            if (!((m->speed_off >> sp) & 1u)) {
+                a.tab.speed_on |= 1u << sp;
+                smax = std::max(smax, sl);
+            }
+            for (int k = 0; k < m->K; ++k) {
+                double c, sn;
+                unit_heading(m->K, k, &c, &sn);
+                a.tab.msx[sp][k] = (float)(sl * c);
+                a.tab.msy[sp][k] = (float)(sl * sn);
+            }
+        }
+        a.tab.lb_gap = (float)(2.0 * smax * std::sin(3.14159265358979323846 / (2.0 * m->K)));
+    }
     a.K = m->K;
     a.G = m->G;
     a.B = m->B;
     a.goals = m->goals;
     a.beta = m->beta;
+}
+
+// The speed set of the belief update and the adjoint (S = 0: one speed).
+void fill_speed_set(const pm_model *m, pm::SpeedSet &sp)
+{
+    std::memset(&sp, 0, sizeof sp);
+    sp.w1 = m->w1;
+    if (!multi_speed(m)) return;
+    sp.S = m->n_speeds;
+    for (int q = 0; q < m->n_speeds; ++q) {
+        sp.mult[q] = m->speed_mult[q];
+        sp.sl[q] = (float)((double)m->speed * (double)m->speed_mult[q] * (double)m->dt);
+        if (!((m->speed_off >> q) & 1u)) sp.speed_on |= 1u << q;
+    }
+}
+
+// Heading tables and model constants of the belief update (per-human tables
+// and observations are set by the caller).
+void fill_posterior_args(const pm_model *m, pm::PosteriorArgs &a)
+{
+    std::memset(&a, 0, sizeof a);
+    const double s = (double)m->speed * (double)m->dt;
+    for (int k = 0; k < m->K; ++k) {
+        double c, sn;
+        unit_heading(m->K, k, &c, &sn);
+        a.ux[k] = (float)c;
+        a.uy[k] = (float)sn;
+    }
+    a.enabled = enabled_mask(m);
+    a.s = (float)s;
+    a.s2 = (float)(s * s);
+    a.two_s = (float)(2.0 * s);
+    a.w2 = m->w2;
+    a.K = m->K;
+    a.G = m->G;
+    a.B = m->B;
+    a.goals = m->goals;
+    a.beta = m->beta;
+    fill_speed_set(m, a.sp);
 }
 
 pm_status ensure_stage(pm_ctx *ctx, size_t bytes)
@@ -303,24 +382,7 @@ pm_status posterior_impl(pm_ctx *ctx, const pm_model *model, const float *obs_xy
     if (!obs_xy) return fail(PM_EINVAL, "obs_xy is NULL");
     DeviceScope dev(ctx->device);
     pm::PosteriorArgs a;
-    std::memset(&a, 0, sizeof a);
-    const double s = (double)model->speed * (double)model->dt;
-    for (int k = 0; k < model->K; ++k) {
-        double c, sn;
-        unit_heading(model->K, k, &c, &sn);
-        a.ux[k] = (float)c;
-        a.uy[k] = (float)sn;
-    }
-    a.enabled = enabled_mask(model);
-    a.s = (float)s;
-    a.s2 = (float)(s * s);
-    a.two_s = (float)(2.0 * s);
-    a.w2 = model->w2;
-    a.K = model->K;
-    a.G = model->G;
-    a.B = model->B;
-    a.goals = model->goals;
-    a.beta = model->beta;
+    fill_posterior_args(model, a);
     a.obs = obs_xy;
     a.n_obs = n_obs;
     a.log_b = log_belief;
@@ -378,6 +440,7 @@ pm_status loglik_impl(pm_ctx *ctx, const pm_model *model, int32_t M, const int32
     a.dt = model->dt;
     a.v = model->speed;
     a.K = model->K;
+    fill_speed_set(model, a.sp);
     a.G = model->G;
     a.B = model->B;
     a.goals = model->goals;
@@ -436,7 +499,7 @@ pm::RolloutShape batch_shape_of(const pm_batch *b) { return pm::RolloutShape{b->
 
 size_t batch_dyn_smem(const pm_batch *b)
 {
-    if (b->warp_hist) return pm::batch_warp_tables_bytes(b->threads);
+    if (b->warp_hist) return pm::batch_warp_tables_bytes(b->threads, multi_speed(&b->shared));
     const int r = batch_radius_cap(b->window_kib, b->threads);
     const size_t cells = (size_t)(2 * r + 1) * (2 * r + 1);
     const size_t stride_words = (((cells + 1) / 2) + 3) & ~(size_t)3;
@@ -543,7 +606,7 @@ pm_status batch_upload(pm_batch *b, cudaStream_t stream)
     pm::RolloutArgs t;
     std::memset(&t, 0, sizeof t);
     fill_rollout_tables(&b->shared, t);
-    b->occ = pm::batch_rollout_occupancy(b->shared.K, t.enabled, batch_shape_of(b), batch_dyn_smem(b));
+    b->occ = pm::batch_rollout_occupancy(b->shared.K, t.enabled, t.tab.S, batch_shape_of(b), batch_dyn_smem(b));
     cudaGetLastError();
     return PM_OK;
 }
@@ -564,6 +627,7 @@ pm_status batch_predict_impl(pm_batch *b, cudaStream_t stream)
     a.enabled = t.enabled;
     a.s2 = t.s2;
     a.w2_log2e = t.w2_log2e;
+    a.w1_vdt_log2e = t.w1_vdt_log2e;
     a.K = b->shared.K;
     a.humans = b->d_humans;
     a.items = b->d_items;
@@ -599,24 +663,7 @@ pm_status pm_internal_posterior_on_scratch(const pm_model *model, const float *o
     if (n_obs == 0) return PM_OK;
     if (!obs_xy) return fail(PM_EINVAL, "obs_xy is NULL");
     pm::PosteriorArgs a;
-    std::memset(&a, 0, sizeof a);
-    const double s = (double)model->speed * (double)model->dt;
-    for (int k = 0; k < model->K; ++k) {
-        double c, sn;
-        unit_heading(model->K, k, &c, &sn);
-        a.ux[k] = (float)c;
-        a.uy[k] = (float)sn;
-    }
-    a.enabled = enabled_mask(model);
-    a.s = (float)s;
-    a.s2 = (float)(s * s);
-    a.two_s = (float)(2.0 * s);
-    a.w2 = model->w2;
-    a.K = model->K;
-    a.G = model->G;
-    a.B = model->B;
-    a.goals = model->goals;
-    a.beta = model->beta;
+    fill_posterior_args(model, a);
     a.obs = obs_xy;
     a.n_obs = n_obs;
     a.log_b = log_belief;
@@ -832,20 +879,7 @@ pm_status pm_batch_update_posterior(pm_batch *b, void *stream)
     if (!b) return fail(PM_EINVAL, "batch is NULL");
     DeviceScope dev(b->ctx->device);
     pm::PosteriorArgs a;
-    std::memset(&a, 0, sizeof a);
-    const double s = (double)b->shared.speed * (double)b->shared.dt;
-    for (int k = 0; k < b->shared.K; ++k) {
-        double c, sn;
-        unit_heading(b->shared.K, k, &c, &sn);
-        a.ux[k] = (float)c;
-        a.uy[k] = (float)sn;
-    }
-    a.enabled = enabled_mask(&b->shared);
-    a.s = (float)s;
-    a.s2 = (float)(s * s);
-    a.two_s = (float)(2.0 * s);
-    a.w2 = b->shared.w2;
-    a.K = b->shared.K;
+    fill_posterior_args(&b->shared, a); // goals/beta per human
     cudaError_t e = pm::launch_posterior_batch(a, b->d_post, b->d_meta + 1, b->max_humans, b->max_chunks, b->max_J,
                                                (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "batched posterior launch");
@@ -960,6 +994,8 @@ pm_status pm_batch_set_config(pm_batch *b, int32_t threads, int32_t shared_windo
     if (threads < 32 || threads > 256 || threads % 32) return fail(PM_EINVAL, "threads=%d must be 32..256, multiple of 32", threads);
     if (ctas_per_sm < 0 || ctas_per_sm > 32) return fail(PM_EINVAL, "ctas_per_sm=%d out of range", ctas_per_sm);
     if (window_kib < 1 || window_kib > 200) return fail(PM_EINVAL, "window_kib=%d out of range", window_kib);
+    if (shared_window && multi_speed(&b->shared))
+        return fail(PM_EINVAL, "several speeds run only the warp-combined emplacement (shared_window=0)");
     DeviceScope dev(b->ctx->device);
     const bool retile = threads != b->threads || (shared_window == 0) != b->warp_hist;
     b->threads = threads;
@@ -970,7 +1006,7 @@ pm_status pm_batch_set_config(pm_batch *b, int32_t threads, int32_t shared_windo
     pm::RolloutArgs t;
     std::memset(&t, 0, sizeof t);
     fill_rollout_tables(&b->shared, t);
-    b->occ = pm::batch_rollout_occupancy(b->shared.K, t.enabled, batch_shape_of(b), batch_dyn_smem(b));
+    b->occ = pm::batch_rollout_occupancy(b->shared.K, t.enabled, t.tab.S, batch_shape_of(b), batch_dyn_smem(b));
     cudaGetLastError();
     return PM_OK;
 }
@@ -994,6 +1030,7 @@ pm_status pm_batch_autotune(pm_batch *b, void *stream)
     float best = 1e30f;
     Cand bc{b->threads, b->warp_hist, b->window_kib};
     for (const Cand &cd : cands) {
+        if (!cd.warp && multi_speed(&b->shared)) continue; // several speeds: warp emplacement only
         b->threads = cd.threads;
         b->warp_hist = cd.warp;
         b->window_kib = cd.window;

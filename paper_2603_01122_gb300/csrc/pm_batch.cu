@@ -123,6 +123,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_rollout_kernel(cons
 // for the current batch, so that a CUDA graph captured on one batch stays
 // valid when humans with more components join later.
 constexpr size_t kWarpTableBytes = (size_t)kMaxJ * 20;
+// Several speeds: also cw1[kMaxJ] (4 B each) after cdf.
+constexpr size_t kWarpTableBytesMS = (size_t)kMaxJ * 24;
 
 // Persistent warps over all humans: each warp takes a 32-particle tile
 // (human, first particle) from the global counter, loads that human's
@@ -130,17 +132,24 @@ constexpr size_t kWarpTableBytes = (size_t)kMaxJ * 20;
 // the human changes, and runs the tile with the warp-combined emplacement.
 // No block barrier after the start, so tiles of different humans and
 // horizons mix freely on every scheduler.
-template <int KT, bool FULL>
+// MS: the control set of several speeds (draw_multi).
+template <int KT, bool FULL, bool MS = false>
 __global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_warp_kernel(const __grid_constant__ BatchArgs a)
 {
-    __shared__ float2 step[kMaxK];
+    __shared__ float2 step[MS ? PM_MAX_SPEEDS * kMaxK : kMaxK];
     extern __shared__ __align__(16) uint32_t dyn[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int k = tid; k < KT; k += blockDim.x) step[k] = make_float2(a.tab.sx[k], a.tab.sy[k]);
+    if constexpr (MS) {
+        for (int u = tid; u < a.tab.S * a.K; u += blockDim.x)
+            step[u] = make_float2(a.tab.msx[u / a.K][u % a.K], a.tab.msy[u / a.K][u % a.K]);
+    } else {
+        for (int k = tid; k < KT; k += blockDim.x) step[k] = make_float2(a.tab.sx[k], a.tab.sy[k]);
+    }
     __syncthreads();
-    char *slab = reinterpret_cast<char *>(dyn) + (size_t)warp * kWarpTableBytes;
+    char *slab = reinterpret_cast<char *>(dyn) + (size_t)warp * (MS ? kWarpTableBytesMS : kWarpTableBytes);
     float4 *comp = reinterpret_cast<float4 *>(slab);
     uint32_t *cdf = reinterpret_cast<uint32_t *>(slab + (size_t)kMaxJ * 16);
+    float *cw1 = reinterpret_cast<float *>(slab + (size_t)kMaxJ * 20); // MS only
     const int n_items = *a.n_items;
     int cur = -1;
     for (;;) {
@@ -157,6 +166,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_warp_kernel(const _
                 const int g = j / h->B, b = j - g * h->B;
                 const float cbj = h->beta[b] * a.w2_log2e;
                 comp[j] = make_float4(cbj, h->goals[2 * g], h->goals[2 * g + 1], lb_flag(a.tab, cbj));
+                if constexpr (MS) cw1[j] = h->beta[b] * a.w1_vdt_log2e;
             }
             belief_cdf(h->log_b, J, cdf, lane);
             __syncwarp();
@@ -193,7 +203,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_warp_kernel(const _
         c.tr_states = nullptr;
         c.tr_head = nullptr;
         c.tr_comp = nullptr;
-        rollout_lane<KT, FULL>(a.tab, a.enabled, a.s2, c, comp, cdf, step);
+        if constexpr (MS) rollout_lane<KT, false, true>(a.tab, a.enabled, a.s2, c, comp, cdf, step, cw1, a.K);
+        else rollout_lane<KT, FULL>(a.tab, a.enabled, a.s2, c, comp, cdf, step);
     }
 }
 
@@ -242,6 +253,8 @@ cudaError_t batch_shape(const BatchArgs &a, const RolloutShape &sh, int blocks, 
 
 cudaError_t batch_dispatch(const BatchArgs &a, const RolloutShape &sh, int blocks, size_t dyn, cudaStream_t s, int *occ)
 {
+    if (a.tab.S > 0) // several speeds: warp-combined emplacement only
+        return launch_or_query(batch_warp_kernel<64, false, true>, a, blocks, sh.threads, dyn, s, occ);
     const int KT = rollout_kt_for(a.K);
     const uint64_t all = (KT >= 64) ? ~0ull : ((1ull << KT) - 1ull);
     const bool full = (a.K == KT) && ((a.enabled & all) == all);
@@ -255,13 +268,17 @@ cudaError_t batch_dispatch(const BatchArgs &a, const RolloutShape &sh, int block
 
 } // namespace
 
-size_t batch_warp_tables_bytes(int threads) { return (size_t)(threads / 32) * kWarpTableBytes; }
+size_t batch_warp_tables_bytes(int threads, bool multi_speed)
+{
+    return (size_t)(threads / 32) * (multi_speed ? kWarpTableBytesMS : kWarpTableBytes);
+}
 
-int batch_rollout_occupancy(int K, uint64_t enabled, const RolloutShape &shape, size_t dyn)
+int batch_rollout_occupancy(int K, uint64_t enabled, int S, const RolloutShape &shape, size_t dyn)
 {
     BatchArgs a;
     a.K = K;
     a.enabled = enabled;
+    a.tab.S = S;
     int n = 0;
     if (batch_dispatch(a, shape, 0, dyn, nullptr, &n) != cudaSuccess) {
         cudaGetLastError();

@@ -128,6 +128,14 @@ struct HeadingTab {
     // triangle bound |r - s| by at most this much (zero when the headings are
     // not all enabled: the bound is then not used)
     float lb_gap;
+    // Several speeds (S >= 2, or one speed with a multiplier != 1): control
+    // u = s*K + k moves sl[s] = v*mult[s]*dt along theta_k.
+    int S;
+    uint32_t speed_on;              // bit s: speed s enabled
+    float mult[PM_MAX_SPEEDS];      // speed multipliers
+    float sl[PM_MAX_SPEEDS];        // v*mult[s]*dt
+    float msx[PM_MAX_SPEEDS][kMaxK]; // Euler step of control (s, k), rounded once from double
+    float msy[PM_MAX_SPEEDS][kMaxK];
 };
 
 // Arguments of the rollout kernel (Algorithm 1 + emplacement).
@@ -136,6 +144,7 @@ struct RolloutArgs {
     uint64_t enabled; // bit k: heading k may be drawn (k < K and not disabled)
     float s2;         // (v*dt)^2
     float w2_log2e;   // w2 * log2(e): beta*w2*log2(e) scales distance differences
+    float w1_vdt_log2e; // w1 * v * dt * log2(e) (several speeds: beta times it times m_s)
     int K, G, B;
     const float *goals;
     const float *beta;
@@ -157,11 +166,22 @@ struct RolloutArgs {
 };
 
 // Arguments of the belief-update kernel (Eq. 3 / Eq. 7).
+// The control set of several speeds as the belief update and the adjoint see
+// it (S = 0: one speed, multiplier 1).
+struct SpeedSet {
+    int S;
+    uint32_t speed_on;         // bit q: speed q enabled
+    float mult[PM_MAX_SPEEDS]; // multipliers m_q
+    float sl[PM_MAX_SPEEDS];   // step lengths v*m_q*dt
+    float w1;
+};
+
 struct PosteriorArgs {
     float ux[kMaxK], uy[kMaxK]; // unit heading vectors
     uint64_t enabled;
     float s, s2, two_s, w2;
     int K, G, B;
+    SpeedSet sp;
     const float *goals;
     const float *beta;
     const float *obs;
@@ -178,6 +198,7 @@ struct AdjointArgs {
     uint64_t enabled;
     float s, s2, two_s, w2, dt, v;
     int K, G, B;
+    SpeedSet sp;
     const float *goals;
     const float *beta;
     int M;                 // trajectories
@@ -267,7 +288,7 @@ struct MppiArgs {
 struct BatchArgs {
     HeadingTab tab;
     uint64_t enabled;
-    float s2, w2_log2e;
+    float s2, w2_log2e, w1_vdt_log2e;
     int K;
     const BatchHuman *humans;
     const int2 *items;   // (human, first particle), longest horizon first
@@ -306,8 +327,8 @@ cudaError_t launch_sfu_probe(int op, int blocks, int threads, int iters, float *
                              cudaStream_t s);
 int rollout_kt_for(int K); // template bucket for K (8, 16, 36 or 64)
 cudaError_t launch_adjoint(const AdjointArgs &a, cudaStream_t s);
-int batch_rollout_occupancy(int K, uint64_t enabled, const RolloutShape &shape, size_t dyn);
-size_t batch_warp_tables_bytes(int threads); // dynamic shared memory of the warp form
+int batch_rollout_occupancy(int K, uint64_t enabled, int S, const RolloutShape &shape, size_t dyn);
+size_t batch_warp_tables_bytes(int threads, bool multi_speed); // dynamic shared memory of the warp form
 cudaError_t launch_batch_rollout(const BatchArgs &a, const RolloutShape &shape, int blocks, size_t dyn, cudaStream_t s);
 cudaError_t launch_batch_zero(const BatchHuman *humans, const int *n_dev, int max_rows, int sm_count, cudaStream_t s);
 size_t adjoint_scratch_bytes(int M, int G);

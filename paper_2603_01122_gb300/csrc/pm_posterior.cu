@@ -7,6 +7,10 @@
 // with a_k = beta w2 (d_obs - d_k), d the distance from the next state to the
 // goal and m_t(j) = max_k a_k. The differences are formed without
 // cancellation: d_obs - d_k = 2 s (e_obs - e_k).(z - g) / (d_obs + d_k).
+// With several speeds (controls u = speed q x heading k, Sec. IV-B) the
+// observed step is read as its direction at the enabled speed nearest to its
+// length, and the logits run over all S*K controls (lanes over the controls,
+// up to eight per lane); the speed term w1 (so - sl_q) joins the distance term.
 //
 // Layout: the observed steps are split into chunks, one CTA per chunk (and
 // per human in the batched form); a warp handles one component at a time with
@@ -110,12 +114,67 @@ __device__ __forceinline__ float rel_logit(float bw, float two_s, float D, float
     return bw * (num / fmaxf(d_o + dk, 1e-30f));
 }
 
+// Controls per lane of the several-speed form: S*K <= 256 over 32 lanes.
+constexpr int kMsPerLane = 8;
+
+// The enabled speed multiplier nearest to r (ties: the lower index).
+__device__ __forceinline__ int snap_speed(const SpeedSet &sp, float r)
+{
+    int q0 = 0;
+    float best = INFINITY;
+    for (int q = 0; q < sp.S; ++q) {
+        const float d = fabsf(sp.mult[q] - r);
+        if (((sp.speed_on >> q) & 1u) && d < best) {
+            best = d;
+            q0 = q;
+        }
+    }
+    return q0;
+}
+
+// Several speeds: the logit of control u = (speed q, heading k) relative to
+// the observed control (snapped speed length so, observed direction e),
+//   beta (Q_u - Q_obs) = beta w1 (so - sl_q) + beta w2 (d_obs - d_u),
+//   d_obs - d_u = ((so - sl)(so + sl) + 2 (so e - sl e_k).(z - g)) / (d_obs + d_u),
+// again without cancellation. cu[u] = (cos, sin of theta_k, sl_q, enabled).
+__device__ __forceinline__ void step_loglik_ms(const SpeedSet &sp, const float4 *cu, int U, float bw1, float bw2,
+                                               float px, float py, float ex, float ey, float so, int lane, float &m,
+                                               float &S)
+{
+    const float P = fmaf(px, px, py * py);
+    const float d_o = sqrtf(fmaxf(fmaf(so, so, P) + 2.0f * so * fmaf(ex, px, ey * py), 0.0f));
+    float lg[kMsPerLane];
+    float mx = -INFINITY;
+#pragma unroll
+    for (int i = 0; i < kMsPerLane; ++i) {
+        const int u = lane + 32 * i;
+        lg[i] = -INFINITY;
+        if (u < U) {
+            const float4 c = cu[u];
+            if (c.w != 0.0f) {
+                const float du = sqrtf(fmaxf(fmaf(c.z, c.z, P) + 2.0f * c.z * fmaf(c.x, px, c.y * py), 0.0f));
+                const float num = fmaf(so - c.z, so + c.z,
+                                       2.0f * fmaf(fmaf(so, ex, -c.z * c.x), px, fmaf(so, ey, -c.z * c.y) * py));
+                lg[i] = fmaf(bw1, so - c.z, bw2 * (num / fmaxf(d_o + du, 1e-30f)));
+            }
+        }
+        mx = fmaxf(mx, lg[i]);
+    }
+    m = warp_max(mx);
+    float sum = 0.0f;
+#pragma unroll
+    for (int i = 0; i < kMsPerLane; ++i) sum += (lg[i] == -INFINITY) ? 0.0f : expf(lg[i] - m);
+    S = warp_sum(sum);
+}
+
 // One chunk of one human's observed steps; the last chunk of the human to
-// finish folds all chunks and writes the posterior.
+// finish folds all chunks and writes the posterior. MS: several speeds.
+template <bool MS>
 __device__ __forceinline__ void posterior_chunk(const PosteriorArgs &a, const PostHuman &h, int chunk, int nchunk)
 {
     __shared__ int last;
     __shared__ float2 su[kMaxK]; // unit heading vectors
+    __shared__ float4 cu[MS ? kMsPerLane * 32 : 1]; // several speeds: (e_k, sl_q, enabled) of control u
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int J = h.G * h.B;
     const int t0 = chunk * h.steps_per_chunk;
@@ -125,6 +184,13 @@ __device__ __forceinline__ void posterior_chunk(const PosteriorArgs &a, const Po
     // at a time by the constant cache
     __syncthreads(); // the previous chunk of this CTA (batched form) is done with su
     for (int k = threadIdx.x; k < kMaxK; k += blockDim.x) su[k] = make_float2(a.ux[k], a.uy[k]);
+    const int U = MS ? a.sp.S * a.K : 0;
+    if constexpr (MS) {
+        for (int u = threadIdx.x; u < U; u += blockDim.x) {
+            const int q = u / a.K, k = u - q * a.K;
+            cu[u] = make_float4(a.ux[k], a.uy[k], a.sp.sl[q], ((a.sp.speed_on >> q) & 1u) ? 1.0f : 0.0f);
+        }
+    }
     __syncthreads();
     const int k0 = lane, k1 = lane + 32;
     const bool on0 = k0 < a.K && ((a.enabled >> k0) & 1ull);
@@ -145,6 +211,14 @@ __device__ __forceinline__ void posterior_chunk(const PosteriorArgs &a, const Po
             if (!(len >= 1e-6f)) continue; // stationary: the belief is unchanged
             const float ex = dx / len, ey = dy / len;
             const float px = zx - gx, py = zy - gy;
+            if constexpr (MS) {
+                const float so = a.sp.sl[snap_speed(a.sp, len / a.s)];
+                float m, S;
+                step_loglik_ms(a.sp, cu, U, h.beta[b] * a.sp.w1, bw, px, py, ex, ey, so, lane, m, S);
+                acc_add(acc, m);
+                acc_mul(acc, S, 0.0f, 0);
+                continue;
+            }
             const float D = fmaf(px, px, fmaf(py, py, a.s2));
             const float d_o = sqrtf(fmaxf(D + a.two_s * fmaf(ex, px, ey * py), 0.0f));
             const float l0 = on0 ? rel_logit(bw, a.two_s, D, px, py, ex, ey, d_o, ux0, uy0) : -INFINITY;
@@ -244,7 +318,8 @@ __global__ void __launch_bounds__(1024) posterior_kernel(const __grid_constant__
     h.log_b = a.log_b;
     h.part = a.part;
     h.ticket = a.ticket;
-    posterior_chunk(a, h, blockIdx.x, gridDim.x);
+    if (a.sp.S > 0) posterior_chunk<true>(a, h, blockIdx.x, gridDim.x);
+    else posterior_chunk<false>(a, h, blockIdx.x, gridDim.x);
 }
 
 // Batched form: blockIdx.y is the human; the CTAs of a row stride over its
@@ -257,7 +332,10 @@ __global__ void __launch_bounds__(1024) posterior_batch_kernel(const __grid_cons
     const PostHuman h = humans[blockIdx.y];
     if (h.n_obs <= 0 || h.log_b == nullptr) return;
     const int nchunk = (h.n_obs + h.steps_per_chunk - 1) / h.steps_per_chunk;
-    for (int ch = blockIdx.x; ch < nchunk; ch += gridDim.x) posterior_chunk(a, h, ch, nchunk);
+    for (int ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+        if (a.sp.S > 0) posterior_chunk<true>(a, h, ch, nchunk);
+        else posterior_chunk<false>(a, h, ch, nchunk);
+    }
 }
 
 } // namespace

@@ -88,6 +88,79 @@ __global__ void __launch_bounds__(kWarpCtaThreads, kWarpCtaMinBlocks)
     }
 }
 
+// The same persistent warps for a control set of several speeds (draw_multi).
+__global__ void __launch_bounds__(kWarpCtaThreads, kWarpCtaMinBlocks)
+    rollout_multi_kernel(const __grid_constant__ RolloutArgs a, unsigned *head)
+{
+    __shared__ float4 comp[kMaxJ];
+    __shared__ float cw1[kMaxJ];
+    __shared__ uint32_t cdf[kMaxJ];
+    __shared__ float2 step[PM_MAX_SPEEDS * kMaxK];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int J = a.G * a.B;
+    for (int j = tid; j < J; j += blockDim.x) {
+        const int g = j / a.B, b = j - g * a.B;
+        const float cbj = a.beta[b] * a.w2_log2e;
+        comp[j] = make_float4(cbj, a.goals[2 * g], a.goals[2 * g + 1], lb_flag(a.tab, cbj));
+        cw1[j] = a.beta[b] * a.w1_vdt_log2e;
+    }
+    for (int u = tid; u < a.tab.S * a.K; u += blockDim.x)
+        step[u] = make_float2(a.tab.msx[u / a.K][u % a.K], a.tab.msy[u / a.K][u % a.K]);
+    if (tid < 32) belief_cdf(a.log_b, J, cdf, tid);
+    __syncthreads();
+
+    TileCtx c;
+    c.z0x = a.z0x;
+    c.z0y = a.z0y;
+    c.T = a.T;
+    c.N = a.N;
+    c.n_trace = a.n_trace;
+    c.seed = a.seed;
+    c.human = a.human;
+    c.J = J;
+    c.hist = a.counts != nullptr;
+    c.gx0 = a.gx0;
+    c.gy0 = a.gy0;
+    c.inv_res = a.inv_res;
+    c.W = a.W;
+    c.H = a.H;
+    c.cx_off = 0;
+    c.cy_off = 0;
+    c.counts = a.counts;
+    c.oob = a.oob;
+    c.win_x0 = c.win_y0 = c.ww = c.wh = 0;
+    c.tr_states = a.tr_states;
+    c.tr_head = a.tr_head;
+    c.tr_comp = a.tr_comp;
+    for (;;) {
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(head, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        const int64_t i0 = (int64_t)item * 32;
+        if (i0 >= a.N) break;
+        c.i = i0 + lane;
+        rollout_lane<64, false, true>(a.tab, a.enabled, a.s2, c, comp, cdf, step, cw1, a.K);
+    }
+}
+
+cudaError_t launch_multi(const RolloutArgs &a, unsigned *head, int sm_count, cudaStream_t s, int *occ)
+{
+    int n = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_multi_kernel, kWarpCtaThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (occ) {
+        *occ = n;
+        return cudaSuccess;
+    }
+    const int64_t chunks = ((int64_t)a.N + 31) / 32;
+    const int64_t need = (chunks + kWarpCtaThreads / 32 - 1) / (kWarpCtaThreads / 32);
+    int64_t blocks = (int64_t)sm_count * (n > 0 ? n : 1);
+    if (need < blocks) blocks = need;
+    cudaGetLastError();
+    rollout_multi_kernel<<<(unsigned)blocks, kWarpCtaThreads, 0, s>>>(a, head);
+    return cudaGetLastError();
+}
+
 template <int KT>
 cudaError_t launch_kt(const RolloutArgs &a, unsigned *head, int sm_count, cudaStream_t s, int *occ)
 {
@@ -112,6 +185,7 @@ cudaError_t launch_kt(const RolloutArgs &a, unsigned *head, int sm_count, cudaSt
 
 cudaError_t dispatch(const RolloutArgs &a, unsigned *head, int sm_count, cudaStream_t s, int *occ)
 {
+    if (a.tab.S > 0) return launch_multi(a, head, sm_count, s, occ);
     switch (rollout_kt_for(a.K)) {
     case 8: return launch_kt<8>(a, head, sm_count, s, occ);
     case 16: return launch_kt<16>(a, head, sm_count, s, occ);

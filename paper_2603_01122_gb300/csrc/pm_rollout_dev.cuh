@@ -92,7 +92,16 @@ __device__ __forceinline__ int draw_heading(const HeadingTab &tab, uint64_t enab
             f2_unpack(dv[q], v0, v1);
             dmin[q & 3] = fminf(dmin[q & 3], fminf(v0, v1));
         }
-        const float dm = fminf(fminf(dmin[0], dmin[1]), fminf(dmin[2], dmin[3]));
+        float dm = fminf(fminf(dmin[0], dmin[1]), fminf(dmin[2], dmin[3]));
+        if (cb < 0.0f) { // beta < 0: the farthest heading is the most probable
+            dm = -INFINITY;
+#pragma unroll
+            for (int q = 0; q < KT / 2; ++q) {
+                float v0, v1;
+                f2_unpack(dv[q], v0, v1);
+                dm = fmaxf(dm, fmaxf(v0, v1));
+            }
+        }
         const f32x2 NC = f2_pack(-cb, -cb);
         const float base = dm * cb;
         const f32x2 BASE = f2_pack(base, base);
@@ -137,11 +146,13 @@ __device__ __forceinline__ int draw_heading(const HeadingTab &tab, uint64_t enab
             if (k == 0) dref = dk;
             dv[k] = fmaf(rk, hD, dk - dref);
         }
-        float dmin = INFINITY;
+        // the most probable heading: the nearest for beta >= 0, the farthest
+        // for beta < 0, so that every exponent below is <= 0
+        float dext = (cb >= 0.0f) ? INFINITY : -INFINITY;
 #pragma unroll
         for (int k = 0; k < KT; ++k)
-            if (FULL || ((enabled >> k) & 1ull)) dmin = fminf(dmin, dv[k]);
-        const float base = dmin * cb;
+            if (FULL || ((enabled >> k) & 1ull)) dext = (cb >= 0.0f) ? fminf(dext, dv[k]) : fmaxf(dext, dv[k]);
+        const float base = dext * cb;
         const float nc = -cb;
         uint32_t C[KT];
         uint32_t S = 0;
@@ -313,6 +324,131 @@ __device__ __forceinline__ int draw(const HeadingTab &tab, uint64_t enabled, flo
     // k < K whenever the total weight S > 0, which finite inputs guarantee;
     // the clamp keeps the step-table read in bounds for any input
     return min(k, KT - 1);
+}
+
+// ---------------------------------------------------------------------------
+// Several speeds: Eq. 2 over the controls u = s*K + k (speed-major), each
+// moving sl[s] = v*m_s*dt along theta_k, with
+//   beta Q_u log2(e) = -(cb d_{k,s} + cw1 m_s),  cb = beta w2 log2(e),
+//   cw1 = beta w1 v dt log2(e).
+// Per speed the distances use the same corrected form as the one-speed draw
+// against a reference REF_s (the triangle bound |r - s_s| pushed out by a few
+// ulps, or with lb false the exact extreme over the speed's headings); the
+// speeds are tied together by C_s = cb (REF_s - REF_b) + cw1 (m_s - m_b) - min,
+// formed from differences of nearby floats (exact), so the exponent
+//   a_{k,s} = -cb U_{k,s} - C_s <= 0,  U_{k,s} = d_{k,s} - REF_s.
+// Pass 1 sums each speed's 22-bit fixed-point weights; the threshold picks
+// the speed from the running per-speed totals, and pass 2 recomputes that
+// speed's weights in heading order until the running sum passes it: the same
+// decision as the inverse CDF over all S*K controls, without storing them.
+// Heading loops run over the runtime K (K a multiple of 4, all enabled).
+// ---------------------------------------------------------------------------
+struct SpeedStep {
+    float D[PM_MAX_SPEEDS], hD[PM_MAX_SPEEDS], REF[PM_MAX_SPEEDS], C[PM_MAX_SPEEDS];
+};
+
+__device__ __forceinline__ uint32_t multi_weight(const HeadingTab &tab, int k, int sp, float dx, float dy,
+                                                 const SpeedStep &q, float cb)
+{
+    const float P = __fmul_rn(fmaf(tab.tx[k], dx, tab.ty[k] * dy), tab.mult[sp]); // 2 s_s e_k.(z - g)
+    const float xk = q.D[sp] + P;
+    const float dk = sqrt_approx(fabsf(xk));
+    const float R = P - fmaf(dk, dk, -q.D[sp]);
+    const float U = fmaf(R, q.hD[sp], dk - q.REF[sp]);
+    // <= 0 up to the rounding of REF (exact extreme form); the clamp keeps the
+    // weight within 22 bits for any beta
+    const float a = fminf(fmaf(U, -cb, -q.C[sp]), 0.0f);
+    return __float_as_uint(fmaf(ex2_approx(a), 4194304.0f, 12582912.0f)) - 0x4B400000u;
+}
+
+__device__ __forceinline__ int draw_multi(const HeadingTab &tab, int K, float x, float y, float gx, float gy,
+                                          float cb, float cw1, bool lb, uint32_t word)
+{
+    const float dx = x - gx, dy = y - gy;
+    const float r2 = fmaf(dx, dx, dy * dy);
+    const float r = sqrt_approx(r2);
+    SpeedStep q;
+    int best = max(__ffs((int)tab.speed_on) - 1, 0); // an enabled speed, whatever the inputs
+    float vbest = -INFINITY;
+#pragma unroll
+    for (int sp = 0; sp < PM_MAX_SPEEDS; ++sp) {
+        q.D[sp] = q.hD[sp] = q.REF[sp] = q.C[sp] = 0.0f;
+        if (sp >= tab.S || !((tab.speed_on >> sp) & 1u)) continue;
+        const float sl = tab.sl[sp];
+        q.D[sp] = fmaf(dx, dx, fmaf(dy, dy, sl * sl));
+        q.hD[sp] = 0.5f * rsqrt_approx(q.D[sp]);
+        if (lb) {
+            const float margin = (r + sl) * 0x1p-20f;
+            q.REF[sp] = (cb >= 0.0f) ? fabsf(r - sl) - margin : r + sl + margin;
+        } else {
+            // the exact extreme of the corrected distances of this speed
+            float ext = (cb >= 0.0f) ? INFINITY : -INFINITY;
+            q.REF[sp] = 0.0f;
+            for (int k = 0; k < K; ++k) {
+                const float P = __fmul_rn(fmaf(tab.tx[k], dx, tab.ty[k] * dy), tab.mult[sp]);
+                const float dk = sqrt_approx(fabsf(q.D[sp] + P));
+                const float d = fmaf(P - fmaf(dk, dk, -q.D[sp]), q.hD[sp], dk);
+                ext = (cb >= 0.0f) ? fminf(ext, d) : fmaxf(ext, d);
+            }
+            q.REF[sp] = ext;
+        }
+        const float v = -fmaf(cb, q.REF[sp], cw1 * tab.mult[sp]);
+        if (v > vbest) {
+            vbest = v;
+            best = sp;
+        }
+    }
+    // offsets between speeds from differences of nearby floats, shifted to >= 0
+    float cmin = INFINITY;
+#pragma unroll
+    for (int sp = 0; sp < PM_MAX_SPEEDS; ++sp) {
+        if (sp >= tab.S || !((tab.speed_on >> sp) & 1u)) continue;
+        q.C[sp] = fmaf(cb, q.REF[sp] - q.REF[best], cw1 * (tab.mult[sp] - tab.mult[best]));
+        cmin = fminf(cmin, q.C[sp]);
+    }
+    uint32_t W[PM_MAX_SPEEDS];
+    uint32_t total = 0u;
+#pragma unroll
+    for (int sp = 0; sp < PM_MAX_SPEEDS; ++sp) {
+        W[sp] = 0u;
+        if (sp >= tab.S || !((tab.speed_on >> sp) & 1u)) continue;
+        q.C[sp] -= cmin;
+        uint32_t w = 0u;
+        for (int k = 0; k < K; ++k) w += multi_weight(tab, k, sp, dx, dy, q, cb);
+        W[sp] = w;
+        total += w;
+    }
+    const uint32_t thr = (uint32_t)(((uint64_t)(word >> 8) * (uint64_t)total) >> 24);
+    // the speed whose running-sum interval holds thr (total > thr always)
+    uint32_t C0 = 0u;
+    int ss = best;
+    {
+        uint32_t run = 0u;
+        bool found = false;
+#pragma unroll
+        for (int sp = 0; sp < PM_MAX_SPEEDS; ++sp) {
+            if (!found && sp < tab.S && ((tab.speed_on >> sp) & 1u)) {
+                if (thr < run + W[sp]) {
+                    ss = sp;
+                    C0 = run;
+                    found = true;
+                } else {
+                    run += W[sp];
+                }
+            }
+        }
+    }
+    // that speed's headings in order until the running sum passes thr
+    uint32_t acc = C0;
+    int kk = K - 1;
+    for (int k = 0; k < K; ++k) {
+        acc += multi_weight(tab, k, ss, dx, dy, q, cb);
+        if (thr < acc) {
+            kk = k;
+            break;
+        }
+    }
+    return ss * K + kk;
 }
 
 // Per-tile state of one human for rollout_tile.
@@ -508,15 +644,18 @@ __device__ __forceinline__ void rollout_tile(const HeadingTab &tab, uint64_t ena
 // emplaced with the lanes of the warp that land in the same cell combined
 // (match.any) into one global reduction. Every lane of the warp must call
 // it with the same c.T (idle lanes pass c.i >= c.N). No block barrier.
-template <int KT, bool FULL>
+// MS: the control set of several speeds (draw_multi; cw1 holds each
+// component's beta w1 v dt log2(e), step the S*K Euler steps, K the headings).
+template <int KT, bool FULL, bool MS = false>
 __device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t enabled, float s2, const TileCtx &c,
-                                             const float4 *comp, const uint32_t *cdf, const float2 *step)
+                                             const float4 *comp, const uint32_t *cdf, const float2 *step,
+                                             const float *cw1 = nullptr, int K = 0)
 {
     const int lane = threadIdx.x & 31;
     const uint64_t i = (uint64_t)c.i;
     const bool act = c.i < c.N;
     const bool trc = c.i < c.n_trace;
-    float x = c.z0x, y = c.z0y, cb = 0.0f, gx = 0.0f, gy = 0.0f;
+    float x = c.z0x, y = c.z0y, cb = 0.0f, gx = 0.0f, gy = 0.0f, cw = 0.0f;
     bool lb = false;
     if (act) {
         const U64x4 r = philox4x64_10(U64x4{i, 0ull, kPurposeSelect, 0ull}, c.seed, c.human);
@@ -532,6 +671,7 @@ __device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t ena
         gx = cc.y;
         gy = cc.z;
         lb = cc.w != 0.0f;
+        if constexpr (MS) cw = cw1[lo];
         if (trc && c.tr_comp) c.tr_comp[i] = lo;
     }
     const size_t plane = (size_t)c.W * (size_t)c.H;
@@ -548,7 +688,9 @@ __device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t ena
             }
             const uint32_t word = q0;
             q0 = q1; q1 = q2; q2 = q3; q3 = q4; q4 = q5; q5 = q6; q6 = q7;
-            const int k = draw<KT, FULL>(tab, enabled, s2, x, y, gx, gy, cb, lb, word);
+            int k;
+            if constexpr (MS) k = draw_multi(tab, K, x, y, gx, gy, cb, cw, lb, word);
+            else k = draw<KT, FULL>(tab, enabled, s2, x, y, gx, gy, cb, lb, word);
             const float2 st = step[k];
             x = __fadd_rn(x, st.x);
             y = __fadd_rn(y, st.y);

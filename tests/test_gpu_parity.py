@@ -239,7 +239,7 @@ def test_paper_scale_sampled_particles_full_launch(ctx, orc):
 
 
 @pytest.mark.parametrize("case", ["ragged_N", "single", "T1", "corner", "outside", "K3", "K37_mask",
-                                  "K64", "J256", "tiny_grid"])
+                                  "K64", "J256", "tiny_grid", "beta_neg_large", "beta_neg_large_mask"])
 def test_edge_cases_full_trace(ctx, orc, case):
     hu = workloads.paper_scale()
     K, goals, beta, heading_off = hu.K, hu.goals, hu.beta, 0
@@ -265,6 +265,12 @@ def test_edge_cases_full_trace(ctx, orc, case):
     elif case == "J256":
         goals = rng.uniform(0, 10, (16, 2)).astype(np.float32)
         beta = workloads.beta_grid(-2.0, 2.0, 16)
+    elif case in ("beta_neg_large", "beta_neg_large_mask"):
+        # |beta| far above the bound-normalised range: the exact-extreme draw,
+        # whose most probable heading is the farthest from the goal
+        beta = np.float32([-3000.0, -40.0, 1e4])
+        if case.endswith("mask"):
+            heading_off = 0b101
     elif case == "tiny_grid":
         grid = (workloads.f32(4.9), workloads.f32(4.95), workloads.f32(0.05), 3, 2)
         dt = workloads.f32(0.05)

@@ -1,0 +1,276 @@
+"""Several speeds with stationary masking (controls = speeds x headings,
+Sec. IV-B) on the GPU against the FP64 oracle: trajectories and histograms of
+the rollout, the belief update, the batched launch and the adjoint.
+
+Tolerances. Trajectories: bit-identical FP32 states for every particle whose
+draws agree, and every particle whose draws differ must differ at a draw that
+the error budget explains (``explain_divergences``): its uniform lies within
+the budget of a boundary of the exact CDF between the two choices. Histograms
+bit-exact given the states; |log b| within 1e-5; L relative 1e-6; gradients
+relative 1e-3 in norm.
+"""
+import math
+import zlib
+
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from gpu_util import GpuHuman, dev, posterior, predict
+from test_gpu_parity import assert_posterior_close, compare_trajectories, poisson_reject_at
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2603_01122_gb300 as pm
+    pm.build()
+    c = pm.pm_create(0)
+    yield c
+    pm.pm_destroy(c)
+
+
+def explain_divergences(orc, m, lb, z0, seed, human, got, ref):
+    """Check each diverged particle at its first differing draw.
+
+    The GPU draws with the inverse CDF of its FP32 policy, evaluated at its
+    FP32 state, with 22-bit fixed-point weights; the oracle with the exact
+    policy at its FP64 state. With C the exact CDF, C' the GPU's, u the shared
+    uniform, kg the GPU's choice and ko the oracle's: kg < ko implies
+    0 <= u - C[kg] < C'[kg] - C[kg], and kg > ko implies
+    0 < C[kg-1] - u <= C[kg-1] - C'[kg-1]. So u lies within max |C' - C| of a
+    boundary. Each logit error is at most A = |beta| (w2 dd + |w1| ds) with dd
+    = |z32 - z64| + 1e-6 (1 + d) (state and FP32 distance errors) and ds =
+    1e-7 max step, so the policy's CDF moves by at most expm1(2 A); the
+    fixed-point weights (largest >= 2^21 units, each within 1.5 units) and the
+    threshold rounding add (1.5 U + 1) 2^-21. The component draw has only the
+    last kind of error, over J components. Returns the number checked."""
+    diverged = np.flatnonzero(np.any(got["headings"] != ref["headings"], axis=1) | (got["comp"] != ref["comp"]))
+    J = m.G * m.B
+    Cb = np.cumsum(np.exp(np.asarray(lb, np.float64)))
+    Cb /= Cb[-1]
+    smax = m.v * m.dt * float(np.max(m.speeds))
+    for i in diverged:
+        i = int(i)
+        kg, ko = int(got["comp"][i]), int(ref["comp"][i])
+        if kg != ko:
+            u = orc.uniform_select(seed, human, i)
+            delta = (u - Cb[kg]) if kg < ko else (Cb[kg - 1] - u)
+            assert 0.0 <= delta <= (2 * J + 1) * 2.0 ** -21, (i, kg, ko, delta)
+            continue
+        g, b = divmod(ko, m.B)
+        t = int(np.flatnonzero(got["headings"][i] != ref["headings"][i])[0])
+        z64 = np.asarray(z0, np.float64) if t == 0 else ref["states64"][i, t - 1]
+        z32 = np.asarray(z0, np.float64) if t == 0 else ref["states32"][i, t - 1].astype(np.float64)
+        C = np.cumsum(np.exp(orc.log_policy(m, z64, m.beta[b], m.goals[g])))
+        C /= C[-1]
+        u = orc.uniform_step(seed, human, i, t + 1)
+        kg, ko = int(got["headings"][i, t]), int(ref["headings"][i, t])
+        delta = (u - C[kg]) if kg < ko else (C[kg - 1] - u)
+        d = math.hypot(*(z64 - m.goals[g])) + smax
+        A = abs(m.beta[b]) * (m.w2 * (math.hypot(*(z32 - z64)) + 1e-6 * (1 + d)) + abs(m.w1) * 1e-7 * smax)
+        budget = math.expm1(2 * A) + (1.5 * m.U + 1) * 2.0 ** -21
+        assert 0.0 <= delta <= budget, (i, t, kg, ko, delta, budget)
+    return len(diverged)
+
+
+def _models(orc, K, speed, dt, goals, beta, speeds, speed_off=0, w1=1.0, w2=1.0, heading_off=0):
+    m = orc.Model(K, speed, dt, goals, beta, w1=w1, w2=w2, mask_off=heading_off, speeds=speeds,
+                  speed_off=speed_off)
+    gh = GpuHuman(K, speed, dt, goals, beta, w1=w1, w2=w2, heading_off=heading_off, speeds=speeds,
+                  speed_off=speed_off)
+    return m, gh
+
+
+CASES = ["U96", "stationary", "U256", "one_mult", "w1_3", "beta_neg_large", "beta_large", "ragged"]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_trajectories_and_histogram(ctx, orc, case):
+    hu = workloads.multi_speed(stationary=(case == "stationary"))
+    K, speeds, speed_off, goals, beta, w1 = hu.K, hu.speeds, hu.speed_off, hu.goals, hu.beta, 1.0
+    N, T, z0, grid = 3001, 40, np.float32([5.0, 5.0]), hu.grid
+    rng = np.random.default_rng(zlib.crc32(case.encode()))
+    if case == "U256":
+        K, speeds = 64, (0.25, 0.5, 1.0, 2.0)
+    elif case == "one_mult":
+        K, speeds = 8, (1.5,)
+    elif case == "w1_3":
+        w1 = 3.0
+    elif case == "beta_neg_large":
+        beta = np.float32([-300.0, -20.0])
+    elif case == "beta_large":
+        beta = np.float32([1e4, 300.0])
+    elif case == "ragged":
+        N = 257 * 13 + 5
+    m, gh = _models(orc, K, hu.speed, hu.dt, goals, beta, speeds, speed_off, w1=w1)
+    J = m.G * m.B
+    lb = np.log(rng.dirichlet(np.ones(J))).astype(np.float32)
+    got = predict(ctx, gh, lb, z0, N, T, grid, 77, 5, n_trace=N)
+    ref = orc.rollout(m, lb, z0, T, 77, 5, 0, N, grid=grid, want_headings=True, want_states32=True,
+                      want_states64=True, want_comp=True)
+    d = compare_trajectories(got, ref)
+    assert explain_divergences(orc, m, lb, z0, 77, 5, got, ref) == d
+    assert d <= 0.05 * N, d
+    c, o = orc.bin_states(got["states32"], grid)
+    np.testing.assert_array_equal(got["counts"], c)
+    np.testing.assert_array_equal(got["oob"], o)
+    assert np.all(got["counts"].reshape(T, -1).sum(1).astype(np.int64) + got["oob"] == N)
+    u = got["headings"].astype(np.int64)
+    assert u.max() < len(speeds) * K
+    if speed_off:
+        assert np.all(((speed_off >> (u // K)) & 1) == 0)  # no masked speed is ever drawn
+    elif len(speeds) > 1 and case != "beta_large":
+        assert len(np.unique(u // K)) == len(speeds)  # every speed is drawn
+
+
+def test_full_launch_sampled_particles(ctx, orc):
+    """The |U| = 96 workload at full size (N = 100k, T = 150) with the first
+    5000 particles traced and recomputed one by one."""
+    hu = workloads.multi_speed()
+    m, gh = _models(orc, hu.K, hu.speed, hu.dt, hu.goals, hu.beta, hu.speeds)
+    obs = orc.simulate(m, hu.true_j, hu.start, hu.n_obs, hu.obs_seed, hu.human_id).astype(np.float32)
+    lb = posterior(ctx, gh, obs, hu.uniform_log_prior())
+    z0 = obs[-1]
+    N, T, n = hu.n_particles, hu.horizon, 5000
+    got = predict(ctx, gh, lb, z0, N, T, hu.grid, hu.seed, hu.human_id, n_trace=n)
+    ref = orc.rollout(m, lb, z0, T, hu.seed, hu.human_id, 0, n, want_counts=False, want_headings=True,
+                      want_states32=True, want_states64=True, want_comp=True)
+    d = compare_trajectories(got, ref)
+    assert explain_divergences(orc, m, lb, z0, hu.seed, hu.human_id, got, ref) == d
+    assert d < poisson_reject_at(n, rate=1e-3), d
+    assert np.all(got["counts"].reshape(T, -1).sum(1).astype(np.int64) + got["oob"] == N)
+    c_sub, _ = orc.bin_states(got["states32"], hu.grid)
+    assert np.all(c_sub <= got["counts"])
+
+
+@pytest.mark.parametrize("stationary", [False, True])
+def test_posterior_matches_oracle(ctx, orc, stationary):
+    """Histories drawn at all three speeds; with the stationary mask every
+    observed step snaps to the one enabled (slow) speed."""
+    hu = workloads.multi_speed(stationary=stationary)
+    gen = orc.Model(hu.K, hu.speed, hu.dt, hu.goals, hu.beta, speeds=hu.speeds)
+    obs = orc.simulate(gen, hu.true_j, hu.start, 200, hu.obs_seed, hu.human_id).astype(np.float32)
+    m, gh = _models(orc, hu.K, hu.speed, hu.dt, hu.goals, hu.beta, hu.speeds, hu.speed_off)
+    # no observed step within 1e-4 of a midpoint between two multipliers (the
+    # two sides snap in different precisions)
+    ln = np.hypot(*np.diff(obs.astype(np.float64), axis=0).T) / (hu.speed * hu.dt)
+    assert np.min(np.abs(ln[:, None] - np.array([0.75, 1.25])[None, :])) > 1e-4
+    want, _ = orc.update_posterior(m, obs.astype(np.float64), hu.uniform_log_prior())
+    got = posterior(ctx, gh, obs, hu.uniform_log_prior())
+    assert_posterior_close(got, want)
+
+
+def test_batch_equals_single(ctx, orc):
+    """Four humans under one shared |U| = 96 model: the batched belief update
+    and histograms equal the single-human calls bit for bit."""
+    import paper_2603_01122_gb300 as pm
+    hu = workloads.multi_speed()
+    rng = np.random.default_rng(9)
+    ds = []
+    for h in range(4):
+        goals = rng.uniform(0, 10, size=(2 + h, 2)).astype(np.float32)
+        m, gh = _models(orc, hu.K, hu.speed, hu.dt, goals, hu.beta, hu.speeds)
+        start = rng.uniform(2, 8, size=2).astype(np.float32)
+        obs = orc.simulate(m, h, start, 30, hu.obs_seed, 40 + h).astype(np.float32)
+        N, T = int(rng.integers(5000, 40000)), int(rng.integers(20, 80))
+        x0, y0, res, W, H = hu.grid
+        lb = np.full(m.G * m.B, -np.log(m.G * m.B), np.float32)
+        ds.append(dict(gh=gh, obs=dev(obs), n_obs=obs.shape[0] - 1, N=N, T=T, lb=dev(lb), z0=dev(obs[-1]),
+                       grid=pm.make_grid(x0, y0, res, W, H), human=40 + h, counts=torch.empty((T, H, W), dtype=torch.int32, device="cuda:0"),
+                       oob=torch.empty(T, dtype=torch.int32, device="cuda:0")))
+    shared = pm.make_model(hu.K, hu.speed, hu.dt, ds[0]["gh"].goals, ds[0]["gh"].beta, speeds=hu.speeds)
+    b = pm.pm_batch_create(ctx, shared, len(ds))
+    try:
+        singles = []
+        for d in ds:
+            lb = d["lb"].clone()
+            pm.pm_update_posterior(ctx, d["gh"].model, d["obs"], d["n_obs"], lb)
+            counts = torch.empty_like(d["counts"])
+            oob = torch.empty_like(d["oob"])
+            z0 = d["z0"].cpu().numpy()
+            pm.pm_predict_occupancy(ctx, d["gh"].model, lb, float(z0[0]), float(z0[1]), d["N"], d["T"],
+                                    d["grid"], hu.seed, d["human"], counts, oob)
+            singles.append((lb.cpu().numpy(), counts.cpu().numpy(), oob.cpu().numpy()))
+        humans = [pm.make_human(d["gh"].goals, d["gh"].beta, d["lb"], d["z0"], d["N"], d["T"], d["grid"],
+                                hu.seed, d["human"], d["counts"], d["oob"], obs_xy=d["obs"], n_obs=d["n_obs"])
+                  for d in ds]
+        pm.pm_batch_set(b, humans)
+        pm.pm_batch_update_posterior(b)
+        pm.pm_batch_predict(b)
+        torch.cuda.synchronize()
+        for d, (lb1, c1, o1) in zip(ds, singles):
+            np.testing.assert_array_equal(d["lb"].cpu().numpy(), lb1)
+            np.testing.assert_array_equal(d["counts"].cpu().numpy(), c1)
+            np.testing.assert_array_equal(d["oob"].cpu().numpy(), o1)
+        with pytest.raises(pm.PmError) as e:
+            pm.pm_batch_set_config(b, 256, 1, 0, 48)  # several speeds: warp emplacement only
+        assert e.value.status == pm.PM_EINVAL
+        pm.pm_batch_autotune(b)
+        pm.pm_batch_predict(b)
+        torch.cuda.synchronize()
+        for d, (_, c1, _) in zip(ds, singles):
+            np.testing.assert_array_equal(d["counts"].cpu().numpy(), c1)
+    finally:
+        pm.pm_batch_destroy(b)
+
+
+def test_adjoint_matches_oracle(ctx, orc):
+    """Marginal log-likelihood and its gradient with two speeds; dL/dw1 is
+    nonzero (identifiable) and matches the oracle."""
+    import paper_2603_01122_gb300 as pm
+    ts = workloads.differentiation()
+    speeds = (0.5, 1.0, 1.5)
+    M = 48
+    trajs = []
+    for i in range(M):
+        g = int(ts.true_goal[i])
+        mm = orc.Model(ts.K - 4, ts.speed, ts.dt, ts.goals[g:g + 1], [ts.true_beta[i]], speeds=speeds)
+        trajs.append(orc.simulate(mm, 0, ts.starts[i], int(ts.lengths[i]), ts.obs_seed, i).astype(np.float32))
+    offsets = np.cumsum([0] + [len(t) for t in trajs]).astype(np.int32)
+    traj = np.concatenate(trajs)
+    K = ts.K - 4  # 32: a multiple of 4
+    prior = np.full(ts.goals.shape[0] * ts.beta.shape[0], -np.log(ts.goals.shape[0] * ts.beta.shape[0]))
+    m = orc.Model(K, ts.speed, ts.dt, ts.goals, ts.beta, w1=0.7, w2=1.3, speeds=speeds)
+    L64, dg64, dv64, dw64 = orc.loglik_grad(m, offsets, traj.astype(np.float64), prior)
+    g = dev(ts.goals)
+    b = dev(ts.beta)
+    model = pm.make_model(K, ts.speed, ts.dt, g, b, w1=0.7, w2=1.3, speeds=speeds)
+    L = torch.empty(1, device="cuda:0")
+    dg = torch.empty_like(g)
+    dv = torch.empty(1, device="cuda:0")
+    dw = torch.empty(2, device="cuda:0")
+    pm.pm_loglik_backward(ctx, model, M, dev(offsets, torch.int32), traj.shape[0], dev(traj), dev(prior), 1.0,
+                          L, dg, dv, dw)
+    torch.cuda.synchronize()
+    assert abs(L.item() - L64) <= 1e-6 * abs(L64)
+    got = np.concatenate([dg.cpu().numpy().ravel(), [dv.item()], dw.cpu().numpy()])
+    want = np.concatenate([dg64.ravel(), [dv64], dw64])
+    gnorm = np.linalg.norm(want)
+    assert np.linalg.norm(got - want) <= 1e-3 * gnorm, (got, want)
+    ok = np.abs(got - want) <= np.maximum(1e-2 * np.abs(want), 1e-4 * gnorm)
+    assert ok.all(), (got, want)
+    assert abs(dw64[0]) > 1e-3  # dL/dw1 is identifiable with several speeds
+
+
+def test_rejected_speed_sets(ctx):
+    import paper_2603_01122_gb300 as pm
+    g = dev(np.float32([[1.0, 2.0]]))
+    b = dev(np.float32([1.0]))
+    lb = dev(np.float32([0.0]))
+    counts = torch.empty((2, 4, 4), dtype=torch.int32, device="cuda:0")
+    oob = torch.empty(2, dtype=torch.int32, device="cuda:0")
+    grid = pm.make_grid(0.0, 0.0, 0.1, 4, 4)
+    bad = [dict(K=30, speeds=(0.5, 1.0)),                   # K not a multiple of 4
+           dict(K=32, speeds=(0.5, 1.0), heading_off=0b1),  # a heading disabled
+           dict(K=32, speeds=(0.5, 1.0), speed_off=0b11),   # every speed disabled
+           dict(K=32, speeds=(0.5, -1.0)),                  # a multiplier <= 0
+           dict(K=32, speeds=(0.5, float("nan")))]
+    for kw in bad:
+        model = pm.make_model(kw["K"], 1.0, 0.1, g, b, heading_off=kw.get("heading_off", 0), speeds=kw["speeds"],
+                              speed_off=kw.get("speed_off", 0))
+        with pytest.raises(pm.PmError) as e:
+            pm.pm_predict_occupancy(ctx, model, lb, 0.0, 0.0, 16, 2, grid, 1, 0, counts, oob)
+        assert e.value.status == pm.PM_EINVAL, kw

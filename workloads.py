@@ -22,6 +22,9 @@ Workloads
                   10 log-spaced beta 0.1..10, true beta log-uniform in [0.1, 10].
 ``serving``       125 Hz for 60 s, Poisson arrivals (2/s), dwell U[5, 30] s,
                   at most 64 live, N = 50k, T = 150, 121 x 121 window at 0.05 m.
+``multi_speed``   ``paper_scale`` with |U| = 96 controls (Table 1): K = 32 headings
+                  at speeds {0.5, 1, 1.5} x 1 m/s; the stationary variant masks
+                  the two faster speeds (Sec. IV-B).
 """
 from __future__ import annotations
 
@@ -64,6 +67,8 @@ class Human:
     w1: float = 1.0
     w2: float = 1.0
     window: int = 0            # serving: side of the output window (0 = full grid)
+    speeds: tuple = (1.0,)     # speed multipliers of the control set
+    speed_off: int = 0         # bit s: speed s disabled (stationary masking)
 
     @property
     def G(self):
@@ -101,6 +106,14 @@ def paper_scale(seed: int = MASTER_SEED) -> Human:
     return Human(K=36, speed=1.0, dt=f32(0.02), goals=goals, beta=beta, true_j=0 * 10 + 5,
                  start=start, n_obs=50, n_particles=100_000, horizon=150,
                  grid=(0.0, 0.0, f32(0.05), 200, 200), seed=seed, human_id=1, obs_seed=seed + 11)
+
+
+def multi_speed(seed: int = MASTER_SEED, stationary: bool = False) -> Human:
+    """``paper_scale`` with 3 speeds x K = 32 headings (|U| = 96); ``stationary``
+    disables the speeds 1 and 1.5 m/s, leaving the slow walk."""
+    hu = paper_scale(seed)
+    return dataclasses.replace(hu, K=32, speeds=(0.5, 1.0, 1.5), speed_off=0b110 if stationary else 0,
+                               human_id=3, obs_seed=seed + 31)
 
 
 def batched(seed: int = MASTER_SEED, n_humans: int = 16) -> List[Human]:
