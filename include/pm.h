@@ -205,7 +205,13 @@ pm_status pm_predict_host(pm_ctx *ctx, const pm_model *model, const float *goals
  *                               grid cell - (cx_off, cy_off)
  *   seed, human_id              Philox key (as pm_predict_occupancy)
  *   counts [horizon][H][W], oob [horizon]  outputs, zeroed by pm_batch_predict;
- *                               states outside the output count in oob. */
+ *                               states outside the output count in oob.
+ *   speed_off                   bit s: speed s disabled for this human on top
+ *                               of the shared model's speed_off (a human seen
+ *                               standing still keeps only the slow controls,
+ *                               Sec. IV-B); 0 unless the shared model has
+ *                               several speeds, and at least one speed must
+ *                               stay enabled (else PM_EINVAL). */
 typedef struct pm_human {
     const float *goals;
     const float *beta;
@@ -225,6 +231,7 @@ typedef struct pm_human {
     uint32_t human_id;
     uint32_t *counts;
     uint32_t *oob;
+    uint32_t speed_off;
 } pm_human;
 
 /* Opaque batch plan: device descriptors, the tile work list, scratch for the

@@ -57,7 +57,8 @@ class pm_human(C.Structure):
                 ("obs_xy", C.c_void_p), ("n_obs", C.c_int32), ("log_belief", C.c_void_p),
                 ("z0_xy", C.c_void_p), ("n_particles", C.c_int32), ("horizon", C.c_int32),
                 ("grid", pm_grid), ("center", C.c_int32), ("cx_off", C.c_int32), ("cy_off", C.c_int32),
-                ("seed", C.c_uint64), ("human_id", C.c_uint32), ("counts", C.c_void_p), ("oob", C.c_void_p)]
+                ("seed", C.c_uint64), ("human_id", C.c_uint32), ("counts", C.c_void_p), ("oob", C.c_void_p),
+                ("speed_off", C.c_uint32)]
 
 
 _lib = None
@@ -219,11 +220,12 @@ def pm_predict_host(ctx, model: pm_model, goals, beta, obs_xy, n_obs, log_prior,
 
 
 def make_human(goals, beta, log_belief, z0_xy, n_particles, horizon, grid: pm_grid, seed, human_id,
-               counts, oob, obs_xy=None, n_obs=0, center=0, cx_off=0, cy_off=0) -> pm_human:
-    """pm_human over device tensors (the tensors are kept alive with the struct)."""
+               counts, oob, obs_xy=None, n_obs=0, center=0, cx_off=0, cy_off=0, speed_off=0) -> pm_human:
+    """pm_human over device tensors (the tensors are kept alive with the struct);
+    ``speed_off`` disables speeds for this human (several-speed models only)."""
     h = pm_human(_p(goals), _p(beta), int(goals.shape[0]), int(beta.shape[0]), _p(obs_xy), int(n_obs),
                  _p(log_belief), _p(z0_xy), int(n_particles), int(horizon), grid, int(center), int(cx_off),
-                 int(cy_off), int(seed), int(human_id), _p(counts), _p(oob))
+                 int(cy_off), int(seed), int(human_id), _p(counts), _p(oob), int(speed_off))
     h._keep = (goals, beta, log_belief, z0_xy, counts, oob, obs_xy)
     return h
 

@@ -467,7 +467,7 @@ pm_status loglik_impl(pm_ctx *ctx, const pm_model *model, int32_t M, const int32
 // ---------------------------------------------------------------------------
 // batched prediction
 // ---------------------------------------------------------------------------
-pm_status check_human(const pm_human &h, int i)
+pm_status check_human(const pm_human &h, int i, const pm_model &shared)
 {
     if (!h.goals || !h.beta || !h.log_belief || !h.z0_xy || !h.counts || !h.oob)
         return fail(PM_EINVAL, "human %d: a device pointer is NULL", i);
@@ -483,7 +483,29 @@ pm_status check_human(const pm_human &h, int i)
     if (!h.center && (std::abs((long long)h.cx_off) + h.grid.W > (1LL << 22) ||
                       std::abs((long long)h.cy_off) + h.grid.H > (1LL << 22)))
         return fail(PM_EINVAL, "human %d: window offset more than 2^22 cells from the grid origin", i);
+    if (h.speed_off != 0u) {
+        if (!multi_speed(&shared)) return fail(PM_EINVAL, "human %d: speed_off needs a model with several speeds", i);
+        const uint32_t all = (1u << shared.n_speeds) - 1u;
+        if (((shared.speed_off | h.speed_off) & all) == all)
+            return fail(PM_EINVAL, "human %d: every speed is disabled", i);
+    }
     return PM_OK;
+}
+
+// Speeds enabled for one human of a batch (several speeds only).
+uint32_t human_speed_on(const pm_model &shared, const pm_human &h)
+{
+    if (!multi_speed(&shared)) return 0u;
+    return ((1u << shared.n_speeds) - 1u) & ~(shared.speed_off | h.speed_off);
+}
+
+// The longest step of the control set, v dt times the largest multiplier.
+double max_step(const pm_model &m)
+{
+    double mult = 1.0;
+    if (multi_speed(&m))
+        for (int q = 0; q < m.n_speeds; ++q) mult = std::max(mult, (double)m.speed_mult[q]);
+    return (double)m.speed * (double)m.dt * mult;
 }
 
 int batch_radius_cap(int window_kib, int threads)
@@ -509,7 +531,7 @@ size_t batch_dyn_smem(const pm_batch *b)
 pm_status batch_upload(pm_batch *b, cudaStream_t stream)
 {
     const int n = (int)b->humans.size();
-    const double s = (double)b->shared.speed * (double)b->shared.dt;
+    const double s = max_step(b->shared); // reach of the fastest control
     std::vector<int2> items;
     for (int h = 0; h < n; ++h)
         for (int p0 = 0; p0 < b->humans[h].n_particles; p0 += (b->warp_hist ? 32 : b->threads))
@@ -544,6 +566,7 @@ pm_status batch_upload(pm_batch *b, cudaStream_t stream)
         d.human = u.human_id;
         d.counts = u.counts;
         d.oob = u.oob;
+        d.speed_on = human_speed_on(b->shared, u);
         pm::PostHuman &q = ph[h];
         q.goals = u.goals;
         q.beta = u.beta;
@@ -557,6 +580,7 @@ pm_status batch_upload(pm_batch *b, cudaStream_t stream)
         q.log_b = u.log_belief;
         q.part = b->d_post_part + (size_t)h * b->post_stride;
         q.ticket = b->d_post_ticket + h;
+        q.speed_on = d.speed_on;
         max_chunks = std::max(max_chunks, nch);
         max_J = std::max(max_J, u.G * u.B);
     }
@@ -866,7 +890,7 @@ pm_status pm_batch_set(pm_batch *b, const pm_human *humans, int32_t n_humans, vo
     if (n_humans < 0 || n_humans > b->max_humans) return fail(PM_EINVAL, "n_humans=%d outside [0, %d]", n_humans, b->max_humans);
     if (n_humans > 0 && !humans) return fail(PM_EINVAL, "humans is NULL");
     for (int i = 0; i < n_humans; ++i) {
-        pm_status st = check_human(humans[i], i);
+        pm_status st = check_human(humans[i], i, b->shared);
         if (st != PM_OK) return st;
     }
     DeviceScope dev(b->ctx->device);

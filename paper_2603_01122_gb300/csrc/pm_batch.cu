@@ -203,7 +203,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_warp_kernel(const _
         c.tr_states = nullptr;
         c.tr_head = nullptr;
         c.tr_comp = nullptr;
-        if constexpr (MS) rollout_lane<KT, false, true>(a.tab, a.enabled, a.s2, c, comp, cdf, step, cw1, a.K);
+        if constexpr (MS)
+            rollout_lane<KT, false, true>(a.tab, a.enabled, a.s2, c, comp, cdf, step, cw1, a.K, h->speed_on);
         else rollout_lane<KT, FULL>(a.tab, a.enabled, a.s2, c, comp, cdf, step);
     }
 }

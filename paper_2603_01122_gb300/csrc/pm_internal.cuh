@@ -227,6 +227,7 @@ struct PostHuman {
     float *log_b;
     float *part;
     unsigned *ticket;
+    uint32_t speed_on; // several speeds: bit q = speed q enabled for this human
 };
 
 // One human of a batched rollout (device array).
@@ -246,6 +247,7 @@ struct BatchHuman {
     uint32_t human;
     uint32_t *counts;
     uint32_t *oob;
+    uint32_t speed_on;    // several speeds: bit q = speed q enabled for this human
 };
 
 // Grid epilogue (Gaussian smoothing, Sec. III-B; max-union, Sec. IV-B).

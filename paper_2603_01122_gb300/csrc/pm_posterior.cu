@@ -118,13 +118,13 @@ __device__ __forceinline__ float rel_logit(float bw, float two_s, float D, float
 constexpr int kMsPerLane = 8;
 
 // The enabled speed multiplier nearest to r (ties: the lower index).
-__device__ __forceinline__ int snap_speed(const SpeedSet &sp, float r)
+__device__ __forceinline__ int snap_speed(const SpeedSet &sp, uint32_t speed_on, float r)
 {
     int q0 = 0;
     float best = INFINITY;
     for (int q = 0; q < sp.S; ++q) {
         const float d = fabsf(sp.mult[q] - r);
-        if (((sp.speed_on >> q) & 1u) && d < best) {
+        if (((speed_on >> q) & 1u) && d < best) {
             best = d;
             q0 = q;
         }
@@ -188,7 +188,7 @@ __device__ __forceinline__ void posterior_chunk(const PosteriorArgs &a, const Po
     if constexpr (MS) {
         for (int u = threadIdx.x; u < U; u += blockDim.x) {
             const int q = u / a.K, k = u - q * a.K;
-            cu[u] = make_float4(a.ux[k], a.uy[k], a.sp.sl[q], ((a.sp.speed_on >> q) & 1u) ? 1.0f : 0.0f);
+            cu[u] = make_float4(a.ux[k], a.uy[k], a.sp.sl[q], ((h.speed_on >> q) & 1u) ? 1.0f : 0.0f);
         }
     }
     __syncthreads();
@@ -212,7 +212,7 @@ __device__ __forceinline__ void posterior_chunk(const PosteriorArgs &a, const Po
             const float ex = dx / len, ey = dy / len;
             const float px = zx - gx, py = zy - gy;
             if constexpr (MS) {
-                const float so = a.sp.sl[snap_speed(a.sp, len / a.s)];
+                const float so = a.sp.sl[snap_speed(a.sp, h.speed_on, len / a.s)];
                 float m, S;
                 step_loglik_ms(a.sp, cu, U, h.beta[b] * a.sp.w1, bw, px, py, ex, ey, so, lane, m, S);
                 acc_add(acc, m);
@@ -318,6 +318,7 @@ __global__ void __launch_bounds__(1024) posterior_kernel(const __grid_constant__
     h.log_b = a.log_b;
     h.part = a.part;
     h.ticket = a.ticket;
+    h.speed_on = a.sp.speed_on;
     if (a.sp.S > 0) posterior_chunk<true>(a, h, blockIdx.x, gridDim.x);
     else posterior_chunk<false>(a, h, blockIdx.x, gridDim.x);
 }

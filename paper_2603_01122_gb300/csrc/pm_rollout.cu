@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kWarpCtaThreads, kWarpCtaMinBlocks)
         const int64_t i0 = (int64_t)item * 32;
         if (i0 >= a.N) break;
         c.i = i0 + lane;
-        rollout_lane<64, false, true>(a.tab, a.enabled, a.s2, c, comp, cdf, step, cw1, a.K);
+        rollout_lane<64, false, true>(a.tab, a.enabled, a.s2, c, comp, cdf, step, cw1, a.K, a.tab.speed_on);
     }
 }
 

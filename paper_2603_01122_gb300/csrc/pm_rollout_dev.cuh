@@ -361,19 +361,19 @@ __device__ __forceinline__ uint32_t multi_weight(const HeadingTab &tab, int k, i
     return __float_as_uint(fmaf(ex2_approx(a), 4194304.0f, 12582912.0f)) - 0x4B400000u;
 }
 
-__device__ __forceinline__ int draw_multi(const HeadingTab &tab, int K, float x, float y, float gx, float gy,
-                                          float cb, float cw1, bool lb, uint32_t word)
+__device__ __forceinline__ int draw_multi(const HeadingTab &tab, uint32_t speed_on, int K, float x, float y,
+                                          float gx, float gy, float cb, float cw1, bool lb, uint32_t word)
 {
     const float dx = x - gx, dy = y - gy;
     const float r2 = fmaf(dx, dx, dy * dy);
     const float r = sqrt_approx(r2);
     SpeedStep q;
-    int best = max(__ffs((int)tab.speed_on) - 1, 0); // an enabled speed, whatever the inputs
+    int best = max(__ffs((int)speed_on) - 1, 0); // an enabled speed, whatever the inputs
     float vbest = -INFINITY;
 #pragma unroll
     for (int sp = 0; sp < PM_MAX_SPEEDS; ++sp) {
         q.D[sp] = q.hD[sp] = q.REF[sp] = q.C[sp] = 0.0f;
-        if (sp >= tab.S || !((tab.speed_on >> sp) & 1u)) continue;
+        if (sp >= tab.S || !((speed_on >> sp) & 1u)) continue;
         const float sl = tab.sl[sp];
         q.D[sp] = fmaf(dx, dx, fmaf(dy, dy, sl * sl));
         q.hD[sp] = 0.5f * rsqrt_approx(q.D[sp]);
@@ -402,7 +402,7 @@ __device__ __forceinline__ int draw_multi(const HeadingTab &tab, int K, float x,
     float cmin = INFINITY;
 #pragma unroll
     for (int sp = 0; sp < PM_MAX_SPEEDS; ++sp) {
-        if (sp >= tab.S || !((tab.speed_on >> sp) & 1u)) continue;
+        if (sp >= tab.S || !((speed_on >> sp) & 1u)) continue;
         q.C[sp] = fmaf(cb, q.REF[sp] - q.REF[best], cw1 * (tab.mult[sp] - tab.mult[best]));
         cmin = fminf(cmin, q.C[sp]);
     }
@@ -411,7 +411,7 @@ __device__ __forceinline__ int draw_multi(const HeadingTab &tab, int K, float x,
 #pragma unroll
     for (int sp = 0; sp < PM_MAX_SPEEDS; ++sp) {
         W[sp] = 0u;
-        if (sp >= tab.S || !((tab.speed_on >> sp) & 1u)) continue;
+        if (sp >= tab.S || !((speed_on >> sp) & 1u)) continue;
         q.C[sp] -= cmin;
         uint32_t w = 0u;
         for (int k = 0; k < K; ++k) w += multi_weight(tab, k, sp, dx, dy, q, cb);
@@ -427,7 +427,7 @@ __device__ __forceinline__ int draw_multi(const HeadingTab &tab, int K, float x,
         bool found = false;
 #pragma unroll
         for (int sp = 0; sp < PM_MAX_SPEEDS; ++sp) {
-            if (!found && sp < tab.S && ((tab.speed_on >> sp) & 1u)) {
+            if (!found && sp < tab.S && ((speed_on >> sp) & 1u)) {
                 if (thr < run + W[sp]) {
                     ss = sp;
                     C0 = run;
@@ -645,11 +645,12 @@ __device__ __forceinline__ void rollout_tile(const HeadingTab &tab, uint64_t ena
 // (match.any) into one global reduction. Every lane of the warp must call
 // it with the same c.T (idle lanes pass c.i >= c.N). No block barrier.
 // MS: the control set of several speeds (draw_multi; cw1 holds each
-// component's beta w1 v dt log2(e), step the S*K Euler steps, K the headings).
+// component's beta w1 v dt log2(e), step the S*K Euler steps, K the headings,
+// speed_on the enabled speeds).
 template <int KT, bool FULL, bool MS = false>
 __device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t enabled, float s2, const TileCtx &c,
                                              const float4 *comp, const uint32_t *cdf, const float2 *step,
-                                             const float *cw1 = nullptr, int K = 0)
+                                             const float *cw1 = nullptr, int K = 0, uint32_t speed_on = 0u)
 {
     const int lane = threadIdx.x & 31;
     const uint64_t i = (uint64_t)c.i;
@@ -689,7 +690,7 @@ __device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t ena
             const uint32_t word = q0;
             q0 = q1; q1 = q2; q2 = q3; q3 = q4; q4 = q5; q5 = q6; q6 = q7;
             int k;
-            if constexpr (MS) k = draw_multi(tab, K, x, y, gx, gy, cb, cw, lb, word);
+            if constexpr (MS) k = draw_multi(tab, speed_on, K, x, y, gx, gy, cb, cw, lb, word);
             else k = draw<KT, FULL>(tab, enabled, s2, x, y, gx, gy, cb, lb, word);
             const float2 st = step[k];
             x = __fadd_rn(x, st.x);

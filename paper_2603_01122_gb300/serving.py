@@ -17,6 +17,11 @@ room grid centred on the human's cell (Algorithm 1, bootstrapped belief).
 * Optionally (``union_sigma``) the frame also blurs every live human's window
   and max-unites them on the shared room grid (Sec. III-B, Sec. IV-B): the
   planner's input, in the same graph.
+* Several speeds (``speeds``): a human seen standing still keeps only the
+  controls that ``stationary_off`` leaves enabled (Sec. IV-B), set per human
+  by ``set_stationary`` or, with ``stationary_eps``, from its last observed
+  step; a change re-uploads the descriptors only. ``reset_belief`` returns a
+  human to the uniform belief when it leaves a goal.
 * Latency = host wall time from the start of the frame (observations in host
   memory) to the occupancy being ready on the device (event synchronised).
 
@@ -72,7 +77,8 @@ class Server:
 
     def __init__(self, ctx, K, speed, dt, room_grid, *, max_live=64, budget_bytes=4 << 30,
                  n_particles=50_000, horizon=150, window=121, g_max=6, b_max=10, w1=1.0, w2=1.0,
-                 use_graph=True, device="cuda:0", union_sigma=None):
+                 use_graph=True, device="cuda:0", union_sigma=None, speeds=None, stationary_off=0,
+                 stationary_eps=None):
         import torch
 
         self.torch = torch
@@ -99,7 +105,12 @@ class Server:
         self.done = torch.cuda.Event()
         shared_goals = torch.zeros((1, 2), device=self.dev)
         shared_beta = torch.ones(1, device=self.dev)
-        self._shared = make_model(K, speed, dt, shared_goals, shared_beta, w1=w1, w2=w2)
+        self.speeds = None if speeds is None else tuple(float(m) for m in speeds)
+        if stationary_off and (self.speeds is None or len(self.speeds) < 2):
+            raise ValueError("stationary masking needs several speeds")
+        self.stationary_off = int(stationary_off)
+        self.stationary_eps = stationary_eps
+        self._shared = make_model(K, speed, dt, shared_goals, shared_beta, w1=w1, w2=w2, speeds=self.speeds)
         self.batch = pm_batch_create(ctx, self._shared, cap)
         self.union_sigma = union_sigma
         self.union = None
@@ -130,7 +141,7 @@ class Server:
         with t.cuda.stream(self.stream):
             self.goals[s, :G].copy_(t.as_tensor(np.asarray(goals, np.float32)))
             self.beta[s, :B].copy_(t.as_tensor(np.asarray(beta, np.float32)))
-        self.meta[s] = dict(key=key, G=G, B=B, seed=int(seed), human_id=int(human_id))
+        self.meta[s] = dict(key=key, G=G, B=B, seed=int(seed), human_id=int(human_id), speed_off=0)
         self.reset_belief(s)
         self.obs_host[s, 0] = t.as_tensor(np.asarray(start, np.float32))
         self.obs_host[s, 1] = self.obs_host[s, 0]
@@ -149,11 +160,21 @@ class Server:
         with self.torch.cuda.stream(self.stream):
             self.log_b[slot, :J].fill_(-float(np.log(J)))
 
+    def set_stationary(self, slot: int, stationary: bool) -> None:
+        """Mask (or restore) the speeds ``stationary_off`` for one human."""
+        off = self.stationary_off if stationary else 0
+        if self.meta[slot]["speed_off"] != off:
+            self.meta[slot]["speed_off"] = off
+            self.dirty = True
+
     def observe(self, slot: int, xy) -> None:
         """The newest observed state of a live human (host side, next frame)."""
         self.obs_host[slot, 0] = self.obs_host[slot, 1]
         self.obs_host[slot, 1, 0] = float(xy[0])
         self.obs_host[slot, 1, 1] = float(xy[1])
+        if self.stationary_eps is not None:
+            step = self.obs_host[slot, 1] - self.obs_host[slot, 0]
+            self.set_stationary(slot, float(step.norm()) < self.stationary_eps)
 
     # -- frames ------------------------------------------------------------------
     def _humans(self):
@@ -162,7 +183,8 @@ class Server:
             m = self.meta[s]
             hs.append(make_human(self.goals[s, :m["G"]], self.beta[s, :m["B"]], self.log_b[s],
                                  self.obs_dev[s, 1], self.N, self.T, self.grid, m["seed"], m["human_id"],
-                                 self.counts[s], self.oob[s], obs_xy=self.obs_dev[s], n_obs=1, center=1))
+                                 self.counts[s], self.oob[s], obs_xy=self.obs_dev[s], n_obs=1, center=1,
+                                 speed_off=m["speed_off"]))
         return hs
 
     def _enqueue(self):

@@ -107,3 +107,51 @@ def test_serving_frame_union_matches_oracle(ctx, orc):
         assert got.max() > 0.0
     finally:
         srv.close()
+
+
+def test_serving_stationary_masking(ctx, orc):
+    """Several speeds with stationary masking (Sec. IV-B): a human whose last
+    observed step is shorter than stationary_eps keeps only the slow speed;
+    each frame's window equals the single-human path under that human's mask."""
+    import paper_2603_01122_gb300 as pm
+    from paper_2603_01122_gb300.serving import Server
+    hu = workloads.multi_speed()
+    speeds, N, T, win = hu.speeds, 3000, 30, 31
+    srv = Server(ctx, hu.K, hu.speed, hu.dt, hu.grid, max_live=3, n_particles=N, horizon=T, window=win,
+                 speeds=speeds, stationary_off=0b110, stationary_eps=1e-4)
+    rng = np.random.default_rng(5)
+    try:
+        slots = [srv.admit(i, hu.goals, hu.beta, [3.0 + i, 4.0], hu.seed, 60 + i) for i in range(3)]
+        pos = [np.array([3.0 + i, 4.0]) for i in range(3)]
+        for f in range(12):
+            for i, s in enumerate(slots):
+                moving = (i == 0) or (i == 2 and f % 4 < 2)
+                if moving:
+                    ang = rng.uniform(0, 2 * np.pi)
+                    pos[i] = pos[i] + hu.speed * hu.dt * np.array([np.cos(ang), np.sin(ang)])
+                srv.observe(s, pos[i].astype(np.float32))
+            srv.frame()
+            torch.cuda.synchronize()
+            for i, s in enumerate(slots):
+                mask = srv.meta[s]["speed_off"]
+                moving = (i == 0) or (i == 2 and f % 4 < 2)
+                assert mask == (0 if moving else 0b110)
+                goals = srv.goals[s, :hu.G].contiguous()
+                beta = srv.beta[s, :hu.B].contiguous()
+                model = pm.make_model(hu.K, hu.speed, hu.dt, goals, beta, speeds=speeds, speed_off=mask)
+                lb = srv.log_b[s, :hu.G * hu.B].contiguous()
+                z0 = srv.obs_dev[s, 1].cpu().numpy()
+                x0, y0, res, W, H = hu.grid
+                full = torch.empty((T, H, W), dtype=torch.int32, device="cuda:0")
+                foob = torch.empty(T, dtype=torch.int32, device="cuda:0")
+                pm.pm_predict_occupancy(ctx, model, lb, float(z0[0]), float(z0[1]), N, T,
+                                        pm.make_grid(x0, y0, res, W, H), hu.seed, 60 + i, full, foob)
+                torch.cuda.synchronize()
+                r = np.float32
+                cx = int(np.floor(r(r(z0[0] - r(x0)) * (r(1.0) / r(res)))))
+                cy = int(np.floor(r(r(z0[1] - r(y0)) * (r(1.0) / r(res)))))
+                ox, oy = cx - (win - 1) // 2, cy - (win - 1) // 2
+                np.testing.assert_array_equal(srv.counts[s].cpu().numpy(),
+                                              full.cpu().numpy()[:, oy:oy + win, ox:ox + win])
+    finally:
+        srv.close()

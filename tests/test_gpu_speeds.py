@@ -164,15 +164,17 @@ def test_posterior_matches_oracle(ctx, orc, stationary):
 
 
 def test_batch_equals_single(ctx, orc):
-    """Four humans under one shared |U| = 96 model: the batched belief update
-    and histograms equal the single-human calls bit for bit."""
+    """Four humans under one shared |U| = 96 model, two with their own speed
+    masks (one standing still): the batched belief update and histograms equal
+    the single-human calls under the same masks bit for bit."""
     import paper_2603_01122_gb300 as pm
     hu = workloads.multi_speed()
     rng = np.random.default_rng(9)
+    masks = [0, 0b110, 0, 0b001]
     ds = []
     for h in range(4):
         goals = rng.uniform(0, 10, size=(2 + h, 2)).astype(np.float32)
-        m, gh = _models(orc, hu.K, hu.speed, hu.dt, goals, hu.beta, hu.speeds)
+        m, gh = _models(orc, hu.K, hu.speed, hu.dt, goals, hu.beta, hu.speeds, speed_off=masks[h])
         start = rng.uniform(2, 8, size=2).astype(np.float32)
         obs = orc.simulate(m, h, start, 30, hu.obs_seed, 40 + h).astype(np.float32)
         N, T = int(rng.integers(5000, 40000)), int(rng.integers(20, 80))
@@ -195,8 +197,16 @@ def test_batch_equals_single(ctx, orc):
                                     d["grid"], hu.seed, d["human"], counts, oob)
             singles.append((lb.cpu().numpy(), counts.cpu().numpy(), oob.cpu().numpy()))
         humans = [pm.make_human(d["gh"].goals, d["gh"].beta, d["lb"], d["z0"], d["N"], d["T"], d["grid"],
-                                hu.seed, d["human"], d["counts"], d["oob"], obs_xy=d["obs"], n_obs=d["n_obs"])
-                  for d in ds]
+                                hu.seed, d["human"], d["counts"], d["oob"], obs_xy=d["obs"], n_obs=d["n_obs"],
+                                speed_off=mk)
+                  for d, mk in zip(ds, masks)]
+        for bad in (0b111, 0b1000 | 0b111):  # every speed of a human disabled
+            h0 = humans[0]
+            h0.speed_off = bad
+            with pytest.raises(pm.PmError) as e:
+                pm.pm_batch_set(b, humans)
+            assert e.value.status == pm.PM_EINVAL
+            h0.speed_off = 0
         pm.pm_batch_set(b, humans)
         pm.pm_batch_update_posterior(b)
         pm.pm_batch_predict(b)
@@ -217,21 +227,29 @@ def test_batch_equals_single(ctx, orc):
         pm.pm_batch_destroy(b)
 
 
-def test_adjoint_matches_oracle(ctx, orc):
-    """Marginal log-likelihood and its gradient with two speeds; dL/dw1 is
-    nonzero (identifiable) and matches the oracle."""
-    import paper_2603_01122_gb300 as pm
-    ts = workloads.differentiation()
-    speeds = (0.5, 1.0, 1.5)
-    M = 48
+SPEEDS3 = (0.5, 1.0, 1.5)
+
+
+def _speed_trajectories(orc, ts, K, M):
+    """M observed trajectories of the differentiation workload, drawn with
+    the three-speed control set over K headings."""
     trajs = []
     for i in range(M):
         g = int(ts.true_goal[i])
-        mm = orc.Model(ts.K - 4, ts.speed, ts.dt, ts.goals[g:g + 1], [ts.true_beta[i]], speeds=speeds)
+        mm = orc.Model(K, ts.speed, ts.dt, ts.goals[g:g + 1], [ts.true_beta[i]], speeds=SPEEDS3)
         trajs.append(orc.simulate(mm, 0, ts.starts[i], int(ts.lengths[i]), ts.obs_seed, i).astype(np.float32))
-    offsets = np.cumsum([0] + [len(t) for t in trajs]).astype(np.int32)
-    traj = np.concatenate(trajs)
+    return np.cumsum([0] + [len(t) for t in trajs]).astype(np.int32), np.concatenate(trajs)
+
+
+def test_adjoint_matches_oracle(ctx, orc):
+    """Marginal log-likelihood and its gradient with three speeds; dL/dw1 is
+    nonzero (identifiable) and matches the oracle."""
+    import paper_2603_01122_gb300 as pm
+    ts = workloads.differentiation()
+    speeds = SPEEDS3
+    M = 48
     K = ts.K - 4  # 32: a multiple of 4
+    offsets, traj = _speed_trajectories(orc, ts, K, M)
     prior = np.full(ts.goals.shape[0] * ts.beta.shape[0], -np.log(ts.goals.shape[0] * ts.beta.shape[0]))
     m = orc.Model(K, ts.speed, ts.dt, ts.goals, ts.beta, w1=0.7, w2=1.3, speeds=speeds)
     L64, dg64, dv64, dw64 = orc.loglik_grad(m, offsets, traj.astype(np.float64), prior)
@@ -253,6 +271,30 @@ def test_adjoint_matches_oracle(ctx, orc):
     ok = np.abs(got - want) <= np.maximum(1e-2 * np.abs(want), 1e-4 * gnorm)
     assert ok.all(), (got, want)
     assert abs(dw64[0]) > 1e-3  # dL/dw1 is identifiable with several speeds
+
+
+def test_autograd_with_speeds(ctx, orc):
+    """The autograd Function over the several-speed adjoint: all of goals,
+    speed and both Q weights receive the oracle's gradient."""
+    from paper_2603_01122_gb300.autograd import marginal_loglik
+    ts = workloads.differentiation()
+    K = ts.K - 4
+    offsets, traj = _speed_trajectories(orc, ts, K, 24)
+    J = ts.goals.shape[0] * ts.beta.shape[0]
+    prior = np.full(J, -np.log(J), np.float32)
+    goals = dev(ts.goals).requires_grad_(True)
+    speed = torch.tensor(ts.speed, requires_grad=True)
+    w = torch.tensor([1.2, 0.8], requires_grad=True)
+    L = marginal_loglik(goals, speed, w, dev(ts.beta), K, ts.dt, dev(offsets, torch.int32), dev(traj), dev(prior),
+                        ctx, speeds=SPEEDS3)
+    (-1.5 * L).backward()
+    m = orc.Model(K, ts.speed, ts.dt, ts.goals, ts.beta, w1=1.2, w2=0.8, speeds=SPEEDS3)
+    L64, dg64, dv64, dw64 = orc.loglik_grad(m, offsets, traj.astype(np.float64), prior)
+    assert abs(L.item() - L64) <= 1e-6 * abs(L64)
+    got = np.concatenate([goals.grad.cpu().numpy().ravel(), [speed.grad.item()], w.grad.numpy()])
+    want = -1.5 * np.concatenate([dg64.ravel(), [dv64], dw64])
+    gnorm = np.linalg.norm(want)
+    assert np.linalg.norm(got - want) <= 1e-3 * gnorm, (got, want)
 
 
 def test_rejected_speed_sets(ctx):
