@@ -268,7 +268,7 @@ def gpu_paths(pm, ctx, torch, dev, hu, n_steps, human_id, start=None):
     whose belief is a point mass on the true component."""
     goals = torch.tensor(hu.goals, device=dev)
     beta = torch.tensor(hu.beta, device=dev)
-    model = pm.make_model(hu.K, hu.speed, hu.dt, goals, beta)
+    model = pm.make_model(hu.K, hu.speed, hu.dt, goals, beta, speeds=speeds_of(hu))
     J = hu.G * hu.B
     onehot = torch.full((J,), -float("inf"), device=dev)
     onehot[hu.true_j] = 0.0
@@ -277,6 +277,11 @@ def gpu_paths(pm, ctx, torch, dev, hu, n_steps, human_id, start=None):
     pm.pm_predict_occupancy_traced(ctx, model, onehot, float(z[0]), float(z[1]), 1, n_steps, None,
                                    hu.obs_seed, human_id, None, None, 1, st, None, None)
     return torch.cat([torch.tensor(np.asarray(z, np.float32), device=dev).view(1, 2), st[0]], 0).contiguous()
+
+
+def speeds_of(hu):
+    """The control set's speed multipliers (None: one speed)."""
+    return None if tuple(hu.speeds) == (1.0,) else tuple(hu.speeds)
 
 
 def time_events(torch, stream, fn, reps):
@@ -508,6 +513,36 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
                                       "frames_waited": res2["frames_waited"]}
     finally:
         srv.close()
+
+    # -- several speeds: |U| = 96 controls (3 speeds x K = 32), and the same
+    #    human standing still (the two faster speeds masked)
+    for name, stationary in (("multi_speed", False), ("multi_speed_stationary", True)):
+        hu = workloads.multi_speed(stationary=stationary)
+        g, b = torch.tensor(hu.goals, device=dev), torch.tensor(hu.beta, device=dev)
+        model = pm.make_model(hu.K, hu.speed, hu.dt, g, b, speeds=hu.speeds, speed_off=hu.speed_off)
+        gen = workloads.multi_speed()
+        obs = gpu_paths(pm, ctx, torch, dev, gen, hu.n_obs, hu.human_id)
+        z0 = obs[-1].cpu().numpy()
+        prior = torch.tensor(hu.uniform_log_prior(), device=dev)
+        lb = torch.empty_like(prior)
+        x0, y0, res, W, H = hu.grid
+        grid = pm.make_grid(x0, y0, res, W, H)
+        counts = torch.empty((hu.horizon, H, W), dtype=torch.int32, device=dev)
+        oob = torch.empty(hu.horizon, dtype=torch.int32, device=dev)
+
+        def ms_step():
+            lb.copy_(prior)
+            pm.pm_update_posterior(ctx, model, obs, hu.n_obs, lb, stream)
+            pm.pm_predict_occupancy(ctx, model, lb, float(z0[0]), float(z0[1]), hu.n_particles, hu.horizon,
+                                    grid, hu.seed, hu.human_id, counts, oob, stream)
+        ms = time_events(torch, stream, ms_step, 20)
+        u_on = hu.K * sum(1 for q in range(len(hu.speeds)) if not (hu.speed_off >> q) & 1)
+        rate = hu.n_particles * hu.horizon / (ms * 1e-3)
+        out[name] = {"ms_per_prediction": ms, "particle_steps_per_s": rate, "controls_enabled": u_on,
+                     "sfu_roofline_frac": rate * 2 * u_on / sfu_peak,
+                     "algorithmic": "2 SFU results (ex2 + sqrt) per enabled control per particle-step",
+                     "config": f"paper_scale room, K=32 x speeds {hu.speeds}, speed_off={hu.speed_off:#b}, "
+                               "N=100k, T=150, 50 observed steps, 200x200 grid; L2 not flushed"}
 
     # -- differentiation: 256 trajectories, adjoint of the marginal log-likelihood
     ts = workloads.differentiation()

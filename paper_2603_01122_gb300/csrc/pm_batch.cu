@@ -254,8 +254,13 @@ cudaError_t batch_shape(const BatchArgs &a, const RolloutShape &sh, int blocks, 
 
 cudaError_t batch_dispatch(const BatchArgs &a, const RolloutShape &sh, int blocks, size_t dyn, cudaStream_t s, int *occ)
 {
-    if (a.tab.S > 0) // several speeds: warp-combined emplacement only
-        return launch_or_query(batch_warp_kernel<64, false, true>, a, blocks, sh.threads, dyn, s, occ);
+    if (a.tab.S > 0) { // several speeds: warp-combined emplacement only
+        switch (a.K) {
+        case 16: return launch_or_query(batch_warp_kernel<16, false, true>, a, blocks, sh.threads, dyn, s, occ);
+        case 32: return launch_or_query(batch_warp_kernel<32, false, true>, a, blocks, sh.threads, dyn, s, occ);
+        default: return launch_or_query(batch_warp_kernel<0, false, true>, a, blocks, sh.threads, dyn, s, occ);
+        }
+    }
     const int KT = rollout_kt_for(a.K);
     const uint64_t all = (KT >= 64) ? ~0ull : ((1ull << KT) - 1ull);
     const bool full = (a.K == KT) && ((a.enabled & all) == all);

@@ -88,7 +88,9 @@ __global__ void __launch_bounds__(kWarpCtaThreads, kWarpCtaMinBlocks)
     }
 }
 
-// The same persistent warps for a control set of several speeds (draw_multi).
+// The same persistent warps for a control set of several speeds: KT > 0 is
+// the heading count of the fused draw (K == KT), KT = 0 the general draw.
+template <int KT>
 __global__ void __launch_bounds__(kWarpCtaThreads, kWarpCtaMinBlocks)
     rollout_multi_kernel(const __grid_constant__ RolloutArgs a, unsigned *head)
 {
@@ -139,14 +141,15 @@ __global__ void __launch_bounds__(kWarpCtaThreads, kWarpCtaMinBlocks)
         const int64_t i0 = (int64_t)item * 32;
         if (i0 >= a.N) break;
         c.i = i0 + lane;
-        rollout_lane<64, false, true>(a.tab, a.enabled, a.s2, c, comp, cdf, step, cw1, a.K, a.tab.speed_on);
+        rollout_lane<KT, false, true>(a.tab, a.enabled, a.s2, c, comp, cdf, step, cw1, a.K, a.tab.speed_on);
     }
 }
 
+template <int KT>
 cudaError_t launch_multi(const RolloutArgs &a, unsigned *head, int sm_count, cudaStream_t s, int *occ)
 {
     int n = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_multi_kernel, kWarpCtaThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_multi_kernel<KT>, kWarpCtaThreads, 0);
     if (e != cudaSuccess) return e;
     if (occ) {
         *occ = n;
@@ -157,7 +160,7 @@ cudaError_t launch_multi(const RolloutArgs &a, unsigned *head, int sm_count, cud
     int64_t blocks = (int64_t)sm_count * (n > 0 ? n : 1);
     if (need < blocks) blocks = need;
     cudaGetLastError();
-    rollout_multi_kernel<<<(unsigned)blocks, kWarpCtaThreads, 0, s>>>(a, head);
+    rollout_multi_kernel<KT><<<(unsigned)blocks, kWarpCtaThreads, 0, s>>>(a, head);
     return cudaGetLastError();
 }
 
@@ -185,7 +188,13 @@ cudaError_t launch_kt(const RolloutArgs &a, unsigned *head, int sm_count, cudaSt
 
 cudaError_t dispatch(const RolloutArgs &a, unsigned *head, int sm_count, cudaStream_t s, int *occ)
 {
-    if (a.tab.S > 0) return launch_multi(a, head, sm_count, s, occ);
+    if (a.tab.S > 0) { // several speeds (all K headings enabled, K % 4 == 0)
+        switch (a.K) {
+        case 16: return launch_multi<16>(a, head, sm_count, s, occ);
+        case 32: return launch_multi<32>(a, head, sm_count, s, occ);
+        default: return launch_multi<0>(a, head, sm_count, s, occ);
+        }
+    }
     switch (rollout_kt_for(a.K)) {
     case 8: return launch_kt<8>(a, head, sm_count, s, occ);
     case 16: return launch_kt<16>(a, head, sm_count, s, occ);

@@ -451,6 +451,157 @@ __device__ __forceinline__ int draw_multi(const HeadingTab &tab, uint32_t speed_
     return ss * K + kk;
 }
 
+// The several-speed draw fused like draw_heading_lb, for KT headings all
+// enabled (KT % 4 == 0) and a component with the bound-normalised flag.
+// Per enabled speed q the loop is the one-speed loop with that speed's
+// constants: P_{k,q} = 2 s e_k.(m_q (z - g)) (the scaled offset rounded once,
+// so heading k + K/2 still has exactly -P), D_q = ||z - g||^2 + sl_q^2 and the
+// bound REF_q of that speed. The exponent of control (q, k) is
+//   -cb (d_{k,q} - REF_q) - C_q,   C_q = cb (REF_q - REF_b) + cw1 (m_q - m_b) - min,
+// evaluated as fma(R, -cb/2d, fma(d~, -cb, RC_q)) with RC_q = round(cb REF_q);
+// the rounding e_q of RC_q and the offset C_q are folded into the fixed-point
+// scale 2^22 2^(e_q - C_q), so they cost nothing per control and the offsets
+// between speeds keep FP32 relative precision. Pass 1 keeps segment sums of G
+// headings per speed (the bits are not stored); the threshold picks the
+// segment and pass 2 recomputes only its G weights, bit for bit.
+template <int KT>
+struct MultiLbConsts {
+    float D, HDNC, RC, SC, mx, my; // D_q, -cb/(2 d_q), round(cb REF_q), scale, m_q (z - g)
+};
+
+template <int KT>
+__device__ __forceinline__ MultiLbConsts<KT> multi_lb_consts(const HeadingTab &tab, int q, float dx, float dy,
+                                                             float cb, float REF, float C)
+{
+    MultiLbConsts<KT> c;
+    const float sl = tab.sl[q];
+    c.D = fmaf(dx, dx, fmaf(dy, dy, sl * sl));
+    c.HDNC = -cb * (0.5f * rsqrt_approx(c.D));
+    c.RC = cb * REF;
+    const float e = fmaf(cb, REF, -c.RC); // cb REF - RC, exact
+    c.SC = 4194304.0f * exp2f(e - C);
+    c.mx = __fmul_rn(dx, tab.mult[q]);
+    c.my = __fmul_rn(dy, tab.mult[q]);
+    return c;
+}
+
+// Fixed-point weight of heading k under the constants of one speed (pass 2).
+template <int KT>
+__device__ __forceinline__ uint32_t multi_lb_weight(const HeadingTab &tab, int k, const MultiLbConsts<KT> &c,
+                                                    float cb)
+{
+    const float P = fmaf(tab.tx[k], c.mx, __fmul_rn(tab.ty[k], c.my));
+    const float d = sqrt_approx(fabsf(c.D + P));
+    const float a = fmaf(P - fmaf(d, d, -c.D), c.HDNC, fmaf(d, -cb, c.RC));
+    return __float_as_uint(fmaf(ex2_approx(a), c.SC, 12582912.0f)) - 0x4B400000u;
+}
+
+template <int KT>
+__device__ __forceinline__ int draw_multi_lb(const HeadingTab &tab, uint32_t speed_on, float x, float y, float gx,
+                                             float gy, float cb, float cw1, uint32_t word)
+{
+    static_assert(KT % 4 == 0, "pairs of headings must not straddle the two halves");
+    constexpr int G = CdfSegs<KT>::G, NS = KT / G, H2 = KT / 2;
+    const float dx = x - gx, dy = y - gy;
+    const float r = sqrt_approx(fmaf(dx, dx, dy * dy));
+    // bounds per speed and the offsets between speeds
+    float REF[PM_MAX_SPEEDS], C[PM_MAX_SPEEDS];
+    float vbest = -INFINITY, refb = 0.0f, mb = 0.0f;
+#pragma unroll
+    for (int q = 0; q < PM_MAX_SPEEDS; ++q) {
+        const float sl = tab.sl[q];
+        const float margin = (r + sl) * 0x1p-20f;
+        REF[q] = (cb >= 0.0f) ? fabsf(r - sl) - margin : r + sl + margin;
+        const float v = -fmaf(cb, REF[q], cw1 * tab.mult[q]);
+        if (q < tab.S && ((speed_on >> q) & 1u) && v > vbest) {
+            vbest = v;
+            refb = REF[q];
+            mb = tab.mult[q];
+        }
+    }
+    float cmin = INFINITY;
+#pragma unroll
+    for (int q = 0; q < PM_MAX_SPEEDS; ++q) {
+        C[q] = fmaf(cb, REF[q] - refb, cw1 * (tab.mult[q] - mb));
+        if (q < tab.S && ((speed_on >> q) & 1u)) cmin = fminf(cmin, C[q]);
+    }
+    const f32x2 NC = f2_pack(-cb, -cb), MG = f2_pack(12582912.0f, 12582912.0f);
+    const f32x2 *TX = reinterpret_cast<const f32x2 *>(tab.tx);
+    const f32x2 *TY = reinterpret_cast<const f32x2 *>(tab.ty);
+    uint32_t seg[PM_MAX_SPEEDS][NS];
+#pragma unroll
+    for (int q = 0; q < PM_MAX_SPEEDS; ++q) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) seg[q][i] = 0u;
+        if (q >= tab.S || !((speed_on >> q) & 1u)) continue;
+        const MultiLbConsts<KT> c = multi_lb_consts<KT>(tab, q, dx, dy, cb, REF[q], C[q] - cmin);
+        const f32x2 MX = f2_pack(c.mx, c.mx), MY = f2_pack(c.my, c.my);
+        const f32x2 DD = f2_pack(c.D, c.D), NDD = f2_pack(-c.D, -c.D);
+        const f32x2 HDNC = f2_pack(c.HDNC, c.HDNC), NHDNC = f2_pack(-c.HDNC, -c.HDNC);
+        const f32x2 RC = f2_pack(c.RC, c.RC), SC = f2_pack(c.SC, c.SC);
+#pragma unroll
+        for (int k2 = 0; k2 < KT / 4; ++k2) {
+            const f32x2 P = f2_fma(TX[k2], MX, f2_mul(TY[k2], MY)); // headings 2k2, 2k2+1; -P for + K/2
+            float x0, x1, y0, y1;
+            f2_unpack(f2_add(DD, P), x0, x1);
+            f2_unpack(f2_sub(DD, P), y0, y1);
+            const f32x2 DA = f2_pack(sqrt_approx(fabsf(x0)), sqrt_approx(fabsf(x1)));
+            const f32x2 DB = f2_pack(sqrt_approx(fabsf(y0)), sqrt_approx(fabsf(y1)));
+            float a0, a1, b0, b1;
+            f2_unpack(f2_fma(f2_sub(P, f2_fma(DA, DA, NDD)), HDNC, f2_fma(DA, NC, RC)), a0, a1);
+            f2_unpack(f2_fma(f2_add(P, f2_fma(DB, DB, NDD)), NHDNC, f2_fma(DB, NC, RC)), b0, b1);
+            float w0, w1, v0, v1;
+            f2_unpack(f2_fma(f2_pack(ex2_approx(a0), ex2_approx(a1)), SC, MG), w0, w1);
+            f2_unpack(f2_fma(f2_pack(ex2_approx(b0), ex2_approx(b1)), SC, MG), v0, v1);
+            seg[q][(2 * k2) / G] += (__float_as_uint(w0) - 0x4B400000u) + (__float_as_uint(w1) - 0x4B400000u);
+            seg[q][(H2 + 2 * k2) / G] += (__float_as_uint(v0) - 0x4B400000u) + (__float_as_uint(v1) - 0x4B400000u);
+        }
+    }
+    uint32_t S = 0u;
+#pragma unroll
+    for (int q = 0; q < PM_MAX_SPEEDS; ++q)
+#pragma unroll
+        for (int i = 0; i < NS; ++i) S += seg[q][i];
+    const uint32_t thr = (uint32_t)(((uint64_t)(word >> 8) * (uint64_t)S) >> 24);
+    // the segment whose running-sum interval holds thr
+    int qs = 0, is = NS - 1;
+    uint32_t C0 = 0u, run = 0u;
+    bool found = false;
+#pragma unroll
+    for (int q = 0; q < PM_MAX_SPEEDS; ++q)
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const bool hit = !found && thr < run + seg[q][i];
+            qs = hit ? q : qs;
+            is = hit ? i : is;
+            C0 = hit ? run : C0;
+            found = found || hit;
+            run += seg[q][i];
+        }
+    if (!found) { // S == 0: only for non-finite inputs; any valid control
+        qs = max(__ffs((int)speed_on) - 1, 0);
+        is = NS - 1;
+        C0 = 0u;
+    }
+    float REFs = REF[0], Cs = C[0];
+#pragma unroll
+    for (int q = 1; q < PM_MAX_SPEEDS; ++q) {
+        REFs = (qs == q) ? REF[q] : REFs;
+        Cs = (qs == q) ? C[q] : Cs;
+    }
+    const MultiLbConsts<KT> c = multi_lb_consts<KT>(tab, qs, dx, dy, cb, REFs, Cs - cmin);
+    uint32_t acc = C0;
+    int kk = is * G + G - 1;
+    for (int k = is * G; k < is * G + G; ++k) {
+        acc += multi_lb_weight<KT>(tab, k, c, cb);
+        if (thr < acc) {
+            kk = k;
+            break;
+        }
+    }
+    return qs * KT + kk;
+}
+
 // Per-tile state of one human for rollout_tile.
 struct TileCtx {
     float z0x, z0y;
@@ -644,9 +795,10 @@ __device__ __forceinline__ void rollout_tile(const HeadingTab &tab, uint64_t ena
 // emplaced with the lanes of the warp that land in the same cell combined
 // (match.any) into one global reduction. Every lane of the warp must call
 // it with the same c.T (idle lanes pass c.i >= c.N). No block barrier.
-// MS: the control set of several speeds (draw_multi; cw1 holds each
-// component's beta w1 v dt log2(e), step the S*K Euler steps, K the headings,
-// speed_on the enabled speeds).
+// MS: the control set of several speeds (cw1 holds each component's
+// beta w1 v dt log2(e), step the S*K Euler steps, K the headings, speed_on the
+// enabled speeds); KT > 0 is then K itself, with draw_multi_lb for the
+// components it applies to, and KT = 0 runs draw_multi for any K.
 template <int KT, bool FULL, bool MS = false>
 __device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t enabled, float s2, const TileCtx &c,
                                              const float4 *comp, const uint32_t *cdf, const float2 *step,
@@ -690,8 +842,16 @@ __device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t ena
             const uint32_t word = q0;
             q0 = q1; q1 = q2; q2 = q3; q3 = q4; q4 = q5; q5 = q6; q6 = q7;
             int k;
-            if constexpr (MS) k = draw_multi(tab, speed_on, K, x, y, gx, gy, cb, cw, lb, word);
-            else k = draw<KT, FULL>(tab, enabled, s2, x, y, gx, gy, cb, lb, word);
+            if constexpr (MS) {
+                if constexpr (KT > 0) { // K == KT, all headings enabled: the fused form where it applies
+                    if (lb) k = draw_multi_lb<KT>(tab, speed_on, x, y, gx, gy, cb, cw, word);
+                    else k = draw_multi(tab, speed_on, K, x, y, gx, gy, cb, cw, lb, word);
+                } else {
+                    k = draw_multi(tab, speed_on, K, x, y, gx, gy, cb, cw, lb, word);
+                }
+            } else {
+                k = draw<KT, FULL>(tab, enabled, s2, x, y, gx, gy, cb, lb, word);
+            }
             const float2 st = step[k];
             x = __fadd_rn(x, st.x);
             y = __fadd_rn(y, st.y);
