@@ -54,6 +54,13 @@ ROLLOUT_SOURCES = ["paper_2603_01122_gb300/csrc/pm_rollout.cu", "paper_2603_0112
                    "paper_2603_01122_gb300/csrc/pm_internal.cuh"]
 
 
+# main-line workloads: generator and the rollout kernel that dominates it
+MAIN_WORKLOADS = {
+    "paper_scale": (workloads.paper_scale, "rollout_warp_kernel<36,true>"),
+    "multi_speed": (workloads.multi_speed, "rollout_multi_kernel<32>"),
+}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -66,6 +73,8 @@ def parse():
     ap.add_argument("--serving-seconds", type=float, default=0.0,
                     help="also run the Poisson arrival process for this many simulated seconds")
     ap.add_argument("--serving-frames", type=int, default=250, help="frames of the forced-64-live run")
+    ap.add_argument("--workload", default="paper_scale", choices=sorted(MAIN_WORKLOADS),
+                    help="the main line's workload (paper_scale: one speed, K = 36; multi_speed: |U| = 96)")
     return ap.parse_args()
 
 
@@ -98,12 +107,13 @@ def job_throughput(world, units_per_rank, seconds):
     return world * units_per_rank / seconds
 
 
-def workload_config(hu):
+def workload_config(hu, name="paper_scale"):
     x0, y0, res, W, H = hu.grid
+    speeds = {} if tuple(hu.speeds) == (1.0,) else {"speeds": list(hu.speeds), "controls": hu.K * len(hu.speeds)}
     return {
-        "workload": "paper_scale",
+        "workload": name,
         "humans_per_gpu": 1,
-        "K": hu.K, "G": hu.G, "B": hu.B, "n_obs": hu.n_obs,
+        "K": hu.K, **speeds, "G": hu.G, "B": hu.B, "n_obs": hu.n_obs,
         "n_particles": hu.n_particles, "horizon": hu.horizon,
         "grid": f"{W}x{H}@{res:.3g}m", "dt": round(hu.dt, 6),
         "l2": "flushed before every timed step (256 MiB write)",
@@ -199,7 +209,7 @@ def oracle_sample(hu, n_particles, obs=None, threads=1):
     import concurrent.futures as cf
 
     import oracle
-    m = oracle.Model(hu.K, hu.speed, hu.dt, hu.goals, hu.beta)
+    m = oracle.Model(hu.K, hu.speed, hu.dt, hu.goals, hu.beta, speeds=hu.speeds, speed_off=hu.speed_off)
     if obs is None:
         obs = oracle.simulate(m, hu.true_j, hu.start, hu.n_obs, hu.obs_seed, hu.human_id).astype(np.float32)
     cuts = np.linspace(0, n_particles, threads + 1).astype(np.int64)
@@ -226,7 +236,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    hu = workloads.paper_scale()
+    hu = MAIN_WORKLOADS[args.workload][0]()
     per_step = []
     threads = host_threads()
     n = max(1000, args.cpu_sample // 4) * threads
@@ -240,7 +250,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (model-drawn observations, seeded)", "config": workload_config(hu),
+            "data": "synthetic (model-drawn observations, seeded)", "config": workload_config(hu, args.workload),
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": threads, "kind": "oracle",
                              "sample": f"{n} of {hu.n_particles} particles x T={hu.horizon} per step, "
                                        f"{threads} host threads over particle ranges"},
@@ -248,10 +258,10 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def load_profile_traffic(kernel_hash):
+def load_profile_traffic(kernel_hash, workload="paper_scale"):
     """DRAM bytes per launch of the rollout kernel from the committed ncu summary,
     if it was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "rollout_paper_scale.json")
+    p = os.path.join(ROOT, "profiles", f"rollout_{workload}.json")
     if not os.path.exists(p):
         return None
     try:
@@ -544,6 +554,35 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
                      "config": f"paper_scale room, K=32 x speeds {hu.speeds}, speed_off={hu.speed_off:#b}, "
                                "N=100k, T=150, 50 observed steps, 200x200 grid; L2 not flushed"}
 
+    # -- Table 1's configuration (1 human, n = 8192, |G| = 10, |B| = 5, |U| = 96,
+    #    50 x 50 grid) at T = 2..10: wall clock of one prediction, as the paper
+    #    times it (warm, mean of repeated runs; here event-timed on the stream)
+    t1 = {}
+    for T in (2, 4, 6, 8, 10):
+        hu = workloads.table1(horizon=T)
+        g, b = torch.tensor(hu.goals, device=dev), torch.tensor(hu.beta, device=dev)
+        model = pm.make_model(hu.K, hu.speed, hu.dt, g, b, speeds=hu.speeds)
+        obs = gpu_paths(pm, ctx, torch, dev, hu, hu.n_obs, hu.human_id)
+        z0 = obs[-1].cpu().numpy()
+        prior = torch.tensor(hu.uniform_log_prior(), device=dev)
+        lb = torch.empty_like(prior)
+        x0, y0, res, W, H = hu.grid
+        grid = pm.make_grid(x0, y0, res, W, H)
+        counts = torch.empty((T, H, W), dtype=torch.int32, device=dev)
+        oob = torch.empty(T, dtype=torch.int32, device=dev)
+
+        def t1_step():
+            lb.copy_(prior)
+            pm.pm_update_posterior(ctx, model, obs, hu.n_obs, lb, stream)
+            pm.pm_predict_occupancy(ctx, model, lb, float(z0[0]), float(z0[1]), hu.n_particles, T, grid,
+                                    hu.seed, hu.human_id, counts, oob, stream)
+        t1[f"T{T}"] = time_events(torch, stream, t1_step, 200)
+    out["table1"] = {"ms_per_prediction": t1,
+                     "paper_ms_rtx2080ti_gpu_jit": {"T2": 7.0, "T4": 7.0, "T6": 7.0, "T8": 7.0, "T10": 8.0},
+                     "config": "1 human, n=8192, |G|=10, |B|=5, |U|=96 (3 speeds x K=32), 50x50 grid at 0.1 m, "
+                               "dt=0.1, 20 observed steps; belief update + rollout + histogram per prediction; "
+                               "the paper's figures are another machine's (context only)"}
+
     # -- differentiation: 256 trajectories, adjoint of the marginal log-likelihood
     ts = workloads.differentiation()
     trajs = []
@@ -586,13 +625,15 @@ def run_native(args):
     ctx = pm.pm_create(local)
     stream = torch.cuda.Stream(device=dev)
 
-    hu = workloads.paper_scale()
+    make_hu, kernel_name = MAIN_WORKLOADS[args.workload]
+    hu = make_hu()
     human_id = rank_human_id(hu.human_id, rank)
     K, N, T = hu.K, hu.n_particles, hu.horizon
+    U = K * sum(1 for q in range(len(hu.speeds)) if not (hu.speed_off >> q) & 1)  # enabled controls
     x0, y0, res, W, H = hu.grid
     goals = torch.tensor(hu.goals, device=dev)
     beta = torch.tensor(hu.beta, device=dev)
-    model = pm.make_model(K, hu.speed, hu.dt, goals, beta)
+    model = pm.make_model(K, hu.speed, hu.dt, goals, beta, speeds=speeds_of(hu), speed_off=hu.speed_off)
     grid = pm.make_grid(x0, y0, res, W, H)
 
     # Observed history drawn from the model by the library itself: one traced
@@ -672,13 +713,14 @@ def run_native(args):
     value = job_throughput(world, N * T, ms_per_step * 1e-3)
 
     # roofline of the dominant kernel (the rollout): algorithmic SFU results
-    # per launch (K exp + K sqrt per particle-step) / its event-timed duration
+    # per launch (one exp + one sqrt per control and particle-step) / its
+    # event-timed duration
     roll_avg_s = statistics.mean(roll_ms) * 1e-3
-    sfu_ops = 2.0 * K * N * T
+    sfu_ops = 2.0 * U * N * T
     achieved = sfu_ops / roll_avg_s / 1e9
     peak = 2.0 / (1.0 / sfu["ex2"] + 1.0 / sfu["sqrt"]) / 1e9
     khash = sources_hash(ROLLOUT_SOURCES)
-    traffic = load_profile_traffic(khash)
+    traffic = load_profile_traffic(khash, args.workload)
 
     # e2e through the host-buffer entry point (pinned buffers)
     goals_h = torch.tensor(hu.goals).pin_memory()
@@ -709,17 +751,17 @@ def run_native(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded; observed history drawn from the model on the GPU)",
-            "config": workload_config(hu),
+            "config": workload_config(hu, args.workload),
             "gpu_launches": 2 * args.steps,
             "wall_s": wall,
             "breakdown_ms": {"posterior": statistics.mean(post_ms), "rollout": statistics.mean(roll_ms)},
-            "roofline": {"bound": "alu", "kernel": "rollout_warp_kernel<36,true>", "achieved": achieved,
+            "roofline": {"bound": "alu", "kernel": kernel_name, "achieved": achieved,
                          "peak": peak, "unit": "G SFU results/s", "frac": achieved / peak,
                          "traffic": traffic,
                          "peak_source": "measured by pm_probe_sfu (ex2/sqrt 1:1 harmonic mean); "
                                         f"ex2 {sfu['ex2'] / 1e9:.1f}, sqrt {sfu['sqrt'] / 1e9:.1f}, "
                                         f"rsqrt {sfu['rsqrt'] / 1e9:.1f} G/s",
-                         "algorithmic": "2K SFU results (K ex2 + K sqrt) per particle-step"},
+                         "algorithmic": f"2U SFU results (U = {U} controls: U ex2 + U sqrt) per particle-step"},
             "device": info,
             "clocks": clk.summary(),
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

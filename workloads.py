@@ -25,6 +25,10 @@ Workloads
 ``multi_speed``   ``paper_scale`` with |U| = 96 controls (Table 1): K = 32 headings
                   at speeds {0.5, 1, 1.5} x 1 m/s; the stationary variant masks
                   the two faster speeds (Sec. IV-B).
+``table1``        Table 1's running example as printed: 1 human, n = 8192
+                  particles, |G| = 10, |B| = 5, |U| = 96 (3 speeds x 32), a 50 x 50
+                  grid, T = 10; the unprinted values (dt = 0.1 s, 0.1 m cells, the
+                  beta values, 20 observed steps) are chosen here.
 """
 from __future__ import annotations
 
@@ -114,6 +118,20 @@ def multi_speed(seed: int = MASTER_SEED, stationary: bool = False) -> Human:
     hu = paper_scale(seed)
     return dataclasses.replace(hu, K=32, speeds=(0.5, 1.0, 1.5), speed_off=0b110 if stationary else 0,
                                human_id=3, obs_seed=seed + 31)
+
+
+def table1(seed: int = MASTER_SEED, horizon: int = 10) -> Human:
+    """Table 1's configuration: 10 goals uniform in a 5 m room, 5 log-spaced beta
+    0.1..10, |U| = 96 = 3 speeds {0.5, 1, 1.5} x K = 32 at v = 1 m/s, dt = 0.1,
+    n = 8192, T = ``horizon``, 50 x 50 grid at 0.1 m; 20 observed steps from a
+    start uniform in [1.5, 3.5]^2 with true (beta_2, goal 0)."""
+    rng = np.random.default_rng([seed, 6])
+    goals = rng.uniform(0.0, 5.0, size=(10, 2)).astype(np.float32)
+    start = rng.uniform(1.5, 3.5, size=2).astype(np.float32)
+    return Human(K=32, speed=1.0, dt=f32(0.1), goals=goals, beta=beta_grid(-1.0, 1.0, 5), true_j=0 * 5 + 2,
+                 start=start, n_obs=20, n_particles=8192, horizon=horizon,
+                 grid=(0.0, 0.0, f32(0.1), 50, 50), seed=seed, human_id=4, obs_seed=seed + 41,
+                 speeds=(0.5, 1.0, 1.5))
 
 
 def batched(seed: int = MASTER_SEED, n_humans: int = 16) -> List[Human]:
