@@ -116,6 +116,16 @@ const char *pm_last_error(void);
 /* Library version string. */
 const char *pm_version(void);
 
+/* Wait for the work queued on `stream` (NULL: the legacy default stream) and
+ * report the errors that kernels of this context latched in its device status
+ * word since the last call, then clear the word. Kernels latch, and carry on
+ * past, inputs they cannot use: a non-finite goal or beta (the results of that
+ * human are meaningless), a log-belief that is NaN, +inf or -inf everywhere, an
+ * observed state or a trajectory point that is not finite (its steps are
+ * skipped). Returns PM_OK, PM_EDEVICE with pm_last_error() naming what was
+ * latched, or PM_ECUDA. Synchronous. */
+pm_status pm_sync_status(pm_ctx *ctx, void *stream);
+
 /* ---- the hot path -------------------------------------------------------- */
 
 /* Bayesian update of the joint belief (Eq. 3), in log space (Eq. 7), over

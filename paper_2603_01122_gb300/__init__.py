@@ -72,6 +72,7 @@ def _signatures(lib):
         "pm_destroy": ([_vp], None),
         "pm_last_error": ([], C.c_char_p),
         "pm_version": ([], C.c_char_p),
+        "pm_sync_status": ([_vp, _vp], C.c_int),
         "pm_update_posterior": ([_vp, P(pm_model), _vp, C.c_int32, _vp, _vp], C.c_int),
         "pm_predict_occupancy": ([_vp, P(pm_model), _vp, C.c_float, C.c_float, C.c_int32, C.c_int32,
                                   P(pm_grid), C.c_uint64, C.c_uint32, _vp, _vp, _vp], C.c_int),
@@ -159,6 +160,12 @@ def pm_version() -> str:
 
 def pm_last_error() -> str:
     return library().pm_last_error().decode()
+
+
+def pm_sync_status(ctx, stream=None):
+    """Wait for ``stream`` and raise PmError(PM_EDEVICE) if kernels of ``ctx``
+    latched unusable inputs since the last call (the word is then cleared)."""
+    _check(library().pm_sync_status(ctx, _stream(stream)))
 
 
 def pm_create(device: int = 0) -> int:

@@ -221,6 +221,10 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(const __grid_const
             const float zx = z[0], zy = z[1];
             const float dx = z[2] - zx, dy = z[3] - zy;
             const float len = sqrtf(fmaf(dx, dx, dy * dy));
+            if (!isfinite(len)) { // unusable point: its steps are skipped and reported
+                flag_status(a.status, kStatusTraj);
+                continue;
+            }
             if (!(len >= 1e-6f)) continue; // stationary step: no information
             const StepGrad s = MS ? step_terms_ms(a, cu, U, zx, zy, dx / len, dy / len, len, gx, gy, beta, grad)
                                   : step_terms<KT>(a, zx, zy, dx / len, dy / len, gx, gy, beta, grad);
@@ -255,7 +259,11 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(const __grid_const
     double *part = a.part + (size_t)m * P;
     if (warp == 0) {
         double mx = -INFINITY;
-        for (int j = lane; j < J; j += 32) mx = fmax(mx, (double)a.log_prior[j] + A_s[j]);
+        for (int j = lane; j < J; j += 32) {
+            const float lp = a.log_prior[j];
+            if (isnan(lp) || lp == INFINITY) flag_status(a.status, kStatusBelief);
+            mx = fmax(mx, (double)lp + A_s[j]);
+        }
         mx = wmax_d(mx);
         float se = 0.0f;
         for (int j = lane; j < J; j += 32) {

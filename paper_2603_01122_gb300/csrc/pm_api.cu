@@ -281,6 +281,9 @@ pm_status ensure_stage(pm_ctx *ctx, size_t bytes)
     return PM_OK;
 }
 
+// Word 3 of the context's counter block is its device status word.
+unsigned *status_word(pm_ctx *ctx) { return ctx->ticket ? ctx->ticket + 3 : nullptr; }
+
 pm_status ensure_posterior_scratch(pm_ctx *ctx, size_t bytes)
 {
     if (!ctx->ticket) {
@@ -343,6 +346,7 @@ pm_status predict_impl(pm_ctx *ctx, const pm_model *model, const float *log_beli
     a.tr_states = states;
     a.tr_head = headings;
     a.tr_comp = components;
+    a.status = status_word(ctx);
     if (hist) {
         a.gx0 = grid->x0;
         a.gy0 = grid->y0;
@@ -391,6 +395,7 @@ pm_status posterior_impl(pm_ctx *ctx, const pm_model *model, const float *obs_xy
     if (st != PM_OK) return st;
     a.part = (float *)ctx->post_scratch;
     a.ticket = ctx->ticket;
+    a.status = status_word(ctx);
     cudaError_t e = pm::launch_posterior(a, n_chunks, stream);
     if (e != cudaSuccess) return cuda_fail(e, "posterior launch");
     return PM_OK;
@@ -454,6 +459,7 @@ pm_status loglik_impl(pm_ctx *ctx, const pm_model *model, int32_t M, const int32
     a.grad_out = grad_out;
     a.part = (double *)ctx->adj_scratch;
     a.ticket = ctx->ticket + 1; // its own word of the ticket block
+    a.status = status_word(ctx);
     a.loglik = loglik;
     a.d_goals = d_goals;
     a.d_speed = d_speed;
@@ -658,6 +664,7 @@ pm_status batch_predict_impl(pm_batch *b, cudaStream_t stream)
     a.n_items = b->d_meta;
     a.head = b->d_head;
     a.win_radius_cap = batch_radius_cap(b->window_kib, b->threads);
+    a.status = status_word(ctx);
     const size_t dyn = batch_dyn_smem(b);
     int occ = b->occ;
     if (occ < 1)
@@ -726,6 +733,14 @@ pm_status pm_create(pm_ctx **out, int device)
     c->clock_khz = clk;
     c->cc = p.major * 10 + p.minor;
     c->smem_optin = p.sharedMemPerBlockOptin;
+    {
+        DeviceScope dev(device);
+        pm_status st = ensure_posterior_scratch(c, 0); // the counter words and the status word
+        if (st != PM_OK) {
+            delete c;
+            return st;
+        }
+    }
     *out = c;
     return PM_OK;
 }
@@ -746,6 +761,26 @@ void pm_destroy(pm_ctx *ctx)
 const char *pm_last_error(void) { return g_err.c_str(); }
 
 const char *pm_version(void) { return "pm 0.1.0 (sm_103a)"; }
+
+pm_status pm_sync_status(pm_ctx *ctx, void *stream)
+{
+    if (!ctx) return fail(PM_EINVAL, "ctx is NULL");
+    DeviceScope dev(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    unsigned word = 0u;
+    e = cudaMemcpy(&word, status_word(ctx), sizeof word, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && word) e = cudaMemset(status_word(ctx), 0, sizeof word);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the status word");
+    if (!word) return PM_OK;
+    std::string what;
+    if (word & pm::kStatusModel) what += " non-finite goal or beta;";
+    if (word & pm::kStatusBelief) what += " log-belief NaN, +inf or all -inf;";
+    if (word & pm::kStatusObs) what += " non-finite observed state (its steps were skipped);";
+    if (word & pm::kStatusTraj) what += " non-finite trajectory point (its steps were skipped);";
+    return fail(PM_EDEVICE, "kernels reported (status 0x%x):%s", word, what.c_str());
+}
 
 pm_status pm_update_posterior(pm_ctx *ctx, const pm_model *model, const float *obs_xy, int32_t n_obs,
                               float *log_belief, void *stream)
@@ -904,6 +939,7 @@ pm_status pm_batch_update_posterior(pm_batch *b, void *stream)
     DeviceScope dev(b->ctx->device);
     pm::PosteriorArgs a;
     fill_posterior_args(&b->shared, a); // goals/beta per human
+    a.status = status_word(b->ctx);
     cudaError_t e = pm::launch_posterior_batch(a, b->d_post, b->d_meta + 1, b->max_humans, b->max_chunks, b->max_J,
                                                (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "batched posterior launch");

@@ -50,8 +50,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_rollout_kernel(cons
                 const int g = j / h->B, b = j - g * h->B;
                 const float cbj = h->beta[b] * a.w2_log2e;
                 sh.comp[j] = make_float4(cbj, h->goals[2 * g], h->goals[2 * g + 1], lb_flag(a.tab, cbj));
+                if (bad_component(cbj, sh.comp[j].y, sh.comp[j].z)) flag_status(a.status, kStatusModel);
             }
-            if (tid < 32) belief_cdf(h->log_b, J, sh.cdf, tid);
+            if (tid < 32 && belief_cdf(h->log_b, J, sh.cdf, tid) && tid == 0) flag_status(a.status, kStatusBelief);
             cur = item.x;
         }
         if (tid == 0) {
@@ -162,13 +163,18 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_warp_kernel(const _
         const int J = min(h->G * h->B, kMaxJ); // the host rejects larger models
         if (item.x != cur) {
             __syncwarp();
+            bool bad = false;
             for (int j = lane; j < J; j += 32) {
                 const int g = j / h->B, b = j - g * h->B;
                 const float cbj = h->beta[b] * a.w2_log2e;
-                comp[j] = make_float4(cbj, h->goals[2 * g], h->goals[2 * g + 1], lb_flag(a.tab, cbj));
+                const float gx = h->goals[2 * g], gy = h->goals[2 * g + 1];
+                comp[j] = make_float4(cbj, gx, gy, lb_flag(a.tab, cbj));
+                bad = bad || bad_component(cbj, gx, gy);
                 if constexpr (MS) cw1[j] = h->beta[b] * a.w1_vdt_log2e;
             }
-            belief_cdf(h->log_b, J, cdf, lane);
+            // one latch per warp and human for unusable inputs
+            const unsigned bits = belief_cdf(h->log_b, J, cdf, lane) | (__any_sync(0xffffffffu, bad) ? kStatusModel : 0u);
+            if (lane == 0 && bits) flag_status(a.status, bits);
             __syncwarp();
             cur = item.x;
         }

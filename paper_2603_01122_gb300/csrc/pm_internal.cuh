@@ -138,6 +138,19 @@ struct HeadingTab {
     float msy[PM_MAX_SPEEDS][kMaxK];
 };
 
+// Device status word of a context: kernels OR these bits into it when they
+// meet inputs they cannot use (the affected work is skipped or its result is
+// meaningless); pm_sync_status reports and clears them.
+constexpr unsigned kStatusModel = 1u;  // a goal or beta value is not finite
+constexpr unsigned kStatusBelief = 2u; // a log-belief is NaN or +inf, or every one is -inf
+constexpr unsigned kStatusObs = 4u;    // an observed state is not finite (its steps are skipped)
+constexpr unsigned kStatusTraj = 8u;   // a trajectory point is not finite (its steps are skipped)
+
+__device__ __forceinline__ void flag_status(unsigned *status, unsigned bit)
+{
+    if (status) atomicOr(status, bit);
+}
+
 // Arguments of the rollout kernel (Algorithm 1 + emplacement).
 struct RolloutArgs {
     HeadingTab tab;
@@ -163,9 +176,9 @@ struct RolloutArgs {
     float *tr_states;
     uint8_t *tr_head;
     int32_t *tr_comp;
+    unsigned *status; // context status word (or NULL)
 };
 
-// Arguments of the belief-update kernel (Eq. 3 / Eq. 7).
 // The control set of several speeds as the belief update and the adjoint see
 // it (S = 0: one speed, multiplier 1).
 struct SpeedSet {
@@ -176,6 +189,7 @@ struct SpeedSet {
     float w1;
 };
 
+// Arguments of the belief-update kernel (Eq. 3 / Eq. 7).
 struct PosteriorArgs {
     float ux[kMaxK], uy[kMaxK]; // unit heading vectors
     uint64_t enabled;
@@ -190,6 +204,7 @@ struct PosteriorArgs {
     float *log_b;
     float *part;         // scratch: per (chunk, component) accumulators
     unsigned *ticket;    // scratch: chunks finished so far (0 between calls)
+    unsigned *status;    // context status word (or NULL)
 };
 
 // Arguments of the log-likelihood / adjoint kernel.
@@ -210,6 +225,7 @@ struct AdjointArgs {
     float grad_out;
     double *part;          // scratch [M][2G+4]
     unsigned *ticket;      // scratch ticket (0 between calls)
+    unsigned *status;      // context status word (or NULL)
     float *loglik;
     float *d_goals;
     float *d_speed;
@@ -297,6 +313,7 @@ struct BatchArgs {
     const int *n_items;
     unsigned *head;      // next tile (zeroed before every launch)
     int win_radius_cap;  // (2r+1)^2 cells fit the dynamic shared memory
+    unsigned *status;    // context status word (or NULL)
 };
 
 // Launch shape of the rollout: threads per CTA, particles per thread (1 or

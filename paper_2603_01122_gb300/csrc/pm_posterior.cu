@@ -208,6 +208,10 @@ __device__ __forceinline__ void posterior_chunk(const PosteriorArgs &a, const Po
             const float zx = h.obs[2 * t], zy = h.obs[2 * t + 1];
             const float dx = h.obs[2 * t + 2] - zx, dy = h.obs[2 * t + 3] - zy;
             const float len = sqrtf(fmaf(dx, dx, dy * dy));
+            if (!isfinite(len)) { // unusable observation: skipped and reported
+                if (lane == 0) flag_status(a.status, kStatusObs);
+                continue;
+            }
             if (!(len >= 1e-6f)) continue; // stationary: the belief is unchanged
             const float ex = dx / len, ey = dy / len;
             const float px = zx - gx, py = zy - gy;
@@ -270,6 +274,7 @@ __device__ __forceinline__ void posterior_chunk(const PosteriorArgs &a, const Po
         }
         if (lane == 0) {
             const float lb = h.log_b[j];
+            if (isnan(lb) || lb == INFINITY) flag_status(a.status, kStatusBelief);
             if (lb == -INFINITY) {
                 L[j] = make_float2(-INFINITY, 0.0f);
             } else {

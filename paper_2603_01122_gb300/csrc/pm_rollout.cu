@@ -49,9 +49,10 @@ __global__ void __launch_bounds__(kWarpCtaThreads, kWarpCtaMinBlocks)
         const int g = j / a.B, b = j - g * a.B;
         const float cbj = a.beta[b] * a.w2_log2e;
         comp[j] = make_float4(cbj, a.goals[2 * g], a.goals[2 * g + 1], lb_flag(a.tab, cbj));
+        if (bad_component(cbj, comp[j].y, comp[j].z)) flag_status(a.status, kStatusModel);
     }
     for (int k = tid; k < KT; k += blockDim.x) step[k] = make_float2(a.tab.sx[k], a.tab.sy[k]);
-    if (tid < 32) belief_cdf(a.log_b, J, cdf, tid);
+    if (tid < 32 && belief_cdf(a.log_b, J, cdf, tid) && tid == 0) flag_status(a.status, kStatusBelief);
     __syncthreads();
 
     TileCtx c;
@@ -104,11 +105,12 @@ __global__ void __launch_bounds__(kWarpCtaThreads, kWarpCtaMinBlocks)
         const int g = j / a.B, b = j - g * a.B;
         const float cbj = a.beta[b] * a.w2_log2e;
         comp[j] = make_float4(cbj, a.goals[2 * g], a.goals[2 * g + 1], lb_flag(a.tab, cbj));
+        if (bad_component(cbj, comp[j].y, comp[j].z)) flag_status(a.status, kStatusModel);
         cw1[j] = a.beta[b] * a.w1_vdt_log2e;
     }
     for (int u = tid; u < a.tab.S * a.K; u += blockDim.x)
         step[u] = make_float2(a.tab.msx[u / a.K][u % a.K], a.tab.msy[u / a.K][u % a.K]);
-    if (tid < 32) belief_cdf(a.log_b, J, cdf, tid);
+    if (tid < 32 && belief_cdf(a.log_b, J, cdf, tid) && tid == 0) flag_status(a.status, kStatusBelief);
     __syncthreads();
 
     TileCtx c;

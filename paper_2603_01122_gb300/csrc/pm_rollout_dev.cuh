@@ -17,18 +17,23 @@ struct __align__(16) RolloutShared {
 // Warp 0 turns the log-belief into a fixed-point cumulative table:
 // e_j = exp(log b_j - max) (accurate expf), E_j = round(e_j * 2^22),
 // cdf[j] = E_0 + ... + E_j. Lane L owns the contiguous block j = 8L..8L+7.
-__device__ inline void belief_cdf(const float *log_b, int J, uint32_t *cdf, int lane)
+// Returns kStatusBelief (the same on every lane) for a NaN or +inf entry or a
+// belief with no finite entry, else 0; the caller latches it.
+__device__ inline unsigned belief_cdf(const float *log_b, int J, uint32_t *cdf, int lane)
 {
     float lb[8];
     float m = -INFINITY;
+    bool bad = false;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int j = lane * 8 + q;
         lb[q] = (j < J) ? log_b[j] : -INFINITY;
+        bad = bad || isnan(lb[q]) || lb[q] == INFINITY;
         m = fmaxf(m, lb[q]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const unsigned bits = (__any_sync(0xffffffffu, bad) || m == -INFINITY) ? kStatusBelief : 0u;
     uint32_t run = 0, pre[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -48,6 +53,7 @@ __device__ inline void belief_cdf(const float *log_b, int J, uint32_t *cdf, int 
         const int j = lane * 8 + q;
         if (j < J) cdf[j] = pre[q] + excl;
     }
+    return bits;
 }
 
 // One heading draw of Eq. 2 at state (x, y) for goal (gx, gy) and
@@ -308,6 +314,9 @@ __device__ __forceinline__ float lb_flag(const HeadingTab &tab, float cb)
 {
     return (fabsf(cb) * tab.lb_gap <= 1.0f) ? 1.0f : 0.0f;
 }
+
+// A component's table entry must be finite (goal and beta w2 log2(e)).
+__device__ __forceinline__ bool bad_component(float cb, float gx, float gy) { return !isfinite(cb + gx + gy); }
 
 // The heading draw of one particle: the fused bound form where it applies.
 template <int KT, bool FULL>
