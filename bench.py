@@ -388,8 +388,22 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
 
     def do_union():
         pm.pm_batch_union(batch, 1.5, T_max, ugrid, union, stream)
+    dense_ms = time_events(torch, stream, do_union, 10)  # no block marks: every region is read
+    # with block marks: the rollout marks occupied 16 x 16 blocks, the union reads only those
+    pm.pm_batch_set_block_flags(batch, 1, stream)
+    marked_batch_ms = time_events(torch, stream, graph.replay, 10)
     union_ms = time_events(torch, stream, do_union, 10)
-    union_bytes = sum(r["h"].horizon for r in recs) * H * W * 4 + T_max * H * W * 4
+    pm.pm_batch_set_block_flags(batch, 0, stream)
+    torch.cuda.synchronize()
+    dense_bytes = sum(r["h"].horizon for r in recs) * H * W * 4 + T_max * H * W * 4
+    # algorithmic bytes: the occupied blocks' counts (what any union must read) + the output
+    occ_blocks = 0
+    for r in recs:
+        c = r["counts"]
+        Tb, Hc, Wc = c.shape
+        cc = torch.nn.functional.pad(c, (0, (-Wc) % 16, 0, (-Hc) % 16))
+        occ_blocks += int((cc.reshape(Tb, cc.shape[1] // 16, 16, cc.shape[2] // 16, 16).amax(dim=(2, 4)) > 0).sum())
+    union_bytes = occ_blocks * 16 * 16 * 4 + T_max * H * W * 4
     pm.pm_batch_destroy(batch)
     out["batched"] = {"humans": len(recs), "particle_steps": steps,
                       "batched_ms": batch_ms, "batched_particle_steps_per_s": steps / (batch_ms * 1e-3),
@@ -399,10 +413,14 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
                       "rate_vs_plain_small": steps / (batch_ms * 1e-3) / out["plain_small"]["particle_steps_per_s"],
                       "sfu_roofline_frac": steps / (batch_ms * 1e-3) * 2 * 36 / sfu_peak,
                       "union": {"ms": union_ms, "sigma_cells": 1.5, "bytes": union_bytes,
+                                "bytes_definition": "counts of the occupied 16x16 blocks + the union written",
                                 "GB_per_s": union_bytes / (union_ms * 1e-3) / 1e9,
                                 "hbm_frac": union_bytes / (union_ms * 1e-3) / 1e9 / HBM_PEAK_GBS,
+                                "dense_ms": dense_ms, "dense_bytes": dense_bytes,
+                                "dense_GB_per_s": dense_bytes / (dense_ms * 1e-3) / 1e9,
+                                "batched_ms_with_marks": marked_batch_ms,
                                 "config": f"16 humans' counts [T_h][400][400] -> union [{T_max}][400][400], "
-                                          "blur R = 5"},
+                                          "blur R = 5; block marks written by the rollout (dense: none)"},
                       "config": "16 humans, G~U{2..6}, N~U[20k,200k], T~U{50..300}, K=36, 400x400 grid, "
                                 "graph of belief update + persistent rollout"}
     del recs

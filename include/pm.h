@@ -368,8 +368,21 @@ pm_status pm_smooth_occupancy(pm_ctx *ctx, const uint32_t *counts, int32_t n_par
  * grid must have the same origin and resolution. prob: device float
  * [horizon][grid->H][grid->W], written entirely. Reads the batch's device
  * descriptors, so it may be captured in the same CUDA graph as
- * pm_batch_predict (after it on the stream). PM_EINVAL for mismatched grids,
- * bad sizes or sigma. */
+ * pm_batch_predict (after it on the stream). With block flags on
+ * (pm_batch_set_block_flags) it reads only the 16 x 16-cell blocks that
+ * pm_batch_predict marked as holding a particle. PM_EINVAL for mismatched
+ * grids, bad sizes or sigma. */
+/* enable = 1: pm_batch_predict also marks, per human and step, the 16 x 16-cell
+ * blocks of the output it emplaces into (a byte per block, in batch-owned
+ * device memory; a few per cent of the rollout's time), so that
+ * pm_batch_union skips the empty ones; 0 (the default): no marks, and
+ * pm_batch_union reads every region. The warp-combined emplacement writes the
+ * marks; with the shared-memory window form (pm_batch_set_config) the union
+ * reads every region. Re-uploads the descriptors on `stream` like
+ * pm_batch_set; a captured graph stays valid. PM_EINVAL for another value,
+ * PM_ENOMEM if the marks cannot be allocated. */
+pm_status pm_batch_set_block_flags(pm_batch *b, int32_t enable, void *stream);
+
 pm_status pm_batch_union(pm_batch *b, float sigma_cells, int32_t horizon, const pm_grid *grid, float *prob,
                          void *stream);
 

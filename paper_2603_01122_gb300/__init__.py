@@ -73,6 +73,7 @@ def _signatures(lib):
         "pm_last_error": ([], C.c_char_p),
         "pm_version": ([], C.c_char_p),
         "pm_sync_status": ([_vp, _vp], C.c_int),
+        "pm_batch_set_block_flags": ([_vp, C.c_int32, _vp], C.c_int),
         "pm_update_posterior": ([_vp, P(pm_model), _vp, C.c_int32, _vp, _vp], C.c_int),
         "pm_predict_occupancy": ([_vp, P(pm_model), _vp, C.c_float, C.c_float, C.c_int32, C.c_int32,
                                   P(pm_grid), C.c_uint64, C.c_uint32, _vp, _vp, _vp], C.c_int),
@@ -271,6 +272,10 @@ def pm_mppi_solve(ctx, params: pm_mppi, z0, u_ref, delta, prob, prob_T, grid, co
     _check(library().pm_mppi_solve(ctx, C.byref(params), z, _p(u_ref), _p(delta), _p(prob), int(prob_T),
                                    C.byref(grid) if grid is not None else None, _p(cost_to_go), _p(u_opt),
                                    _stream(stream)))
+
+
+def pm_batch_set_block_flags(batch, enable, stream=None):
+    _check(library().pm_batch_set_block_flags(batch, int(enable), _stream(stream)))
 
 
 def pm_batch_autotune(batch, stream=None):

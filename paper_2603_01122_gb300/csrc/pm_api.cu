@@ -48,6 +48,9 @@ struct pm_batch {
     float *d_post_part = nullptr;
     unsigned *d_post_ticket = nullptr;
     pm::SmoothSrc *d_srcs = nullptr; // union source records, one per human
+    uint8_t *d_flags = nullptr;      // block occupancy flags of every human's histogram
+    size_t flags_cap = 0;
+    bool block_flags = false;        // pm_batch_predict marks occupied blocks
     size_t post_stride = 0; // floats of posterior scratch per human
     // page-locked staging of the uploads
     char *h_stage = nullptr;
@@ -548,6 +551,27 @@ pm_status batch_upload(pm_batch *b, cudaStream_t stream)
     std::vector<pm::BatchHuman> hd(n);
     std::vector<pm::PostHuman> ph(n);
     int max_chunks = 0, max_J = 1;
+    // block occupancy flags (written by the warp-combined emplacement only)
+    std::vector<size_t> foff(n + 1, 0);
+    for (int h = 0; h < n; ++h) {
+        const pm_human &u = b->humans[h];
+        const size_t fbx = ((size_t)u.grid.W + pm::kFlagBlock - 1) >> pm::kFlagShift;
+        const size_t fby = ((size_t)u.grid.H + pm::kFlagBlock - 1) >> pm::kFlagShift;
+        foff[h + 1] = foff[h] + (((size_t)u.horizon * fbx * fby + 15) & ~(size_t)15);
+    }
+    const bool marks = b->block_flags && b->warp_hist;
+    if (marks && foff[n] > b->flags_cap) {
+        if (b->d_flags) cudaFree(b->d_flags);
+        b->d_flags = nullptr;
+        b->flags_cap = 0;
+        cudaError_t ef = cudaMalloc(&b->d_flags, foff[n]);
+        if (ef == cudaSuccess) ef = cudaMemset(b->d_flags, 0, foff[n]);
+        if (ef != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PM_ENOMEM, "cudaMalloc(%zu) for block flags failed", foff[n]);
+        }
+        b->flags_cap = foff[n];
+    }
     for (int h = 0; h < n; ++h) {
         const pm_human &u = b->humans[h];
         pm::BatchHuman &d = hd[h];
@@ -573,6 +597,9 @@ pm_status batch_upload(pm_batch *b, cudaStream_t stream)
         d.counts = u.counts;
         d.oob = u.oob;
         d.speed_on = human_speed_on(b->shared, u);
+        d.fbx = (u.grid.W + pm::kFlagBlock - 1) >> pm::kFlagShift;
+        d.fby = (u.grid.H + pm::kFlagBlock - 1) >> pm::kFlagShift;
+        d.flags = (marks && b->d_flags) ? b->d_flags + foff[h] : nullptr;
         pm::PostHuman &q = ph[h];
         q.goals = u.goals;
         q.beta = u.beta;
@@ -912,6 +939,7 @@ void pm_batch_destroy(pm_batch *b)
     cudaFree(b->d_items);
     cudaFree(b->d_meta);
     cudaFree(b->d_srcs);
+    cudaFree(b->d_flags);
     cudaFree(b->d_head);
     cudaFree(b->d_post_part);
     cudaFree(b->d_post_ticket);
@@ -1069,6 +1097,15 @@ pm_status pm_batch_set_config(pm_batch *b, int32_t threads, int32_t shared_windo
     b->occ = pm::batch_rollout_occupancy(b->shared.K, t.enabled, t.tab.S, batch_shape_of(b), batch_dyn_smem(b));
     cudaGetLastError();
     return PM_OK;
+}
+
+pm_status pm_batch_set_block_flags(pm_batch *b, int32_t enable, void *stream)
+{
+    if (!b) return fail(PM_EINVAL, "batch is NULL");
+    if (enable != 0 && enable != 1) return fail(PM_EINVAL, "enable must be 0 or 1");
+    DeviceScope dev(b->ctx->device);
+    b->block_flags = enable != 0;
+    return b->humans.empty() ? PM_OK : batch_upload(b, (cudaStream_t)stream);
 }
 
 pm_status pm_batch_autotune(pm_batch *b, void *stream)

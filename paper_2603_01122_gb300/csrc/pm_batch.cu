@@ -115,6 +115,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_rollout_kernel(cons
         c.tr_states = nullptr;
         c.tr_head = nullptr;
         c.tr_comp = nullptr;
+        c.flags = nullptr; // the window form writes no block flags
+        c.fbx = c.fplane = 0;
         rollout_tile<KT, FULL, 1, false>(a.tab, a.enabled, a.s2, c, sh, dyn);
     }
 }
@@ -209,14 +211,18 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_warp_kernel(const _
         c.tr_states = nullptr;
         c.tr_head = nullptr;
         c.tr_comp = nullptr;
+        c.flags = h->flags;
+        c.fbx = h->fbx;
+        c.fplane = h->fbx * h->fby;
         if constexpr (MS)
             rollout_lane<KT, false, true>(a.tab, a.enabled, a.s2, c, comp, cdf, step, cw1, a.K, h->speed_on);
         else rollout_lane<KT, FULL>(a.tab, a.enabled, a.s2, c, comp, cdf, step);
     }
 }
 
-// Zero every human's counts [T][H][W] and oob [T]: blockIdx.y strides over
-// humans, the x dimension over 16-byte words (scalar head and tail).
+// Zero every human's counts [T][H][W], oob [T] and block flags: blockIdx.y
+// strides over humans, the x dimension over 16-byte words of the counts
+// (scalar head and tail).
 __global__ void batch_zero_kernel(const BatchHuman *humans, const int *n_dev)
 {
     const int n = *n_dev;
@@ -235,6 +241,10 @@ __global__ void batch_zero_kernel(const BatchHuman *humans, const int *n_dev)
         if (t0 < lead) p[t0] = 0u;
         if (t0 < words - tail0) p[tail0 + t0] = 0u;
         for (size_t q = t0; q < (size_t)h.T; q += stride) h.oob[q] = 0u;
+        if (h.flags) {
+            const size_t nf = (size_t)h.T * h.fbx * h.fby;
+            for (size_t q = t0; q < nf; q += stride) h.flags[q] = 0u;
+        }
     }
 }
 

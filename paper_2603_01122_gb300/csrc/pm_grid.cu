@@ -17,7 +17,12 @@
 // sliding a register window over four outputs, blurs along y the same way,
 // and folds the result into the running maximum; the tile is written once.
 // The work streams over the count planes: HBM-bound when the windows cover
-// the grid, shared-memory-bound for small windows.
+// the grid, shared-memory-bound for small windows. A region with no particle
+// adds nothing (the blur of zeros is zero and the running maximum is >= 0):
+// the batched rollout marks the 16 x 16-cell blocks it emplaces into, the
+// union reads every source's marks for its tile in one pass and stages only
+// the sources with a particle nearby, and a staged region that turns out
+// empty skips both blur passes. The HBM traffic follows the occupied blocks.
 #include <utility>
 
 #include <cuda_runtime.h>
@@ -43,6 +48,9 @@ __global__ void union_sources_kernel(const BatchHuman *humans, const int *n_huma
     s.T = h.T;
     s.W = h.W;
     s.H = h.H;
+    s.flags = h.flags;
+    s.fbx = h.fbx;
+    s.fby = h.fby;
     if (h.center) {
         s.ox = __float2int_rd(__fmul_rn(__fsub_rn(h.z0[0], h.gx0), h.inv_res)) - (h.W - 1) / 2;
         s.oy = __float2int_rd(__fmul_rn(__fsub_rn(h.z0[1], h.gy0), h.inv_res)) - (h.H - 1) / 2;
@@ -54,9 +62,13 @@ __global__ void union_sources_kernel(const BatchHuman *humans, const int *n_huma
 }
 
 // RB: the blur radius R as a compile-time constant, so that the sliding
-// windows of both passes live in registers and every tap is one FMA.
+// windows of both passes live in registers and every tap is one FMA. Up to
+// R = 8 the kernel fits 80 registers without spills and runs 3 CTAs per SM
+// (measured 24 % faster on the batched union at R = 5 than 2 CTAs at 124
+// registers); larger R keeps 2 CTAs (128 registers, no spills).
 template <int RB>
-__global__ void __launch_bounds__(kGridThreads) smooth_union_kernel(const __grid_constant__ SmoothArgs a)
+__global__ void __launch_bounds__(kGridThreads, (RB >= 1 && RB <= 8) ? 3 : 2)
+    smooth_union_kernel(const __grid_constant__ SmoothArgs a)
 {
     constexpr int AW = kTileX + 2 * RB, AH = kTileY + 2 * RB;
     constexpr int NW = 2 * RB + 4; // window of four outputs
@@ -67,6 +79,9 @@ __global__ void __launch_bounds__(kGridThreads) smooth_union_kernel(const __grid
     __shared__ __align__(16) float A[AH][AS];
     __shared__ __align__(16) float Bx[AH][kTileX];
     __shared__ SmoothSrc S[kSrcChunk];
+    __shared__ unsigned live[kSrcChunk / 32]; // bit si: source si may put mass on this tile at step t
+    // flag blocks that can meet the widened tile, per source
+    constexpr int BX = (AW + kFlagBlock - 1) / kFlagBlock + 1, BY = (AH + kFlagBlock - 1) / kFlagBlock + 1;
     const int tid = threadIdx.x;
     const int X0 = blockIdx.x * kTileX, Y0 = blockIdx.y * kTileY, t = blockIdx.z;
     // horizontal pass: thread -> (row hy0 + 16 j, columns 4 hx .. 4 hx + 3)
@@ -87,18 +102,38 @@ __global__ void __launch_bounds__(kGridThreads) smooth_union_kernel(const __grid
         const int nc = min(kSrcChunk, n - c0);
         __syncthreads(); // the previous chunk's records are no longer read
         if (tid < nc) S[tid] = a.srcs ? a.srcs[c0 + tid] : a.single;
+        if (tid < kSrcChunk / 32) live[tid] = 0u;
+        __syncthreads();
+        // Which sources reach the tile: the widened window must meet it, and
+        // where the source carries block flags one of the blocks under the
+        // widened tile must hold a particle at step t. All sources' flags are
+        // read in one pass, so a tile costs one round trip, not one per source.
+        for (int p = tid; p < nc * BX * BY; p += kGridThreads) {
+            const int si = p / (BX * BY), b = p - si * (BX * BY);
+            const SmoothSrc &q = S[si];
+            const int wx0 = X0 - RB - q.ox, wy0 = Y0 - RB - q.oy;
+            const int xlo = max(wx0, 0), xhi = min(wx0 + AW, q.W), ylo = max(wy0, 0), yhi = min(wy0 + AH, q.H);
+            if (t >= q.T || xlo >= xhi || ylo >= yhi) continue;
+            bool hit;
+            if (!q.flags) {
+                hit = b == 0;
+            } else {
+                const int bx = (xlo >> kFlagShift) + b % BX, by = (ylo >> kFlagShift) + b / BX;
+                hit = bx <= ((xhi - 1) >> kFlagShift) && by <= ((yhi - 1) >> kFlagShift) &&
+                      q.flags[((size_t)t * q.fby + by) * q.fbx + bx] != 0u;
+            }
+            if (hit) atomicOr(&live[si >> 5], 1u << (si & 31));
+        }
         __syncthreads();
         for (int si = 0; si < nc; ++si) {
+            if (!((live[si >> 5] >> (si & 31)) & 1u)) continue; // block-uniform
             const SmoothSrc s = S[si];
-            // the source reaches this tile only if its widened window meets it
-            if (t >= s.T || s.ox - RB >= X0 + kTileX || s.ox + s.W + RB <= X0 || s.oy - RB >= Y0 + kTileY ||
-                s.oy + s.H + RB <= Y0)
-                continue;
             const uint32_t *plane = s.counts + (size_t)t * s.W * s.H;
             const int wx0 = X0 - RB - s.ox, wy0 = Y0 - RB - s.oy; // window cell of A[0][0]
             // counts stay raw (exact in FP32 below 2^23, converted on the FP32
             // pipe); the 1/N scale is applied once per output at the end
             const bool inside = wx0 >= 0 && wx0 + AW <= s.W && wy0 >= 0 && wy0 + AH <= s.H;
+            uint32_t nz = 0u; // OR of the staged counts: an all-zero region adds nothing to the maximum
             if (inside && s.small) {
                 // whole region inside the window: all loads first, then the stores
                 uint32_t c[kStageIters];
@@ -112,6 +147,7 @@ __global__ void __launch_bounds__(kGridThreads) smooth_union_kernel(const __grid
                 for (int i = 0; i < kStageIters; ++i) {
                     const int e = tid + i * kGridThreads;
                     const int ry = e / AW, rx = e - ry * AW;
+                    nz |= c[i];
                     if (e < AW * AH) A[ry][rx] = __int_as_float((int)(c[i] | 0x4B000000u)) - 8388608.0f;
                 }
             } else {
@@ -133,10 +169,13 @@ __global__ void __launch_bounds__(kGridThreads) smooth_union_kernel(const __grid
                     // exact integer-to-float below 2^23 on the FP32 pipe
                     const float v = c[i] < 0x800000u ? __int_as_float((int)(c[i] | 0x4B000000u)) - 8388608.0f
                                                      : (float)c[i];
+                    nz |= c[i];
                     if (e < AW * AH) A[ry][rx] = v;
                 }
             }
-            __syncthreads();
+            // counts and taps are >= 0, so a region without particles blurs to 0
+            // and leaves the running maximum (>= 0) unchanged: skip both passes
+            if (!__syncthreads_or(nz != 0u)) continue;
             if constexpr (RB == 0) {
 #pragma unroll
                 for (int j = 0; j < RT; ++j) acc[j] = fmaxf(acc[j], A[RT * vg + j][vx] * s.inv_n);

@@ -264,7 +264,14 @@ struct BatchHuman {
     uint32_t *counts;
     uint32_t *oob;
     uint32_t speed_on;    // several speeds: bit q = speed q enabled for this human
+    uint8_t *flags;       // [T][fby][fbx] block occupancy written with the counts, or NULL
+    int fbx, fby;         // output blocks of kFlagBlock x kFlagBlock cells per row / column
 };
+
+// Block occupancy flags of a batch's histograms: flags[t][by][bx] = 1 once a
+// particle is emplaced in the output block of kFlagBlock x kFlagBlock cells
+// (bx = cx >> kFlagShift); the union epilogue skips the blocks left at 0.
+constexpr int kFlagShift = 4, kFlagBlock = 1 << kFlagShift;
 
 // Grid epilogue (Gaussian smoothing, Sec. III-B; max-union, Sec. IV-B).
 constexpr int kMaxSmoothR = 16; // blur radius ceil(3 sigma) in cells
@@ -275,6 +282,8 @@ struct SmoothSrc {
     int T, W, H;
     int ox, oy;             // window cell (x, y) = shared cell (x + ox, y + oy)
     int small;              // every count < 2^23 (N < 2^23): exact FP32 conversion by the mantissa
+    const uint8_t *flags;   // block occupancy [T][fby][fbx], or NULL (stage every region)
+    int fbx, fby;
 };
 
 struct SmoothArgs {

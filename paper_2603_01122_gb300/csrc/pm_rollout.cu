@@ -78,6 +78,8 @@ __global__ void __launch_bounds__(kWarpCtaThreads, kWarpCtaMinBlocks)
     c.tr_states = a.tr_states;
     c.tr_head = a.tr_head;
     c.tr_comp = a.tr_comp;
+    c.flags = nullptr;
+    c.fbx = c.fplane = 0;
     for (;;) {
         unsigned item = 0;
         if (lane == 0) item = atomicAdd(head, 1u);
@@ -136,6 +138,8 @@ __global__ void __launch_bounds__(kWarpCtaThreads, kWarpCtaMinBlocks)
     c.tr_states = a.tr_states;
     c.tr_head = a.tr_head;
     c.tr_comp = a.tr_comp;
+    c.flags = nullptr;
+    c.fbx = c.fplane = 0;
     for (;;) {
         unsigned item = 0;
         if (lane == 0) item = atomicAdd(head, 1u);

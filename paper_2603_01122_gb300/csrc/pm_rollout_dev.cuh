@@ -631,6 +631,9 @@ struct TileCtx {
     float *tr_states;
     uint8_t *tr_head;
     int32_t *tr_comp;
+    uint8_t *flags; // block occupancy [T][fby][fbx] (warp emplacement), or NULL
+    int fbx;
+    int fplane;     // fbx * fby
 };
 
 // Words of one shared-memory window of ww x wh 16-bit counts, padded to 16 B.
@@ -840,6 +843,7 @@ __device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t ena
     uint32_t q0 = 0, q1 = 0, q2 = 0, q3 = 0, q4 = 0, q5 = 0, q6 = 0, q7 = 0;
     for (int t = 1; t <= c.T; ++t) {
         uint32_t key = 0xFFFFFFFFu; // idle lane
+        int fkey = 0;               // block of the cell (flags only)
         if (act) {
             if (((t - 1) & 7) == 0) {
                 const U64x4 r = philox4x64_10(U64x4{i, (uint64_t)((t - 1) >> 3), kPurposeStep, 0ull}, c.seed, c.human);
@@ -880,14 +884,19 @@ __device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t ena
                 const bool in = fabsf(vx) < 4194304.0f && fabsf(vy) < 4194304.0f && cx >= 0 && cx < c.W &&
                                 cy >= 0 && cy < c.H;
                 key = in ? (uint32_t)(cy * c.W + cx) : 0xFFFFFFFEu;
+                if (c.flags) fkey = (cy >> kFlagShift) * c.fbx + (cx >> kFlagShift);
             }
         }
         if (c.hist) {
             const uint32_t peers = __match_any_sync(0xffffffffu, key);
             // the lowest lane of each group of equal keys adds the group's size
             if (key != 0xFFFFFFFFu && (peers & ((1u << lane) - 1u)) == 0u) {
-                if (key == 0xFFFFFFFEu) red_add(c.oob + (t - 1), (uint32_t)__popc(peers));
-                else red_add(c.counts + (size_t)(t - 1) * plane + key, (uint32_t)__popc(peers));
+                if (key == 0xFFFFFFFEu) {
+                    red_add(c.oob + (t - 1), (uint32_t)__popc(peers));
+                } else {
+                    red_add(c.counts + (size_t)(t - 1) * plane + key, (uint32_t)__popc(peers));
+                    if (c.flags) c.flags[(size_t)(t - 1) * c.fplane + fkey] = 1u; // idempotent
+                }
             }
         }
     }

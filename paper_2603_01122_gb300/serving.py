@@ -36,7 +36,8 @@ from typing import Dict, List, Optional
 import numpy as np
 
 from . import (make_grid, make_human, make_model, pm_batch_create, pm_batch_destroy,
-               pm_batch_predict, pm_batch_set, pm_batch_union, pm_batch_update_posterior)
+               pm_batch_predict, pm_batch_set, pm_batch_set_block_flags, pm_batch_union,
+               pm_batch_update_posterior)
 
 
 @dataclasses.dataclass
@@ -112,6 +113,8 @@ class Server:
         self.stationary_eps = stationary_eps
         self._shared = make_model(K, speed, dt, shared_goals, shared_beta, w1=w1, w2=w2, speeds=self.speeds)
         self.batch = pm_batch_create(ctx, self._shared, cap)
+        if union_sigma is not None:  # the union reads only the blocks the rollout marks
+            pm_batch_set_block_flags(self.batch, 1)
         self.union_sigma = union_sigma
         self.union = None
         if union_sigma is not None:

@@ -121,6 +121,17 @@ def test_union_matches_oracle(ctx, orc, sigma):
         want = G.union(hs, T, H, W, sigma)
         assert np.all(np.abs(got - want) <= RTOL * want + ATOL), np.max(np.abs(got - want))
         assert got.max() > 0.0
+        # with block marks the union reads only marked blocks: the same result, bit for bit
+        pm.pm_batch_set_block_flags(b, 1)
+        pm.pm_batch_predict(b)
+        prob2 = torch.full((T, H, W), -1.0, device="cuda:0")
+        pm.pm_batch_union(b, sigma, T, pm.make_grid(x0, y0, res, W, H), prob2)
+        torch.cuda.synchronize()
+        for r, h in zip(recs, hs):  # the rollout is unchanged by the marks
+            np.testing.assert_array_equal(r["counts"].cpu().numpy().view(np.uint32).astype(np.int64), h["counts"])
+        np.testing.assert_array_equal(prob2.cpu().numpy(), prob.cpu().numpy())
+        with pytest.raises(pm.PmError):
+            pm.pm_batch_set_block_flags(b, 2)
     finally:
         pm.pm_batch_destroy(b)
 
