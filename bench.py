@@ -391,7 +391,15 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
     dense_ms = time_events(torch, stream, do_union, 10)  # no block marks: every region is read
     # with block marks: the rollout marks occupied 16 x 16 blocks, the union reads only those
     pm.pm_batch_set_block_flags(batch, 1, stream)
-    marked_batch_ms = time_events(torch, stream, graph.replay, 10)
+    graph_m = torch.cuda.CUDAGraph()  # the kernel variant is fixed at capture: capture again
+    with torch.cuda.stream(stream):
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph_m, stream=stream):
+            for r in recs:
+                r["lb"].copy_(r["prior"])
+            pm.pm_batch_update_posterior(batch, stream)
+            pm.pm_batch_predict(batch, stream)
+    marked_batch_ms = time_events(torch, stream, graph_m.replay, 10)
     union_ms = time_events(torch, stream, do_union, 10)
     pm.pm_batch_set_block_flags(batch, 0, stream)
     torch.cuda.synchronize()

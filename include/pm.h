@@ -285,8 +285,9 @@ pm_status pm_batch_autotune(pm_batch *b, void *stream);
  * that land in the same cell into one global reduction; 1: a CTA takes a
  * tile of `threads` particles and counts each step in its shared-memory
  * window, flushed once per touched cell. pm_batch_set_config rebuilds the
- * work list when the tile size changes (queued on the legacy stream). Every
- * shape gives the same counts. */
+ * work list when the tile size changes (queued on the legacy stream); a CUDA
+ * graph that captured pm_batch_predict must be captured again after a change
+ * of shape. Every shape gives the same counts. */
 pm_status pm_batch_get_config(const pm_batch *b, int32_t *threads, int32_t *shared_window, int32_t *ctas_per_sm,
                               int32_t *window_kib);
 pm_status pm_batch_set_config(pm_batch *b, int32_t threads, int32_t shared_window, int32_t ctas_per_sm,
@@ -359,6 +360,19 @@ pm_status pm_update_posterior_noalloc(const pm_model *model, const float *obs_xy
 pm_status pm_smooth_occupancy(pm_ctx *ctx, const uint32_t *counts, int32_t n_particles, int32_t horizon,
                               const pm_grid *grid, float sigma_cells, float *prob, void *stream);
 
+/* enable = 1: pm_batch_predict also marks, per human and step, the 16 x 16-cell
+ * blocks of the output it emplaces into (a byte per block, in batch-owned
+ * device memory; a few per cent of the rollout's time), so that
+ * pm_batch_union skips the empty ones; 0 (the default): no marks, and
+ * pm_batch_union reads every region. The warp-combined emplacement writes the
+ * marks; with the shared-memory window form (pm_batch_set_config) the union
+ * reads every region. Re-uploads the descriptors on `stream` like
+ * pm_batch_set. The kernel variant is chosen when pm_batch_predict is
+ * enqueued, so a CUDA graph that captured it must be captured again after a
+ * change. PM_EINVAL for another value, PM_ENOMEM if the marks cannot be
+ * allocated. */
+pm_status pm_batch_set_block_flags(pm_batch *b, int32_t enable, void *stream);
+
 /* Multi-human prediction on one shared grid (Sec. IV-B): every human of the
  * batch contributes its occupancy, blurred as pm_smooth_occupancy does (its
  * window widened by R cells, so mass blurred past the window is kept), at its
@@ -372,17 +386,6 @@ pm_status pm_smooth_occupancy(pm_ctx *ctx, const uint32_t *counts, int32_t n_par
  * (pm_batch_set_block_flags) it reads only the 16 x 16-cell blocks that
  * pm_batch_predict marked as holding a particle. PM_EINVAL for mismatched
  * grids, bad sizes or sigma. */
-/* enable = 1: pm_batch_predict also marks, per human and step, the 16 x 16-cell
- * blocks of the output it emplaces into (a byte per block, in batch-owned
- * device memory; a few per cent of the rollout's time), so that
- * pm_batch_union skips the empty ones; 0 (the default): no marks, and
- * pm_batch_union reads every region. The warp-combined emplacement writes the
- * marks; with the shared-memory window form (pm_batch_set_config) the union
- * reads every region. Re-uploads the descriptors on `stream` like
- * pm_batch_set; a captured graph stays valid. PM_EINVAL for another value,
- * PM_ENOMEM if the marks cannot be allocated. */
-pm_status pm_batch_set_block_flags(pm_batch *b, int32_t enable, void *stream);
-
 pm_status pm_batch_union(pm_batch *b, float sigma_cells, int32_t horizon, const pm_grid *grid, float *prob,
                          void *stream);
 

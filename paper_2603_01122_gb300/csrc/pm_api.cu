@@ -663,7 +663,8 @@ pm_status batch_upload(pm_batch *b, cudaStream_t stream)
     pm::RolloutArgs t;
     std::memset(&t, 0, sizeof t);
     fill_rollout_tables(&b->shared, t);
-    b->occ = pm::batch_rollout_occupancy(b->shared.K, t.enabled, t.tab.S, batch_shape_of(b), batch_dyn_smem(b));
+    b->occ = pm::batch_rollout_occupancy(b->shared.K, t.enabled, t.tab.S, b->block_flags && b->warp_hist,
+                                         batch_shape_of(b), batch_dyn_smem(b));
     cudaGetLastError();
     return PM_OK;
 }
@@ -692,6 +693,7 @@ pm_status batch_predict_impl(pm_batch *b, cudaStream_t stream)
     a.head = b->d_head;
     a.win_radius_cap = batch_radius_cap(b->window_kib, b->threads);
     a.status = status_word(ctx);
+    a.marks = (b->block_flags && b->warp_hist && b->d_flags) ? 1 : 0;
     const size_t dyn = batch_dyn_smem(b);
     int occ = b->occ;
     if (occ < 1)
@@ -1094,7 +1096,8 @@ pm_status pm_batch_set_config(pm_batch *b, int32_t threads, int32_t shared_windo
     pm::RolloutArgs t;
     std::memset(&t, 0, sizeof t);
     fill_rollout_tables(&b->shared, t);
-    b->occ = pm::batch_rollout_occupancy(b->shared.K, t.enabled, t.tab.S, batch_shape_of(b), batch_dyn_smem(b));
+    b->occ = pm::batch_rollout_occupancy(b->shared.K, t.enabled, t.tab.S, b->block_flags && b->warp_hist,
+                                         batch_shape_of(b), batch_dyn_smem(b));
     cudaGetLastError();
     return PM_OK;
 }

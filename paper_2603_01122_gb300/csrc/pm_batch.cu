@@ -136,7 +136,9 @@ constexpr size_t kWarpTableBytesMS = (size_t)kMaxJ * 24;
 // No block barrier after the start, so tiles of different humans and
 // horizons mix freely on every scheduler.
 // MS: the control set of several speeds (draw_multi).
-template <int KT, bool FULL, bool MS = false>
+// MARKS: also write the block occupancy flags (a separate instantiation, so
+// the kernel without marks carries none of their code).
+template <int KT, bool FULL, bool MS = false, bool MARKS = false>
 __global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_warp_kernel(const __grid_constant__ BatchArgs a)
 {
     __shared__ float2 step[MS ? PM_MAX_SPEEDS * kMaxK : kMaxK];
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_warp_kernel(const _
         c.tr_states = nullptr;
         c.tr_head = nullptr;
         c.tr_comp = nullptr;
-        c.flags = h->flags;
+        c.flags = MARKS ? h->flags : nullptr;
         c.fbx = h->fbx;
         c.fplane = h->fbx * h->fby;
         if constexpr (MS)
@@ -264,7 +266,10 @@ cudaError_t launch_or_query(Kern k, const BatchArgs &a, int blocks, int threads,
 template <int KT, bool FULL>
 cudaError_t batch_shape(const BatchArgs &a, const RolloutShape &sh, int blocks, size_t dyn, cudaStream_t s, int *occ)
 {
-    if (sh.warp_hist) return launch_or_query(batch_warp_kernel<KT, FULL>, a, blocks, sh.threads, dyn, s, occ);
+    if (sh.warp_hist) {
+        if (a.marks) return launch_or_query(batch_warp_kernel<KT, FULL, false, true>, a, blocks, sh.threads, dyn, s, occ);
+        return launch_or_query(batch_warp_kernel<KT, FULL>, a, blocks, sh.threads, dyn, s, occ);
+    }
     return launch_or_query(batch_rollout_kernel<KT, FULL>, a, blocks, sh.threads, dyn, s, occ);
 }
 
@@ -272,9 +277,15 @@ cudaError_t batch_dispatch(const BatchArgs &a, const RolloutShape &sh, int block
 {
     if (a.tab.S > 0) { // several speeds: warp-combined emplacement only
         switch (a.K) {
-        case 16: return launch_or_query(batch_warp_kernel<16, false, true>, a, blocks, sh.threads, dyn, s, occ);
-        case 32: return launch_or_query(batch_warp_kernel<32, false, true>, a, blocks, sh.threads, dyn, s, occ);
-        default: return launch_or_query(batch_warp_kernel<0, false, true>, a, blocks, sh.threads, dyn, s, occ);
+        case 16:
+            return a.marks ? launch_or_query(batch_warp_kernel<16, false, true, true>, a, blocks, sh.threads, dyn, s, occ)
+                           : launch_or_query(batch_warp_kernel<16, false, true>, a, blocks, sh.threads, dyn, s, occ);
+        case 32:
+            return a.marks ? launch_or_query(batch_warp_kernel<32, false, true, true>, a, blocks, sh.threads, dyn, s, occ)
+                           : launch_or_query(batch_warp_kernel<32, false, true>, a, blocks, sh.threads, dyn, s, occ);
+        default:
+            return a.marks ? launch_or_query(batch_warp_kernel<0, false, true, true>, a, blocks, sh.threads, dyn, s, occ)
+                           : launch_or_query(batch_warp_kernel<0, false, true>, a, blocks, sh.threads, dyn, s, occ);
         }
     }
     const int KT = rollout_kt_for(a.K);
@@ -295,12 +306,13 @@ size_t batch_warp_tables_bytes(int threads, bool multi_speed)
     return (size_t)(threads / 32) * (multi_speed ? kWarpTableBytesMS : kWarpTableBytes);
 }
 
-int batch_rollout_occupancy(int K, uint64_t enabled, int S, const RolloutShape &shape, size_t dyn)
+int batch_rollout_occupancy(int K, uint64_t enabled, int S, bool marks, const RolloutShape &shape, size_t dyn)
 {
     BatchArgs a;
     a.K = K;
     a.enabled = enabled;
     a.tab.S = S;
+    a.marks = marks ? 1 : 0;
     int n = 0;
     if (batch_dispatch(a, shape, 0, dyn, nullptr, &n) != cudaSuccess) {
         cudaGetLastError();

@@ -323,6 +323,7 @@ struct BatchArgs {
     unsigned *head;      // next tile (zeroed before every launch)
     int win_radius_cap;  // (2r+1)^2 cells fit the dynamic shared memory
     unsigned *status;    // context status word (or NULL)
+    int marks;           // write block occupancy flags (the humans' flags are set)
 };
 
 // Launch shape of the rollout: threads per CTA, particles per thread (1 or
@@ -355,7 +356,7 @@ cudaError_t launch_sfu_probe(int op, int blocks, int threads, int iters, float *
                              cudaStream_t s);
 int rollout_kt_for(int K); // template bucket for K (8, 16, 36 or 64)
 cudaError_t launch_adjoint(const AdjointArgs &a, cudaStream_t s);
-int batch_rollout_occupancy(int K, uint64_t enabled, int S, const RolloutShape &shape, size_t dyn);
+int batch_rollout_occupancy(int K, uint64_t enabled, int S, bool marks, const RolloutShape &shape, size_t dyn);
 size_t batch_warp_tables_bytes(int threads, bool multi_speed); // dynamic shared memory of the warp form
 cudaError_t launch_batch_rollout(const BatchArgs &a, const RolloutShape &shape, int blocks, size_t dyn, cudaStream_t s);
 cudaError_t launch_batch_zero(const BatchHuman *humans, const int *n_dev, int max_rows, int sm_count, cudaStream_t s);
