@@ -1,5 +1,7 @@
 """Helpers for the GPU tests: run the library through its C ABI on torch
 device buffers, and the matching oracle calls on the same inputs."""
+import math
+
 import numpy as np
 import torch
 
@@ -60,3 +62,47 @@ def predict(ctx, gh, log_b, z0, N, T, grid, seed, human, n_trace=0, hist=True):
         out["headings"] = heads.cpu().numpy()
         out["comp"] = comps.cpu().numpy()
     return out
+
+
+def explain_divergences(orc, m, lb, z0, seed, human, got, ref):
+    """Check each diverged particle at its first differing draw.
+
+    The GPU draws with the inverse CDF of its FP32 policy, evaluated at its
+    FP32 state, with 22-bit fixed-point weights; the oracle with the exact
+    policy at its FP64 state. With C the exact CDF, C' the GPU's, u the shared
+    uniform, kg the GPU's choice and ko the oracle's: kg < ko implies
+    0 <= u - C[kg] < C'[kg] - C[kg], and kg > ko implies
+    0 < C[kg-1] - u <= C[kg-1] - C'[kg-1]. So u lies within max |C' - C| of a
+    boundary. Each logit error is at most A = |beta| (w2 dd + |w1| ds) with dd
+    = |z32 - z64| + 1e-6 (1 + d) (state and FP32 distance errors) and ds =
+    1e-7 max step, so the policy's CDF moves by at most expm1(2 A); the
+    fixed-point weights (largest >= 2^21 units, each within 1.5 units) and the
+    threshold rounding add (1.5 U + 1) 2^-21. The component draw has only the
+    last kind of error, over J components. Returns the number checked."""
+    diverged = np.flatnonzero(np.any(got["headings"] != ref["headings"], axis=1) | (got["comp"] != ref["comp"]))
+    J = m.G * m.B
+    Cb = np.cumsum(np.exp(np.asarray(lb, np.float64)))
+    Cb /= Cb[-1]
+    smax = m.v * m.dt * float(np.max(m.speeds))
+    for i in diverged:
+        i = int(i)
+        kg, ko = int(got["comp"][i]), int(ref["comp"][i])
+        if kg != ko:
+            u = orc.uniform_select(seed, human, i)
+            delta = (u - Cb[kg]) if kg < ko else (Cb[kg - 1] - u)
+            assert 0.0 <= delta <= (2 * J + 1) * 2.0 ** -21, (i, kg, ko, delta)
+            continue
+        g, b = divmod(ko, m.B)
+        t = int(np.flatnonzero(got["headings"][i] != ref["headings"][i])[0])
+        z64 = np.asarray(z0, np.float64) if t == 0 else ref["states64"][i, t - 1]
+        z32 = np.asarray(z0, np.float64) if t == 0 else ref["states32"][i, t - 1].astype(np.float64)
+        C = np.cumsum(np.exp(orc.log_policy(m, z64, m.beta[b], m.goals[g])))
+        C /= C[-1]
+        u = orc.uniform_step(seed, human, i, t + 1)
+        kg, ko = int(got["headings"][i, t]), int(ref["headings"][i, t])
+        delta = (u - C[kg]) if kg < ko else (C[kg - 1] - u)
+        d = math.hypot(*(z64 - m.goals[g])) + smax
+        A = abs(m.beta[b]) * (m.w2 * (math.hypot(*(z32 - z64)) + 1e-6 * (1 + d)) + abs(m.w1) * 1e-7 * smax)
+        budget = math.expm1(2 * A) + (1.5 * m.U + 1) * 2.0 ** -21
+        assert 0.0 <= delta <= budget, (i, t, kg, ko, delta, budget)
+    return len(diverged)

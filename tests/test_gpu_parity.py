@@ -7,7 +7,9 @@ Tolerances (stated once, used below):
   trajectories identical heading sequences and (beta, g) draws under the
               shared Philox streams except at most 1e-4 of the particles
               (FP32 CDF boundaries); non-diverged particles have bit-identical
-              FP32 states;
+              FP32 states; every diverged particle differs first at a draw
+              whose uniform lies within the error budget of a boundary of
+              the exact CDF (gpu_util.explain_divergences);
   histogram   bit-exact given identical FP32 states;
   occupancy   per-step TV against exact propagation within the allowance of
               test_oracle_rollout.tv_bound.
@@ -20,7 +22,7 @@ import pytest
 import torch
 
 import workloads
-from gpu_util import GpuHuman, dev, posterior, predict
+from gpu_util import GpuHuman, dev, explain_divergences, posterior, predict
 from test_oracle_rollout import lattice_k4, tv, tv_bound
 
 pytestmark = pytest.mark.gpu
@@ -158,9 +160,10 @@ def test_plain_small_trajectories_and_histogram(ctx, orc):
     N, T = hu.n_particles, hu.horizon
     got = predict(ctx, gh, lb, z0, N, T, hu.grid, hu.seed, hu.human_id, n_trace=N)
     ref = orc.rollout(m, lb, z0, T, hu.seed, hu.human_id, 0, N, grid=hu.grid, want_headings=True,
-                      want_states32=True, want_comp=True)
+                      want_states32=True, want_states64=True, want_comp=True)
     d = compare_trajectories(got, ref)
     assert d <= TRAJ_RATE * N, d
+    assert explain_divergences(orc, m, lb, z0, hu.seed, hu.human_id, got, ref) == d
     c, o = orc.bin_states(got["states32"], hu.grid)
     np.testing.assert_array_equal(got["counts"], c)
     np.testing.assert_array_equal(got["oob"], o)
@@ -220,10 +223,11 @@ def test_paper_scale_sampled_particles_full_launch(ctx, orc):
     N, T, n = hu.n_particles, hu.horizon, 20000
     got = predict(ctx, gh, lb, z0, N, T, hu.grid, hu.seed, hu.human_id, n_trace=n)
     ref = orc.rollout(m, lb, z0, T, hu.seed, hu.human_id, 0, n, want_counts=False,
-                      want_headings=True, want_states32=True, want_comp=True)
+                      want_headings=True, want_states32=True, want_states64=True, want_comp=True)
     d = compare_trajectories(got, ref)
     print(f"paper_scale: {d} of {n} sampled particles diverged")
     assert d <= TRAJ_RATE * n, d
+    assert explain_divergences(orc, m, lb, z0, hu.seed, hu.human_id, got, ref) == d
     counts, oob = got["counts"], got["oob"]
     assert np.all(counts.reshape(T, -1).sum(1).astype(np.int64) + oob == N)
     # every count lies within reach of z0 after t steps (|z_t - z0| <= t v dt)
@@ -280,8 +284,9 @@ def test_edge_cases_full_trace(ctx, orc, case):
     gh = GpuHuman(K, hu.speed, dt, goals, beta, heading_off=heading_off)
     got = predict(ctx, gh, lb, z0, N, T, grid, 77, 5, n_trace=N)
     ref = orc.rollout(m, lb, z0, T, 77, 5, 0, N, grid=grid, want_headings=True, want_states32=True,
-                      want_comp=True)
+                      want_states64=True, want_comp=True)
     d = compare_trajectories(got, ref)
+    assert explain_divergences(orc, m, lb, z0, 77, 5, got, ref) == d
     assert d < poisson_reject_at(N), d
     c, o = orc.bin_states(got["states32"], grid)
     np.testing.assert_array_equal(got["counts"], c)

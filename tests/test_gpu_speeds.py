@@ -4,12 +4,11 @@ the rollout, the belief update, the batched launch and the adjoint.
 
 Tolerances. Trajectories: bit-identical FP32 states for every particle whose
 draws agree, and every particle whose draws differ must differ at a draw that
-the error budget explains (``explain_divergences``): its uniform lies within
-the budget of a boundary of the exact CDF between the two choices. Histograms
+the error budget explains (``gpu_util.explain_divergences``): its uniform lies
+within the budget of a boundary of the exact CDF between the two choices. Histograms
 bit-exact given the states; |log b| within 1e-5; L relative 1e-6; gradients
 relative 1e-3 in norm.
 """
-import math
 import zlib
 
 import numpy as np
@@ -17,7 +16,7 @@ import pytest
 import torch
 
 import workloads
-from gpu_util import GpuHuman, dev, posterior, predict
+from gpu_util import GpuHuman, dev, explain_divergences, posterior, predict
 from test_gpu_parity import assert_posterior_close, compare_trajectories, poisson_reject_at
 
 pytestmark = pytest.mark.gpu
@@ -30,50 +29,6 @@ def ctx():
     c = pm.pm_create(0)
     yield c
     pm.pm_destroy(c)
-
-
-def explain_divergences(orc, m, lb, z0, seed, human, got, ref):
-    """Check each diverged particle at its first differing draw.
-
-    The GPU draws with the inverse CDF of its FP32 policy, evaluated at its
-    FP32 state, with 22-bit fixed-point weights; the oracle with the exact
-    policy at its FP64 state. With C the exact CDF, C' the GPU's, u the shared
-    uniform, kg the GPU's choice and ko the oracle's: kg < ko implies
-    0 <= u - C[kg] < C'[kg] - C[kg], and kg > ko implies
-    0 < C[kg-1] - u <= C[kg-1] - C'[kg-1]. So u lies within max |C' - C| of a
-    boundary. Each logit error is at most A = |beta| (w2 dd + |w1| ds) with dd
-    = |z32 - z64| + 1e-6 (1 + d) (state and FP32 distance errors) and ds =
-    1e-7 max step, so the policy's CDF moves by at most expm1(2 A); the
-    fixed-point weights (largest >= 2^21 units, each within 1.5 units) and the
-    threshold rounding add (1.5 U + 1) 2^-21. The component draw has only the
-    last kind of error, over J components. Returns the number checked."""
-    diverged = np.flatnonzero(np.any(got["headings"] != ref["headings"], axis=1) | (got["comp"] != ref["comp"]))
-    J = m.G * m.B
-    Cb = np.cumsum(np.exp(np.asarray(lb, np.float64)))
-    Cb /= Cb[-1]
-    smax = m.v * m.dt * float(np.max(m.speeds))
-    for i in diverged:
-        i = int(i)
-        kg, ko = int(got["comp"][i]), int(ref["comp"][i])
-        if kg != ko:
-            u = orc.uniform_select(seed, human, i)
-            delta = (u - Cb[kg]) if kg < ko else (Cb[kg - 1] - u)
-            assert 0.0 <= delta <= (2 * J + 1) * 2.0 ** -21, (i, kg, ko, delta)
-            continue
-        g, b = divmod(ko, m.B)
-        t = int(np.flatnonzero(got["headings"][i] != ref["headings"][i])[0])
-        z64 = np.asarray(z0, np.float64) if t == 0 else ref["states64"][i, t - 1]
-        z32 = np.asarray(z0, np.float64) if t == 0 else ref["states32"][i, t - 1].astype(np.float64)
-        C = np.cumsum(np.exp(orc.log_policy(m, z64, m.beta[b], m.goals[g])))
-        C /= C[-1]
-        u = orc.uniform_step(seed, human, i, t + 1)
-        kg, ko = int(got["headings"][i, t]), int(ref["headings"][i, t])
-        delta = (u - C[kg]) if kg < ko else (C[kg - 1] - u)
-        d = math.hypot(*(z64 - m.goals[g])) + smax
-        A = abs(m.beta[b]) * (m.w2 * (math.hypot(*(z32 - z64)) + 1e-6 * (1 + d)) + abs(m.w1) * 1e-7 * smax)
-        budget = math.expm1(2 * A) + (1.5 * m.U + 1) * 2.0 ** -21
-        assert 0.0 <= delta <= budget, (i, t, kg, ko, delta, budget)
-    return len(diverged)
 
 
 def _models(orc, K, speed, dt, goals, beta, speeds, speed_off=0, w1=1.0, w2=1.0, heading_off=0):
