@@ -42,8 +42,12 @@ def test_noalloc_matches_context_path_twice(orc):
                               start=np.float32([5.0, 5.0]), n_obs=200, n_particles=1, horizon=1,
                               grid=(0, 0, 1, 1, 1), seed=0, human_id=3, obs_seed=3)
         cases.append((hu2, orc.simulate(orc.Model(64, 1.0, hu2.dt, goals, beta), 37, hu2.start, 200, 3, 3)))
+        # third call: the several-speed control set (|U| = 96), history drawn at all speeds
+        hu3 = workloads.multi_speed()
+        cases.append((hu3, orc.simulate(orc.Model(hu3.K, hu3.speed, hu3.dt, hu3.goals, hu3.beta, speeds=hu3.speeds),
+                                        hu3.true_j, hu3.start, hu3.n_obs, hu3.obs_seed, hu3.human_id)))
         for hu, obs in cases:
-            gh = GpuHuman.of(hu)
+            gh = GpuHuman.of(hu, speeds=None if tuple(hu.speeds) == (1.0,) else hu.speeds)
             obs_d = dev(obs.astype(np.float32))
             prior = hu.uniform_log_prior()
             a = dev(prior)
