@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--serving-seconds", type=float, default=0.0,
                     help="also run the Poisson arrival process for this many simulated seconds")
     ap.add_argument("--serving-frames", type=int, default=250, help="frames of the forced-64-live run")
+    ap.add_argument("--sections", default="all", type=lambda v: set(v.split(",")),
+                    help="extra sections to run: all, or a comma list of batched, serving, speeds, table1, "
+                         "differentiation (plain_small always runs)")
     ap.add_argument("--workload", default="paper_scale", choices=sorted(MAIN_WORKLOADS),
                     help="the main line's workload (paper_scale: one speed, K = 36; multi_speed: |U| = 96)")
     return ap.parse_args()
@@ -311,6 +314,10 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
     """Batched, serving, differentiation and small-case numbers (secondary
     workloads; each quoted with its own unit)."""
     out = {}
+
+    def want(name):
+        return "all" in args.sections or name in args.sections
+
     # -- plain_small: latency of one prediction (1 human, K = 8, N = 10k, T = 20)
     hu = workloads.plain_small()
     g, b = torch.tensor(hu.goals, device=dev), torch.tensor(hu.beta, device=dev)
@@ -334,305 +341,310 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
                           "particle_steps_per_s": hu.n_particles * hu.horizon / (ms * 1e-3),
                           "config": "1 human, K=8, N=10k, T=20, 20 observed steps, 100x100 grid"}
 
-    # -- batched: 16 humans, one persistent launch in a CUDA graph vs the plain per-human path
-    hs = workloads.batched()
-    recs = []
-    for k, h in enumerate(hs):
-        gg, bb = torch.tensor(h.goals, device=dev), torch.tensor(h.beta, device=dev)
-        ob = gpu_paths(pm, ctx, torch, dev, h, h.n_obs, h.human_id)
-        x0, y0, res, W, H = h.grid
-        recs.append(dict(h=h, g=gg, b=bb, obs=ob, prior=torch.tensor(h.uniform_log_prior(), device=dev),
-                         lb=torch.tensor(h.uniform_log_prior(), device=dev), z0=ob[-1].clone(),
-                         grid=pm.make_grid(x0, y0, res, W, H),
-                         counts=torch.empty((h.horizon, H, W), dtype=torch.int32, device=dev),
-                         oob=torch.empty(h.horizon, dtype=torch.int32, device=dev),
-                         model=pm.make_model(h.K, h.speed, h.dt, gg, bb)))
-    steps = sum(r["h"].n_particles * r["h"].horizon for r in recs)
+    if want("batched"):
+        # -- batched: 16 humans, one persistent launch in a CUDA graph vs the plain per-human path
+        hs = workloads.batched()
+        recs = []
+        for k, h in enumerate(hs):
+            gg, bb = torch.tensor(h.goals, device=dev), torch.tensor(h.beta, device=dev)
+            ob = gpu_paths(pm, ctx, torch, dev, h, h.n_obs, h.human_id)
+            x0, y0, res, W, H = h.grid
+            recs.append(dict(h=h, g=gg, b=bb, obs=ob, prior=torch.tensor(h.uniform_log_prior(), device=dev),
+                             lb=torch.tensor(h.uniform_log_prior(), device=dev), z0=ob[-1].clone(),
+                             grid=pm.make_grid(x0, y0, res, W, H),
+                             counts=torch.empty((h.horizon, H, W), dtype=torch.int32, device=dev),
+                             oob=torch.empty(h.horizon, dtype=torch.int32, device=dev),
+                             model=pm.make_model(h.K, h.speed, h.dt, gg, bb)))
+        steps = sum(r["h"].n_particles * r["h"].horizon for r in recs)
 
-    def plain_batched():
-        for r in recs:
-            r["lb"].copy_(r["prior"])
-            pm.pm_update_posterior(ctx, r["model"], r["obs"], r["h"].n_obs, r["lb"], stream)
-            z = r["z0h"]
-            pm.pm_predict_occupancy(ctx, r["model"], r["lb"], z[0], z[1], r["h"].n_particles, r["h"].horizon,
-                                    r["grid"], r["h"].seed, r["h"].human_id, r["counts"], r["oob"], stream)
-    for r in recs:
-        r["z0h"] = [float(v) for v in r["z0"].cpu().numpy()]
-    plain_ms = time_events(torch, stream, plain_batched, 5)
-    batch = pm.pm_batch_create(ctx, recs[0]["model"], len(recs))
-    humans = [pm.make_human(r["g"], r["b"], r["lb"], r["z0"], r["h"].n_particles, r["h"].horizon, r["grid"],
-                            r["h"].seed, r["h"].human_id, r["counts"], r["oob"], obs_xy=r["obs"],
-                            n_obs=r["h"].n_obs) for r in recs]
-    pm.pm_batch_set(batch, humans, stream)
-    t0 = time.perf_counter()
-    pm.pm_batch_autotune(batch, stream)
-    tune_s = time.perf_counter() - t0
-    tuned = pm.pm_batch_get_config(batch)
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.stream(stream):
-        for r in recs:
-            r["lb"].copy_(r["prior"])
-        torch.cuda.synchronize()
-        with torch.cuda.graph(graph, stream=stream):
+        def plain_batched():
             for r in recs:
                 r["lb"].copy_(r["prior"])
-            pm.pm_batch_update_posterior(batch, stream)
-            pm.pm_batch_predict(batch, stream)
-    batch_ms = time_events(torch, stream, graph.replay, 10)
-    # grid epilogue: every human's counts blurred (sigma 1.5 cells) and
-    # max-united on the shared 400 x 400 grid
-    x0, y0, res, W, H = recs[0]["h"].grid
-    T_max = max(r["h"].horizon for r in recs)
-    union = torch.empty((T_max, H, W), device=dev)
-    ugrid = pm.make_grid(x0, y0, res, W, H)
-
-    def do_union():
-        pm.pm_batch_union(batch, 1.5, T_max, ugrid, union, stream)
-    dense_ms = time_events(torch, stream, do_union, 10)  # no block marks: every region is read
-    # with block marks: the rollout marks occupied 16 x 16 blocks, the union reads only those
-    pm.pm_batch_set_block_flags(batch, 1, stream)
-    graph_m = torch.cuda.CUDAGraph()  # the kernel variant is fixed at capture: capture again
-    with torch.cuda.stream(stream):
-        torch.cuda.synchronize()
-        with torch.cuda.graph(graph_m, stream=stream):
+                pm.pm_update_posterior(ctx, r["model"], r["obs"], r["h"].n_obs, r["lb"], stream)
+                z = r["z0h"]
+                pm.pm_predict_occupancy(ctx, r["model"], r["lb"], z[0], z[1], r["h"].n_particles, r["h"].horizon,
+                                        r["grid"], r["h"].seed, r["h"].human_id, r["counts"], r["oob"], stream)
+        for r in recs:
+            r["z0h"] = [float(v) for v in r["z0"].cpu().numpy()]
+        plain_ms = time_events(torch, stream, plain_batched, 5)
+        batch = pm.pm_batch_create(ctx, recs[0]["model"], len(recs))
+        humans = [pm.make_human(r["g"], r["b"], r["lb"], r["z0"], r["h"].n_particles, r["h"].horizon, r["grid"],
+                                r["h"].seed, r["h"].human_id, r["counts"], r["oob"], obs_xy=r["obs"],
+                                n_obs=r["h"].n_obs) for r in recs]
+        pm.pm_batch_set(batch, humans, stream)
+        t0 = time.perf_counter()
+        pm.pm_batch_autotune(batch, stream)
+        tune_s = time.perf_counter() - t0
+        tuned = pm.pm_batch_get_config(batch)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
             for r in recs:
                 r["lb"].copy_(r["prior"])
-            pm.pm_batch_update_posterior(batch, stream)
-            pm.pm_batch_predict(batch, stream)
-    marked_batch_ms = time_events(torch, stream, graph_m.replay, 10)
-    union_ms = time_events(torch, stream, do_union, 10)
-    pm.pm_batch_set_block_flags(batch, 0, stream)
-    torch.cuda.synchronize()
-    dense_bytes = sum(r["h"].horizon for r in recs) * H * W * 4 + T_max * H * W * 4
-    # algorithmic bytes: the occupied blocks' counts (what any union must read) + the output
-    occ_blocks = 0
-    for r in recs:
-        c = r["counts"]
-        Tb, Hc, Wc = c.shape
-        cc = torch.nn.functional.pad(c, (0, (-Wc) % 16, 0, (-Hc) % 16))
-        occ_blocks += int((cc.reshape(Tb, cc.shape[1] // 16, 16, cc.shape[2] // 16, 16).amax(dim=(2, 4)) > 0).sum())
-    union_bytes = occ_blocks * 16 * 16 * 4 + T_max * H * W * 4
-    pm.pm_batch_destroy(batch)
-    out["batched"] = {"humans": len(recs), "particle_steps": steps,
-                      "batched_ms": batch_ms, "batched_particle_steps_per_s": steps / (batch_ms * 1e-3),
-                      "plain_ms": plain_ms, "plain_particle_steps_per_s": steps / (plain_ms * 1e-3),
-                      "speedup_vs_plain": plain_ms / batch_ms, "autotune_s": tune_s,
-                      "tuned": tuned,
-                      "rate_vs_plain_small": steps / (batch_ms * 1e-3) / out["plain_small"]["particle_steps_per_s"],
-                      "sfu_roofline_frac": steps / (batch_ms * 1e-3) * 2 * 36 / sfu_peak,
-                      "union": {"ms": union_ms, "sigma_cells": 1.5, "bytes": union_bytes,
-                                "bytes_definition": "counts of the occupied 16x16 blocks + the union written",
-                                "GB_per_s": union_bytes / (union_ms * 1e-3) / 1e9,
-                                "hbm_frac": union_bytes / (union_ms * 1e-3) / 1e9 / HBM_PEAK_GBS,
-                                "dense_ms": dense_ms, "dense_bytes": dense_bytes,
-                                "dense_GB_per_s": dense_bytes / (dense_ms * 1e-3) / 1e9,
-                                "batched_ms_with_marks": marked_batch_ms,
-                                "config": f"16 humans' counts [T_h][400][400] -> union [{T_max}][400][400], "
-                                          "blur R = 5; block marks written by the rollout (dense: none)"},
-                      "config": "16 humans, G~U{2..6}, N~U[20k,200k], T~U{50..300}, K=36, 400x400 grid, "
-                                "graph of belief update + persistent rollout"}
-    del recs
+            torch.cuda.synchronize()
+            with torch.cuda.graph(graph, stream=stream):
+                for r in recs:
+                    r["lb"].copy_(r["prior"])
+                pm.pm_batch_update_posterior(batch, stream)
+                pm.pm_batch_predict(batch, stream)
+        batch_ms = time_events(torch, stream, graph.replay, 10)
+        # grid epilogue: every human's counts blurred (sigma 1.5 cells) and
+        # max-united on the shared 400 x 400 grid
+        x0, y0, res, W, H = recs[0]["h"].grid
+        T_max = max(r["h"].horizon for r in recs)
+        union = torch.empty((T_max, H, W), device=dev)
+        ugrid = pm.make_grid(x0, y0, res, W, H)
 
-    # -- serving: 64 live humans forced, one frame per observation
-    from paper_2603_01122_gb300.serving import Server, run_arrivals
-    wl = workloads.serving()
-    arr = wl["arrivals"]
-    hu0 = arr[0].human
-    srv = Server(ctx, hu0.K, hu0.speed, hu0.dt, hu0.grid, max_live=64, n_particles=hu0.n_particles,
-                 horizon=hu0.horizon, window=hu0.window)
-    try:
-        live = []
-        paths = []
-        for i in range(64):
-            h = arr[i % len(arr)].human
-            p = gpu_paths(pm, ctx, torch, dev, h, args.serving_frames + 1, h.human_id + 100000 * (i // len(arr)))
-            paths.append(p.cpu().numpy())
-            s_ = srv.admit(i, h.goals, h.beta, paths[-1][0], h.seed, h.human_id + 100000 * (i // len(arr)))
-            live.append(s_)
-        lat = []
-        for f in range(args.serving_frames):
-            for i, s_ in enumerate(live):
-                if f >= 1:
-                    srv.observe(s_, paths[i][f])
-            lat.append(srv.frame())
-        lat = np.array(lat[5:])
-        ps = srv.particle_steps_per_frame()
-        # plain path for the same 64 humans: one belief update and one prediction per human
-        x0, y0, res, W, H = hu0.grid
-        win = hu0.window
-        plain_counts = torch.empty((hu0.horizon, win, win), dtype=torch.int32, device=dev)
-        plain_oob = torch.empty(hu0.horizon, dtype=torch.int32, device=dev)
-        models = []
-        for s_ in live:
-            m_ = srv.meta[s_]
-            models.append((pm.make_model(hu0.K, hu0.speed, hu0.dt, srv.goals[s_, :m_["G"]].contiguous(),
-                                         srv.beta[s_, :m_["B"]].contiguous()), s_, m_))
-        zh = srv.obs_dev[:, 1].cpu().numpy()
+        def do_union():
+            pm.pm_batch_union(batch, 1.5, T_max, ugrid, union, stream)
+        dense_ms = time_events(torch, stream, do_union, 10)  # no block marks: every region is read
+        # with block marks: the rollout marks occupied 16 x 16 blocks, the union reads only those
+        pm.pm_batch_set_block_flags(batch, 1, stream)
+        graph_m = torch.cuda.CUDAGraph()  # the kernel variant is fixed at capture: capture again
+        with torch.cuda.stream(stream):
+            torch.cuda.synchronize()
+            with torch.cuda.graph(graph_m, stream=stream):
+                for r in recs:
+                    r["lb"].copy_(r["prior"])
+                pm.pm_batch_update_posterior(batch, stream)
+                pm.pm_batch_predict(batch, stream)
+        marked_batch_ms = time_events(torch, stream, graph_m.replay, 10)
+        union_ms = time_events(torch, stream, do_union, 10)
+        pm.pm_batch_set_block_flags(batch, 0, stream)
+        torch.cuda.synchronize()
+        dense_bytes = sum(r["h"].horizon for r in recs) * H * W * 4 + T_max * H * W * 4
+        # algorithmic bytes: the occupied blocks' counts (what any union must read) + the output
+        occ_blocks = 0
+        for r in recs:
+            c = r["counts"]
+            Tb, Hc, Wc = c.shape
+            cc = torch.nn.functional.pad(c, (0, (-Wc) % 16, 0, (-Hc) % 16))
+            occ_blocks += int((cc.reshape(Tb, cc.shape[1] // 16, 16, cc.shape[2] // 16, 16).amax(dim=(2, 4)) > 0).sum())
+        union_bytes = occ_blocks * 16 * 16 * 4 + T_max * H * W * 4
+        pm.pm_batch_destroy(batch)
+        out["batched"] = {"humans": len(recs), "particle_steps": steps,
+                          "batched_ms": batch_ms, "batched_particle_steps_per_s": steps / (batch_ms * 1e-3),
+                          "plain_ms": plain_ms, "plain_particle_steps_per_s": steps / (plain_ms * 1e-3),
+                          "speedup_vs_plain": plain_ms / batch_ms, "autotune_s": tune_s,
+                          "tuned": tuned,
+                          "rate_vs_plain_small": steps / (batch_ms * 1e-3) / out["plain_small"]["particle_steps_per_s"],
+                          "sfu_roofline_frac": steps / (batch_ms * 1e-3) * 2 * 36 / sfu_peak,
+                          "union": {"ms": union_ms, "sigma_cells": 1.5, "bytes": union_bytes,
+                                    "bytes_definition": "counts of the occupied 16x16 blocks + the union written",
+                                    "GB_per_s": union_bytes / (union_ms * 1e-3) / 1e9,
+                                    "hbm_frac": union_bytes / (union_ms * 1e-3) / 1e9 / HBM_PEAK_GBS,
+                                    "dense_ms": dense_ms, "dense_bytes": dense_bytes,
+                                    "dense_GB_per_s": dense_bytes / (dense_ms * 1e-3) / 1e9,
+                                    "batched_ms_with_marks": marked_batch_ms,
+                                    "config": f"16 humans' counts [T_h][400][400] -> union [{T_max}][400][400], "
+                                              "blur R = 5; block marks written by the rollout (dense: none)"},
+                          "config": "16 humans, G~U{2..6}, N~U[20k,200k], T~U{50..300}, K=36, 400x400 grid, "
+                                    "graph of belief update + persistent rollout"}
+        del recs
 
-        def plain_frame():
-            for model_, s_, m_ in models:
-                pm.pm_update_posterior(ctx, model_, srv.obs_dev[s_], 1, srv.log_b[s_], stream)
-                z = zh[s_]
-                gx0 = float(np.float32(x0 + (np.floor((z[0] - x0) / res) - (win - 1) // 2) * res))
-                gy0 = float(np.float32(y0 + (np.floor((z[1] - y0) / res) - (win - 1) // 2) * res))
-                pm.pm_predict_occupancy(ctx, model_, srv.log_b[s_], float(z[0]), float(z[1]), hu0.n_particles,
-                                        hu0.horizon, pm.make_grid(gx0, gy0, res, win, win), m_["seed"],
-                                        m_["human_id"], plain_counts, plain_oob, stream)
-        plain_ms = time_events(torch, stream, plain_frame, 3)
-        out["serving_forced_64"] = {
-            "live": 64, "frames": int(lat.size), "p50_ms": float(np.percentile(lat, 50) * 1e3),
-            "p99_ms": float(np.percentile(lat, 99) * 1e3), "max_ms": float(lat.max() * 1e3),
-            "particle_steps_per_frame": ps, "particle_steps_per_s": ps / float(np.median(lat)),
-            "plain_path_ms_per_frame": plain_ms, "speedup_vs_plain": plain_ms / float(np.median(lat) * 1e3),
-            "rate_vs_plain_small": ps / float(np.median(lat)) / out["plain_small"]["particle_steps_per_s"],
-            "sfu_roofline_frac": ps / float(np.median(lat)) * 2 * 36 / sfu_peak,
-            "target": "p99 < 8 ms at 64 humans",
-            "config": "64 humans, K=36, N=50k, T=150, 121x121 window at 0.05 m, 1 observation/frame, graph replay"}
-        # the same frames with the grid epilogue (blur + max-union on the room grid) in the graph
-        srv_u = Server(ctx, hu0.K, hu0.speed, hu0.dt, hu0.grid, max_live=64, n_particles=hu0.n_particles,
-                       horizon=hu0.horizon, window=hu0.window, union_sigma=1.5)
+    if want("serving"):
+        # -- serving: 64 live humans forced, one frame per observation
+        from paper_2603_01122_gb300.serving import Server, run_arrivals
+        wl = workloads.serving()
+        arr = wl["arrivals"]
+        hu0 = arr[0].human
+        srv = Server(ctx, hu0.K, hu0.speed, hu0.dt, hu0.grid, max_live=64, n_particles=hu0.n_particles,
+                     horizon=hu0.horizon, window=hu0.window)
         try:
-            live_u = []
+            live = []
+            paths = []
             for i in range(64):
                 h = arr[i % len(arr)].human
-                live_u.append(srv_u.admit(i, h.goals, h.beta, paths[i][0], h.seed,
-                                          h.human_id + 100000 * (i // len(arr))))
-            lat_u = []
-            for f in range(min(args.serving_frames, 120)):
-                for i, s_ in enumerate(live_u):
+                p = gpu_paths(pm, ctx, torch, dev, h, args.serving_frames + 1, h.human_id + 100000 * (i // len(arr)))
+                paths.append(p.cpu().numpy())
+                s_ = srv.admit(i, h.goals, h.beta, paths[-1][0], h.seed, h.human_id + 100000 * (i // len(arr)))
+                live.append(s_)
+            lat = []
+            for f in range(args.serving_frames):
+                for i, s_ in enumerate(live):
                     if f >= 1:
-                        srv_u.observe(s_, paths[i][f])
-                lat_u.append(srv_u.frame())
-            lat_u = np.array(lat_u[5:])
-            out["serving_forced_64"]["with_union"] = {
-                "frames": int(lat_u.size), "p50_ms": float(np.percentile(lat_u, 50) * 1e3),
-                "p99_ms": float(np.percentile(lat_u, 99) * 1e3), "sigma_cells": 1.5,
-                "union_grid": f"[{hu0.horizon}][{hu0.grid[4]}][{hu0.grid[3]}]"}
-            # MPPI local planner on that union grid: 8192 perturbed sequences of
-            # 30 steps of 0.1 s (every 5th prediction step)
-            Nm, Tm = 8192, 30
-            rng = np.random.default_rng([workloads.MASTER_SEED, 9])
-            mp = pm.make_mppi(Nm, Tm, 0.1, 5, [3.0, 3.0, 10.0, 0.0], [0.6, 0.6, 2.0, 0.0], [2.0, 1.0],
-                              [15.0, 15.0, 0.5, 0.0], 0.1, 1000.0, 0.1, 2.0)
-            u_ref = torch.zeros((Tm, 2), device=dev)
-            delta = torch.tensor((rng.normal(size=(Tm, Nm, 2)) * [0.6, 0.5]).astype(np.float32), device=dev)
-            ctg = torch.empty((Tm, Nm), device=dev)
-            u_opt = torch.empty((Tm, 2), device=dev)
+                        srv.observe(s_, paths[i][f])
+                lat.append(srv.frame())
+            lat = np.array(lat[5:])
+            ps = srv.particle_steps_per_frame()
+            # plain path for the same 64 humans: one belief update and one prediction per human
             x0, y0, res, W, H = hu0.grid
-            rg = pm.make_grid(x0, y0, res, W, H)
+            win = hu0.window
+            plain_counts = torch.empty((hu0.horizon, win, win), dtype=torch.int32, device=dev)
+            plain_oob = torch.empty(hu0.horizon, dtype=torch.int32, device=dev)
+            models = []
+            for s_ in live:
+                m_ = srv.meta[s_]
+                models.append((pm.make_model(hu0.K, hu0.speed, hu0.dt, srv.goals[s_, :m_["G"]].contiguous(),
+                                             srv.beta[s_, :m_["B"]].contiguous()), s_, m_))
+            zh = srv.obs_dev[:, 1].cpu().numpy()
 
-            def mppi():
-                pm.pm_mppi_solve(ctx, mp, [5.0, 5.0, 0.5, 0.6], u_ref, delta, srv_u.union, hu0.horizon, rg, ctg,
-                                 u_opt, stream)
-            mppi_ms = time_events(torch, stream, mppi, 20)
-            out["mppi"] = {"ms_per_solve": mppi_ms, "samples": Nm, "steps": Tm,
-                           "sample_steps_per_s": Nm * Tm / (mppi_ms * 1e-3),
-                           "config": "robot of Eq. 8, 8192 samples x 30 steps of 0.1 s, collision cost from the "
-                                     "64-human union grid [150][400][400]"}
+            def plain_frame():
+                for model_, s_, m_ in models:
+                    pm.pm_update_posterior(ctx, model_, srv.obs_dev[s_], 1, srv.log_b[s_], stream)
+                    z = zh[s_]
+                    gx0 = float(np.float32(x0 + (np.floor((z[0] - x0) / res) - (win - 1) // 2) * res))
+                    gy0 = float(np.float32(y0 + (np.floor((z[1] - y0) / res) - (win - 1) // 2) * res))
+                    pm.pm_predict_occupancy(ctx, model_, srv.log_b[s_], float(z[0]), float(z[1]), hu0.n_particles,
+                                            hu0.horizon, pm.make_grid(gx0, gy0, res, win, win), m_["seed"],
+                                            m_["human_id"], plain_counts, plain_oob, stream)
+            plain_ms = time_events(torch, stream, plain_frame, 3)
+            out["serving_forced_64"] = {
+                "live": 64, "frames": int(lat.size), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3), "max_ms": float(lat.max() * 1e3),
+                "particle_steps_per_frame": ps, "particle_steps_per_s": ps / float(np.median(lat)),
+                "plain_path_ms_per_frame": plain_ms, "speedup_vs_plain": plain_ms / float(np.median(lat) * 1e3),
+                "rate_vs_plain_small": ps / float(np.median(lat)) / out["plain_small"]["particle_steps_per_s"],
+                "sfu_roofline_frac": ps / float(np.median(lat)) * 2 * 36 / sfu_peak,
+                "target": "p99 < 8 ms at 64 humans",
+                "config": "64 humans, K=36, N=50k, T=150, 121x121 window at 0.05 m, 1 observation/frame, graph replay"}
+            # the same frames with the grid epilogue (blur + max-union on the room grid) in the graph
+            srv_u = Server(ctx, hu0.K, hu0.speed, hu0.dt, hu0.grid, max_live=64, n_particles=hu0.n_particles,
+                           horizon=hu0.horizon, window=hu0.window, union_sigma=1.5)
+            try:
+                live_u = []
+                for i in range(64):
+                    h = arr[i % len(arr)].human
+                    live_u.append(srv_u.admit(i, h.goals, h.beta, paths[i][0], h.seed,
+                                              h.human_id + 100000 * (i // len(arr))))
+                lat_u = []
+                for f in range(min(args.serving_frames, 120)):
+                    for i, s_ in enumerate(live_u):
+                        if f >= 1:
+                            srv_u.observe(s_, paths[i][f])
+                    lat_u.append(srv_u.frame())
+                lat_u = np.array(lat_u[5:])
+                out["serving_forced_64"]["with_union"] = {
+                    "frames": int(lat_u.size), "p50_ms": float(np.percentile(lat_u, 50) * 1e3),
+                    "p99_ms": float(np.percentile(lat_u, 99) * 1e3), "sigma_cells": 1.5,
+                    "union_grid": f"[{hu0.horizon}][{hu0.grid[4]}][{hu0.grid[3]}]"}
+                # MPPI local planner on that union grid: 8192 perturbed sequences of
+                # 30 steps of 0.1 s (every 5th prediction step)
+                Nm, Tm = 8192, 30
+                rng = np.random.default_rng([workloads.MASTER_SEED, 9])
+                mp = pm.make_mppi(Nm, Tm, 0.1, 5, [3.0, 3.0, 10.0, 0.0], [0.6, 0.6, 2.0, 0.0], [2.0, 1.0],
+                                  [15.0, 15.0, 0.5, 0.0], 0.1, 1000.0, 0.1, 2.0)
+                u_ref = torch.zeros((Tm, 2), device=dev)
+                delta = torch.tensor((rng.normal(size=(Tm, Nm, 2)) * [0.6, 0.5]).astype(np.float32), device=dev)
+                ctg = torch.empty((Tm, Nm), device=dev)
+                u_opt = torch.empty((Tm, 2), device=dev)
+                x0, y0, res, W, H = hu0.grid
+                rg = pm.make_grid(x0, y0, res, W, H)
+
+                def mppi():
+                    pm.pm_mppi_solve(ctx, mp, [5.0, 5.0, 0.5, 0.6], u_ref, delta, srv_u.union, hu0.horizon, rg, ctg,
+                                     u_opt, stream)
+                mppi_ms = time_events(torch, stream, mppi, 20)
+                out["mppi"] = {"ms_per_solve": mppi_ms, "samples": Nm, "steps": Tm,
+                               "sample_steps_per_s": Nm * Tm / (mppi_ms * 1e-3),
+                               "config": "robot of Eq. 8, 8192 samples x 30 steps of 0.1 s, collision cost from the "
+                                         "64-human union grid [150][400][400]"}
+            finally:
+                srv_u.close()
+            if args.serving_seconds > 0:
+                paths2 = []
+                for a in arr:
+                    n = int((a.t_leave - a.t_arrive) * wl["frame_hz"]) + 2
+                    paths2.append(gpu_paths(pm, ctx, torch, dev, a.human, min(n, 4096), a.human.human_id).cpu().numpy())
+                res2 = run_arrivals(srv_fresh := Server(ctx, hu0.K, hu0.speed, hu0.dt, hu0.grid, max_live=64,
+                                                        n_particles=hu0.n_particles, horizon=hu0.horizon,
+                                                        window=hu0.window),
+                                    arr, paths2, frame_hz=wl["frame_hz"], duration_s=args.serving_seconds)
+                srv_fresh.close()
+                l2 = res2["latency_s"]
+                out["serving_poisson"] = {"seconds": args.serving_seconds, "frames": int(l2.size),
+                                          "p50_ms": float(np.percentile(l2, 50) * 1e3),
+                                          "p99_ms": float(np.percentile(l2, 99) * 1e3),
+                                          "mean_live": float(res2["live"].mean()), "max_live": int(res2["live"].max()),
+                                          "frames_waited": res2["frames_waited"]}
         finally:
-            srv_u.close()
-        if args.serving_seconds > 0:
-            paths2 = []
-            for a in arr:
-                n = int((a.t_leave - a.t_arrive) * wl["frame_hz"]) + 2
-                paths2.append(gpu_paths(pm, ctx, torch, dev, a.human, min(n, 4096), a.human.human_id).cpu().numpy())
-            res2 = run_arrivals(srv_fresh := Server(ctx, hu0.K, hu0.speed, hu0.dt, hu0.grid, max_live=64,
-                                                    n_particles=hu0.n_particles, horizon=hu0.horizon,
-                                                    window=hu0.window),
-                                arr, paths2, frame_hz=wl["frame_hz"], duration_s=args.serving_seconds)
-            srv_fresh.close()
-            l2 = res2["latency_s"]
-            out["serving_poisson"] = {"seconds": args.serving_seconds, "frames": int(l2.size),
-                                      "p50_ms": float(np.percentile(l2, 50) * 1e3),
-                                      "p99_ms": float(np.percentile(l2, 99) * 1e3),
-                                      "mean_live": float(res2["live"].mean()), "max_live": int(res2["live"].max()),
-                                      "frames_waited": res2["frames_waited"]}
-    finally:
-        srv.close()
+            srv.close()
 
-    # -- several speeds: |U| = 96 controls (3 speeds x K = 32), and the same
-    #    human standing still (the two faster speeds masked)
-    for name, stationary in (("multi_speed", False), ("multi_speed_stationary", True)):
-        hu = workloads.multi_speed(stationary=stationary)
-        g, b = torch.tensor(hu.goals, device=dev), torch.tensor(hu.beta, device=dev)
-        model = pm.make_model(hu.K, hu.speed, hu.dt, g, b, speeds=hu.speeds, speed_off=hu.speed_off)
-        gen = workloads.multi_speed()
-        obs = gpu_paths(pm, ctx, torch, dev, gen, hu.n_obs, hu.human_id)
-        z0 = obs[-1].cpu().numpy()
-        prior = torch.tensor(hu.uniform_log_prior(), device=dev)
-        lb = torch.empty_like(prior)
-        x0, y0, res, W, H = hu.grid
-        grid = pm.make_grid(x0, y0, res, W, H)
-        counts = torch.empty((hu.horizon, H, W), dtype=torch.int32, device=dev)
-        oob = torch.empty(hu.horizon, dtype=torch.int32, device=dev)
+    if want("speeds"):
+        # -- several speeds: |U| = 96 controls (3 speeds x K = 32), and the same
+        #    human standing still (the two faster speeds masked)
+        for name, stationary in (("multi_speed", False), ("multi_speed_stationary", True)):
+            hu = workloads.multi_speed(stationary=stationary)
+            g, b = torch.tensor(hu.goals, device=dev), torch.tensor(hu.beta, device=dev)
+            model = pm.make_model(hu.K, hu.speed, hu.dt, g, b, speeds=hu.speeds, speed_off=hu.speed_off)
+            gen = workloads.multi_speed()
+            obs = gpu_paths(pm, ctx, torch, dev, gen, hu.n_obs, hu.human_id)
+            z0 = obs[-1].cpu().numpy()
+            prior = torch.tensor(hu.uniform_log_prior(), device=dev)
+            lb = torch.empty_like(prior)
+            x0, y0, res, W, H = hu.grid
+            grid = pm.make_grid(x0, y0, res, W, H)
+            counts = torch.empty((hu.horizon, H, W), dtype=torch.int32, device=dev)
+            oob = torch.empty(hu.horizon, dtype=torch.int32, device=dev)
 
-        def ms_step():
-            lb.copy_(prior)
-            pm.pm_update_posterior(ctx, model, obs, hu.n_obs, lb, stream)
-            pm.pm_predict_occupancy(ctx, model, lb, float(z0[0]), float(z0[1]), hu.n_particles, hu.horizon,
-                                    grid, hu.seed, hu.human_id, counts, oob, stream)
-        ms = time_events(torch, stream, ms_step, 20)
-        u_on = hu.K * sum(1 for q in range(len(hu.speeds)) if not (hu.speed_off >> q) & 1)
-        rate = hu.n_particles * hu.horizon / (ms * 1e-3)
-        out[name] = {"ms_per_prediction": ms, "particle_steps_per_s": rate, "controls_enabled": u_on,
-                     "sfu_roofline_frac": rate * 2 * u_on / sfu_peak,
-                     "algorithmic": "2 SFU results (ex2 + sqrt) per enabled control per particle-step",
-                     "config": f"paper_scale room, K=32 x speeds {hu.speeds}, speed_off={hu.speed_off:#b}, "
-                               "N=100k, T=150, 50 observed steps, 200x200 grid; L2 not flushed"}
+            def ms_step():
+                lb.copy_(prior)
+                pm.pm_update_posterior(ctx, model, obs, hu.n_obs, lb, stream)
+                pm.pm_predict_occupancy(ctx, model, lb, float(z0[0]), float(z0[1]), hu.n_particles, hu.horizon,
+                                        grid, hu.seed, hu.human_id, counts, oob, stream)
+            ms = time_events(torch, stream, ms_step, 20)
+            u_on = hu.K * sum(1 for q in range(len(hu.speeds)) if not (hu.speed_off >> q) & 1)
+            rate = hu.n_particles * hu.horizon / (ms * 1e-3)
+            out[name] = {"ms_per_prediction": ms, "particle_steps_per_s": rate, "controls_enabled": u_on,
+                         "sfu_roofline_frac": rate * 2 * u_on / sfu_peak,
+                         "algorithmic": "2 SFU results (ex2 + sqrt) per enabled control per particle-step",
+                         "config": f"paper_scale room, K=32 x speeds {hu.speeds}, speed_off={hu.speed_off:#b}, "
+                                   "N=100k, T=150, 50 observed steps, 200x200 grid; L2 not flushed"}
 
-    # -- Table 1's configuration (1 human, n = 8192, |G| = 10, |B| = 5, |U| = 96,
-    #    50 x 50 grid) at T = 2..10: wall clock of one prediction, as the paper
-    #    times it (warm, mean of repeated runs; here event-timed on the stream)
-    t1 = {}
-    for T in (2, 4, 6, 8, 10):
-        hu = workloads.table1(horizon=T)
-        g, b = torch.tensor(hu.goals, device=dev), torch.tensor(hu.beta, device=dev)
-        model = pm.make_model(hu.K, hu.speed, hu.dt, g, b, speeds=hu.speeds)
-        obs = gpu_paths(pm, ctx, torch, dev, hu, hu.n_obs, hu.human_id)
-        z0 = obs[-1].cpu().numpy()
-        prior = torch.tensor(hu.uniform_log_prior(), device=dev)
-        lb = torch.empty_like(prior)
-        x0, y0, res, W, H = hu.grid
-        grid = pm.make_grid(x0, y0, res, W, H)
-        counts = torch.empty((T, H, W), dtype=torch.int32, device=dev)
-        oob = torch.empty(T, dtype=torch.int32, device=dev)
+    if want("table1"):
+        # -- Table 1's configuration (1 human, n = 8192, |G| = 10, |B| = 5, |U| = 96,
+        #    50 x 50 grid) at T = 2..10: wall clock of one prediction, as the paper
+        #    times it (warm, mean of repeated runs; here event-timed on the stream)
+        t1 = {}
+        for T in (2, 4, 6, 8, 10):
+            hu = workloads.table1(horizon=T)
+            g, b = torch.tensor(hu.goals, device=dev), torch.tensor(hu.beta, device=dev)
+            model = pm.make_model(hu.K, hu.speed, hu.dt, g, b, speeds=hu.speeds)
+            obs = gpu_paths(pm, ctx, torch, dev, hu, hu.n_obs, hu.human_id)
+            z0 = obs[-1].cpu().numpy()
+            prior = torch.tensor(hu.uniform_log_prior(), device=dev)
+            lb = torch.empty_like(prior)
+            x0, y0, res, W, H = hu.grid
+            grid = pm.make_grid(x0, y0, res, W, H)
+            counts = torch.empty((T, H, W), dtype=torch.int32, device=dev)
+            oob = torch.empty(T, dtype=torch.int32, device=dev)
 
-        def t1_step():
-            lb.copy_(prior)
-            pm.pm_update_posterior(ctx, model, obs, hu.n_obs, lb, stream)
-            pm.pm_predict_occupancy(ctx, model, lb, float(z0[0]), float(z0[1]), hu.n_particles, T, grid,
-                                    hu.seed, hu.human_id, counts, oob, stream)
-        t1[f"T{T}"] = time_events(torch, stream, t1_step, 200)
-    out["table1"] = {"ms_per_prediction": t1,
-                     "paper_ms_rtx2080ti_gpu_jit": {"T2": 7.0, "T4": 7.0, "T6": 7.0, "T8": 7.0, "T10": 8.0},
-                     "config": "1 human, n=8192, |G|=10, |B|=5, |U|=96 (3 speeds x K=32), 50x50 grid at 0.1 m, "
-                               "dt=0.1, 20 observed steps; belief update + rollout + histogram per prediction; "
-                               "the paper's figures are another machine's (context only)"}
+            def t1_step():
+                lb.copy_(prior)
+                pm.pm_update_posterior(ctx, model, obs, hu.n_obs, lb, stream)
+                pm.pm_predict_occupancy(ctx, model, lb, float(z0[0]), float(z0[1]), hu.n_particles, T, grid,
+                                        hu.seed, hu.human_id, counts, oob, stream)
+            t1[f"T{T}"] = time_events(torch, stream, t1_step, 200)
+        out["table1"] = {"ms_per_prediction": t1,
+                         "paper_ms_rtx2080ti_gpu_jit": {"T2": 7.0, "T4": 7.0, "T6": 7.0, "T8": 7.0, "T10": 8.0},
+                         "config": "1 human, n=8192, |G|=10, |B|=5, |U|=96 (3 speeds x K=32), 50x50 grid at 0.1 m, "
+                                   "dt=0.1, 20 observed steps; belief update + rollout + histogram per prediction; "
+                                   "the paper's figures are another machine's (context only)"}
 
-    # -- differentiation: 256 trajectories, adjoint of the marginal log-likelihood
-    ts = workloads.differentiation()
-    trajs = []
-    for m in range(ts.M):
-        h = workloads.Human(K=ts.K, speed=ts.speed, dt=ts.dt, goals=ts.goals[ts.true_goal[m]:ts.true_goal[m] + 1],
-                            beta=ts.true_beta[m:m + 1], true_j=0, start=ts.starts[m], n_obs=0, n_particles=1,
-                            horizon=1, grid=(0, 0, 1, 1, 1), seed=0, human_id=m, obs_seed=ts.obs_seed)
-        trajs.append(gpu_paths(pm, ctx, torch, dev, h, int(ts.lengths[m]), m))
-    offsets = torch.tensor(np.cumsum([0] + [t.shape[0] for t in trajs]), dtype=torch.int32, device=dev)
-    traj = torch.cat(trajs, 0).contiguous()
-    gg, bb = torch.tensor(ts.goals, device=dev), torch.tensor(ts.beta, device=dev)
-    model = pm.make_model(ts.K, ts.speed, ts.dt, gg, bb)
-    lp = torch.full((40,), -float(np.log(40.0)), device=dev)
-    L = torch.empty(1, device=dev)
-    dg, dv, dw = torch.empty_like(gg), torch.empty(1, device=dev), torch.empty(2, device=dev)
+    if want("differentiation"):
+        # -- differentiation: 256 trajectories, adjoint of the marginal log-likelihood
+        ts = workloads.differentiation()
+        trajs = []
+        for m in range(ts.M):
+            h = workloads.Human(K=ts.K, speed=ts.speed, dt=ts.dt, goals=ts.goals[ts.true_goal[m]:ts.true_goal[m] + 1],
+                                beta=ts.true_beta[m:m + 1], true_j=0, start=ts.starts[m], n_obs=0, n_particles=1,
+                                horizon=1, grid=(0, 0, 1, 1, 1), seed=0, human_id=m, obs_seed=ts.obs_seed)
+            trajs.append(gpu_paths(pm, ctx, torch, dev, h, int(ts.lengths[m]), m))
+        offsets = torch.tensor(np.cumsum([0] + [t.shape[0] for t in trajs]), dtype=torch.int32, device=dev)
+        traj = torch.cat(trajs, 0).contiguous()
+        gg, bb = torch.tensor(ts.goals, device=dev), torch.tensor(ts.beta, device=dev)
+        model = pm.make_model(ts.K, ts.speed, ts.dt, gg, bb)
+        lp = torch.full((40,), -float(np.log(40.0)), device=dev)
+        L = torch.empty(1, device=dev)
+        dg, dv, dw = torch.empty_like(gg), torch.empty(1, device=dev), torch.empty(2, device=dev)
 
-    def adj():
-        pm.pm_loglik_backward(ctx, model, ts.M, offsets, traj.shape[0], traj, lp, 1.0, L, dg, dv, dw, stream)
-    ms = time_events(torch, stream, adj, 20)
-    nsteps = int(traj.shape[0]) - ts.M
-    out["differentiation"] = {"ms_per_backward": ms, "trajectory_steps_per_s": nsteps / (ms * 1e-3),
-                              "q_evals_per_s": nsteps * 40 * (ts.K + 1) / (ms * 1e-3),
-                              "config": "256 trajectories, lengths U{50..200}, K=36, 4 goals x 10 beta, "
-                                        "loss + d/d(goals, speed, w1, w2)"}
+        def adj():
+            pm.pm_loglik_backward(ctx, model, ts.M, offsets, traj.shape[0], traj, lp, 1.0, L, dg, dv, dw, stream)
+        ms = time_events(torch, stream, adj, 20)
+        nsteps = int(traj.shape[0]) - ts.M
+        out["differentiation"] = {"ms_per_backward": ms, "trajectory_steps_per_s": nsteps / (ms * 1e-3),
+                                  "q_evals_per_s": nsteps * 40 * (ts.K + 1) / (ms * 1e-3),
+                                  "config": "256 trajectories, lengths U{50..200}, K=36, 4 goals x 10 beta, "
+                                            "loss + d/d(goals, speed, w1, w2)"}
     return out
 
 
