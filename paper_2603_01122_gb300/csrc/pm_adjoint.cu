@@ -11,8 +11,9 @@
 //   speeds (Sec. IV-B) each control carries its multiplier m_q in the step
 //   and in these derivatives, which makes dL/dw1 nonzero.
 //
-// One CTA per trajectory; a warp per component (beta, g) with its lanes over
-// the trajectory's steps and the headings unrolled in registers. The
+// A CTA per (trajectory, group of eight components); a warp per component
+// (beta, g) with its lanes over the trajectory's steps and the headings
+// unrolled in registers. The
 // per-step log pi is FP32; its sum over a trajectory (up to hundreds of
 // steps of about -log K each) is accumulated in FP64, the one place where
 // FP32 would lose the differences between components. Per-trajectory
@@ -26,6 +27,7 @@ namespace pm {
 namespace {
 
 constexpr int kAdjThreads = 256;
+constexpr float kLog2e = 1.4426950408889634f, kLn2 = 0.6931471805599453f;
 
 __device__ __forceinline__ float wsum(float v)
 {
@@ -63,6 +65,7 @@ __device__ __forceinline__ StepGrad step_terms(const AdjointArgs &a, float zx, f
     const float ro = rsqrtf(fmaxf(xo, 1e-30f));
     const float d_o = xo * ro;
     const float bw = beta * a.w2;
+    const float bw2 = bw * kLog2e; // logits in base 2: exponentials on the SFU
     float lg[KT];
     float m = -INFINITY;
 #pragma unroll
@@ -72,17 +75,17 @@ __device__ __forceinline__ StepGrad step_terms(const AdjointArgs &a, float zx, f
         const float dk = xk * rsqrtf(fmaxf(xk, 1e-30f));
         // beta w2 (d_obs - d_k), formed as a difference of squares
         const float num = a.two_s * fmaf(ex - a.ux[k], px, (ey - a.uy[k]) * py);
-        lg[k] = on ? bw * (num / fmaxf(d_o + dk, 1e-30f)) : -INFINITY;
+        lg[k] = on ? bw2 * __fdividef(num, fmaxf(d_o + dk, 1e-30f)) : -INFINITY;
         m = fmaxf(m, lg[k]);
     }
     float S = 0.0f;
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
-        lg[k] = (lg[k] == -INFINITY) ? 0.0f : expf(lg[k] - m);
+        lg[k] = (lg[k] == -INFINITY) ? 0.0f : ex2_approx(lg[k] - m);
         S += lg[k];
     }
     StepGrad r;
-    r.logpi = -m - logf(S);
+    r.logpi = -(m + log2f(S)) * kLn2;
     if (!grad) return r;
     const float inv = 1.0f / S;
     float sux = 0.f, suy = 0.f, seu = 0.f, sd = 0.f, sp = 0.f;
@@ -138,13 +141,15 @@ __device__ __forceinline__ StepGrad step_terms_ms(const AdjointArgs &a, const fl
     const float xo = fmaxf(fmaf(so, so, P) + 2.0f * so * fmaf(ex, px, ey * py), 0.0f);
     const float ro = rsqrtf(fmaxf(xo, 1e-30f));
     const float d_o = xo * ro;
-    const float bw1 = beta * a.sp.w1, bw2 = beta * a.w2;
+    const float bw2 = beta * a.w2;
+    // logits in base 2 (exponentials on the SFU)
+    const float bl1 = beta * a.sp.w1 * kLog2e, bl2 = bw2 * kLog2e;
     auto logit = [&](const float4 &c, float &du, float &rk) {
         const float xk = fmaxf(fmaf(c.z, c.z, P) + 2.0f * c.z * fmaf(c.x, px, c.y * py), 0.0f);
         rk = rsqrtf(fmaxf(xk, 1e-30f));
         du = xk * rk;
         const float num = fmaf(so - c.z, so + c.z, 2.0f * fmaf(fmaf(so, ex, -c.z * c.x), px, fmaf(so, ey, -c.z * c.y) * py));
-        return fmaf(bw1, so - c.z, bw2 * (num / fmaxf(d_o + du, 1e-30f)));
+        return fmaf(bl1, so - c.z, bl2 * __fdividef(num, fmaxf(d_o + du, 1e-30f)));
     };
     float m = -INFINITY;
     for (int u = 0; u < U; ++u) {
@@ -158,10 +163,10 @@ __device__ __forceinline__ StepGrad step_terms_ms(const AdjointArgs &a, const fl
         const float4 c = cu[u];
         if (c.w == 0.0f) continue;
         float du, rk;
-        S += expf(logit(c, du, rk) - m);
+        S += ex2_approx(logit(c, du, rk) - m);
     }
     StepGrad res;
-    res.logpi = -m - logf(S);
+    res.logpi = -(m + log2f(S)) * kLn2;
     if (!grad) return res;
     const float inv = 1.0f / S;
     float sux = 0.f, suy = 0.f, smeu = 0.f, sm = 0.f, sd = 0.f;
@@ -169,7 +174,7 @@ __device__ __forceinline__ StepGrad step_terms_ms(const AdjointArgs &a, const fl
         const float4 c = cu[u];
         if (c.w == 0.0f) continue;
         float du, rk;
-        const float pk = expf(logit(c, du, rk) - m) * inv;
+        const float pk = ex2_approx(logit(c, du, rk) - m) * inv;
         const float uxk = fmaf(c.z, c.x, px) * rk, uyk = fmaf(c.z, c.y, py) * rk; // (z + sl e_k - g) / d_u
         sux = fmaf(pk, uxk, sux);
         suy = fmaf(pk, uyk, suy);
@@ -186,6 +191,11 @@ __device__ __forceinline__ StepGrad step_terms_ms(const AdjointArgs &a, const fl
     return res;
 }
 
+// Grid: blockIdx.x = trajectory m, blockIdx.y = a group of kCompsPerCta
+// components (a warp each). A CTA writes its components' sums to scratch; the
+// last CTA of a trajectory (ticket per trajectory) combines them into the
+// trajectory's partials, and the last trajectory to finish (global ticket)
+// sums the partials in trajectory order. No CTA waits for another.
 template <int KT, bool MS = false>
 __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(const __grid_constant__ AdjointArgs a)
 {
@@ -209,8 +219,10 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(const __grid_const
     const int p1 = min(max(a.offsets[m + 1], p0), a.n_points);
     const int nsteps = max(p1 - p0 - 1, 0);
     const bool grad = a.want_grad != 0;
+    double *cA = a.comp_A + (size_t)m * J; // this trajectory's per-component sums
+    float *cG = a.comp_G + (size_t)m * J * 5;
 
-    for (int j = warp; j < J; j += nwarp) {
+    for (int j = blockIdx.y * nwarp + warp; j < min(J, (int)(blockIdx.y + 1) * nwarp); j += nwarp) {
         const int g = j / a.B, b = j - g * a.B;
         const float beta = a.beta[b];
         const float gx = a.goals[2 * g], gy = a.goals[2 * g + 1];
@@ -246,14 +258,28 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(const __grid_const
             Gw2 = wsum(Gw2);
         }
         if (lane == 0) {
-            A_s[j] = A;
-            G_s[j][0] = Gx;
-            G_s[j][1] = Gy;
-            G_s[j][2] = Gv;
-            G_s[j][3] = Gw1;
-            G_s[j][4] = Gw2;
+            cA[j] = A;
+            cG[5 * j + 0] = Gx;
+            cG[5 * j + 1] = Gy;
+            cG[5 * j + 2] = Gv;
+            cG[5 * j + 3] = Gw1;
+            cG[5 * j + 4] = Gw2;
         }
     }
+
+    // the last CTA of this trajectory combines its components
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(a.traj_ticket + m, 1u) == gridDim.y - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int j = threadIdx.x; j < J; j += blockDim.x) {
+        A_s[j] = ((volatile double *)cA)[j];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) G_s[j][c] = ((volatile float *)cG)[5 * j + c];
+    }
+    if (threadIdx.x == 0) a.traj_ticket[m] = 0u;
     __syncthreads();
 
     double *part = a.part + (size_t)m * P;
@@ -343,20 +369,43 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(const __grid_const
 
 } // namespace
 
-size_t adjoint_scratch_bytes(int M, int G) { return (size_t)M * (2 * G + 4) * sizeof(double); }
+// Scratch: per-trajectory partials [M][2G+4] doubles, per-component sums
+// [M][J] doubles and [M][J][5] floats, and one ticket word per trajectory.
+size_t adjoint_scratch_bytes(int M, int G, int J)
+{
+    return (size_t)M * (2 * G + 4) * sizeof(double) + (size_t)M * J * sizeof(double) +
+           (size_t)M * J * 5 * sizeof(float) + (size_t)M * sizeof(unsigned);
+}
+
+void adjoint_scratch_layout(void *base, int M, int G, int J, AdjointArgs &a)
+{
+    char *p = static_cast<char *>(base);
+    a.part = reinterpret_cast<double *>(p);
+    p += (size_t)M * (2 * G + 4) * sizeof(double);
+    a.comp_A = reinterpret_cast<double *>(p);
+    p += (size_t)M * J * sizeof(double);
+    a.comp_G = reinterpret_cast<float *>(p);
+    p += (size_t)M * J * 5 * sizeof(float);
+    a.traj_ticket = reinterpret_cast<unsigned *>(p);
+}
 
 cudaError_t launch_adjoint(const AdjointArgs &a, cudaStream_t s)
 {
+    // the per-trajectory tickets start at zero whatever an earlier call left
+    cudaError_t e = cudaMemsetAsync(a.traj_ticket, 0, (size_t)a.M * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    const int J = a.G * a.B;
+    const dim3 grid((unsigned)a.M, (unsigned)((J + kAdjThreads / 32 - 1) / (kAdjThreads / 32)));
     if (a.sp.S > 0) {
-        adjoint_kernel<8, true><<<a.M, kAdjThreads, 0, s>>>(a);
+        adjoint_kernel<8, true><<<grid, kAdjThreads, 0, s>>>(a);
         return cudaGetLastError();
     }
     const int KT = rollout_kt_for(a.K);
     switch (KT) {
-    case 8: adjoint_kernel<8><<<a.M, kAdjThreads, 0, s>>>(a); break;
-    case 16: adjoint_kernel<16><<<a.M, kAdjThreads, 0, s>>>(a); break;
-    case 36: adjoint_kernel<36><<<a.M, kAdjThreads, 0, s>>>(a); break;
-    default: adjoint_kernel<64><<<a.M, kAdjThreads, 0, s>>>(a); break;
+    case 8: adjoint_kernel<8><<<grid, kAdjThreads, 0, s>>>(a); break;
+    case 16: adjoint_kernel<16><<<grid, kAdjThreads, 0, s>>>(a); break;
+    case 36: adjoint_kernel<36><<<grid, kAdjThreads, 0, s>>>(a); break;
+    default: adjoint_kernel<64><<<grid, kAdjThreads, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }

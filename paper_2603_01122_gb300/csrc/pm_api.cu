@@ -419,7 +419,7 @@ pm_status loglik_impl(pm_ctx *ctx, const pm_model *model, int32_t M, const int32
     DeviceScope dev(ctx->device);
     st = ensure_posterior_scratch(ctx, 0); // allocates the ticket word
     if (st != PM_OK) return st;
-    const size_t bytes = pm::adjoint_scratch_bytes(M, model->G);
+    const size_t bytes = pm::adjoint_scratch_bytes(M, model->G, model->G * model->B);
     if (ctx->adj_scratch_bytes < bytes) {
         if (ctx->adj_scratch) cudaFree(ctx->adj_scratch);
         ctx->adj_scratch = nullptr;
@@ -460,7 +460,7 @@ pm_status loglik_impl(pm_ctx *ctx, const pm_model *model, int32_t M, const int32
     a.log_prior = log_prior;
     a.want_grad = want_grad ? 1 : 0;
     a.grad_out = grad_out;
-    a.part = (double *)ctx->adj_scratch;
+    pm::adjoint_scratch_layout(ctx->adj_scratch, M, model->G, model->G * model->B, a);
     a.ticket = ctx->ticket + 1; // its own word of the ticket block
     a.status = status_word(ctx);
     a.loglik = loglik;

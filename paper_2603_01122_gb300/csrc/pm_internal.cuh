@@ -224,6 +224,9 @@ struct AdjointArgs {
     int want_grad;
     float grad_out;
     double *part;          // scratch [M][2G+4]
+    double *comp_A;        // scratch [M][J]: sum_t log pi per component
+    float *comp_G;         // scratch [M][J][5]: the component's gradient sums
+    unsigned *traj_ticket; // scratch [M]: CTAs of the trajectory finished (zeroed per call)
     unsigned *ticket;      // scratch ticket (0 between calls)
     unsigned *status;      // context status word (or NULL)
     float *loglik;
@@ -360,6 +363,7 @@ int batch_rollout_occupancy(int K, uint64_t enabled, int S, bool marks, const Ro
 size_t batch_warp_tables_bytes(int threads, bool multi_speed); // dynamic shared memory of the warp form
 cudaError_t launch_batch_rollout(const BatchArgs &a, const RolloutShape &shape, int blocks, size_t dyn, cudaStream_t s);
 cudaError_t launch_batch_zero(const BatchHuman *humans, const int *n_dev, int max_rows, int sm_count, cudaStream_t s);
-size_t adjoint_scratch_bytes(int M, int G);
+size_t adjoint_scratch_bytes(int M, int G, int J);
+void adjoint_scratch_layout(void *base, int M, int G, int J, AdjointArgs &a);
 
 } // namespace pm
