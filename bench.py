@@ -643,6 +643,9 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
         nsteps = int(traj.shape[0]) - ts.M
         out["differentiation"] = {"ms_per_backward": ms, "trajectory_steps_per_s": nsteps / (ms * 1e-3),
                                   "q_evals_per_s": nsteps * 40 * (ts.K + 1) / (ms * 1e-3),
+                                  # algorithmic SFU results: K + 1 distances and K exponentials
+                                  # per step and component
+                                  "sfu_roofline_frac": nsteps * 40 * (2 * ts.K + 1) / (ms * 1e-3) / sfu_peak,
                                   "config": "256 trajectories, lengths U{50..200}, K=36, 4 goals x 10 beta, "
                                             "loss + d/d(goals, speed, w1, w2)"}
     return out
