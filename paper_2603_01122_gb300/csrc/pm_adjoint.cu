@@ -21,7 +21,7 @@
 // them over trajectories in a fixed order and writes the outputs.
 #include <cuda_runtime.h>
 
-#include "pm_internal.cuh"
+#include "pm_kernels.cuh"
 
 namespace pm {
 namespace {

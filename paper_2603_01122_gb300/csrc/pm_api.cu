@@ -13,7 +13,7 @@
 #include <cuda_runtime.h>
 
 #include "pm.h"
-#include "pm_internal.cuh"
+#include "pm_kernels.cuh"
 
 struct pm_ctx {
     int device = 0;

@@ -14,7 +14,7 @@
 // start, particles, horizon and output differ per human.
 #include <cuda_runtime.h>
 
-#include "pm_internal.cuh"
+#include "pm_kernels.cuh"
 #include "pm_rollout_dev.cuh"
 
 namespace pm {

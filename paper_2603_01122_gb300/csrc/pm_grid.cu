@@ -27,7 +27,7 @@
 
 #include <cuda_runtime.h>
 
-#include "pm_internal.cuh"
+#include "pm_kernels.cuh"
 
 namespace pm {
 namespace {

@@ -2,7 +2,7 @@
 // special-function-unit throughput probe used as the roofline denominator.
 #include <cuda_runtime.h>
 
-#include "pm_internal.cuh"
+#include "pm_kernels.cuh"
 
 namespace pm {
 namespace {

@@ -16,7 +16,7 @@
 // in a fixed order (deterministic).
 #include <cuda_runtime.h>
 
-#include "pm_internal.cuh"
+#include "pm_kernels.cuh"
 
 namespace pm {
 namespace {

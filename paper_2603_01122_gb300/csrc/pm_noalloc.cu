@@ -11,7 +11,7 @@
 #include <cuda_runtime.h>
 
 #include "pm.h"
-#include "pm_internal.cuh"
+#include "pm_kernels.cuh"
 
 pm_status pm_internal_posterior_on_scratch(const pm_model *model, const float *obs_xy, int32_t n_obs,
                                            float *log_belief, float *part, unsigned *ticket, size_t part_bytes,

@@ -25,7 +25,7 @@
 // common to every component -- and resets the ticket for the next call.
 #include <cuda_runtime.h>
 
-#include "pm_internal.cuh"
+#include "pm_kernels.cuh"
 
 namespace pm {
 namespace {
