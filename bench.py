@@ -72,8 +72,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=20000, help="particles in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched / serving / adjoint sections")
-    ap.add_argument("--serving-seconds", type=float, default=0.0,
-                    help="also run the Poisson arrival process for this many simulated seconds")
+    ap.add_argument("--serving-seconds", type=float, default=60.0,
+                    help="run the Poisson arrival process for this many simulated seconds (0: skip)")
     ap.add_argument("--serving-frames", type=int, default=250, help="frames of the forced-64-live run")
     ap.add_argument("--sections", default="all", type=lambda v: set(v.split(",")),
                     help="extra sections to run: all, or a comma list of batched, serving, speeds, table1, "
