@@ -209,6 +209,7 @@ void fill_rollout_tables(const pm_model *m, pm::RolloutArgs &a)
         for (int sp = 0; sp < m->n_speeds; ++sp) {
             const double sl = (double)m->speed * (double)m->speed_mult[sp] * (double)m->dt;
             a.tab.mult[sp] = m->speed_mult[sp];
+            a.tab.inv_mult[sp] = 1.0f / m->speed_mult[sp];
             a.tab.sl[sp] = (float)sl;
             if (!((m->speed_off >> sp) & 1u)) {
                 a.tab.speed_on |= 1u << sp;

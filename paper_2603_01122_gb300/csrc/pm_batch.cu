@@ -283,6 +283,9 @@ cudaError_t batch_dispatch(const BatchArgs &a, const RolloutShape &sh, int block
         case 32:
             return a.marks ? launch_or_query(batch_warp_kernel<32, false, true, true>, a, blocks, sh.threads, dyn, s, occ)
                            : launch_or_query(batch_warp_kernel<32, false, true>, a, blocks, sh.threads, dyn, s, occ);
+        case 36:
+            return a.marks ? launch_or_query(batch_warp_kernel<36, false, true, true>, a, blocks, sh.threads, dyn, s, occ)
+                           : launch_or_query(batch_warp_kernel<36, false, true>, a, blocks, sh.threads, dyn, s, occ);
         default:
             return a.marks ? launch_or_query(batch_warp_kernel<0, false, true, true>, a, blocks, sh.threads, dyn, s, occ)
                            : launch_or_query(batch_warp_kernel<0, false, true>, a, blocks, sh.threads, dyn, s, occ);

@@ -133,6 +133,7 @@ struct HeadingTab {
     int S;
     uint32_t speed_on;              // bit s: speed s enabled
     float mult[PM_MAX_SPEEDS];      // speed multipliers
+    float inv_mult[PM_MAX_SPEEDS];  // 1 / mult (FP32)
     float sl[PM_MAX_SPEEDS];        // v*mult[s]*dt
     float msx[PM_MAX_SPEEDS][kMaxK]; // Euler step of control (s, k), rounded once from double
     float msy[PM_MAX_SPEEDS][kMaxK];

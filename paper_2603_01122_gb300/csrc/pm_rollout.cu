@@ -198,6 +198,7 @@ cudaError_t dispatch(const RolloutArgs &a, unsigned *head, int sm_count, cudaStr
         switch (a.K) {
         case 16: return launch_multi<16>(a, head, sm_count, s, occ);
         case 32: return launch_multi<32>(a, head, sm_count, s, occ);
+        case 36: return launch_multi<36>(a, head, sm_count, s, occ);
         default: return launch_multi<0>(a, head, sm_count, s, occ);
         }
     }

@@ -196,17 +196,22 @@ struct LbStep {
     float ref;    // reference distance (see above)
 };
 
-__device__ __forceinline__ LbStep lb_step(const HeadingTab &tab, float s2, float x, float y, float gx, float gy,
-                                          float cb)
+__device__ __forceinline__ LbStep lb_step_d(const HeadingTab &tab, float s2, float dx, float dy, float cb)
 {
     LbStep q;
-    q.dx = x - gx;
-    q.dy = y - gy;
+    q.dx = dx;
+    q.dy = dy;
     q.D = fmaf(q.dx, q.dx, fmaf(q.dy, q.dy, s2));
     q.r = sqrt_approx(fmaf(q.dx, q.dx, q.dy * q.dy));
     const float margin = (q.r + tab.s) * 0x1p-20f;
     q.ref = (cb >= 0.0f) ? fabsf(q.r - tab.s) - margin : q.r + tab.s + margin;
     return q;
+}
+
+__device__ __forceinline__ LbStep lb_step(const HeadingTab &tab, float s2, float x, float y, float gx, float gy,
+                                          float cb)
+{
+    return lb_step_d(tab, s2, x - gx, y - gy, cb);
 }
 
 // Segments of the running sums of the inverse CDF: KT/G segments of G
@@ -822,6 +827,8 @@ __device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t ena
     const bool trc = c.i < c.n_trace;
     float x = c.z0x, y = c.z0y, cb = 0.0f, gx = 0.0f, gy = 0.0f, cw = 0.0f;
     bool lb = false;
+    // several speeds with exactly one enabled: its index (else -1)
+    const int one_speed = (MS && __popc(speed_on) == 1) ? __ffs((int)speed_on) - 1 : -1;
     if (act) {
         const U64x4 r = philox4x64_10(U64x4{i, 0ull, kPurposeSelect, 0ull}, c.seed, c.human);
         const uint32_t thr = (uint32_t)(((uint64_t)((uint32_t)r.a >> 8) * (uint64_t)cdf[c.J - 1]) >> 24);
@@ -857,8 +864,19 @@ __device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t ena
             int k;
             if constexpr (MS) {
                 if constexpr (KT > 0) { // K == KT, all headings enabled: the fused form where it applies
-                    if (lb) k = draw_multi_lb<KT>(tab, speed_on, x, y, gx, gy, cb, cw, word);
-                    else k = draw_multi(tab, speed_on, K, x, y, gx, gy, cb, cw, lb, word);
+                    if (lb && one_speed >= 0) {
+                        // one enabled speed m (a human standing still keeps only the
+                        // slow one): ||z + s m e_k - g|| = m ||(z - g) / m + s e_k||, so
+                        // the one-speed draw at the scaled offset with cb m draws the
+                        // same policy (the speed term is common to every control)
+                        const float im = tab.inv_mult[one_speed], cbm = cb * tab.mult[one_speed];
+                        k = one_speed * KT +
+                            draw_heading_lb<KT>(tab, lb_step_d(tab, s2, (x - gx) * im, (y - gy) * im, cbm), cbm, word);
+                    } else if (lb) {
+                        k = draw_multi_lb<KT>(tab, speed_on, x, y, gx, gy, cb, cw, word);
+                    } else {
+                        k = draw_multi(tab, speed_on, K, x, y, gx, gy, cb, cw, lb, word);
+                    }
                 } else {
                     k = draw_multi(tab, speed_on, K, x, y, gx, gy, cb, cw, lb, word);
                 }

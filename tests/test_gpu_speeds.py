@@ -39,7 +39,7 @@ def _models(orc, K, speed, dt, goals, beta, speeds, speed_off=0, w1=1.0, w2=1.0,
     return m, gh
 
 
-CASES = ["U96", "stationary", "U256", "one_mult", "w1_3", "beta_neg_large", "beta_large", "ragged"]
+CASES = ["U96", "stationary", "U256", "K36_U108", "one_mult", "w1_3", "beta_neg_large", "beta_large", "ragged"]
 
 
 @pytest.mark.parametrize("case", CASES)
@@ -50,6 +50,8 @@ def test_trajectories_and_histogram(ctx, orc, case):
     rng = np.random.default_rng(zlib.crc32(case.encode()))
     if case == "U256":
         K, speeds = 64, (0.25, 0.5, 1.0, 2.0)
+    elif case == "K36_U108":
+        K = 36
     elif case == "one_mult":
         K, speeds = 8, (1.5,)
     elif case == "w1_3":
