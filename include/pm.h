@@ -197,6 +197,27 @@ pm_status pm_predict_host(pm_ctx *ctx, const pm_model *model, const float *goals
                           float *posterior_out, uint32_t *counts_out, uint32_t *oob_out,
                           void *stream);
 
+/* The same prediction without waiting, for a caller that issues one
+ * prediction after another: the inputs are copied in and the prediction runs
+ * on `stream` in one of two device staging slots of the context (alternating
+ * per call), and the posterior and histogram are copied out on a copy stream
+ * of the context, so that a call's copy-out overlaps the next call's
+ * prediction. The outputs of a call are complete once pm_host_fence has made
+ * a stream wait for the pending copies and that stream has been synchronised.
+ * The host buffers must stay valid, and must not be reused by the caller, until
+ * then; the inputs are read when `stream` reaches the call. Host buffers as
+ * pm_predict_host (page-locked: pageable ones make the copies synchronous). */
+pm_status pm_predict_host_async(pm_ctx *ctx, const pm_model *model, const float *goals,
+                                const float *beta, const float *obs_xy, int32_t n_obs,
+                                const float *log_prior, int32_t n_particles, int32_t horizon,
+                                const pm_grid *grid, uint64_t seed, uint32_t human_id,
+                                float *posterior_out, uint32_t *counts_out, uint32_t *oob_out,
+                                void *stream);
+
+/* Make `stream` wait for every copy-out that pm_predict_host_async has queued
+ * on this context (no host wait). */
+pm_status pm_host_fence(pm_ctx *ctx, void *stream);
+
 /* ---- many humans in one launch -------------------------------------------- */
 
 /* One human of a batch. Device pointers unless stated.

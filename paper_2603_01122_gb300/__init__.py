@@ -82,6 +82,9 @@ def _signatures(lib):
                                          C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
         "pm_predict_host": ([_vp, P(pm_model), _vp, _vp, _vp, C.c_int32, _vp, C.c_int32, C.c_int32,
                              P(pm_grid), C.c_uint64, C.c_uint32, _vp, _vp, _vp, _vp], C.c_int),
+        "pm_predict_host_async": ([_vp, P(pm_model), _vp, _vp, _vp, C.c_int32, _vp, C.c_int32, C.c_int32,
+                                   P(pm_grid), C.c_uint64, C.c_uint32, _vp, _vp, _vp, _vp], C.c_int),
+        "pm_host_fence": ([_vp, _vp], C.c_int),
         "pm_batch_create": ([_vp, P(pm_model), C.c_int32, P(_vp)], C.c_int),
         "pm_batch_set": ([_vp, P(pm_human), C.c_int32, _vp], C.c_int),
         "pm_batch_update_posterior": ([_vp, _vp], C.c_int),
@@ -225,6 +228,21 @@ def pm_predict_host(ctx, model: pm_model, goals, beta, obs_xy, n_obs, log_prior,
                                      _hp(log_prior), int(n_particles), int(horizon), C.byref(grid),
                                      int(seed), int(human_id), _hp(posterior_out), _hp(counts_out),
                                      _hp(oob_out), _stream(stream)))
+
+
+def pm_predict_host_async(ctx, model: pm_model, goals, beta, obs_xy, n_obs, log_prior, n_particles,
+                          horizon, grid: pm_grid, seed, human_id, posterior_out, counts_out, oob_out,
+                          stream=None):
+    """pm_predict_host without waiting (pinned CPU tensors; the outputs are
+    complete after pm_host_fence and a synchronisation of the stream)."""
+    _check(library().pm_predict_host_async(ctx, C.byref(model), _hp(goals), _hp(beta), _hp(obs_xy), int(n_obs),
+                                           _hp(log_prior), int(n_particles), int(horizon), C.byref(grid),
+                                           int(seed), int(human_id), _hp(posterior_out), _hp(counts_out),
+                                           _hp(oob_out), _stream(stream)))
+
+
+def pm_host_fence(ctx, stream=None):
+    _check(library().pm_host_fence(ctx, _stream(stream)))
 
 
 def make_human(goals, beta, log_belief, z0_xy, n_particles, horizon, grid: pm_grid, seed, human_id,

@@ -31,6 +31,14 @@ struct pm_ctx {
     // scratch of the log-likelihood adjoint: per-trajectory partials
     void *adj_scratch = nullptr;
     size_t adj_scratch_bytes = 0;
+    // asynchronous host-buffer predictions: two staging slots, a copy stream,
+    // and per slot the event after which its copy-out has read it
+    void *slot[2] = {nullptr, nullptr};
+    size_t slot_bytes[2] = {0, 0};
+    cudaEvent_t slot_free[2] = {nullptr, nullptr};
+    cudaEvent_t computed = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    int next_slot = 0;
 };
 
 struct pm_batch {
@@ -784,6 +792,13 @@ void pm_destroy(pm_ctx *ctx)
         if (ctx->post_scratch) cudaFree(ctx->post_scratch);
         if (ctx->ticket) cudaFree(ctx->ticket);
         if (ctx->adj_scratch) cudaFree(ctx->adj_scratch);
+        if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
+        for (int i = 0; i < 2; ++i) {
+            if (ctx->slot[i]) cudaFree(ctx->slot[i]);
+            if (ctx->slot_free[i]) cudaEventDestroy(ctx->slot_free[i]);
+        }
+        if (ctx->computed) cudaEventDestroy(ctx->computed);
+        if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     }
     delete ctx;
 }
@@ -838,10 +853,17 @@ pm_status pm_predict_occupancy_traced(pm_ctx *ctx, const pm_model *model, const 
                         counts, oob, n_trace, states, headings, components, (cudaStream_t)stream);
 }
 
-pm_status pm_predict_host(pm_ctx *ctx, const pm_model *model, const float *goals, const float *beta,
-                          const float *obs_xy, int32_t n_obs, const float *log_prior, int32_t n_particles,
-                          int32_t horizon, const pm_grid *grid, uint64_t seed, uint32_t human_id,
-                          float *posterior_out, uint32_t *counts_out, uint32_t *oob_out, void *stream)
+namespace {
+
+// Host-buffer prediction on a device staging area `base` of `cap` bytes (or
+// the context's synchronous stage when base is NULL): inputs in, belief
+// update and rollout on `s`, outputs out on `out_stream` after `s` has
+// computed them (same stream: in order).
+pm_status predict_host_impl(pm_ctx *ctx, const pm_model *model, const float *goals, const float *beta,
+                            const float *obs_xy, int32_t n_obs, const float *log_prior, int32_t n_particles,
+                            int32_t horizon, const pm_grid *grid, uint64_t seed, uint32_t human_id,
+                            float *posterior_out, uint32_t *counts_out, uint32_t *oob_out, cudaStream_t s,
+                            int slot)
 {
     if (!ctx) return fail(PM_EINVAL, "ctx is NULL");
     pm_status st = check_model(model, false);
@@ -854,16 +876,44 @@ pm_status pm_predict_host(pm_ctx *ctx, const pm_model *model, const float *goals
     if (horizon < 1 || horizon > PM_MAX_HORIZON) return fail(PM_EINVAL, "horizon out of range");
     if (n_particles < 1) return fail(PM_EINVAL, "n_particles must be >= 1");
     DeviceScope dev(ctx->device);
-    cudaStream_t s = (cudaStream_t)stream;
     const int J = model->G * model->B;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t plane = (size_t)grid->W * (size_t)grid->H;
     const size_t b_goals = al((size_t)model->G * 2 * 4), b_beta = al((size_t)model->B * 4);
     const size_t b_obs = al((size_t)(n_obs + 1) * 2 * 4), b_lb = al((size_t)J * 4);
     const size_t b_counts = al(plane * (size_t)horizon * 4), b_oob = al((size_t)horizon * 4);
-    st = ensure_stage(ctx, b_goals + b_beta + b_obs + b_lb + b_counts + b_oob);
-    if (st != PM_OK) return st;
-    char *p = (char *)ctx->stage;
+    const size_t need = b_goals + b_beta + b_obs + b_lb + b_counts + b_oob;
+    char *p;
+    cudaStream_t out_stream = s;
+    if (slot < 0) {
+        st = ensure_stage(ctx, need);
+        if (st != PM_OK) return st;
+        p = (char *)ctx->stage;
+    } else {
+        cudaError_t e = cudaSuccess;
+        if (!ctx->copy_stream) e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+            if (!ctx->slot_free[i]) e = cudaEventCreateWithFlags(&ctx->slot_free[i], cudaEventDisableTiming);
+        if (e == cudaSuccess && !ctx->computed) e = cudaEventCreateWithFlags(&ctx->computed, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "copy stream or events");
+        // the slot's previous copy-out must have read it before it is refilled
+        e = cudaStreamWaitEvent(s, ctx->slot_free[slot], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "waiting for the staging slot");
+        if (ctx->slot_bytes[slot] < need) {
+            cudaStreamSynchronize(s); // the slot may still be read by an earlier copy-out
+            if (ctx->slot[slot]) cudaFree(ctx->slot[slot]);
+            ctx->slot[slot] = nullptr;
+            ctx->slot_bytes[slot] = 0;
+            e = cudaMalloc(&ctx->slot[slot], need);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(PM_ENOMEM, "cudaMalloc(%zu) for a staging slot failed", need);
+            }
+            ctx->slot_bytes[slot] = need;
+        }
+        p = (char *)ctx->slot[slot];
+        out_stream = ctx->copy_stream;
+    }
     float *d_goals = (float *)p; p += b_goals;
     float *d_beta = (float *)p; p += b_beta;
     float *d_obs = (float *)p; p += b_obs;
@@ -884,11 +934,59 @@ pm_status pm_predict_host(pm_ctx *ctx, const pm_model *model, const float *goals
     st = predict_impl(ctx, &m, d_lb, z0x, z0y, n_particles, horizon, grid, seed, human_id, d_counts, d_oob, 0,
                       nullptr, nullptr, nullptr, s);
     if (st != PM_OK) return st;
-    e = cudaMemcpyAsync(posterior_out, d_lb, (size_t)J * 4, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(counts_out, d_counts, plane * (size_t)horizon * 4, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(oob_out, d_oob, (size_t)horizon * 4, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (out_stream != s) {
+        e = cudaEventRecord(ctx->computed, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(out_stream, ctx->computed, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "ordering the copy-out");
+    }
+    e = cudaMemcpyAsync(posterior_out, d_lb, (size_t)J * 4, cudaMemcpyDeviceToHost, out_stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(counts_out, d_counts, plane * (size_t)horizon * 4, cudaMemcpyDeviceToHost, out_stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(oob_out, d_oob, (size_t)horizon * 4, cudaMemcpyDeviceToHost, out_stream);
+    if (e == cudaSuccess && slot >= 0) e = cudaEventRecord(ctx->slot_free[slot], out_stream);
     if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    return PM_OK;
+}
+
+} // namespace
+
+pm_status pm_predict_host(pm_ctx *ctx, const pm_model *model, const float *goals, const float *beta,
+                          const float *obs_xy, int32_t n_obs, const float *log_prior, int32_t n_particles,
+                          int32_t horizon, const pm_grid *grid, uint64_t seed, uint32_t human_id,
+                          float *posterior_out, uint32_t *counts_out, uint32_t *oob_out, void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    pm_status st = predict_host_impl(ctx, model, goals, beta, obs_xy, n_obs, log_prior, n_particles, horizon, grid,
+                                     seed, human_id, posterior_out, counts_out, oob_out, s, -1);
+    if (st != PM_OK) return st;
+    DeviceScope dev(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    return PM_OK;
+}
+
+pm_status pm_predict_host_async(pm_ctx *ctx, const pm_model *model, const float *goals, const float *beta,
+                                const float *obs_xy, int32_t n_obs, const float *log_prior, int32_t n_particles,
+                                int32_t horizon, const pm_grid *grid, uint64_t seed, uint32_t human_id,
+                                float *posterior_out, uint32_t *counts_out, uint32_t *oob_out, void *stream)
+{
+    if (!ctx) return fail(PM_EINVAL, "ctx is NULL");
+    const int slot = ctx->next_slot;
+    pm_status st = predict_host_impl(ctx, model, goals, beta, obs_xy, n_obs, log_prior, n_particles, horizon, grid,
+                                     seed, human_id, posterior_out, counts_out, oob_out, (cudaStream_t)stream, slot);
+    if (st == PM_OK) ctx->next_slot = slot ^ 1;
+    return st;
+}
+
+pm_status pm_host_fence(pm_ctx *ctx, void *stream)
+{
+    if (!ctx) return fail(PM_EINVAL, "ctx is NULL");
+    DeviceScope dev(ctx->device);
+    for (int i = 0; i < 2; ++i) {
+        if (!ctx->slot_free[i]) continue;
+        cudaError_t e = cudaStreamWaitEvent((cudaStream_t)stream, ctx->slot_free[i], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "fence");
+    }
     return PM_OK;
 }
 

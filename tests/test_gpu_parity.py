@@ -328,6 +328,39 @@ def test_host_api_matches_device_path(ctx, orc):
     np.testing.assert_array_equal(oob, want["oob"])
 
 
+def test_async_host_api_in_a_pipeline(ctx, orc):
+    """Five asynchronous host calls in a row (seeds and horizons vary, two
+    sets of pinned outputs alternate, a larger grid midway forces a staging
+    slot to grow): after the fence, each call's outputs equal the device path's
+    for the same inputs."""
+    import paper_2603_01122_gb300 as pm
+    hu = workloads.paper_scale()
+    m, obs, post = _obs_and_post(orc, hu)
+    gh = GpuHuman.of(hu)
+    lb = posterior(ctx, gh, obs, hu.uniform_log_prior())
+    x0, y0, res, W, H = hu.grid
+    N = 8000
+    calls = [(60, hu.seed, W, H), (40, hu.seed + 1, W, H), (60, hu.seed + 2, W + 64, H + 32), (20, hu.seed + 3, W, H),
+             (60, hu.seed + 4, W, H)]
+    outs = []
+    stream = torch.cuda.Stream()
+    for i, (T, seed, Wc, Hc) in enumerate(calls):
+        o = (torch.zeros(hu.G * hu.B, dtype=torch.float32).pin_memory(),
+             torch.zeros((T, Hc, Wc), dtype=torch.int32).pin_memory(), torch.zeros(T, dtype=torch.int32).pin_memory())
+        outs.append(o)
+        pm.pm_predict_host_async(ctx, gh.model, torch.tensor(hu.goals).pin_memory(), torch.tensor(hu.beta).pin_memory(),
+                                 torch.tensor(obs).pin_memory(), hu.n_obs,
+                                 torch.tensor(hu.uniform_log_prior()).pin_memory(), N, T,
+                                 pm.make_grid(x0, y0, res, Wc, Hc), seed, hu.human_id, o[0], o[1], o[2], stream)
+    pm.pm_host_fence(ctx, stream)
+    stream.synchronize()
+    for (T, seed, Wc, Hc), o in zip(calls, outs):
+        want = predict(ctx, gh, lb, obs[-1], N, T, (x0, y0, res, Wc, Hc), seed, hu.human_id)
+        np.testing.assert_array_equal(o[0].numpy(), lb)
+        np.testing.assert_array_equal(o[1].numpy().view(np.uint32), want["counts"])
+        np.testing.assert_array_equal(o[2].numpy().view(np.uint32), want["oob"])
+
+
 def test_invalid_arguments_rejected(ctx):
     import paper_2603_01122_gb300 as pm
     hu = workloads.plain_small()
