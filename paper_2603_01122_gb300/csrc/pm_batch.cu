@@ -1,17 +1,24 @@
 // pm_batch.cu -- many humans in one persistent launch.
 //
-// The work list holds tiles (human, first particle) of blockDim particles,
-// sorted on the host by horizon (longest first). A grid of SMs x CTAs-per-SM
-// persistent CTAs takes tiles from a global counter (one atomicAdd per tile,
-// no waiting), loads the human's component table and belief CDF into shared
-// memory when the human changes, places the shared-memory histogram window
-// around the human's start cell and runs Algorithm 1 for the tile with the
+// The work list holds tiles (human, first particle), sorted on the host by
+// horizon (longest first). A grid of SMs x CTAs-per-SM persistent CTAs (or
+// warps) takes tiles from a global counter (one atomicAdd per tile, no
+// waiting), loads the human's component table and belief CDF into shared
+// memory when the human changes and runs Algorithm 1 for the tile with the
 // same device code as the single-human kernel, so each human's histogram is
 // bit-identical alone and in the mix (its random numbers are keyed on
 // (seed, human_id, particle) only and the counts are integer sums).
-// Every human of a batch shares K, v, dt, w and the disabled headings (the
-// heading tables live in the kernel parameters); goals, beta grid, belief,
-// start, particles, horizon and output differ per human.
+// Every human of a batch shares K, v, dt, w, the speeds and the disabled
+// headings (the heading tables live in the kernel parameters); goals, beta
+// grid, belief, start, particles, horizon, output and the speeds masked for
+// the human differ per human.
+//
+// Two forms: batch_warp_kernel (persistent warps take 32-particle tiles and
+// emplace with warp-combined global reductions; optionally also mark the
+// occupied 16 x 16-cell blocks for the union epilogue) and
+// batch_rollout_kernel (CTAs take tiles of blockDim particles and count each
+// step in a shared-memory window around the human's start cell). The
+// autotuner times both.
 #include <cuda_runtime.h>
 
 #include "pm_kernels.cuh"

@@ -19,6 +19,9 @@
 // is binned with FP32 operations (x - x0) * inv_res and the lanes of the warp
 // that land in the same cell are combined (match.any) into one global
 // reduction per cell and step.
+// rollout_multi_kernel<KT> is the same kernel for a control set of several
+// speeds (controls = speeds x headings, Sec. IV-B): the fused per-speed draw
+// for K = KT, the general one for any K (KT = 0).
 #include <cuda_runtime.h>
 
 #include "pm_internal.cuh"
