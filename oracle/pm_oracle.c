@@ -19,17 +19,17 @@
  *   orc_loglik_grad     marginal log-likelihood of observed trajectories and its
  *                       analytic gradient (built on Eq. 2 / Eq. 3)
  *
- * Readings of points the paper leaves open (each listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - Q(z, theta; g) = -w1*v*dt - w2*|| z + v*dt*(cos theta, sin theta) - g ||,
  *     evaluated at the next state (the running example's Q is heading-free).
  *   - K headings theta_k = 2*pi*k/K, counter-clockwise from +x; the controls
  *     are those headings at speeds v*mult[s] (one speed, mult = {1}, unless
  *     given), index u = s*K + k; a disabled heading or speed has Q = -inf.
- *   - the observed control: the continuous heading of the displacement and the
- *     enabled speed whose multiplier is nearest to its length / (v*dt).
  *   - the observed control is the continuous heading atan2(dy, dx) of the
- *     displacement; Q is evaluated there and normalised over the K headings;
- *     a displacement shorter than 1e-6 m leaves the belief unchanged.
+ *     displacement at the enabled speed whose multiplier is nearest to its
+ *     length / (v*dt) (ties: the lower index); Q is evaluated there and
+ *     normalised over the controls; a displacement shorter than 1e-6 m leaves
+ *     the belief unchanged.
  *   - belief index j = g*B + b (goal-major).
  *   - inverse-CDF sampling: smallest k with u*S < C_k, C_k the running sum in
  *     index order, S the total; u = (32-bit word >> 8) * 2^-24.
