@@ -21,7 +21,8 @@ room grid centred on the human's cell (Algorithm 1, bootstrapped belief).
   controls that ``stationary_off`` leaves enabled (Sec. IV-B), set per human
   by ``set_stationary`` or, with ``stationary_eps``, from its last observed
   step; a change re-uploads the descriptors only. ``reset_belief`` returns a
-  human to the uniform belief when it leaves a goal.
+  human to the uniform belief; with ``goal_radius`` the server does so itself
+  when a human leaves a goal (``GoalDeparture``).
 * Latency = host wall time from the start of the frame (observations in host
   memory) to the occupancy being ready on the device (event synchronised).
 
@@ -71,6 +72,28 @@ class SlotTable:
         self.free.sort(reverse=True)
 
 
+@dataclasses.dataclass
+class GoalDeparture:
+    """Detects that a human has left a goal (host logic only): after one of its
+    observed states came within ``radius`` of a goal, the first observed
+    state farther than ``radius`` from every goal is a departure (the
+    belief is then reset to uniform, Sec. IV-B)."""
+    goals: np.ndarray
+    radius: float
+
+    def __post_init__(self):
+        self.goals = np.asarray(self.goals, np.float64).reshape(-1, 2)
+        self.at_goal = False
+
+    def update(self, xy) -> bool:
+        """Feed the newest observed state; True on a departure."""
+        d = np.hypot(*(self.goals - np.asarray(xy, np.float64)[None, :]).T)
+        near = bool((d <= self.radius).any())
+        left = self.at_goal and not near
+        self.at_goal = near
+        return left
+
+
 class Server:
     """Device-resident serving state for up to ``max_live`` humans sharing K, v,
     dt, w and the room grid; per-human goals (up to ``g_max``) and beta grid
@@ -79,7 +102,7 @@ class Server:
     def __init__(self, ctx, K, speed, dt, room_grid, *, max_live=64, budget_bytes=4 << 30,
                  n_particles=50_000, horizon=150, window=121, g_max=6, b_max=10, w1=1.0, w2=1.0,
                  use_graph=True, device="cuda:0", union_sigma=None, speeds=None, stationary_off=0,
-                 stationary_eps=None):
+                 stationary_eps=None, goal_radius=None):
         import torch
 
         self.torch = torch
@@ -111,6 +134,7 @@ class Server:
             raise ValueError("stationary masking needs several speeds")
         self.stationary_off = int(stationary_off)
         self.stationary_eps = stationary_eps
+        self.goal_radius = goal_radius
         self._shared = make_model(K, speed, dt, shared_goals, shared_beta, w1=w1, w2=w2, speeds=self.speeds)
         self.batch = pm_batch_create(ctx, self._shared, cap)
         if union_sigma is not None:  # the union reads only the blocks the rollout marks
@@ -144,7 +168,8 @@ class Server:
         with t.cuda.stream(self.stream):
             self.goals[s, :G].copy_(t.as_tensor(np.asarray(goals, np.float32)))
             self.beta[s, :B].copy_(t.as_tensor(np.asarray(beta, np.float32)))
-        self.meta[s] = dict(key=key, G=G, B=B, seed=int(seed), human_id=int(human_id), speed_off=0)
+        self.meta[s] = dict(key=key, G=G, B=B, seed=int(seed), human_id=int(human_id), speed_off=0,
+                            departure=None if self.goal_radius is None else GoalDeparture(goals, self.goal_radius))
         self.reset_belief(s)
         self.obs_host[s, 0] = t.as_tensor(np.asarray(start, np.float32))
         self.obs_host[s, 1] = self.obs_host[s, 0]
@@ -178,6 +203,9 @@ class Server:
         if self.stationary_eps is not None:
             step = self.obs_host[slot, 1] - self.obs_host[slot, 0]
             self.set_stationary(slot, float(step.norm()) < self.stationary_eps)
+        dep = self.meta[slot]["departure"]
+        if dep is not None and dep.update(xy):
+            self.reset_belief(slot)
 
     # -- frames ------------------------------------------------------------------
     def _humans(self):

@@ -155,3 +155,30 @@ def test_serving_stationary_masking(ctx, orc):
                                               full.cpu().numpy()[:, oy:oy + win, ox:ox + win])
     finally:
         srv.close()
+
+
+def test_serving_resets_the_belief_when_a_human_leaves_a_goal(ctx):
+    """With goal_radius, a human that reaches a goal and then moves away has its
+    belief reset to uniform (Sec. IV-B) before the next frame's update."""
+    from paper_2603_01122_gb300.serving import Server
+    hu = workloads.paper_scale()
+    srv = Server(ctx, hu.K, hu.speed, hu.dt, hu.grid, max_live=2, n_particles=2000, horizon=20, window=31,
+                 goal_radius=0.1)
+    try:
+        g0 = np.asarray(hu.goals[0], np.float64)
+        s = srv.admit("a", hu.goals, hu.beta, (g0 - [0.5, 0.0]).astype(np.float32), hu.seed, 7)
+        J = hu.G * hu.B
+        for k in range(1, 26):  # walk onto the goal along +x
+            srv.observe(s, (g0 + [-0.5 + 0.02 * k, 0.0]).astype(np.float32))
+            srv.frame()
+        torch.cuda.synchronize()
+        lb = srv.log_b[s, :J].cpu().numpy()
+        assert np.max(np.abs(lb - (-np.log(J)))) > 1e-3  # the walk has informed the belief
+        for k in range(1, 5):  # leave it along +y: the fourth step (0.12 m) passes the radius
+            srv.observe(s, (g0 + [0.0, 0.03 * k]).astype(np.float32))
+            if k < 4:
+                srv.frame()
+        srv.stream.synchronize()
+        np.testing.assert_allclose(srv.log_b[s, :J].cpu().numpy(), -np.log(J), rtol=0, atol=1e-6)
+    finally:
+        srv.close()
