@@ -78,6 +78,8 @@ struct UnionSmem {
     unsigned live[kSrcChunk / 32];
     int list[kSrcChunk];    // the live sources, in order
     int n_live;
+    int4 cand[kSrcChunk];   // sources whose widened window meets the tile: (index, bx0, by0, nbx | nby << 16)
+    int n_cand;
 };
 
 template <int RB>
@@ -185,28 +187,40 @@ __global__ void __launch_bounds__(kGridThreads, (RB >= 1 && RB <= 8) ? 3 : 2)
     for (int c0 = 0; c0 < n; c0 += kSrcChunk) {
         const int nc = min(kSrcChunk, n - c0);
         __syncthreads(); // the previous chunk's records and buffers are no longer read
-        if (tid < nc) sm.S[tid] = a.srcs ? a.srcs[c0 + tid] : a.single;
         if (tid < kSrcChunk / 32) sm.live[tid] = 0u;
+        if (tid == 0) sm.n_cand = 0;
         __syncthreads();
-        // Which sources reach the tile: the widened window must meet it, and
-        // where the source carries block flags one of the blocks under the
-        // widened tile must hold a particle at step t. All sources' flags are
-        // read in one pass, so a tile costs one round trip, not one per source.
-        for (int p = tid; p < nc * BX * BY; p += kGridThreads) {
-            const int si = p / (BX * BY), b = p - si * (BX * BY);
-            const SmoothSrc &q = sm.S[si];
+        // Which sources reach the tile: the widened window must meet it (one
+        // thread per source), and where the source carries block flags one of
+        // the blocks under the widened tile must hold a particle at step t.
+        // All candidates' flags are read in one pass, so a tile costs one
+        // round trip, not one per source.
+        if (tid < nc) {
+            const SmoothSrc q = a.srcs ? a.srcs[c0 + tid] : a.single;
+            sm.S[tid] = q;
             const int wx0 = X0 - RB - q.ox, wy0 = Y0 - RB - q.oy;
             const int xlo = max(wx0, 0), xhi = min(wx0 + AW, q.W), ylo = max(wy0, 0), yhi = min(wy0 + AH, q.H);
-            if (t >= q.T || xlo >= xhi || ylo >= yhi) continue;
+            if (t < q.T && xlo < xhi && ylo < yhi) {
+                const int bx0 = xlo >> kFlagShift, by0 = ylo >> kFlagShift;
+                const int nbx = ((xhi - 1) >> kFlagShift) - bx0 + 1, nby = ((yhi - 1) >> kFlagShift) - by0 + 1;
+                sm.cand[atomicAdd(&sm.n_cand, 1)] = make_int4(tid, bx0, by0, nbx | (nby << 16));
+            }
+        }
+        __syncthreads();
+        const int ncand = sm.n_cand;
+        for (int p = tid; p < ncand * BX * BY; p += kGridThreads) {
+            const int ci = p / (BX * BY), b = p - ci * (BX * BY);
+            const int4 cd = sm.cand[ci];
+            const SmoothSrc &q = sm.S[cd.x];
             bool hit;
             if (!q.flags) {
                 hit = b == 0;
             } else {
-                const int bx = (xlo >> kFlagShift) + b % BX, by = (ylo >> kFlagShift) + b / BX;
-                hit = bx <= ((xhi - 1) >> kFlagShift) && by <= ((yhi - 1) >> kFlagShift) &&
-                      q.flags[((size_t)t * q.fby + by) * q.fbx + bx] != 0u;
+                const int bxr = b % BX, byr = b / BX;
+                hit = bxr < (cd.w & 0xFFFF) && byr < (cd.w >> 16) &&
+                      q.flags[((size_t)t * q.fby + cd.z + byr) * q.fbx + cd.y + bxr] != 0u;
             }
-            if (hit) atomicOr(&sm.live[si >> 5], 1u << (si & 31));
+            if (hit) atomicOr(&sm.live[cd.x >> 5], 1u << (cd.x & 31));
         }
         __syncthreads();
         if (tid == 0) { // the live sources in order
