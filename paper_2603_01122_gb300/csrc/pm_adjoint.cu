@@ -113,6 +113,101 @@ __device__ __forceinline__ StepGrad step_terms(const AdjointArgs &a, float zx, f
     return r;
 }
 
+// The same terms for KT (even) headings that are all enabled, on packed FP32
+// pairs of consecutive headings (the same IEEE operations per element as
+// step_terms, in half the issue slots; only the order of the final sums of
+// the expectations differs: two interleaved partial sums).
+template <int KT>
+__device__ __forceinline__ StepGrad step_terms_full(const AdjointArgs &a, float zx, float zy, float ex, float ey,
+                                                    float gx, float gy, float beta, bool grad)
+{
+    static_assert(KT % 2 == 0, "pairs of headings");
+    const float px = zx - gx, py = zy - gy;
+    const float D = fmaf(px, px, fmaf(py, py, a.s2));
+    const float xo = fmaxf(D + a.two_s * fmaf(ex, px, ey * py), 0.0f);
+    const float ro = rsqrtf(fmaxf(xo, 1e-30f));
+    const float d_o = xo * ro;
+    const float bw = beta * a.w2;
+    const float bw2 = bw * kLog2e;
+    const f32x2 *UX = reinterpret_cast<const f32x2 *>(a.ux);
+    const f32x2 *UY = reinterpret_cast<const f32x2 *>(a.uy);
+    const f32x2 PX = f2_pack(px, px), PY = f2_pack(py, py), EX = f2_pack(ex, ex), EY = f2_pack(ey, ey);
+    const f32x2 DD = f2_pack(D, D), TS = f2_pack(a.two_s, a.two_s), DO = f2_pack(d_o, d_o);
+    const f32x2 BW2 = f2_pack(bw2, bw2);
+    // X_k = D + 2 s e_k.(z - g), its reciprocal square root, d_k = X_k rsqrt(X_k)
+    auto dist = [&](int k2, f32x2 &X, f32x2 &RK) {
+        const f32x2 PU = f2_fma(UX[k2], PX, f2_mul(UY[k2], PY));
+        float x0, x1;
+        f2_unpack(f2_fma(TS, PU, DD), x0, x1);
+        x0 = fmaxf(x0, 0.0f);
+        x1 = fmaxf(x1, 0.0f);
+        X = f2_pack(x0, x1);
+        RK = f2_pack(rsqrtf(fmaxf(x0, 1e-30f)), rsqrtf(fmaxf(x1, 1e-30f)));
+    };
+    f32x2 LG[KT / 2];
+    float m = -INFINITY;
+#pragma unroll
+    for (int k2 = 0; k2 < KT / 2; ++k2) {
+        f32x2 X, RK;
+        dist(k2, X, RK);
+        const f32x2 DK = f2_mul(X, RK);
+        // beta w2 (d_obs - d_k) in base 2, formed as a difference of squares
+        const f32x2 NUM = f2_mul(TS, f2_fma(f2_sub(EX, UX[k2]), PX, f2_mul(f2_sub(EY, UY[k2]), PY)));
+        float q0, q1, n0, n1;
+        f2_unpack(f2_add(DO, DK), q0, q1);
+        f2_unpack(NUM, n0, n1);
+        LG[k2] = f2_mul(BW2, f2_pack(__fdividef(n0, fmaxf(q0, 1e-30f)), __fdividef(n1, fmaxf(q1, 1e-30f))));
+        float l0, l1;
+        f2_unpack(LG[k2], l0, l1);
+        m = fmaxf(m, fmaxf(l0, l1));
+    }
+    f32x2 SS = f2_pack(0.0f, 0.0f);
+    const f32x2 NM = f2_pack(-m, -m);
+#pragma unroll
+    for (int k2 = 0; k2 < KT / 2; ++k2) {
+        float l0, l1;
+        f2_unpack(f2_add(LG[k2], NM), l0, l1);
+        LG[k2] = f2_pack(ex2_approx(l0), ex2_approx(l1));
+        SS = f2_add(SS, LG[k2]);
+    }
+    float s0, s1;
+    f2_unpack(SS, s0, s1);
+    const float S = s0 + s1;
+    StepGrad r;
+    r.logpi = -(m + log2f(S)) * kLn2;
+    if (!grad) return r;
+    const float inv = 1.0f / S;
+    const f32x2 INV = f2_pack(inv, inv), SV = f2_pack(a.s, a.s);
+    f32x2 SUX = f2_pack(0.f, 0.f), SUY = SUX, SEU = SUX, SD = SUX, SP = SUX;
+#pragma unroll
+    for (int k2 = 0; k2 < KT / 2; ++k2) {
+        const f32x2 PK = f2_mul(LG[k2], INV);
+        f32x2 X, RK;
+        dist(k2, X, RK);
+        const f32x2 DK = f2_mul(X, RK);
+        const f32x2 UXK = f2_mul(f2_fma(SV, UX[k2], PX), RK), UYK = f2_mul(f2_fma(SV, UY[k2], PY), RK);
+        SUX = f2_fma(PK, UXK, SUX);
+        SUY = f2_fma(PK, UYK, SUY);
+        SEU = f2_fma(PK, f2_fma(UX[k2], UXK, f2_mul(UY[k2], UYK)), SEU);
+        SD = f2_fma(PK, DK, SD);
+        SP = f2_add(SP, PK);
+    }
+    auto fold = [](f32x2 v) {
+        float lo, hi;
+        f2_unpack(v, lo, hi);
+        return lo + hi;
+    };
+    const float sux = fold(SUX), suy = fold(SUY), seu = fold(SEU), sd = fold(SD), sp = fold(SP);
+    const float qox = fmaf(a.s, ex, px), qoy = fmaf(a.s, ey, py);
+    const float uox = qox * ro, uoy = qoy * ro;
+    r.gx = bw * (uox - sux);
+    r.gy = bw * (uoy - suy);
+    r.gv = bw * a.dt * (seu - fmaf(ex, uox, ey * uoy));
+    r.gw1 = beta * a.v * a.dt * (sp - 1.0f); // dQ/dw1 is the same for every heading
+    r.gw2 = beta * (sd - d_o);
+    return r;
+}
+
 // Several speeds (control u = speed q x heading k moving sl_q = v m_q dt):
 // Q_u = -w1 v m_q dt - w2 d_u, so
 //   dQ_u/dg = w2 u_u, dQ_u/dv = -m_q dt (w1 + w2 e_k.u_u), dQ_u/dw1 = -v m_q dt,
@@ -196,7 +291,8 @@ __device__ __forceinline__ StepGrad step_terms_ms(const AdjointArgs &a, const fl
 // last CTA of a trajectory (ticket per trajectory) combines them into the
 // trajectory's partials, and the last trajectory to finish (global ticket)
 // sums the partials in trajectory order. No CTA waits for another.
-template <int KT, bool MS = false>
+// FULL: KT headings, all enabled (the packed step_terms_full).
+template <int KT, bool MS = false, bool FULL = false>
 __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(const __grid_constant__ AdjointArgs a)
 {
     __shared__ double A_s[kMaxJ];
@@ -238,8 +334,10 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(const __grid_const
                 continue;
             }
             if (!(len >= 1e-6f)) continue; // stationary step: no information
-            const StepGrad s = MS ? step_terms_ms(a, cu, U, zx, zy, dx / len, dy / len, len, gx, gy, beta, grad)
-                                  : step_terms<KT>(a, zx, zy, dx / len, dy / len, gx, gy, beta, grad);
+            StepGrad s;
+            if constexpr (MS) s = step_terms_ms(a, cu, U, zx, zy, dx / len, dy / len, len, gx, gy, beta, grad);
+            else if constexpr (FULL) s = step_terms_full<KT>(a, zx, zy, dx / len, dy / len, gx, gy, beta, grad);
+            else s = step_terms<KT>(a, zx, zy, dx / len, dy / len, gx, gy, beta, grad);
             A += (double)s.logpi;
             if (grad) {
                 Gx += s.gx;
@@ -401,11 +499,17 @@ cudaError_t launch_adjoint(const AdjointArgs &a, cudaStream_t s)
         return cudaGetLastError();
     }
     const int KT = rollout_kt_for(a.K);
+    const uint64_t all = (KT >= 64) ? ~0ull : ((1ull << KT) - 1ull);
+    const bool full = a.K == KT && (a.enabled & all) == all;
     switch (KT) {
-    case 8: adjoint_kernel<8><<<grid, kAdjThreads, 0, s>>>(a); break;
-    case 16: adjoint_kernel<16><<<grid, kAdjThreads, 0, s>>>(a); break;
-    case 36: adjoint_kernel<36><<<grid, kAdjThreads, 0, s>>>(a); break;
-    default: adjoint_kernel<64><<<grid, kAdjThreads, 0, s>>>(a); break;
+    case 8: full ? adjoint_kernel<8, false, true><<<grid, kAdjThreads, 0, s>>>(a)
+                 : adjoint_kernel<8><<<grid, kAdjThreads, 0, s>>>(a); break;
+    case 16: full ? adjoint_kernel<16, false, true><<<grid, kAdjThreads, 0, s>>>(a)
+                  : adjoint_kernel<16><<<grid, kAdjThreads, 0, s>>>(a); break;
+    case 36: full ? adjoint_kernel<36, false, true><<<grid, kAdjThreads, 0, s>>>(a)
+                  : adjoint_kernel<36><<<grid, kAdjThreads, 0, s>>>(a); break;
+    default: full ? adjoint_kernel<64, false, true><<<grid, kAdjThreads, 0, s>>>(a)
+                  : adjoint_kernel<64><<<grid, kAdjThreads, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }
