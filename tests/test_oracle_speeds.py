@@ -100,3 +100,55 @@ def test_w1_is_identifiable_with_several_speeds(orc):
     Lm = orc.loglik_grad(_m(orc, v=1.0 - h, **base), offs, traj, prior)[0]
     assert dv == pytest.approx((Lp - Lm) / (2 * h), rel=1e-5)
     assert abs(orc.loglik_grad(_m(orc), offs, traj, prior)[3][0]) < 1e-12
+
+
+def test_speed_term_alone_closed_form(orc):
+    """With w2 = 0 only the speed term is left: pi(s, k) is uniform over the
+    headings and proportional to exp(-beta w1 v m_s dt) over the speeds."""
+    speeds = [0.5, 1.0, 1.5]
+    m = _m(orc, speeds=speeds, w1=2.0, w2=0.0, speed_off=0b100)
+    beta, v, dt = 1.3, 1.0, 0.1
+    lp = orc.log_policy(m, [0.7, -0.4], beta, GOALS[1])
+    logits = np.array([-beta * 2.0 * v * ms * dt for ms in speeds])
+    logits[2] = -np.inf
+    want = np.repeat(logits - (math.log(8.0) + np.log(np.exp(logits[:2]).sum())), 8)
+    assert np.all(lp[16:] == -np.inf)
+    assert np.allclose(lp[:16], want[:16], atol=1e-14)
+
+
+def test_observed_speed_snaps_among_enabled_speeds(orc):
+    """With the middle speed masked, a step of 0.95 v dt is read at the nearest
+    enabled multiplier (0.5), never at the masked one: the one-step posterior
+    is the prior plus that control's log-probability."""
+    m = _m(orc, speeds=[0.5, 1.0, 1.5], speed_off=0b010)
+    z = np.array([0.4, -0.3])
+    obs = np.stack([z, z + 0.95 * 0.1 * np.array([0.0, 1.0])])  # heading 2
+    prior = np.log(np.full(4, 0.25))
+    post, _ = orc.update_posterior(m, obs, prior)
+    want = np.array([prior[g * 2 + b] + orc.log_policy(m, z, BETA[b], GOALS[g])[0 * 8 + 2]
+                     for g in range(2) for b in range(2)])
+    want -= np.log(np.exp(want - want.max()).sum()) + want.max()
+    assert np.all(np.isfinite(post))
+    assert np.allclose(post, want, atol=1e-12)
+
+
+def test_loglik_is_the_marginal_of_the_policy(orc):
+    """L of loglik_grad equals log sum_j prior_j prod_t pi_j(u_t | z_t), built
+    here from log_policy with each observed step read at its heading and the
+    nearest multiplier (headings on the lattice: every step is a control)."""
+    rng = np.random.default_rng(11)
+    speeds = [0.5, 1.0, 1.5]
+    m = _m(orc, speeds=speeds)
+    z = np.array([0.2, 0.1])
+    pts, ctrl = [z], []
+    for _ in range(12):
+        s, h = int(rng.integers(0, 3)), int(rng.integers(0, 8))
+        ctrl.append(s * 8 + h)
+        pts.append(pts[-1] + 0.1 * speeds[s] * np.array([math.cos(2 * math.pi * h / 8), math.sin(2 * math.pi * h / 8)]))
+    traj = np.array(pts)
+    prior = np.log(np.array([0.1, 0.2, 0.3, 0.4]))
+    L, _, _, _ = orc.loglik_grad(m, [0, len(pts)], traj, prior)
+    A = np.array([sum(orc.log_policy(m, traj[t], BETA[b], GOALS[g])[ctrl[t]] for t in range(12))
+                  for g in range(2) for b in range(2)])
+    want = np.log(np.exp(prior + A - (prior + A).max()).sum()) + (prior + A).max()
+    assert L == pytest.approx(want, abs=1e-10)
