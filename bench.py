@@ -334,8 +334,7 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
     oob = torch.empty(hu.horizon, dtype=torch.int32, device=dev)
 
     def small():
-        lb.copy_(prior)
-        pm.pm_update_posterior(ctx, model, obs, hu.n_obs, lb, stream)
+        pm.pm_update_posterior_into(ctx, model, obs, hu.n_obs, prior, lb, stream)
         pm.pm_predict_occupancy(ctx, model, lb, float(z0[0]), float(z0[1]), hu.n_particles, hu.horizon, grid,
                                 hu.seed, hu.human_id, counts, oob, stream)
     ms = time_events(torch, stream, small, 200)
@@ -347,12 +346,17 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
         # -- batched: 16 humans, one persistent launch in a CUDA graph vs the plain per-human path
         hs = workloads.batched()
         recs = []
+        # every human's prior and belief are slices of two flat buffers, so
+        # one copy resets all beliefs before a replay
+        offs = np.cumsum([0] + [h.G * h.B for h in hs])
+        prior_flat = torch.tensor(np.concatenate([h.uniform_log_prior() for h in hs]), device=dev)
+        lb_flat = prior_flat.clone()
         for k, h in enumerate(hs):
             gg, bb = torch.tensor(h.goals, device=dev), torch.tensor(h.beta, device=dev)
             ob = gpu_paths(pm, ctx, torch, dev, h, h.n_obs, h.human_id)
             x0, y0, res, W, H = h.grid
-            recs.append(dict(h=h, g=gg, b=bb, obs=ob, prior=torch.tensor(h.uniform_log_prior(), device=dev),
-                             lb=torch.tensor(h.uniform_log_prior(), device=dev), z0=ob[-1].clone(),
+            recs.append(dict(h=h, g=gg, b=bb, obs=ob, prior=prior_flat[offs[k]:offs[k + 1]],
+                             lb=lb_flat[offs[k]:offs[k + 1]], z0=ob[-1].clone(),
                              grid=pm.make_grid(x0, y0, res, W, H),
                              counts=torch.empty((h.horizon, H, W), dtype=torch.int32, device=dev),
                              oob=torch.empty(h.horizon, dtype=torch.int32, device=dev),
@@ -361,8 +365,7 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
 
         def plain_batched():
             for r in recs:
-                r["lb"].copy_(r["prior"])
-                pm.pm_update_posterior(ctx, r["model"], r["obs"], r["h"].n_obs, r["lb"], stream)
+                pm.pm_update_posterior_into(ctx, r["model"], r["obs"], r["h"].n_obs, r["prior"], r["lb"], stream)
                 z = r["z0h"]
                 pm.pm_predict_occupancy(ctx, r["model"], r["lb"], z[0], z[1], r["h"].n_particles, r["h"].horizon,
                                         r["grid"], r["h"].seed, r["h"].human_id, r["counts"], r["oob"], stream)
@@ -380,12 +383,10 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
         tuned = pm.pm_batch_get_config(batch)
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.stream(stream):
-            for r in recs:
-                r["lb"].copy_(r["prior"])
+            lb_flat.copy_(prior_flat)
             torch.cuda.synchronize()
             with torch.cuda.graph(graph, stream=stream):
-                for r in recs:
-                    r["lb"].copy_(r["prior"])
+                lb_flat.copy_(prior_flat)
                 pm.pm_batch_update_posterior(batch, stream)
                 pm.pm_batch_predict(batch, stream)
         batch_ms = time_events(torch, stream, graph.replay, 10)
@@ -405,8 +406,7 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
         with torch.cuda.stream(stream):
             torch.cuda.synchronize()
             with torch.cuda.graph(graph_m, stream=stream):
-                for r in recs:
-                    r["lb"].copy_(r["prior"])
+                lb_flat.copy_(prior_flat)
                 pm.pm_batch_update_posterior(batch, stream)
                 pm.pm_batch_predict(batch, stream)
         marked_batch_ms = time_events(torch, stream, graph_m.replay, 10)
@@ -579,8 +579,7 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
             oob = torch.empty(hu.horizon, dtype=torch.int32, device=dev)
 
             def ms_step():
-                lb.copy_(prior)
-                pm.pm_update_posterior(ctx, model, obs, hu.n_obs, lb, stream)
+                pm.pm_update_posterior_into(ctx, model, obs, hu.n_obs, prior, lb, stream)
                 pm.pm_predict_occupancy(ctx, model, lb, float(z0[0]), float(z0[1]), hu.n_particles, hu.horizon,
                                         grid, hu.seed, hu.human_id, counts, oob, stream)
             ms = time_events(torch, stream, ms_step, 20)
@@ -611,8 +610,7 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
             oob = torch.empty(T, dtype=torch.int32, device=dev)
 
             def t1_step():
-                lb.copy_(prior)
-                pm.pm_update_posterior(ctx, model, obs, hu.n_obs, lb, stream)
+                pm.pm_update_posterior_into(ctx, model, obs, hu.n_obs, prior, lb, stream)
                 pm.pm_predict_occupancy(ctx, model, lb, float(z0[0]), float(z0[1]), hu.n_particles, T, grid,
                                         hu.seed, hu.human_id, counts, oob, stream)
             t1[f"T{T}"] = time_events(torch, stream, t1_step, 200)
@@ -698,8 +696,7 @@ def run_native(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step():
-        lb.copy_(prior)
-        pm.pm_update_posterior(ctx, model, obs, hu.n_obs, lb, stream)
+        pm.pm_update_posterior_into(ctx, model, obs, hu.n_obs, prior, lb, stream)
         pm.pm_predict_occupancy(ctx, model, lb, float(z0[0]), float(z0[1]), N, T, grid, hu.seed, human_id,
                                 counts, oob, stream)
 
@@ -735,8 +732,7 @@ def run_native(args):
             for i in range(args.steps):
                 flush.fill_(float(i))
                 ev[i][0].record(stream)
-                lb.copy_(prior)
-                pm.pm_update_posterior(ctx, model, obs, hu.n_obs, lb, stream)
+                pm.pm_update_posterior_into(ctx, model, obs, hu.n_obs, prior, lb, stream)
                 ev[i][1].record(stream)
                 pm.pm_predict_occupancy(ctx, model, lb, float(z0[0]), float(z0[1]), N, T, grid, hu.seed,
                                         human_id, counts, oob, stream)
@@ -818,7 +814,8 @@ def run_native(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded; observed history drawn from the model on the GPU)",
             "config": workload_config(hu, args.workload),
-            "gpu_launches": 2 * args.steps,
+            # per step: the belief update, the zeroing of the outputs, the rollout
+            "gpu_launches": 3 * args.steps,
             "wall_s": wall,
             "breakdown_ms": {"posterior": statistics.mean(post_ms), "rollout": statistics.mean(roll_ms)},
             "roofline": {"bound": "alu", "kernel": kernel_name, "achieved": achieved,

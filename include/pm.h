@@ -137,11 +137,22 @@ pm_status pm_sync_status(pm_ctx *ctx, void *stream);
  * flatness: the heading of the displacement; Q is evaluated at that
  * continuous heading and normalised over the K headings. A displacement
  * shorter than 1e-6 m leaves the belief unchanged for that step. n_obs = 0
- * is a no-op. Per-step log-likelihoods are summed in FP64 on the device and
- * the LogSumExp normalisation is applied once, which equals the sequential
- * form of Eq. 7 exactly in real arithmetic. */
+ * is a no-op. The per-step log-likelihoods are accumulated in double-float
+ * (pairs of FP32) on the device and the LogSumExp normalisation is applied
+ * once, which equals the sequential form of Eq. 7 exactly in real
+ * arithmetic. */
 pm_status pm_update_posterior(pm_ctx *ctx, const pm_model *model, const float *obs_xy,
                               int32_t n_obs, float *log_belief, void *stream);
+
+/* The same update out of place: the prior is read from `log_prior` [G*B]
+ * (device, normalised, left unchanged) and the posterior is written to
+ * `log_belief` [G*B] (device). The two are either the same buffer (then this
+ * is pm_update_posterior) or disjoint; a partial overlap is PM_EINVAL. With
+ * n_obs = 0 the prior is copied. A caller that keeps its prior, or runs the
+ * same update repeatedly, needs no copy of its own. */
+pm_status pm_update_posterior_into(pm_ctx *ctx, const pm_model *model, const float *obs_xy,
+                                   int32_t n_obs, const float *log_prior, float *log_belief,
+                                   void *stream);
 
 /* Algorithm 1 with the bootstrapped belief (Sec. III-B): `n_particles`
  * particles start at (z0x, z0y), each draws (beta, g) once from
@@ -188,7 +199,9 @@ pm_status pm_predict_occupancy_traced(pm_ctx *ctx, const pm_model *model,
  * are on the host. Host pointers: goals [G][2], beta [B], obs_xy
  * [n_obs+1][2], log_prior [G*B], posterior_out [G*B], counts_out
  * [horizon][H][W], oob_out [horizon]. The model's goals/beta fields are
- * ignored. Page-locked host memory makes the copies asynchronous. The
+ * ignored. The inputs are read during the call (into page-locked staging of
+ * the context, uploaded in one copy), so they may be pageable and are free on
+ * return; page-locked output buffers make the copies out asynchronous. The
  * rollout starts at the last observed state. */
 pm_status pm_predict_host(pm_ctx *ctx, const pm_model *model, const float *goals,
                           const float *beta, const float *obs_xy, int32_t n_obs,
@@ -204,9 +217,11 @@ pm_status pm_predict_host(pm_ctx *ctx, const pm_model *model, const float *goals
  * of the context, so that a call's copy-out overlaps the next call's
  * prediction. The outputs of a call are complete once pm_host_fence has made
  * a stream wait for the pending copies and that stream has been synchronised.
- * The host buffers must stay valid, and must not be reused by the caller, until
- * then; the inputs are read when `stream` reaches the call. Host buffers as
- * pm_predict_host (page-locked: pageable ones make the copies synchronous). */
+ * The output buffers must stay valid, and must not be reused by the caller,
+ * until then; the inputs are read during the call and are free on return.
+ * A call may wait on the host for the upload of the call before the previous
+ * one (its staging is reused). Output buffers as pm_predict_host
+ * (page-locked: pageable ones make the copies synchronous). */
 pm_status pm_predict_host_async(pm_ctx *ctx, const pm_model *model, const float *goals,
                                 const float *beta, const float *obs_xy, int32_t n_obs,
                                 const float *log_prior, int32_t n_particles, int32_t horizon,

@@ -75,6 +75,7 @@ def _signatures(lib):
         "pm_sync_status": ([_vp, _vp], C.c_int),
         "pm_batch_set_block_flags": ([_vp, C.c_int32, _vp], C.c_int),
         "pm_update_posterior": ([_vp, P(pm_model), _vp, C.c_int32, _vp, _vp], C.c_int),
+        "pm_update_posterior_into": ([_vp, P(pm_model), _vp, C.c_int32, _vp, _vp, _vp], C.c_int),
         "pm_predict_occupancy": ([_vp, P(pm_model), _vp, C.c_float, C.c_float, C.c_int32, C.c_int32,
                                   P(pm_grid), C.c_uint64, C.c_uint32, _vp, _vp, _vp], C.c_int),
         "pm_predict_occupancy_traced": ([_vp, P(pm_model), _vp, C.c_float, C.c_float, C.c_int32,
@@ -201,6 +202,11 @@ def make_grid(x0, y0, res, W, H) -> pm_grid:
 def pm_update_posterior(ctx, model: pm_model, obs_xy, n_obs, log_belief, stream=None):
     _check(library().pm_update_posterior(ctx, C.byref(model), _p(obs_xy), int(n_obs), _p(log_belief),
                                          _stream(stream)))
+
+
+def pm_update_posterior_into(ctx, model: pm_model, obs_xy, n_obs, log_prior, log_belief, stream=None):
+    _check(library().pm_update_posterior_into(ctx, C.byref(model), _p(obs_xy), int(n_obs), _p(log_prior),
+                                              _p(log_belief), _stream(stream)))
 
 
 def pm_predict_occupancy(ctx, model: pm_model, log_belief, z0x, z0y, n_particles, horizon,

@@ -39,6 +39,12 @@ struct pm_ctx {
     cudaEvent_t computed = nullptr;
     cudaStream_t copy_stream = nullptr;
     int next_slot = 0;
+    // page-locked host staging of the host-buffer calls' inputs (one per slot,
+    // and [2] for the synchronous call) and the event after which its upload
+    // has read it
+    char *hin[3] = {nullptr, nullptr, nullptr};
+    size_t hin_bytes[3] = {0, 0, 0};
+    cudaEvent_t hin_read[3] = {nullptr, nullptr, nullptr};
 };
 
 struct pm_batch {
@@ -367,40 +373,49 @@ pm_status predict_impl(pm_ctx *ctx, const pm_model *model, const float *log_beli
         a.H = grid->H;
         a.counts = counts;
         a.oob = oob;
-        const size_t plane = (size_t)grid->W * (size_t)grid->H;
-        cudaError_t e = cudaMemsetAsync(counts, 0, plane * (size_t)horizon * sizeof(uint32_t), stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(oob, 0, (size_t)horizon * sizeof(uint32_t), stream);
-        if (e != cudaSuccess) return cuda_fail(e, "zeroing counts/oob");
     } else {
         a.W = a.H = 1;
         a.inv_res = 1.0f;
     }
-    // persistent warps take 32-particle chunks from a context-owned counter
+    // persistent warps take 32-particle chunks from a context-owned counter;
+    // one launch zeroes it with the counts and oob
     st = ensure_posterior_scratch(ctx, 0);
     if (st != PM_OK) return st;
     unsigned *head = ctx->ticket + 2;
-    cudaError_t ez = cudaMemsetAsync(head, 0, sizeof(unsigned), stream);
-    if (ez != cudaSuccess) return cuda_fail(ez, "chunk counter");
+    const size_t words = hist ? (size_t)grid->W * (size_t)grid->H * (size_t)horizon : 0;
+    cudaError_t ez = pm::launch_zero_outputs(hist ? counts : nullptr, words, hist ? oob : nullptr, horizon, head,
+                                             ctx->sm_count, stream);
+    if (ez != cudaSuccess) return cuda_fail(ez, "zeroing counts, oob and the chunk counter");
     cudaError_t e = pm::launch_rollout(a, head, ctx->sm_count, stream);
     if (e != cudaSuccess) return cuda_fail(e, "rollout launch");
     return PM_OK;
 }
 
 pm_status posterior_impl(pm_ctx *ctx, const pm_model *model, const float *obs_xy, int32_t n_obs,
-                         float *log_belief, cudaStream_t stream)
+                         const float *log_prior, float *log_belief, cudaStream_t stream)
 {
     if (!ctx) return fail(PM_EINVAL, "ctx is NULL");
     pm_status st = check_model(model);
     if (st != PM_OK) return st;
     if (n_obs < 0) return fail(PM_EINVAL, "n_obs=%d must be >= 0", n_obs);
     if (!log_belief) return fail(PM_EINVAL, "log_belief is NULL");
-    if (n_obs == 0) return PM_OK;
+    if (!log_prior) return fail(PM_EINVAL, "log_prior is NULL");
+    const size_t J = (size_t)model->G * (size_t)model->B;
+    if (log_prior != log_belief && log_prior < log_belief + J && log_belief < log_prior + J)
+        return fail(PM_EINVAL, "log_prior and log_belief overlap without being the same buffer");
+    if (n_obs == 0) {
+        if (log_prior == log_belief) return PM_OK;
+        DeviceScope dev(ctx->device);
+        cudaError_t e = cudaMemcpyAsync(log_belief, log_prior, J * sizeof(float), cudaMemcpyDeviceToDevice, stream);
+        return e == cudaSuccess ? PM_OK : cuda_fail(e, "copying the prior");
+    }
     if (!obs_xy) return fail(PM_EINVAL, "obs_xy is NULL");
     DeviceScope dev(ctx->device);
     pm::PosteriorArgs a;
     fill_posterior_args(model, a);
     a.obs = obs_xy;
     a.n_obs = n_obs;
+    a.log_prior = log_prior;
     a.log_b = log_belief;
     const int n_chunks = pm::posterior_chunks(n_obs, &a.steps_per_chunk);
     st = ensure_posterior_scratch(ctx, pm::posterior_scratch_bytes(n_chunks, model->G * model->B));
@@ -619,6 +634,7 @@ pm_status batch_upload(pm_batch *b, cudaStream_t stream)
         int spc = 1;
         const int nch = u.n_obs > 0 ? pm::posterior_chunks(u.n_obs, &spc) : 0;
         q.steps_per_chunk = spc;
+        q.log_prior = u.log_belief;
         q.log_b = u.log_belief;
         q.part = b->d_post_part + (size_t)h * b->post_stride;
         q.ticket = b->d_post_ticket + h;
@@ -735,6 +751,7 @@ pm_status pm_internal_posterior_on_scratch(const pm_model *model, const float *o
     fill_posterior_args(model, a);
     a.obs = obs_xy;
     a.n_obs = n_obs;
+    a.log_prior = log_belief;
     a.log_b = log_belief;
     a.steps_per_chunk = (n_obs + max_chunks - 1) / max_chunks;
     const int n_chunks = (n_obs + a.steps_per_chunk - 1) / a.steps_per_chunk;
@@ -799,6 +816,11 @@ void pm_destroy(pm_ctx *ctx)
         }
         if (ctx->computed) cudaEventDestroy(ctx->computed);
         if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+        for (int i = 0; i < 3; ++i) {
+            if (ctx->hin_read[i]) cudaEventSynchronize(ctx->hin_read[i]);
+            if (ctx->hin[i]) cudaFreeHost(ctx->hin[i]);
+            if (ctx->hin_read[i]) cudaEventDestroy(ctx->hin_read[i]);
+        }
     }
     delete ctx;
 }
@@ -830,7 +852,13 @@ pm_status pm_sync_status(pm_ctx *ctx, void *stream)
 pm_status pm_update_posterior(pm_ctx *ctx, const pm_model *model, const float *obs_xy, int32_t n_obs,
                               float *log_belief, void *stream)
 {
-    return posterior_impl(ctx, model, obs_xy, n_obs, log_belief, (cudaStream_t)stream);
+    return posterior_impl(ctx, model, obs_xy, n_obs, log_belief, log_belief, (cudaStream_t)stream);
+}
+
+pm_status pm_update_posterior_into(pm_ctx *ctx, const pm_model *model, const float *obs_xy, int32_t n_obs,
+                                   const float *log_prior, float *log_belief, void *stream)
+{
+    return posterior_impl(ctx, model, obs_xy, n_obs, log_prior, log_belief, (cudaStream_t)stream);
 }
 
 pm_status pm_predict_occupancy(pm_ctx *ctx, const pm_model *model, const float *log_belief, float z0x,
@@ -914,21 +942,46 @@ pm_status predict_host_impl(pm_ctx *ctx, const pm_model *model, const float *goa
         p = (char *)ctx->slot[slot];
         out_stream = ctx->copy_stream;
     }
+    char *const d_in = p;
     float *d_goals = (float *)p; p += b_goals;
     float *d_beta = (float *)p; p += b_beta;
     float *d_obs = (float *)p; p += b_obs;
     float *d_lb = (float *)p; p += b_lb;
     uint32_t *d_counts = (uint32_t *)p; p += b_counts;
     uint32_t *d_oob = (uint32_t *)p;
-    cudaError_t e = cudaMemcpyAsync(d_goals, goals, (size_t)model->G * 8, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_beta, beta, (size_t)model->B * 4, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_obs, obs_xy, (size_t)(n_obs + 1) * 8, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_lb, log_prior, (size_t)J * 4, cudaMemcpyHostToDevice, s);
+    // the four inputs go through page-locked staging with the device layout,
+    // so one upload carries them and the caller's buffers are free on return
+    const size_t in_bytes = b_goals + b_beta + b_obs + b_lb;
+    const int hs = slot < 0 ? 2 : slot;
+    cudaError_t e = cudaSuccess;
+    if (!ctx->hin_read[hs]) e = cudaEventCreateWithFlags(&ctx->hin_read[hs], cudaEventDisableTiming);
+    // the staging's previous upload must have read it before it is refilled
+    if (e == cudaSuccess) e = cudaEventSynchronize(ctx->hin_read[hs]);
+    if (e != cudaSuccess) return cuda_fail(e, "input staging event");
+    if (ctx->hin_bytes[hs] < in_bytes) {
+        if (ctx->hin[hs]) cudaFreeHost(ctx->hin[hs]);
+        ctx->hin[hs] = nullptr;
+        ctx->hin_bytes[hs] = 0;
+        const size_t cap = std::max(in_bytes, (size_t)4096);
+        e = cudaHostAlloc((void **)&ctx->hin[hs], cap, cudaHostAllocDefault);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PM_ENOMEM, "cudaHostAlloc(%zu) for the input staging failed", cap);
+        }
+        ctx->hin_bytes[hs] = cap;
+    }
+    char *h = ctx->hin[hs];
+    std::memcpy(h, goals, (size_t)model->G * 8);
+    std::memcpy(h + b_goals, beta, (size_t)model->B * 4);
+    std::memcpy(h + b_goals + b_beta, obs_xy, (size_t)(n_obs + 1) * 8);
+    std::memcpy(h + b_goals + b_beta + b_obs, log_prior, (size_t)J * 4);
+    e = cudaMemcpyAsync(d_in, h, in_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->hin_read[hs], s);
     if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
     pm_model m = *model;
     m.goals = d_goals;
     m.beta = d_beta;
-    st = posterior_impl(ctx, &m, d_obs, n_obs, d_lb, s);
+    st = posterior_impl(ctx, &m, d_obs, n_obs, d_lb, d_lb, s);
     if (st != PM_OK) return st;
     const float z0x = obs_xy[2 * n_obs], z0y = obs_xy[2 * n_obs + 1];
     st = predict_impl(ctx, &m, d_lb, z0x, z0y, n_particles, horizon, grid, seed, human_id, d_counts, d_oob, 0,

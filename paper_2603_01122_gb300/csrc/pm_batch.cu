@@ -257,6 +257,28 @@ __global__ void batch_zero_kernel(const BatchHuman *humans, const int *n_dev)
     }
 }
 
+// The single-human form of the above: the counts in 16-byte words (scalar
+// head and tail), oob and the chunk counter, so one launch replaces three
+// memsets before the rollout.
+__global__ void zero_outputs_kernel(uint32_t *counts, size_t words, uint32_t *oob, int T, unsigned *head)
+{
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (counts) {
+        const size_t lead0 = ((16 - ((uintptr_t)counts & 15)) & 15) / 4;
+        const size_t lead = lead0 < words ? lead0 : words;
+        const size_t nvec = (words - lead) / 4;
+        const size_t tail0 = lead + nvec * 4;
+        uint4 *v = reinterpret_cast<uint4 *>(counts + lead);
+        for (size_t q = t0; q < nvec; q += stride) v[q] = make_uint4(0u, 0u, 0u, 0u);
+        if (t0 < lead) counts[t0] = 0u;
+        if (t0 < words - tail0) counts[tail0 + t0] = 0u;
+    }
+    if (oob)
+        for (size_t q = t0; q < (size_t)T; q += stride) oob[q] = 0u;
+    if (t0 == 0) *head = 0u;
+}
+
 template <typename Kern>
 cudaError_t launch_or_query(Kern k, const BatchArgs &a, int blocks, int threads, size_t dyn, cudaStream_t s, int *occ)
 {
@@ -334,6 +356,20 @@ int batch_rollout_occupancy(int K, uint64_t enabled, int S, bool marks, const Ro
 cudaError_t launch_batch_rollout(const BatchArgs &a, const RolloutShape &shape, int blocks, size_t dyn, cudaStream_t s)
 {
     return batch_dispatch(a, shape, blocks, dyn, s, nullptr);
+}
+
+cudaError_t launch_zero_outputs(uint32_t *counts, size_t words, uint32_t *oob, int T, unsigned *head, int sm_count,
+                                cudaStream_t s)
+{
+    // enough threads for a few 16-byte stores each at paper-scale sizes,
+    // never more than the work
+    const size_t nvec = words / 4 + 1;
+    size_t blocks = (nvec + 255) / 256;
+    const size_t cap = (size_t)(sm_count > 0 ? sm_count : 1) * 4;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    zero_outputs_kernel<<<(unsigned)blocks, 256, 0, s>>>(counts, words, oob, T, head);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_batch_zero(const BatchHuman *humans, const int *n_dev, int max_rows, int sm_count, cudaStream_t s)

@@ -30,6 +30,7 @@ struct PosteriorArgs {
     const float *obs;
     int n_obs;
     int steps_per_chunk; // observed steps handled by one CTA
+    const float *log_prior; // read by the fold (may equal log_b)
     float *log_b;
     float *part;         // scratch: per (chunk, component) accumulators
     unsigned *ticket;    // scratch: chunks finished so far (0 between calls)
@@ -72,6 +73,7 @@ struct PostHuman {
     const float *obs;
     int n_obs;
     int steps_per_chunk;
+    const float *log_prior; // read by the fold (the batch passes log_b)
     float *log_b;
     float *part;
     unsigned *ticket;
@@ -184,6 +186,10 @@ int batch_rollout_occupancy(int K, uint64_t enabled, int S, bool marks, const Ro
 size_t batch_warp_tables_bytes(int threads, bool multi_speed); // dynamic shared memory of the warp form
 cudaError_t launch_batch_rollout(const BatchArgs &a, const RolloutShape &shape, int blocks, size_t dyn, cudaStream_t s);
 cudaError_t launch_batch_zero(const BatchHuman *humans, const int *n_dev, int max_rows, int sm_count, cudaStream_t s);
+// One human's outputs before its rollout, in one launch: counts [words]
+// (or NULL), oob [T] (or NULL) and the chunk counter.
+cudaError_t launch_zero_outputs(uint32_t *counts, size_t words, uint32_t *oob, int T, unsigned *head, int sm_count,
+                                cudaStream_t s);
 size_t adjoint_scratch_bytes(int M, int G, int J);
 void adjoint_scratch_layout(void *base, int M, int G, int J, AdjointArgs &a);
 

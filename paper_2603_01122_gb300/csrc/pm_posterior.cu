@@ -273,7 +273,7 @@ __device__ __forceinline__ void posterior_chunk(const PosteriorArgs &a, const Po
             acc_merge(acc, q);
         }
         if (lane == 0) {
-            const float lb = h.log_b[j];
+            const float lb = h.log_prior[j];
             if (isnan(lb) || lb == INFINITY) flag_status(a.status, kStatusBelief);
             if (lb == -INFINITY) {
                 L[j] = make_float2(-INFINITY, 0.0f);
@@ -320,6 +320,7 @@ __global__ void __launch_bounds__(1024) posterior_kernel(const __grid_constant__
     h.obs = a.obs;
     h.n_obs = a.n_obs;
     h.steps_per_chunk = a.steps_per_chunk;
+    h.log_prior = a.log_prior;
     h.log_b = a.log_b;
     h.part = a.part;
     h.ticket = a.ticket;
@@ -336,7 +337,7 @@ __global__ void __launch_bounds__(1024) posterior_batch_kernel(const __grid_cons
 {
     if ((int)blockIdx.y >= *n_humans) return;
     const PostHuman h = humans[blockIdx.y];
-    if (h.n_obs <= 0 || h.log_b == nullptr) return;
+    if (h.n_obs <= 0 || h.log_b == nullptr || h.log_prior == nullptr) return;
     const int nchunk = (h.n_obs + h.steps_per_chunk - 1) / h.steps_per_chunk;
     for (int ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
         if (a.sp.S > 0) posterior_chunk<true>(a, h, ch, nchunk);

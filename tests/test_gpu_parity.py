@@ -135,6 +135,40 @@ def test_posterior_one_step_calls_equal_one_call(ctx, orc):
     assert_posterior_close(lb.cpu().numpy(), want)
 
 
+def test_posterior_out_of_place(ctx, orc):
+    """pm_update_posterior_into reads the prior from one buffer and writes the
+    posterior to another: the prior is unchanged, the posterior equals the
+    oracle's and, bit for bit, the in-place call's; n_obs = 0 copies the
+    prior; buffers that overlap without being the same are rejected."""
+    import paper_2603_01122_gb300 as pm
+    hu = workloads.paper_scale()
+    m, obs, want = _obs_and_post(orc, hu)
+    gh = GpuHuman.of(hu)
+    obs_d = dev(obs)
+    rng = np.random.default_rng(4)
+    prior_np = np.log(rng.dirichlet(np.ones(hu.G * hu.B))).astype(np.float32)
+    want_p, _ = orc.update_posterior(m, obs.astype(np.float64), prior_np.astype(np.float64))
+    prior = dev(prior_np)
+    out = torch.full_like(prior, float("nan"))
+    pm.pm_update_posterior_into(ctx, gh.model, obs_d, hu.n_obs, prior, out)
+    inplace = prior.clone()
+    pm.pm_update_posterior(ctx, gh.model, obs_d, hu.n_obs, inplace)
+    same = prior.clone()
+    pm.pm_update_posterior_into(ctx, gh.model, obs_d, hu.n_obs, same, same)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(prior.cpu().numpy(), prior_np)
+    assert_posterior_close(out.cpu().numpy(), want_p)
+    np.testing.assert_array_equal(out.cpu().numpy(), inplace.cpu().numpy())
+    np.testing.assert_array_equal(same.cpu().numpy(), inplace.cpu().numpy())
+    copy = torch.full_like(prior, float("nan"))
+    pm.pm_update_posterior_into(ctx, gh.model, obs_d, 0, prior, copy)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(copy.cpu().numpy(), prior_np)
+    buf = torch.zeros(2 * hu.G * hu.B, device="cuda:0")
+    with pytest.raises(pm.PmError):
+        pm.pm_update_posterior_into(ctx, gh.model, obs_d, hu.n_obs, buf[:hu.G * hu.B], buf[1:hu.G * hu.B + 1])
+
+
 def test_posterior_large_history_max_components(ctx, orc):
     """G*B = 256 components, 200 steps, K = 64."""
     rng = np.random.default_rng(4)
@@ -332,7 +366,8 @@ def test_async_host_api_in_a_pipeline(ctx, orc):
     """Five asynchronous host calls in a row (seeds and horizons vary, two
     sets of pinned outputs alternate, a larger grid midway forces a staging
     slot to grow): after the fence, each call's outputs equal the device path's
-    for the same inputs."""
+    for the same inputs. The inputs are pageable and are overwritten with NaN
+    as soon as each call returns (a call reads them before it returns)."""
     import paper_2603_01122_gb300 as pm
     hu = workloads.paper_scale()
     m, obs, post = _obs_and_post(orc, hu)
@@ -348,10 +383,13 @@ def test_async_host_api_in_a_pipeline(ctx, orc):
         o = (torch.zeros(hu.G * hu.B, dtype=torch.float32).pin_memory(),
              torch.zeros((T, Hc, Wc), dtype=torch.int32).pin_memory(), torch.zeros(T, dtype=torch.int32).pin_memory())
         outs.append(o)
-        pm.pm_predict_host_async(ctx, gh.model, torch.tensor(hu.goals).pin_memory(), torch.tensor(hu.beta).pin_memory(),
-                                 torch.tensor(obs).pin_memory(), hu.n_obs,
-                                 torch.tensor(hu.uniform_log_prior()).pin_memory(), N, T,
+        ins = [np.array(hu.goals, np.float32), np.array(hu.beta, np.float32), np.array(obs, np.float32),
+               np.array(hu.uniform_log_prior(), np.float32)]
+        t_in = [torch.from_numpy(a) for a in ins]
+        pm.pm_predict_host_async(ctx, gh.model, t_in[0], t_in[1], t_in[2], hu.n_obs, t_in[3], N, T,
                                  pm.make_grid(x0, y0, res, Wc, Hc), seed, hu.human_id, o[0], o[1], o[2], stream)
+        for a in ins:
+            a.fill(np.nan)
     pm.pm_host_fence(ctx, stream)
     stream.synchronize()
     for (T, seed, Wc, Hc), o in zip(calls, outs):
