@@ -36,8 +36,9 @@ def _setup(orc, humans, scale=1.0):
         d = dict(hu=hu, gh=gh, obs=dev(obs), n_obs=obs.shape[0] - 1, N=N, T=T,
                  lb=dev(hu.uniform_log_prior()), z0=dev(obs[-1]), grid=pm.make_grid(x0, y0, res, W, H),
                  full_grid=pm.make_grid(x0, y0, res, hu.grid[3], hu.grid[4]),
-                 counts=torch.empty((T, H, W), dtype=torch.int32, device="cuda:0"),
-                 oob=torch.empty(T, dtype=torch.int32, device="cuda:0"))
+                 # garbage: the batched rollout must zero every cell itself
+                 counts=torch.full((T, H, W), 0x3C3C3C3C, dtype=torch.int32, device="cuda:0"),
+                 oob=torch.full((T,), 777, dtype=torch.int32, device="cuda:0"))
         out.append(d)
     return out
 
@@ -90,6 +91,41 @@ def test_batched_workload_alone_equals_in_mix(ctx, orc):
             assert torch.equal(d["oob"], o)
             tot = d["counts"].view(d["T"], -1).sum(1, dtype=torch.int64) + d["oob"]
             assert torch.all(tot == d["N"])
+    finally:
+        pm.pm_batch_destroy(b)
+
+
+def test_outputs_zeroed_at_odd_offsets(ctx, orc):
+    """Outputs that start 4, 8 and 12 bytes past a 16-byte boundary and hold a
+    word count that is no multiple of 4 (ragged head and tail of the batch's
+    16-byte zeroing) come out equal to the single path, from garbage, on two
+    launches in a row (the second reuses the dirty buffers), in both
+    emplacement forms."""
+    import paper_2603_01122_gb300 as pm
+    hu = workloads.plain_small()
+    ds = _setup(orc, [hu, hu, hu], scale=0.5)
+    shapes = [(37, 171, 83), (5, 13, 7), (61, 129, 255)]  # T, H, W: 525,141 / 455 / 2,006,595 words
+    for k, (d, (T, H, W)) in enumerate(zip(ds, shapes)):
+        buf = torch.full((T * H * W + 8,), 0x3C3C3C3C, dtype=torch.int32, device="cuda:0")
+        d["counts"] = buf[k + 1:k + 1 + T * H * W].view(T, H, W)
+        d["oob"] = torch.full((T + 3,), 777, dtype=torch.int32, device="cuda:0")[k + 1:k + 1 + T]
+        d["T"] = T
+        d["grid"] = d["full_grid"] = pm.make_grid(hu.grid[0], hu.grid[1], hu.grid[2], W, H)
+        d["hu"] = hu
+    b = pm.pm_batch_create(ctx, _shared_model(hu, ds[0]["gh"]), 4)
+    try:
+        for warp, threads in ((1, 128), (0, 256)):
+            pm.pm_batch_set_config(b, threads, 0 if warp else 1, 0, 48)
+            pm.pm_batch_set(b, _pm_humans(ds))
+            for rep in range(2):
+                pm.pm_batch_predict(b)
+                torch.cuda.synchronize()
+                for d in ds:
+                    c, o = _single(ctx, d, d["lb"])
+                    torch.cuda.synchronize()
+                    assert torch.equal(d["counts"], c), (warp, rep, d["T"])
+                    assert torch.equal(d["oob"], o)
+        pm.pm_sync_status(ctx)
     finally:
         pm.pm_batch_destroy(b)
 
