@@ -69,7 +69,13 @@ typedef struct pm_ctx pm_ctx;
  * need K a multiple of 4 with no heading disabled, S*K <= 256, and
  * multipliers > 0; the observed control of a displacement is its continuous
  * heading at the enabled speed whose multiplier is nearest to its length /
- * (v*dt). Traced heading indices are control indices u. */
+ * (v*dt). Traced heading indices are control indices u.
+ *
+ * `snap_heading` = 1 reads the heading of an observed displacement as the
+ * enabled heading theta_k nearest to it (largest e_k . dz, the lower index on
+ * a tie), so the belief update and the log-likelihood evaluate the discrete
+ * control's Q; 0 (the default) keeps the continuous heading. The nearest
+ * heading is decided in FP32. */
 typedef struct pm_model {
     int32_t K;
     float speed; /* v  [m/s]            */
@@ -84,6 +90,7 @@ typedef struct pm_model {
     int32_t n_speeds;                 /* 0: one speed, multiplier 1      */
     float speed_mult[PM_MAX_SPEEDS];  /* speed s is v * speed_mult[s]    */
     uint32_t speed_off;               /* bit s set: speed s disabled     */
+    int32_t snap_heading;             /* 0 or 1, see above               */
 } pm_model;
 
 /* Occupancy grid: cell (cx, cy) covers [x0 + cx*res, x0 + (cx+1)*res) x

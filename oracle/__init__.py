@@ -67,7 +67,7 @@ _i32p = C.POINTER(C.c_int32)
 _u8p = C.POINTER(C.c_uint8)
 
 _MODEL = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_uint64, C.c_int,
-          C.POINTER(C.c_double), C.c_uint32]
+          C.POINTER(C.c_double), C.c_uint32, C.c_int]
 
 
 def _declare(lib):
@@ -122,10 +122,13 @@ class Model:
     Q_u = -w1*v*m_s*dt - w2*||z + v*m_s*dt*e_theta - g||; ``goals`` [G, 2];
     ``beta`` [B]; ``mask_off`` bit k disables heading k and ``speed_off`` bit s
     disables speed s (Q = -inf: the stationary masking of Sec. IV-B).
+    ``snap``: the observed heading is read as the nearest enabled heading
+    (the discrete control) instead of the continuous one.
     Float inputs are kept exactly as given (FP32 inputs stay FP32-valued).
     """
 
-    def __init__(self, K, v, dt, goals, beta, w1=1.0, w2=1.0, mask_off=0, speeds=(1.0,), speed_off=0):
+    def __init__(self, K, v, dt, goals, beta, w1=1.0, w2=1.0, mask_off=0, speeds=(1.0,), speed_off=0,
+                 snap=False):
         self.K = int(K)
         self.v = float(v)
         self.dt = float(dt)
@@ -136,6 +139,7 @@ class Model:
         self.mask_off = int(mask_off)
         self.speeds = np.ascontiguousarray(np.asarray(speeds, dtype=np.float64).reshape(-1))
         self.speed_off = int(speed_off)
+        self.snap = bool(snap)
 
     @property
     def S(self):
@@ -155,7 +159,7 @@ class Model:
 
     def _args(self):
         return [self.K, self.v, self.dt, self.w1, self.w2, C.c_uint64(self.mask_off), self.S,
-                _ptr(self.speeds, _dp), C.c_uint32(self.speed_off)]
+                _ptr(self.speeds, _dp), C.c_uint32(self.speed_off), C.c_int(1 if self.snap else 0)]
 
 
 def philox4x64(ctr, key):

@@ -29,7 +29,10 @@
  *     displacement at the enabled speed whose multiplier is nearest to its
  *     length / (v*dt) (ties: the lower index); Q is evaluated there and
  *     normalised over the controls; a displacement shorter than 1e-6 m leaves
- *     the belief unchanged.
+ *     the belief unchanged. With `snap` set, the heading is read as the
+ *     enabled heading theta_k nearest to atan2(dy, dx) instead (largest
+ *     cos(theta - theta_k); ties: the lower index), so the observed control
+ *     is one of the discrete controls.
  *   - belief index j = g*B + b (goal-major).
  *   - inverse-CDF sampling: smallest k with u*S < C_k, C_k the running sum in
  *     index order, S the total; u = (32-bit word >> 8) * 2^-24.
@@ -117,6 +120,7 @@ typedef struct {
     int S;               /* speeds: control u = s*K + k moves v*mult[s]*dt along theta_k */
     const double *mult;  /* [S] speed multipliers (> 0) */
     uint32_t speed_off;  /* bit s set: speed s disabled, Q = -inf (stationary masking) */
+    int snap;            /* 1: the observed heading is read as the nearest enabled heading */
 } orc_model;
 
 /* Unit vector of heading k, theta_k = 2*pi*k/K. Quarter turns are exact. */
@@ -188,8 +192,8 @@ double orc_log_policy_raw(const orc_model *m, double zx, double zy, double beta,
 }
 
 #define ORC_MODEL_ARGS int K, double v, double dt, double w1, double w2, uint64_t mask_off, \
-                       int S, const double *mult, uint32_t speed_off
-#define ORC_MODEL(G_, goals_, B_, beta_) {K, v, dt, w1, w2, G_, B_, goals_, beta_, mask_off, S, mult, speed_off}
+                       int S, const double *mult, uint32_t speed_off, int snap
+#define ORC_MODEL(G_, goals_, B_, beta_) {K, v, dt, w1, w2, G_, B_, goals_, beta_, mask_off, S, mult, speed_off, snap}
 
 /* Flat-argument form of orc_log_policy_raw for the Python wrapper
  * (logpi [S*K], control u = s*K + k). */
@@ -199,15 +203,37 @@ void orc_log_policy(ORC_MODEL_ARGS, double zx, double zy, double beta, double gx
     orc_log_policy_raw(&m, zx, zy, beta, gx, gy, logpi);
 }
 
+/* Direction (c, s) of the observed heading th: th itself, or with m->snap
+ * the enabled heading nearest to it (largest cos(th - theta_k), the lower
+ * index on a tie). */
+static void orc_obs_heading(const orc_model *m, double th, double *c, double *s)
+{
+    if (!m->snap) {
+        *c = cos(th);
+        *s = sin(th);
+        return;
+    }
+    double best = -INFINITY;
+    int kb = 0;
+    for (int k = 0; k < m->K; ++k) {
+        if ((m->mask_off >> k) & 1u) continue;
+        double d = cos(th - 2.0 * M_PI * (double)k / (double)m->K);
+        if (d > best) { best = d; kb = k; }
+    }
+    orc_heading(m->K, kb, c, s);
+}
+
 /* log pi(u_obs | z; beta, g) for the observed control recovered from two
- * states (differential flatness): the continuous heading th and the enabled
- * speed nearest to the displacement length len. */
+ * states (differential flatness): the heading th (continuous, or snapped)
+ * and the enabled speed nearest to the displacement length len. */
 static double orc_log_policy_obs(const orc_model *m, double zx, double zy, double th, double len,
                                  double beta, double gx, double gy, double *scratch)
 {
     double lse = orc_log_policy_raw(m, zx, zy, beta, gx, gy, scratch);
     double ms = m->mult[orc_snap_speed(m, len)];
-    return beta * orc_Q(m, zx, zy, cos(th), sin(th), ms, gx, gy) - lse;
+    double c, s;
+    orc_obs_heading(m, th, &c, &s);
+    return beta * orc_Q(m, zx, zy, c, s, ms, gx, gy) - lse;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -562,7 +588,8 @@ int orc_loglik_grad(ORC_MODEL_ARGS, int G, const double *goals, int B, const dou
             double dx = traj[2 * pt + 2] - zx, dy = traj[2 * pt + 3] - zy;
             double len = sqrt(dx * dx + dy * dy);
             if (len < 1e-6) continue;
-            double th = atan2(dy, dx), co = cos(th), so = sin(th);
+            double co, so;
+            orc_obs_heading(&m, atan2(dy, dx), &co, &so);
             double mo = mult[orc_snap_speed(&m, len)]; /* the observed control's speed */
             for (int j = 0; j < J; ++j) {
                 int g = j / B, b = j % B;

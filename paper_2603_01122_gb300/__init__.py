@@ -30,7 +30,7 @@ class pm_model(C.Structure):
     _fields_ = [("K", C.c_int32), ("speed", C.c_float), ("dt", C.c_float), ("w1", C.c_float),
                 ("w2", C.c_float), ("G", C.c_int32), ("B", C.c_int32), ("goals", C.c_void_p),
                 ("beta", C.c_void_p), ("heading_off", C.c_uint64), ("n_speeds", C.c_int32),
-                ("speed_mult", C.c_float * 4), ("speed_off", C.c_uint32)]
+                ("speed_mult", C.c_float * 4), ("speed_off", C.c_uint32), ("snap_heading", C.c_int32)]
 
 
 class pm_mppi(C.Structure):
@@ -183,14 +183,17 @@ def pm_destroy(ctx) -> None:
     library().pm_destroy(ctx)
 
 
-def make_model(K, speed, dt, goals, beta, w1=1.0, w2=1.0, heading_off=0, speeds=None, speed_off=0) -> pm_model:
+def make_model(K, speed, dt, goals, beta, w1=1.0, w2=1.0, heading_off=0, speeds=None, speed_off=0,
+               snap_heading=False) -> pm_model:
     """pm_model over device tensors ``goals`` [G, 2] and ``beta`` [B] (float32);
-    ``speeds``: speed multipliers of the control set (None: one speed)."""
+    ``speeds``: speed multipliers of the control set (None: one speed);
+    ``snap_heading``: read observed headings as the nearest enabled heading."""
     G = int(goals.shape[0])
     B = int(beta.shape[0])
     mult = list(speeds) if speeds is not None else []
     m = pm_model(int(K), float(speed), float(dt), float(w1), float(w2), G, B, _p(goals), _p(beta),
-                 int(heading_off), len(mult), (C.c_float * 4)(*(mult + [0.0] * (4 - len(mult)))), int(speed_off))
+                 int(heading_off), len(mult), (C.c_float * 4)(*(mult + [0.0] * (4 - len(mult)))), int(speed_off),
+                 1 if snap_heading else 0)
     m._keep = (goals, beta)  # keep the tensors alive with the struct
     return m
 

@@ -1,13 +1,14 @@
 """torch.autograd.Function over the library's log-likelihood adjoint.
 
-``MarginalLogLik.apply(goals, speed, w, beta, K, dt, offsets, traj, log_prior, ctx, speeds)``
+``MarginalLogLik.apply(goals, speed, w, beta, K, dt, offsets, traj, log_prior, ctx, speeds, snap_heading)``
 returns the marginal log-likelihood L of the observed trajectories (a CUDA
 scalar). Its backward calls pm_loglik_backward with the incoming gradient,
 so the gradient with respect to the goal coordinates, the speed and the Q
 weights is computed by the adjoint kernel; this module only moves pointers
 and scalars. ``speed`` and ``w`` are read to the host once per call (the
 C ABI takes them as scalars). ``speeds`` (a tuple of multipliers, or None
-for one speed) selects the control set of several speeds.
+for one speed) selects the control set of several speeds; ``snap_heading``
+reads each observed heading as the nearest enabled heading.
 """
 from __future__ import annotations
 
@@ -18,17 +19,17 @@ from . import make_model, pm_loglik_backward, pm_loglik_forward
 
 class MarginalLogLik(torch.autograd.Function):
     @staticmethod
-    def forward(fctx, goals, speed, w, beta, K, dt, offsets, traj, log_prior, ctx, speeds=None):
+    def forward(fctx, goals, speed, w, beta, K, dt, offsets, traj, log_prior, ctx, speeds=None, snap_heading=False):
         v = float(speed.detach().reshape(()).item())
         w1, w2 = (float(x) for x in w.detach().reshape(2).tolist())
         goals_c = goals.detach().contiguous()
-        model = make_model(K, v, dt, goals_c, beta, w1=w1, w2=w2, speeds=speeds)
+        model = make_model(K, v, dt, goals_c, beta, w1=w1, w2=w2, speeds=speeds, snap_heading=snap_heading)
         out = torch.empty((), dtype=torch.float32, device=goals.device)
         n_points = traj.shape[0]
         stream = torch.cuda.current_stream(goals.device)
         pm_loglik_forward(ctx, model, offsets.numel() - 1, offsets, n_points, traj, log_prior, out, stream)
         fctx.save_for_backward(goals_c, speed, w, beta, offsets, traj, log_prior)
-        fctx.K, fctx.dt, fctx.ctx, fctx.speeds = K, dt, ctx, speeds
+        fctx.K, fctx.dt, fctx.ctx, fctx.speeds, fctx.snap = K, dt, ctx, speeds, snap_heading
         return out
 
     @staticmethod
@@ -36,7 +37,8 @@ class MarginalLogLik(torch.autograd.Function):
         goals, speed, w, beta, offsets, traj, log_prior = fctx.saved_tensors
         v = float(speed.detach().reshape(()).item())
         w1, w2 = (float(x) for x in w.detach().reshape(2).tolist())
-        model = make_model(fctx.K, v, fctx.dt, goals, beta, w1=w1, w2=w2, speeds=fctx.speeds)
+        model = make_model(fctx.K, v, fctx.dt, goals, beta, w1=w1, w2=w2, speeds=fctx.speeds,
+                           snap_heading=fctx.snap)
         dev = goals.device
         L = torch.empty((), dtype=torch.float32, device=dev)
         d_goals = torch.empty_like(goals)
@@ -50,10 +52,10 @@ class MarginalLogLik(torch.autograd.Function):
         gg = d_goals if need[0] else None
         gs = d_speed.to(speed.device).reshape(speed.shape) if need[1] else None
         gw = d_w.to(w.device).reshape(w.shape) if need[2] else None
-        return gg, gs, gw, None, None, None, None, None, None, None, None
+        return gg, gs, gw, None, None, None, None, None, None, None, None, None
 
 
-def marginal_loglik(goals, speed, w, beta, K, dt, offsets, traj, log_prior, ctx, speeds=None):
+def marginal_loglik(goals, speed, w, beta, K, dt, offsets, traj, log_prior, ctx, speeds=None, snap_heading=False):
     """Differentiable marginal log-likelihood (see MarginalLogLik)."""
     return MarginalLogLik.apply(goals, speed, w, beta, K, dt, offsets, traj, log_prior, ctx,
-                                None if speeds is None else tuple(speeds))
+                                None if speeds is None else tuple(speeds), bool(snap_heading))

@@ -334,10 +334,16 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(const __grid_const
                 continue;
             }
             if (!(len >= 1e-6f)) continue; // stationary step: no information
+            float ex = dx / len, ey = dy / len;
+            if (a.snap) { // the discrete control nearest to the observed heading
+                const float2 e = nearest_heading(a.ux, a.uy, a.enabled, a.K, dx, dy);
+                ex = e.x;
+                ey = e.y;
+            }
             StepGrad s;
-            if constexpr (MS) s = step_terms_ms(a, cu, U, zx, zy, dx / len, dy / len, len, gx, gy, beta, grad);
-            else if constexpr (FULL) s = step_terms_full<KT>(a, zx, zy, dx / len, dy / len, gx, gy, beta, grad);
-            else s = step_terms<KT>(a, zx, zy, dx / len, dy / len, gx, gy, beta, grad);
+            if constexpr (MS) s = step_terms_ms(a, cu, U, zx, zy, ex, ey, len, gx, gy, beta, grad);
+            else if constexpr (FULL) s = step_terms_full<KT>(a, zx, zy, ex, ey, gx, gy, beta, grad);
+            else s = step_terms<KT>(a, zx, zy, ex, ey, gx, gy, beta, grad);
             A += (double)s.logpi;
             if (grad) {
                 Gx += s.gx;

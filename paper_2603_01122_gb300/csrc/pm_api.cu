@@ -183,6 +183,8 @@ pm_status check_model(const pm_model *m, bool need_tables = true)
             return fail(PM_EINVAL, "several speeds need K a multiple of 4 with every heading enabled");
         if (m->n_speeds * m->K > 256) return fail(PM_EINVAL, "n_speeds*K=%d above 256", m->n_speeds * m->K);
     }
+    if (m->snap_heading != 0 && m->snap_heading != 1)
+        return fail(PM_EINVAL, "snap_heading=%d must be 0 or 1", m->snap_heading);
     return PM_OK;
 }
 
@@ -281,6 +283,7 @@ void fill_posterior_args(const pm_model *m, pm::PosteriorArgs &a)
     a.B = m->B;
     a.goals = m->goals;
     a.beta = m->beta;
+    a.snap = m->snap_heading;
     fill_speed_set(m, a.sp);
 }
 
@@ -464,6 +467,7 @@ pm_status loglik_impl(pm_ctx *ctx, const pm_model *model, int32_t M, const int32
         a.ux[k] = (float)c;
         a.uy[k] = (float)sn;
     }
+    a.snap = model->snap_heading;
     a.enabled = enabled_mask(model);
     a.s = (float)s;
     a.s2 = (float)(s * s);

@@ -18,6 +18,24 @@ struct SpeedSet {
     float w1;
 };
 
+// The enabled heading nearest to the direction (dx, dy): the largest
+// e_k . (dx, dy), the lower index on a tie, decided in FP32 (the snapped
+// reading of an observed control). Returns its unit vector.
+__device__ __forceinline__ float2 nearest_heading(const float *ux, const float *uy, uint64_t enabled, int K, float dx,
+                                                  float dy)
+{
+    float best = -INFINITY;
+    int kb = 0;
+    for (int k = 0; k < K; ++k) {
+        const float c = fmaf(ux[k], dx, uy[k] * dy);
+        if (((enabled >> k) & 1ull) && c > best) {
+            best = c;
+            kb = k;
+        }
+    }
+    return make_float2(ux[kb], uy[kb]);
+}
+
 // Arguments of the belief-update kernel (Eq. 3 / Eq. 7).
 struct PosteriorArgs {
     float ux[kMaxK], uy[kMaxK]; // unit heading vectors
@@ -30,6 +48,7 @@ struct PosteriorArgs {
     const float *obs;
     int n_obs;
     int steps_per_chunk; // observed steps handled by one CTA
+    int snap;               // observed headings read as the nearest enabled heading
     const float *log_prior; // read by the fold (may equal log_b)
     float *log_b;
     float *part;         // scratch: per (chunk, component) accumulators
@@ -52,6 +71,7 @@ struct AdjointArgs {
     const float *traj;     // [n_points][2]
     const float *log_prior; // [G*B]
     int want_grad;
+    int snap;              // observed headings read as the nearest enabled heading
     float grad_out;
     double *part;          // scratch [M][2G+4]
     double *comp_A;        // scratch [M][J]: sum_t log pi per component

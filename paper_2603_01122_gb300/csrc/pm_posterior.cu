@@ -213,7 +213,12 @@ __device__ __forceinline__ void posterior_chunk(const PosteriorArgs &a, const Po
                 continue;
             }
             if (!(len >= 1e-6f)) continue; // stationary: the belief is unchanged
-            const float ex = dx / len, ey = dy / len;
+            float ex = dx / len, ey = dy / len;
+            if (a.snap) { // the discrete control nearest to the observed heading
+                const float2 e = nearest_heading(a.ux, a.uy, a.enabled, a.K, dx, dy);
+                ex = e.x;
+                ey = e.y;
+            }
             const float px = zx - gx, py = zy - gy;
             if constexpr (MS) {
                 const float so = a.sp.sl[snap_speed(a.sp, h.speed_on, len / a.s)];

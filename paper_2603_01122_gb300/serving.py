@@ -102,7 +102,7 @@ class Server:
     def __init__(self, ctx, K, speed, dt, room_grid, *, max_live=64, budget_bytes=4 << 30,
                  n_particles=50_000, horizon=150, window=121, g_max=6, b_max=10, w1=1.0, w2=1.0,
                  use_graph=True, device="cuda:0", union_sigma=None, speeds=None, stationary_off=0,
-                 stationary_eps=None, goal_radius=None):
+                 stationary_eps=None, goal_radius=None, snap_heading=False):
         import torch
 
         self.torch = torch
@@ -135,7 +135,8 @@ class Server:
         self.stationary_off = int(stationary_off)
         self.stationary_eps = stationary_eps
         self.goal_radius = goal_radius
-        self._shared = make_model(K, speed, dt, shared_goals, shared_beta, w1=w1, w2=w2, speeds=self.speeds)
+        self._shared = make_model(K, speed, dt, shared_goals, shared_beta, w1=w1, w2=w2, speeds=self.speeds,
+                                  snap_heading=snap_heading)
         self.batch = pm_batch_create(ctx, self._shared, cap)
         if union_sigma is not None:  # the union reads only the blocks the rollout marks
             pm_batch_set_block_flags(self.batch, 1)

@@ -17,11 +17,13 @@ def dev(a, dtype=torch.float32):
 class GpuHuman:
     """Device-side model of a workloads.Human (or explicit parameters)."""
 
-    def __init__(self, K, speed, dt, goals, beta, w1=1.0, w2=1.0, heading_off=0, speeds=None, speed_off=0):
+    def __init__(self, K, speed, dt, goals, beta, w1=1.0, w2=1.0, heading_off=0, speeds=None, speed_off=0,
+                 snap_heading=False):
         self.goals = dev(np.asarray(goals, np.float32).reshape(-1, 2))
         self.beta = dev(np.asarray(beta, np.float32).reshape(-1))
         self.model = pm.make_model(K, speed, dt, self.goals, self.beta, w1=w1, w2=w2,
-                                   heading_off=heading_off, speeds=speeds, speed_off=speed_off)
+                                   heading_off=heading_off, speeds=speeds, speed_off=speed_off,
+                                   snap_heading=snap_heading)
 
     @classmethod
     def of(cls, hu, **kw):
