@@ -237,6 +237,50 @@ def oracle_sample(hu, n_particles, obs=None, threads=1):
                       f"update, FP64 C, {threads} host threads over particle ranges ({dt:.2f} s wall)"}
 
 
+def oracle_other_configs(threads):
+    """The oracle (as it stands) on the other configurations: the plain one
+    (K = 8, N = 10k, T = 20) whole, a 1/50 sample of every batched human's
+    particles (scaled by particle-steps), and the exact Markov propagation of
+    the plain one's occupancy (Eq. 4 / Eq. 5, single-threaded)."""
+    import concurrent.futures as cf
+
+    import oracle
+    out = {}
+    hu = workloads.plain_small()
+    cb = oracle_sample(hu, hu.n_particles, threads=threads)
+    out["plain_small"] = {"value": cb["value"], "cores": threads, "sample": cb["sample"],
+                          "one_thread": oracle_sample(hu, hu.n_particles)["value"]}
+    hs = workloads.batched()
+    jobs = []
+    for h in hs:
+        m = oracle.Model(h.K, h.speed, h.dt, h.goals, h.beta)
+        obs = oracle.simulate(m, h.true_j, h.start, h.n_obs, h.obs_seed, h.human_id)
+        jobs.append((h, m, obs, max(256, h.n_particles // 50)))
+    t0 = time.perf_counter()
+    parts = []
+    for h, m, obs, n in jobs:
+        post, _ = oracle.update_posterior(m, obs, h.uniform_log_prior())
+        # each call bins into its own full grid: few, large ranges per human
+        nr = max(1, threads // len(jobs))
+        cuts = np.linspace(0, n, nr + 1).astype(np.int64)
+        parts += [(h, m, post.astype(np.float32), obs[-1], int(cuts[r]), int(cuts[r + 1])) for r in range(nr)]
+    with cf.ThreadPoolExecutor(threads) as ex:
+        list(ex.map(lambda a: oracle.rollout(a[1], a[2], a[3], a[0].horizon, a[0].seed, a[0].human_id, a[4], a[5],
+                                             grid=a[0].grid), parts))
+    dt = time.perf_counter() - t0
+    ps = sum(n * h.horizon for h, _, _, n in jobs)
+    out["batched_sampled"] = {"value": ps / dt, "cores": threads,
+                              "sample": f"1/50 of each of the 16 humans' particles ({ps:.3g} particle-steps) "
+                                        f"+ their 50-step belief updates, FP64 C ({dt:.2f} s wall)"}
+    m = oracle.Model(hu.K, hu.speed, hu.dt, hu.goals, hu.beta)
+    obs = oracle.simulate(m, hu.true_j, hu.start, hu.n_obs, hu.obs_seed, hu.human_id)
+    post, _ = oracle.update_posterior(m, obs, hu.uniform_log_prior())
+    t0 = time.perf_counter()
+    oracle.exact_occupancy(m, post, obs[-1], hu.horizon, hu.grid)
+    out["exact_propagation_plain_small_s"] = time.perf_counter() - t0
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -839,6 +883,7 @@ def run_native(args):
             threads = host_threads()
             cb = oracle_sample(hu, args.cpu_sample * max(1, threads // 4), threads=threads)
             cb["one_thread"] = oracle_sample(hu, max(2000, args.cpu_sample // 4))["value"]
+            cb["other_configs"] = oracle_other_configs(threads)
             line["cpu_baseline"] = cb
         print(json.dumps(line), flush=True)
     pm.pm_destroy(ctx)
