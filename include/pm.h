@@ -33,14 +33,11 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "pm_limits.h"
+
 #ifdef __cplusplus
 extern "C" {
 #endif
-
-#define PM_MAX_HEADINGS 64    /* K in [1, 64]                      */
-#define PM_MAX_COMPONENTS 256 /* G*B in [1, 256]                   */
-#define PM_MAX_GOALS 64       /* G in [1, 64]                      */
-#define PM_MAX_HORIZON 4096   /* T in [1, 4096]                    */
 
 typedef enum pm_status {
     PM_OK = 0,
@@ -53,8 +50,6 @@ typedef enum pm_status {
 /* Opaque context: one device, its properties, scratch buffers and tuned
  * launch parameters. Not thread-safe; use one context per host thread. */
 typedef struct pm_ctx pm_ctx;
-
-#define PM_MAX_SPEEDS 4        /* speeds of the control set          */
 
 /* Human model. `goals` and `beta` are device pointers ([G][2] and [B]).
  * `heading_off` bit k set disables heading k (Q = -inf, so pi = 0), the
@@ -186,7 +181,8 @@ pm_status pm_predict_occupancy(pm_ctx *ctx, const pm_model *model, const float *
 
 /* The same launch as pm_predict_occupancy, also recording the trajectories
  * of particles [0, n_trace):
- *   states      [n_trace][horizon][2] FP32 state after each step, or NULL
+ *   states      [n_trace][horizon][2] FP32 state after each step, or NULL;
+ *               8-byte aligned (each state is stored as one pair), else PM_EINVAL
  *   headings    [n_trace][horizon] uint8 heading index of each step, or NULL
  *   components  [n_trace] int32 drawn component j, or NULL
  * `counts`/`oob` may both be NULL to skip the histogram (then `grid` may be
@@ -460,7 +456,7 @@ typedef struct pm_mppi {
 } pm_mppi;
 
 /* z0: robot state (host, 4 floats). u_ref: device [T][2]; delta: device
- * [T][N][2] (sample-minor, the caller draws it); prob: device [prob_T][H][W]
+ * [T][N][2] (sample-minor, the caller draws it; 8-byte aligned, else PM_EINVAL); prob: device [prob_T][H][W]
  * predicted occupancy on `grid` (e.g. pm_batch_union's output), or NULL for
  * no collision cost. Outputs (device, caller-owned): cost_to_go [T][N]
  * (S_i(t); S_i(0) is sample i's total cost) and u_opt [T][2]. Two kernels,

@@ -350,6 +350,9 @@ pm_status predict_impl(pm_ctx *ctx, const pm_model *model, const float *log_beli
         if (st != PM_OK) return st;
     }
     if (n_trace < 0 || n_trace > n_particles) return fail(PM_EINVAL, "n_trace=%d outside [0, n_particles]", n_trace);
+    // the kernel stores each traced state as one 8-byte pair
+    if (n_trace > 0 && states && ((uintptr_t)states & 7u))
+        return fail(PM_EINVAL, "states must be 8-byte aligned");
     if (!hist && n_trace == 0) return fail(PM_EINVAL, "nothing to compute: no histogram and no trace");
     DeviceScope dev(ctx->device);
 
@@ -1360,6 +1363,7 @@ pm_status pm_mppi_solve(pm_ctx *ctx, const pm_mppi *p, const float *z0, const fl
 {
     if (!ctx || !p || !z0 || !u_ref || !delta || !cost_to_go || !u_opt)
         return fail(PM_EINVAL, "ctx/params/z0/u_ref/delta/cost_to_go/u_opt is NULL");
+    if ((uintptr_t)delta & 7u) return fail(PM_EINVAL, "delta must be 8-byte aligned (read as pairs)");
     if (p->n_samples < 1 || p->horizon < 1 || p->pred_stride < 1)
         return fail(PM_EINVAL, "n_samples=%d horizon=%d pred_stride=%d must be >= 1", p->n_samples, p->horizon,
                     p->pred_stride);

@@ -5,7 +5,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "pm.h"
+#include "pm_limits.h"
 
 namespace pm {
 
