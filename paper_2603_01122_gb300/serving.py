@@ -23,6 +23,11 @@ room grid centred on the human's cell (Algorithm 1, bootstrapped belief).
   step; a change re-uploads the descriptors only. ``reset_belief`` returns a
   human to the uniform belief; with ``goal_radius`` the server does so itself
   when a human leaves a goal (``GoalDeparture``).
+* Checkpoint and resume: ``export_state`` reads a live human's state (its
+  device-resident log-belief, goals, beta grid, last two observed states,
+  seed, human id, speed mask and goal-departure state) back as plain host
+  data; ``import_state`` re-admits a human from it, on this server or on a
+  new one, and the frames that follow equal those of an uninterrupted run.
 * Latency = host wall time from the start of the frame (observations in host
   memory) to the occupancy being ready on the device (event synchronised).
 
@@ -246,6 +251,37 @@ class Server:
         self.done.synchronize()
         self.frames += 1
         return time.perf_counter() - t0
+
+    # -- checkpoint and resume ---------------------------------------------------
+    def export_state(self, slot: int) -> dict:
+        """A live human's state as plain host data (numpy arrays, Python
+        scalars); waits for the server's stream so the belief is current."""
+        m = self.meta[slot]
+        self.stream.synchronize()
+        dep = m["departure"]
+        return dict(key=m["key"], goals=self.goals[slot, :m["G"]].cpu().numpy(),
+                    beta=self.beta[slot, :m["B"]].cpu().numpy(),
+                    log_b=self.log_b[slot, :m["G"] * m["B"]].cpu().numpy(),
+                    obs=self.obs_host[slot].numpy().copy(), seed=m["seed"], human_id=m["human_id"],
+                    speed_off=m["speed_off"], at_goal=None if dep is None else dep.at_goal)
+
+    def import_state(self, state: dict) -> Optional[int]:
+        """Re-admit a human from ``export_state``'s data; returns its slot, or
+        None when no slot or budget is left."""
+        s = self.admit(state["key"], state["goals"], state["beta"], state["obs"][1], state["seed"],
+                       state["human_id"])
+        if s is None:
+            return None
+        lb = np.asarray(state["log_b"], np.float32)
+        with self.torch.cuda.stream(self.stream):
+            self.log_b[s, :lb.shape[0]].copy_(self.torch.as_tensor(lb))
+        self.obs_host[s].copy_(self.torch.as_tensor(np.asarray(state["obs"], np.float32)))
+        self.meta[s]["speed_off"] = int(state["speed_off"])
+        dep = self.meta[s]["departure"]
+        if dep is not None and state.get("at_goal") is not None:
+            dep.at_goal = bool(state["at_goal"])
+        self.dirty = True
+        return s
 
     def occupancy(self, slot: int):
         """(counts [T, W, W], oob [T]) of a live slot after the last frame (device)."""

@@ -182,3 +182,57 @@ def test_serving_resets_the_belief_when_a_human_leaves_a_goal(ctx):
         np.testing.assert_allclose(srv.log_b[s, :J].cpu().numpy(), -np.log(J), rtol=0, atol=1e-6)
     finally:
         srv.close()
+
+
+def test_checkpoint_and_resume(ctx, orc):
+    """Three humans served for 12 frames. At frame 5 one is exported, retired
+    and re-admitted from its state, and another is moved to a second server
+    the same way; every later frame of all three equals the uninterrupted
+    run's, bit for bit (counts and beliefs)."""
+    from paper_2603_01122_gb300.serving import Server
+    arr = workloads.serving(duration_s=6.0, rate_hz=3.0)["arrivals"][:3]
+    paths = []
+    for a in arr:
+        hu = a.human
+        m = orc.Model(hu.K, hu.speed, hu.dt, hu.goals, hu.beta)
+        paths.append(orc.simulate(m, hu.true_j, hu.start, 20, hu.obs_seed, hu.human_id).astype(np.float32))
+    hu0 = arr[0].human
+    kw = dict(max_live=4, n_particles=2000, horizon=25, window=41)
+
+    def admit_all(srv):
+        return [srv.admit(i, a.human.goals, a.human.beta, paths[i][0], a.human.seed, a.human.human_id)
+                for i, a in enumerate(arr)]
+
+    ref = Server(ctx, hu0.K, hu0.speed, hu0.dt, hu0.grid, **kw)
+    a_srv = Server(ctx, hu0.K, hu0.speed, hu0.dt, hu0.grid, **kw)
+    b_srv = Server(ctx, hu0.K, hu0.speed, hu0.dt, hu0.grid, **kw)
+    try:
+        rs, as_ = admit_all(ref), admit_all(a_srv)
+        where = {i: (a_srv, as_[i]) for i in range(3)}
+        for f in range(1, 13):
+            if f == 5:
+                st0 = a_srv.export_state(where[0][1])
+                a_srv.retire(where[0][1])
+                where[0] = (a_srv, a_srv.import_state(st0))
+                st2 = a_srv.export_state(where[2][1])
+                a_srv.retire(where[2][1])
+                where[2] = (b_srv, b_srv.import_state(st2))
+            for i in range(3):
+                ref.observe(rs[i], paths[i][f])
+                srv, s = where[i]
+                srv.observe(s, paths[i][f])
+            ref.frame()
+            a_srv.frame()
+            if b_srv.slots.live:
+                b_srv.frame()
+            torch.cuda.synchronize()
+            for i in range(3):
+                srv, s = where[i]
+                J = arr[i].human.G * arr[i].human.B
+                assert torch.equal(srv.log_b[s, :J], ref.log_b[rs[i], :J]), (f, i)
+                assert torch.equal(srv.counts[s], ref.counts[rs[i]]), (f, i)
+                assert torch.equal(srv.oob[s], ref.oob[rs[i]]), (f, i)
+    finally:
+        ref.close()
+        a_srv.close()
+        b_srv.close()
