@@ -234,7 +234,7 @@ def oracle_sample(hu, n_particles, obs=None, threads=1):
     dt = time.perf_counter() - t0
     ps = n_particles * hu.horizon
     return {"value": ps / dt, "unit": METRIC, "cores": threads, "kind": "oracle",
-            "sample": f"{n_particles} of {hu.n_particles} particles x T={hu.horizon} + 50-step belief "
+            "sample": f"{n_particles} of {hu.n_particles} particles x T={hu.horizon} + {hu.n_obs}-step belief "
                       f"update, FP64 C, {threads} host threads over particle ranges ({dt:.2f} s wall)"}
 
 
