@@ -297,7 +297,9 @@ def run_reference(args):
         per_step.append(n * hu.horizon / r["value"])
     total = sum(per_step)
     value = n * hu.horizon * args.steps / total
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 0,
+    # n_gpus is the launch's N (the line pairs with the native arm's); the
+    # oracle itself runs on rank 0's host cores only
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "gpus_used": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (model-drawn observations, seeded)", "config": workload_config(hu, args.workload),
