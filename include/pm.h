@@ -109,7 +109,10 @@ typedef struct pm_grid {
  * until a call needs scratch. */
 pm_status pm_create(pm_ctx **ctx, int device);
 
-/* Release the context and the device memory it owns. NULL is accepted. */
+/* Release the context and the device and page-locked memory it owns, after
+ * waiting for the context's copy stream and the uploads of its host-buffer
+ * calls. Work the caller queued on its own streams with this context must
+ * have finished (synchronise those streams first). NULL is accepted. */
 void pm_destroy(pm_ctx *ctx);
 
 /* Message of the last failed call on the calling thread ("" if none). */
