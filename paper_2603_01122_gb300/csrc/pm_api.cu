@@ -11,6 +11,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "pm.h"
 #include "pm_kernels.cuh"
@@ -80,6 +81,16 @@ struct pm_batch {
     int max_J = 1;
     int occ = 0; // resident CTAs per SM of the current shape (queried outside any capture)
 };
+
+// A named NVTX range over one C ABI call, so that a profiler attributes the
+// call's device work to it; without an attached tool it costs one check.
+struct CallRange {
+    explicit CallRange(const char *name) { nvtxRangePushA(name); }
+    ~CallRange() { nvtxRangePop(); }
+    CallRange(const CallRange &) = delete;
+    CallRange &operator=(const CallRange &) = delete;
+};
+#define PM_RANGE(name) CallRange pm_call_range_(name)
 
 namespace {
 
@@ -748,6 +759,7 @@ pm_status pm_internal_posterior_on_scratch(const pm_model *model, const float *o
                                            float *log_belief, float *part, unsigned *ticket, size_t part_bytes,
                                            int max_chunks, void *stream)
 {
+    PM_RANGE("pm_internal_posterior_on_scratch");
     pm_status st = check_model(model);
     if (st != PM_OK) return st;
     if (n_obs < 0) return fail(PM_EINVAL, "n_obs=%d must be >= 0", n_obs);
@@ -778,6 +790,7 @@ extern "C" {
 
 pm_status pm_create(pm_ctx **out, int device)
 {
+    PM_RANGE("pm_create");
     if (!out) return fail(PM_EINVAL, "out is NULL");
     *out = nullptr;
     int n = 0;
@@ -809,6 +822,7 @@ pm_status pm_create(pm_ctx **out, int device)
 
 void pm_destroy(pm_ctx *ctx)
 {
+    PM_RANGE("pm_destroy");
     if (!ctx) return;
     {
         DeviceScope dev(ctx->device);
@@ -838,6 +852,7 @@ const char *pm_version(void) { return "pm 0.1.0 (sm_103a)"; }
 
 pm_status pm_sync_status(pm_ctx *ctx, void *stream)
 {
+    PM_RANGE("pm_sync_status");
     if (!ctx) return fail(PM_EINVAL, "ctx is NULL");
     DeviceScope dev(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -859,12 +874,14 @@ pm_status pm_sync_status(pm_ctx *ctx, void *stream)
 pm_status pm_update_posterior(pm_ctx *ctx, const pm_model *model, const float *obs_xy, int32_t n_obs,
                               float *log_belief, void *stream)
 {
+    PM_RANGE("pm_update_posterior");
     return posterior_impl(ctx, model, obs_xy, n_obs, log_belief, log_belief, (cudaStream_t)stream);
 }
 
 pm_status pm_update_posterior_into(pm_ctx *ctx, const pm_model *model, const float *obs_xy, int32_t n_obs,
                                    const float *log_prior, float *log_belief, void *stream)
 {
+    PM_RANGE("pm_update_posterior_into");
     return posterior_impl(ctx, model, obs_xy, n_obs, log_prior, log_belief, (cudaStream_t)stream);
 }
 
@@ -873,6 +890,7 @@ pm_status pm_predict_occupancy(pm_ctx *ctx, const pm_model *model, const float *
                                uint64_t seed, uint32_t human_id, uint32_t *counts, uint32_t *oob,
                                void *stream)
 {
+    PM_RANGE("pm_predict_occupancy");
     if (!counts || !oob) return fail(PM_EINVAL, "counts and oob are required");
     return predict_impl(ctx, model, log_belief, z0x, z0y, n_particles, horizon, grid, seed, human_id,
                         counts, oob, 0, nullptr, nullptr, nullptr, (cudaStream_t)stream);
@@ -884,6 +902,7 @@ pm_status pm_predict_occupancy_traced(pm_ctx *ctx, const pm_model *model, const 
                                       uint32_t *counts, uint32_t *oob, int32_t n_trace, float *states,
                                       uint8_t *headings, int32_t *components, void *stream)
 {
+    PM_RANGE("pm_predict_occupancy_traced");
     return predict_impl(ctx, model, log_belief, z0x, z0y, n_particles, horizon, grid, seed, human_id,
                         counts, oob, n_trace, states, headings, components, (cudaStream_t)stream);
 }
@@ -1015,6 +1034,7 @@ pm_status pm_predict_host(pm_ctx *ctx, const pm_model *model, const float *goals
                           int32_t horizon, const pm_grid *grid, uint64_t seed, uint32_t human_id,
                           float *posterior_out, uint32_t *counts_out, uint32_t *oob_out, void *stream)
 {
+    PM_RANGE("pm_predict_host");
     cudaStream_t s = (cudaStream_t)stream;
     pm_status st = predict_host_impl(ctx, model, goals, beta, obs_xy, n_obs, log_prior, n_particles, horizon, grid,
                                      seed, human_id, posterior_out, counts_out, oob_out, s, -1);
@@ -1030,6 +1050,7 @@ pm_status pm_predict_host_async(pm_ctx *ctx, const pm_model *model, const float 
                                 int32_t horizon, const pm_grid *grid, uint64_t seed, uint32_t human_id,
                                 float *posterior_out, uint32_t *counts_out, uint32_t *oob_out, void *stream)
 {
+    PM_RANGE("pm_predict_host_async");
     if (!ctx) return fail(PM_EINVAL, "ctx is NULL");
     const int slot = ctx->next_slot;
     pm_status st = predict_host_impl(ctx, model, goals, beta, obs_xy, n_obs, log_prior, n_particles, horizon, grid,
@@ -1040,6 +1061,7 @@ pm_status pm_predict_host_async(pm_ctx *ctx, const pm_model *model, const float 
 
 pm_status pm_host_fence(pm_ctx *ctx, void *stream)
 {
+    PM_RANGE("pm_host_fence");
     if (!ctx) return fail(PM_EINVAL, "ctx is NULL");
     DeviceScope dev(ctx->device);
     for (int i = 0; i < 2; ++i) {
@@ -1053,6 +1075,7 @@ pm_status pm_host_fence(pm_ctx *ctx, void *stream)
 
 pm_status pm_batch_create(pm_ctx *ctx, const pm_model *shared, int32_t max_humans, pm_batch **out)
 {
+    PM_RANGE("pm_batch_create");
     if (!ctx || !out) return fail(PM_EINVAL, "ctx/out is NULL");
     *out = nullptr;
     pm_status st = check_model(shared, false);
@@ -1089,6 +1112,7 @@ pm_status pm_batch_create(pm_ctx *ctx, const pm_model *shared, int32_t max_human
 
 void pm_batch_destroy(pm_batch *b)
 {
+    PM_RANGE("pm_batch_destroy");
     if (!b) return;
     DeviceScope dev(b->ctx->device);
     if (b->staged) {
@@ -1110,6 +1134,7 @@ void pm_batch_destroy(pm_batch *b)
 
 pm_status pm_batch_set(pm_batch *b, const pm_human *humans, int32_t n_humans, void *stream)
 {
+    PM_RANGE("pm_batch_set");
     if (!b) return fail(PM_EINVAL, "batch is NULL");
     if (n_humans < 0 || n_humans > b->max_humans) return fail(PM_EINVAL, "n_humans=%d outside [0, %d]", n_humans, b->max_humans);
     if (n_humans > 0 && !humans) return fail(PM_EINVAL, "humans is NULL");
@@ -1124,6 +1149,7 @@ pm_status pm_batch_set(pm_batch *b, const pm_human *humans, int32_t n_humans, vo
 
 pm_status pm_batch_update_posterior(pm_batch *b, void *stream)
 {
+    PM_RANGE("pm_batch_update_posterior");
     if (!b) return fail(PM_EINVAL, "batch is NULL");
     DeviceScope dev(b->ctx->device);
     pm::PosteriorArgs a;
@@ -1137,6 +1163,7 @@ pm_status pm_batch_update_posterior(pm_batch *b, void *stream)
 
 pm_status pm_batch_predict(pm_batch *b, void *stream)
 {
+    PM_RANGE("pm_batch_predict");
     if (!b) return fail(PM_EINVAL, "batch is NULL");
     DeviceScope dev(b->ctx->device);
     return batch_predict_impl(b, (cudaStream_t)stream);
@@ -1167,6 +1194,7 @@ pm_status smooth_taps(float sigma, pm::SmoothArgs &a)
 pm_status pm_smooth_occupancy(pm_ctx *ctx, const uint32_t *counts, int32_t n_particles, int32_t horizon,
                               const pm_grid *grid, float sigma_cells, float *prob, void *stream)
 {
+    PM_RANGE("pm_smooth_occupancy");
     if (!ctx || !counts || !prob) return fail(PM_EINVAL, "ctx/counts/prob is NULL");
     if (n_particles < 1) return fail(PM_EINVAL, "n_particles=%d must be >= 1", n_particles);
     if (horizon < 1 || horizon > PM_MAX_HORIZON) return fail(PM_EINVAL, "horizon=%d out of range", horizon);
@@ -1196,6 +1224,7 @@ pm_status pm_smooth_occupancy(pm_ctx *ctx, const uint32_t *counts, int32_t n_par
 pm_status pm_batch_union(pm_batch *b, float sigma_cells, int32_t horizon, const pm_grid *grid, float *prob,
                          void *stream)
 {
+    PM_RANGE("pm_batch_union");
     if (!b || !prob) return fail(PM_EINVAL, "batch/prob is NULL");
     if (horizon < 1 || horizon > PM_MAX_HORIZON) return fail(PM_EINVAL, "horizon=%d out of range", horizon);
     pm_status st = check_grid(grid);
@@ -1227,6 +1256,7 @@ pm_status pm_batch_union(pm_batch *b, float sigma_cells, int32_t horizon, const 
 pm_status pm_batch_get_config(const pm_batch *b, int32_t *threads, int32_t *shared_window, int32_t *ctas_per_sm,
                               int32_t *window_kib)
 {
+    PM_RANGE("pm_batch_get_config");
     if (!b) return fail(PM_EINVAL, "batch is NULL");
     if (threads) *threads = b->threads;
     if (shared_window) *shared_window = b->warp_hist ? 0 : 1;
@@ -1238,6 +1268,7 @@ pm_status pm_batch_get_config(const pm_batch *b, int32_t *threads, int32_t *shar
 pm_status pm_batch_set_config(pm_batch *b, int32_t threads, int32_t shared_window, int32_t ctas_per_sm,
                               int32_t window_kib)
 {
+    PM_RANGE("pm_batch_set_config");
     if (!b) return fail(PM_EINVAL, "batch is NULL");
     if (shared_window != 0 && shared_window != 1) return fail(PM_EINVAL, "shared_window must be 0 or 1");
     if (threads < 32 || threads > 256 || threads % 32) return fail(PM_EINVAL, "threads=%d must be 32..256, multiple of 32", threads);
@@ -1263,6 +1294,7 @@ pm_status pm_batch_set_config(pm_batch *b, int32_t threads, int32_t shared_windo
 
 pm_status pm_batch_set_block_flags(pm_batch *b, int32_t enable, void *stream)
 {
+    PM_RANGE("pm_batch_set_block_flags");
     if (!b) return fail(PM_EINVAL, "batch is NULL");
     if (enable != 0 && enable != 1) return fail(PM_EINVAL, "enable must be 0 or 1");
     DeviceScope dev(b->ctx->device);
@@ -1272,6 +1304,7 @@ pm_status pm_batch_set_block_flags(pm_batch *b, int32_t enable, void *stream)
 
 pm_status pm_batch_autotune(pm_batch *b, void *stream)
 {
+    PM_RANGE("pm_batch_autotune");
     if (!b) return fail(PM_EINVAL, "batch is NULL");
     if (b->humans.empty()) return PM_OK;
     DeviceScope dev(b->ctx->device);
@@ -1333,6 +1366,7 @@ pm_status pm_loglik_forward(pm_ctx *ctx, const pm_model *model, int32_t M, const
                             int32_t n_points, const float *traj_xy, const float *log_prior, float *loglik,
                             void *stream)
 {
+    PM_RANGE("pm_loglik_forward");
     return loglik_impl(ctx, model, M, offsets, n_points, traj_xy, log_prior, false, 1.0f, loglik, nullptr,
                        nullptr, nullptr, (cudaStream_t)stream);
 }
@@ -1341,6 +1375,7 @@ pm_status pm_loglik_backward(pm_ctx *ctx, const pm_model *model, int32_t M, cons
                              int32_t n_points, const float *traj_xy, const float *log_prior, float grad_out,
                              float *loglik, float *d_goals, float *d_speed, float *d_w, void *stream)
 {
+    PM_RANGE("pm_loglik_backward");
     return loglik_impl(ctx, model, M, offsets, n_points, traj_xy, log_prior, true, grad_out, loglik, d_goals,
                        d_speed, d_w, (cudaStream_t)stream);
 }
@@ -1348,6 +1383,7 @@ pm_status pm_loglik_backward(pm_ctx *ctx, const pm_model *model, int32_t M, cons
 pm_status pm_philox_blocks(pm_ctx *ctx, uint64_t seed, uint32_t human_id, uint32_t purpose, uint64_t particle0,
                            uint64_t block, int32_t n, uint64_t *out, void *stream)
 {
+    PM_RANGE("pm_philox_blocks");
     if (!ctx || !out) return fail(PM_EINVAL, "ctx/out is NULL");
     if (n < 0) return fail(PM_EINVAL, "n must be >= 0");
     if (n == 0) return PM_OK;
@@ -1361,6 +1397,7 @@ pm_status pm_mppi_solve(pm_ctx *ctx, const pm_mppi *p, const float *z0, const fl
                         const float *prob, int32_t prob_T, const pm_grid *grid, float *cost_to_go, float *u_opt,
                         void *stream)
 {
+    PM_RANGE("pm_mppi_solve");
     if (!ctx || !p || !z0 || !u_ref || !delta || !cost_to_go || !u_opt)
         return fail(PM_EINVAL, "ctx/params/z0/u_ref/delta/cost_to_go/u_opt is NULL");
     if ((uintptr_t)delta & 7u) return fail(PM_EINVAL, "delta must be 8-byte aligned (read as pairs)");
@@ -1419,6 +1456,7 @@ pm_status pm_mppi_solve(pm_ctx *ctx, const pm_mppi *p, const float *z0, const fl
 
 pm_status pm_probe_sfu(pm_ctx *ctx, int op, double *results_per_s)
 {
+    PM_RANGE("pm_probe_sfu");
     if (!ctx || !results_per_s) return fail(PM_EINVAL, "ctx/results is NULL");
     if (op < 0 || op > 5) return fail(PM_EINVAL, "op %d outside [0, 5]", op);
     DeviceScope dev(ctx->device);
@@ -1452,6 +1490,7 @@ pm_status pm_probe_sfu(pm_ctx *ctx, int op, double *results_per_s)
 
 pm_status pm_device_info(pm_ctx *ctx, int *sm_count, int *clock_khz, int *cc)
 {
+    PM_RANGE("pm_device_info");
     if (!ctx) return fail(PM_EINVAL, "ctx is NULL");
     if (sm_count) *sm_count = ctx->sm_count;
     if (clock_khz) *clock_khz = ctx->clock_khz;
