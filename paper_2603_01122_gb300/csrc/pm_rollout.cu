@@ -31,8 +31,8 @@ namespace pm {
 namespace {
 
 
-constexpr int kWarpCtaThreads = 256; // 8 warps: two per SM sub-partition
-constexpr int kWarpCtaMinBlocks = 3;
+constexpr int kWarpCtaThreads = 128; // 4 warps: one per SM sub-partition
+constexpr int kWarpCtaMinBlocks = 6;
 
 // Persistent warps over one human: the CTA loads the component table, the
 // belief CDF and the Euler steps into shared memory once, then each warp
