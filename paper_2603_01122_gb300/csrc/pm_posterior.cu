@@ -315,6 +315,10 @@ __device__ __forceinline__ void posterior_chunk(const PosteriorArgs &a, const Po
     }
 }
 
+// MS: several speeds. A template parameter rather than a branch, so that a
+// launch carries only its own form's code (the kernel runs once per call on
+// a cold instruction cache).
+template <bool MS>
 __global__ void __launch_bounds__(1024) posterior_kernel(const __grid_constant__ PosteriorArgs a)
 {
     PostHuman h;
@@ -330,13 +334,13 @@ __global__ void __launch_bounds__(1024) posterior_kernel(const __grid_constant__
     h.part = a.part;
     h.ticket = a.ticket;
     h.speed_on = a.sp.speed_on;
-    if (a.sp.S > 0) posterior_chunk<true>(a, h, blockIdx.x, gridDim.x);
-    else posterior_chunk<false>(a, h, blockIdx.x, gridDim.x);
+    posterior_chunk<MS>(a, h, blockIdx.x, gridDim.x);
 }
 
 // Batched form: blockIdx.y is the human; the CTAs of a row stride over its
 // chunks, so any number of observed steps fits a fixed grid (as a captured
 // CUDA graph requires); humans with no observed steps leave their row idle.
+template <bool MS>
 __global__ void __launch_bounds__(1024) posterior_batch_kernel(const __grid_constant__ PosteriorArgs a,
                                                                const PostHuman *humans, const int *n_humans)
 {
@@ -345,8 +349,7 @@ __global__ void __launch_bounds__(1024) posterior_batch_kernel(const __grid_cons
     if (h.n_obs <= 0 || h.log_b == nullptr || h.log_prior == nullptr) return;
     const int nchunk = (h.n_obs + h.steps_per_chunk - 1) / h.steps_per_chunk;
     for (int ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
-        if (a.sp.S > 0) posterior_chunk<true>(a, h, ch, nchunk);
-        else posterior_chunk<false>(a, h, ch, nchunk);
+        posterior_chunk<MS>(a, h, ch, nchunk);
     }
 }
 
@@ -370,7 +373,9 @@ cudaError_t launch_posterior_batch(const PosteriorArgs &a, const PostHuman *huma
     int threads = 32 * max_J;
     if (threads > 1024) threads = 1024;
     if (max_rows <= 0) return cudaSuccess;
-    posterior_batch_kernel<<<dim3(max_chunks > 0 ? max_chunks : 1, max_rows), threads, 0, s>>>(a, humans, n_humans);
+    const dim3 grid(max_chunks > 0 ? max_chunks : 1, max_rows);
+    if (a.sp.S > 0) posterior_batch_kernel<true><<<grid, threads, 0, s>>>(a, humans, n_humans);
+    else posterior_batch_kernel<false><<<grid, threads, 0, s>>>(a, humans, n_humans);
     return cudaGetLastError();
 }
 
@@ -379,7 +384,8 @@ cudaError_t launch_posterior(const PosteriorArgs &a, int n_chunks, cudaStream_t 
     const int J = a.G * a.B;
     int threads = 32 * J;
     if (threads > 1024) threads = 1024;
-    posterior_kernel<<<n_chunks, threads, 0, s>>>(a);
+    if (a.sp.S > 0) posterior_kernel<true><<<n_chunks, threads, 0, s>>>(a);
+    else posterior_kernel<false><<<n_chunks, threads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
