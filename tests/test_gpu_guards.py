@@ -99,6 +99,55 @@ def test_posterior_and_host_call(ctx, orc, speeds):
     assert abs(float(torch.exp(out.view.double()).sum()) - 1.0) < 1e-6
 
 
+def test_noalloc_posterior(ctx, orc):
+    import paper_2603_01122_gb300 as pm
+    hu = workloads.paper_scale()
+    gh = GpuHuman.of(hu)
+    m = orc.Model(hu.K, hu.speed, hu.dt, hu.goals, hu.beta)
+    obs = orc.simulate(m, hu.true_j, hu.start, hu.n_obs, hu.obs_seed, hu.human_id).astype(np.float32)
+    lb = Guarded((hu.G * hu.B,), torch.float32)
+    lb.view.copy_(dev(hu.uniform_log_prior()))
+    pm.pm_update_posterior_noalloc(gh.model, dev(obs), hu.n_obs, lb.view)
+    torch.cuda.synchronize()
+    assert lb.intact()
+    assert abs(float(torch.exp(lb.view.double()).sum()) - 1.0) < 1e-6
+
+
+def test_batched_several_speeds(ctx, orc):
+    """The several-speed batched kernel with per-human speed masks and block
+    marks, ragged N and T, windows past the grid's edge."""
+    import paper_2603_01122_gb300 as pm
+    speeds = (0.5, 1.0, 1.5)
+    hs = workloads.batched()[:4]
+    ds = []
+    for k, hu in enumerate(hs):
+        m = orc.Model(32, hu.speed, hu.dt, hu.goals, hu.beta, speeds=speeds)
+        obs = orc.simulate(m, hu.true_j, hu.start, hu.n_obs, hu.obs_seed, hu.human_id).astype(np.float32)
+        x0, y0, res, W, H = hu.grid
+        if k % 2:
+            W = H = 61
+        N, T = 2003 + 31 * k, 17 + 2 * k
+        gh = GpuHuman(32, hu.speed, hu.dt, hu.goals, hu.beta, speeds=speeds)
+        ds.append(dict(hu=hu, gh=gh, obs=dev(obs), z0=dev(obs[-1]), N=N, T=T, center=k % 2,
+                       grid=pm.make_grid(x0, y0, res, W, H), lb=dev(hu.uniform_log_prior()),
+                       counts=Guarded((T, H, W), fill=7), oob=Guarded((T,), fill=7), speed_off=0b110 if k == 2 else 0))
+    b = pm.pm_batch_create(ctx, ds[0]["gh"].model, 4)
+    try:
+        pm.pm_batch_set_block_flags(b, 1)
+        pm.pm_batch_set(b, [pm.make_human(d["gh"].goals, d["gh"].beta, d["lb"], d["z0"], d["N"], d["T"], d["grid"],
+                                          d["hu"].seed, d["hu"].human_id, d["counts"].view, d["oob"].view,
+                                          obs_xy=d["obs"], n_obs=d["hu"].n_obs, center=d["center"],
+                                          speed_off=d["speed_off"]) for d in ds])
+        pm.pm_batch_update_posterior(b)
+        pm.pm_batch_predict(b)
+        torch.cuda.synchronize()
+        for d in ds:
+            assert d["counts"].intact() and d["oob"].intact()
+            assert _hist_ok(d["counts"].view, d["oob"].view, d["N"])
+    finally:
+        pm.pm_batch_destroy(b)
+
+
 def test_batched_full_grids_and_windows(ctx, orc):
     """Humans whose windows reach past the shared grid's edge, centred
     windows, ragged particle counts; then the smoothing and the union."""
