@@ -386,8 +386,7 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
                                 hu.seed, hu.human_id, counts, oob, stream)
     ms = time_events(torch, stream, small, 200)
     out["plain_small"] = {"ms_per_prediction": ms, "hz": 1e3 / ms,
-                          "particle_steps_per_s": hu.n_particles * hu.horizon / (ms * 1e-3),
-                          "config": "1 human, K=8, N=10k, T=20, 20 observed steps, 100x100 grid"}
+                          "particle_steps_per_s": hu.n_particles * hu.horizon / (ms * 1e-3)}
 
     if want("batched"):
         # -- batched: 16 humans, one persistent launch in a CUDA graph vs the plain per-human path
@@ -478,16 +477,11 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
                           "rate_vs_plain_small": steps / (batch_ms * 1e-3) / out["plain_small"]["particle_steps_per_s"],
                           "sfu_roofline_frac": steps / (batch_ms * 1e-3) * 2 * 36 / sfu_peak,
                           "union": {"ms": union_ms, "sigma_cells": 1.5, "bytes": union_bytes,
-                                    "bytes_definition": "counts of the occupied 16x16 blocks + the union written",
                                     "GB_per_s": union_bytes / (union_ms * 1e-3) / 1e9,
                                     "hbm_frac": union_bytes / (union_ms * 1e-3) / 1e9 / HBM_PEAK_GBS,
                                     "dense_ms": dense_ms, "dense_bytes": dense_bytes,
                                     "dense_GB_per_s": dense_bytes / (dense_ms * 1e-3) / 1e9,
-                                    "batched_ms_with_marks": marked_batch_ms,
-                                    "config": f"16 humans' counts [T_h][400][400] -> union [{T_max}][400][400], "
-                                              "blur R = 5; block marks written by the rollout (dense: none)"},
-                          "config": "16 humans, G~U{2..6}, N~U[20k,200k], T~U{50..300}, K=36, 400x400 grid, "
-                                    "graph of belief update + persistent rollout"}
+                                    "batched_ms_with_marks": marked_batch_ms}}
         del recs
 
     if want("serving"):
@@ -543,9 +537,7 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
                 "particle_steps_per_frame": ps, "particle_steps_per_s": ps / float(np.median(lat)),
                 "plain_path_ms_per_frame": plain_ms, "speedup_vs_plain": plain_ms / float(np.median(lat) * 1e3),
                 "rate_vs_plain_small": ps / float(np.median(lat)) / out["plain_small"]["particle_steps_per_s"],
-                "sfu_roofline_frac": ps / float(np.median(lat)) * 2 * 36 / sfu_peak,
-                "target": "p99 < 8 ms at 64 humans",
-                "config": "64 humans, K=36, N=50k, T=150, 121x121 window at 0.05 m, 1 observation/frame, graph replay"}
+                "sfu_roofline_frac": ps / float(np.median(lat)) * 2 * 36 / sfu_peak}
             # the same frames with the grid epilogue (blur + max-union on the room grid) in the graph
             srv_u = Server(ctx, hu0.K, hu0.speed, hu0.dt, hu0.grid, max_live=64, n_particles=hu0.n_particles,
                            horizon=hu0.horizon, window=hu0.window, union_sigma=1.5)
@@ -564,8 +556,7 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
                 lat_u = np.array(lat_u[5:])
                 out["serving_forced_64"]["with_union"] = {
                     "frames": int(lat_u.size), "p50_ms": float(np.percentile(lat_u, 50) * 1e3),
-                    "p99_ms": float(np.percentile(lat_u, 99) * 1e3), "sigma_cells": 1.5,
-                    "union_grid": f"[{hu0.horizon}][{hu0.grid[4]}][{hu0.grid[3]}]"}
+                    "p99_ms": float(np.percentile(lat_u, 99) * 1e3), "sigma_cells": 1.5}
                 # MPPI local planner on that union grid: 8192 perturbed sequences of
                 # 30 steps of 0.1 s (every 5th prediction step)
                 Nm, Tm = 8192, 30
@@ -584,9 +575,7 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
                                      u_opt, stream)
                 mppi_ms = time_events(torch, stream, mppi, 20)
                 out["mppi"] = {"ms_per_solve": mppi_ms, "samples": Nm, "steps": Tm,
-                               "sample_steps_per_s": Nm * Tm / (mppi_ms * 1e-3),
-                               "config": "robot of Eq. 8, 8192 samples x 30 steps of 0.1 s, collision cost from the "
-                                         "64-human union grid [150][400][400]"}
+                               "sample_steps_per_s": Nm * Tm / (mppi_ms * 1e-3)}
             finally:
                 srv_u.close()
             if args.serving_seconds > 0:
@@ -633,10 +622,7 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
             u_on = hu.K * sum(1 for q in range(len(hu.speeds)) if not (hu.speed_off >> q) & 1)
             rate = hu.n_particles * hu.horizon / (ms * 1e-3)
             out[name] = {"ms_per_prediction": ms, "particle_steps_per_s": rate, "controls_enabled": u_on,
-                         "sfu_roofline_frac": rate * 2 * u_on / sfu_peak,
-                         "algorithmic": "2 SFU results (ex2 + sqrt) per enabled control per particle-step",
-                         "config": f"paper_scale room, K=32 x speeds {hu.speeds}, speed_off={hu.speed_off:#b}, "
-                                   "N=100k, T=150, 50 observed steps, 200x200 grid; L2 not flushed"}
+                         "sfu_roofline_frac": rate * 2 * u_on / sfu_peak}
 
     if want("table1"):
         # -- Table 1's configuration (1 human, n = 8192, |G| = 10, |B| = 5, |U| = 96,
@@ -662,10 +648,7 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
                                         hu.seed, hu.human_id, counts, oob, stream)
             t1[f"T{T}"] = time_events(torch, stream, t1_step, 200)
         out["table1"] = {"ms_per_prediction": t1,
-                         "paper_ms_rtx2080ti_gpu_jit": {"T2": 7.0, "T4": 7.0, "T6": 7.0, "T8": 7.0, "T10": 8.0},
-                         "config": "1 human, n=8192, |G|=10, |B|=5, |U|=96 (3 speeds x K=32), 50x50 grid at 0.1 m, "
-                                   "dt=0.1, 20 observed steps; belief update + rollout + histogram per prediction; "
-                                   "the paper's figures are another machine's (context only)"}
+                         "paper_ms_rtx2080ti_gpu_jit": {"T2": 7.0, "T4": 7.0, "T6": 7.0, "T8": 7.0, "T10": 8.0}}
 
     if want("differentiation"):
         # -- differentiation: 256 trajectories, adjoint of the marginal log-likelihood
@@ -692,10 +675,50 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
                                   "q_evals_per_s": nsteps * 40 * (ts.K + 1) / (ms * 1e-3),
                                   # algorithmic SFU results: K + 1 distances and K exponentials
                                   # per step and component
-                                  "sfu_roofline_frac": nsteps * 40 * (2 * ts.K + 1) / (ms * 1e-3) / sfu_peak,
-                                  "config": "256 trajectories, lengths U{50..200}, K=36, 4 goals x 10 beta, "
-                                            "loss + d/d(goals, speed, w1, w2)"}
+                                  "sfu_roofline_frac": nsteps * 40 * (2 * ts.K + 1) / (ms * 1e-3) / sfu_peak}
     return out
+
+
+def sig(x, n=4):
+    """x rounded to n significant digits (None passes through)."""
+    if x is None:
+        return None
+    x = float(x)
+    return float(f"{x:.{n}g}")
+
+
+def target_summary(line, extra):
+    """The figures the targets are stated in, compact: the rollout's SFU
+    fraction, the batched and served rates against the plain per-human path
+    (the plain configuration's rate, and the same humans issued one by one)
+    and the 64-human frame latency with and without the grid epilogue."""
+    t = {"rollout_sfu_frac": sig(line["roofline"]["frac"], 3), "value": sig(line["value"])}
+    if not extra:
+        return t
+    t["plain_small_rate"] = sig(extra["plain_small"]["particle_steps_per_s"])
+    b = extra.get("batched")
+    if b:
+        t["batched"] = {"rate": sig(b["batched_particle_steps_per_s"]), "sfu_frac": sig(b["sfu_roofline_frac"], 3),
+                        "x_plain_small": sig(b["rate_vs_plain_small"], 3),
+                        "x_same_humans_one_by_one": sig(b["speedup_vs_plain"], 3), "ms": sig(b["batched_ms"])}
+    f = extra.get("serving_forced_64")
+    if f:
+        t["served_64"] = {"p50_ms": sig(f["p50_ms"]), "p99_ms": sig(f["p99_ms"]),
+                          "with_union_p99_ms": sig(f.get("with_union", {}).get("p99_ms")),
+                          "with_union_p50_ms": sig(f.get("with_union", {}).get("p50_ms")),
+                          "rate": sig(f["particle_steps_per_s"]), "sfu_frac": sig(f["sfu_roofline_frac"], 3),
+                          "x_plain_small": sig(f["rate_vs_plain_small"], 3),
+                          "x_same_humans_one_by_one": sig(f["speedup_vs_plain"], 3)}
+    p = extra.get("serving_poisson")
+    if p:
+        t["served_poisson"] = {"p50_ms": sig(p["p50_ms"]), "p99_ms": sig(p["p99_ms"]), "max_live": p["max_live"]}
+    d = extra.get("differentiation")
+    if d:
+        t["adjoint_ms"] = sig(d["ms_per_backward"])
+    m = extra.get("multi_speed")
+    if m:
+        t["multi_speed_sfu_frac"] = sig(m["sfu_roofline_frac"], 3)
+    return t
 
 
 def run_native(args):
@@ -765,15 +788,20 @@ def run_native(args):
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     phys = vis.split(",")[local] if vis and vis.split(",")[local].isdigit() else str(local)
     with ClockSampler(phys) as clk:
-        pre = 200 if args.steps >= 100 else 0  # keep the GPU busy while nvidia-smi starts
-        if pre:
-            time.sleep(1.0)
-        with torch.cuda.stream(stream):
-            for _ in range(pre):
-                flush.fill_(1.0)
-                step()
-        torch.cuda.synchronize()
-        wall_t0 = time.time()
+        # nvidia-smi samples every 200 ms, longer than a short timed region:
+        # after it has started, the same steps run for about a second right
+        # before the timed ones, and the clocks are those of the pre-roll and
+        # the timed region together
+        time.sleep(1.0)
+        pre_t0 = time.time()
+        pre = 0
+        while time.time() - pre_t0 < 1.0:
+            with torch.cuda.stream(stream):
+                for _ in range(20):
+                    flush.fill_(1.0)
+                    step()
+            torch.cuda.synchronize()
+            pre += 20
         wall0 = time.perf_counter()
         with torch.cuda.stream(stream):
             for i in range(args.steps):
@@ -786,9 +814,8 @@ def run_native(args):
                 ev[i][2].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
-        clk.mark(wall_t0, time.time())
-        if pre:
-            time.sleep(0.3)
+        clk.mark(pre_t0, time.time())
+        time.sleep(0.3)
     if world > 1:
         tdist.barrier()
     step_ms = [a.elapsed_time(c) for a, b, c in ev]
@@ -873,21 +900,25 @@ def run_native(args):
                                         f"rsqrt {sfu['rsqrt'] / 1e9:.1f} G/s",
                          "algorithmic": f"2U SFU results (U = {U} controls: U ex2 + U sqrt) per particle-step"},
             "device": info,
-            "clocks": clk.summary(),
+            "clocks": {**clk.summary(), "window": f"{pre} pre-roll steps + the timed region"},
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "api": "pm_predict_host_async (one prediction after another; each step's copy-out "
                            "overlaps the next step)", "steps": a_steps,
                     "sync_value": e2e_sync_value, "sync_api": "pm_predict_host (waits for each step's outputs)"},
-            "paper_context": "125 Hz for 1 human, n=8192, T<=10, |U|=96 on an RTX 2080 Ti (Table 1); not this metric",
+            "paper_context": "125 Hz, 1 human, n=8192, T<=10, |U|=96, RTX 2080 Ti (Table 1)",
         }
+        extra = None
         if not args.no_extra:
-            line["extra"] = run_extra(args, pm, ctx, torch, dev, stream, peak * 1e9)
+            extra = run_extra(args, pm, ctx, torch, dev, stream, peak * 1e9)
+            line["extra"] = extra
         if not args.no_cpu_baseline:
             threads = host_threads()
             cb = oracle_sample(hu, args.cpu_sample * max(1, threads // 4), threads=threads)
             cb["one_thread"] = oracle_sample(hu, max(2000, args.cpu_sample // 4))["value"]
             cb["other_configs"] = oracle_other_configs(threads)
             line["cpu_baseline"] = cb
+        # the target figures last, so that the end of the line carries them whole
+        line["targets"] = target_summary(line, extra)
         print(json.dumps(line), flush=True)
     pm.pm_destroy(ctx)
     if world > 1:

@@ -53,7 +53,12 @@ typedef struct pm_ctx pm_ctx;
 
 /* Human model. `goals` and `beta` are device pointers ([G][2] and [B]).
  * `heading_off` bit k set disables heading k (Q = -inf, so pi = 0), the
- * control masking of Sec. IV-B. beta values must be >= 0.
+ * control masking of Sec. IV-B. The beta values (device memory, so not
+ * checked on the host) may be any finite numbers: beta > 0 is the goal-seeking
+ * Boltzmann policy of Eq. 2, beta = 0 the uniform policy over the enabled
+ * controls, and beta < 0 a policy whose most probable heading is the one
+ * farthest from the goal. The predictions latch a non-finite beta or goal
+ * in the context's status word (pm_sync_status then returns PM_EDEVICE).
  *
  * Controls: with n_speeds = 0 (or 1 with speed_mult[0] = 1) the K headings at
  * the one speed v. With n_speeds = S in [1, PM_MAX_SPEEDS], the S*K controls
@@ -375,14 +380,23 @@ pm_status pm_loglik_backward(pm_ctx *ctx, const pm_model *model, int32_t M, cons
  * runs, work enqueued during a stream capture whose mode rejects cudaMalloc,
  * or an application whose device memory belongs to its own pool. It computes
  * what pm_update_posterior computes (same arguments, same belief layout and
- * validation) without a context, and allocates nothing: its scratch is a
- * static device array of this library, 165,888 bytes, which every GPU that
- * loads the library holds until the process exits. Limit: G*B <= 256 (larger
- * models are rejected with PM_EINVAL); the observed steps are split over at
- * most 32 CTAs. The first call on a device looks up the array's device
- * address, so make that first call before any stream capture. Every call
- * shares the array: calls whose work overlaps on the GPU (different streams,
- * or several host threads) race on it and must be serialised by the caller.
+ * host-side validation) without a context, and allocates nothing: its
+ * scratch is a static device array of this library, 164,096 bytes, which
+ * every GPU that loads the library holds until the process exits. Limit:
+ * G*B <= 256 (larger models are rejected with PM_EINVAL); the observed steps
+ * are split over at most 32 CTAs. The first call on a device looks up the
+ * array's device address (loading the library's device code, which
+ * allocates), so make that first call before any stream capture; a first call
+ * inside a capture returns PM_EINVAL. Later calls outside a capture look the
+ * address up again, so the call stays valid after a device reset; inside a
+ * capture they use the last address found on that device. Every call shares
+ * the array, which keeps the last call's contents (the call clears the one
+ * word that must start at zero): calls whose work overlaps on the GPU
+ * (different streams, or several host threads) race on it and must be
+ * serialised by the caller. Inputs that only the kernel can check are
+ * handled as in pm_update_posterior (a step touching a non-finite observed
+ * state is skipped; a NaN or +inf prior entry propagates) but are not
+ * reported: there is no context whose status word pm_sync_status could read.
  * The belief may differ from pm_update_posterior's in the last bits (the
  * steps are summed in other chunks). */
 pm_status pm_update_posterior_noalloc(const pm_model *model, const float *obs_xy, int32_t n_obs,

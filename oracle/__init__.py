@@ -92,7 +92,7 @@ def _declare(lib):
     lib.orc_rollout.argtypes = _MODEL + [C.c_int, _dp, C.c_int, _dp, _dp, C.c_float, C.c_float,
                                          C.c_int, C.c_uint64, C.c_uint32, C.c_int64, C.c_int64,
                                          C.c_float, C.c_float, C.c_float, C.c_int, C.c_int,
-                                         _u32p, _u32p, _u8p, _fp, _dp, _i32p]
+                                         _u32p, _u32p, _u8p, _fp, _dp, _i32p, C.c_int]
     lib.orc_rollout.restype = None
     lib.orc_bin_states.argtypes = [_fp, C.c_int64, C.c_int, C.c_float, C.c_float, C.c_float,
                                    C.c_int, C.c_int, _u32p, _u32p]
@@ -232,9 +232,17 @@ def bin_point(x, y, grid):
 
 
 def rollout(model: Model, log_b, z0, T, seed, human, i0, i1, grid=None, want_counts=True,
-            want_headings=False, want_states32=False, want_states64=False, want_comp=False):
+            want_headings=False, want_states32=False, want_states64=False, want_comp=False,
+            decide_f32=False):
     """Algorithm 1 for particles [i0, i1) of stream (seed, human); ``headings``
     holds the drawn control index u = s*K + k.
+
+    The particle state is carried in FP64 and, beside it, in FP32 (the same
+    FP32 steps an FP32 implementation takes; the FP32 state is what is binned).
+    ``decide_f32`` False evaluates the policy of each draw (Eq. 2) at the FP64
+    state; True at the FP32 state, still in FP64 arithmetic: the particle
+    state of Algorithm 1 held in the paper's FP32, so that a draw can differ
+    from an FP32 implementation's only through that draw's own arithmetic.
 
     ``z0`` is taken as FP32 (the observed state handed to the GPU); ``log_b``
     is the belief b^{t'} (FP32 values from the GPU side are exact in FP64).
@@ -260,7 +268,7 @@ def rollout(model: Model, log_b, z0, T, seed, human, i0, i1, grid=None, want_cou
                     _ptr(lb, _dp), np.float32(z0[0]), np.float32(z0[1]), int(T), C.c_uint64(seed),
                     C.c_uint32(human), int(i0), int(i1), np.float32(x0), np.float32(y0),
                     np.float32(res), int(W), int(H), _ptr(counts, _u32p), _ptr(oob, _u32p),
-                    _ptr(hd, _u8p), _ptr(s32, _fp), _ptr(s64, _dp), _ptr(comp, _i32p))
+                    _ptr(hd, _u8p), _ptr(s32, _fp), _ptr(s64, _dp), _ptr(comp, _i32p), int(bool(decide_f32)))
     if want_counts:
         out["counts"] = counts
         out["oob"] = oob

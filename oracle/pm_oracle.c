@@ -339,15 +339,19 @@ float orc_inv_res(float res)
 /*   states32 [i1-i0][T][2] (FP32 shadow state) may be NULL                   */
 /*   states64 [i1-i0][T][2] (FP64 state)        may be NULL                   */
 /*   comp [i1-i0] (drawn j)                     may be NULL                   */
-/* The policy is evaluated at the FP64 particle state; a shadow FP32 state   */
-/* takes the same FP32 steps (float)(v*dt*cos theta_k) and is what is binned. */
+/* A shadow FP32 state takes the same FP32 steps (float)(v*dt*cos theta_k)  */
+/* and is what is binned. With decide_f32 = 0 the policy (Eq. 2) is          */
+/* evaluated at the FP64 particle state; with decide_f32 = 1 at the FP32     */
+/* state (the particle state of Algorithm 1 held in the paper's FP32, the    */
+/* policy still computed in FP64), so that a draw differs from an FP32       */
+/* implementation's only through the arithmetic of that draw.                */
 /* ------------------------------------------------------------------------ */
 void orc_rollout(ORC_MODEL_ARGS, int G, const double *goals, int B, const double *beta,
                  const double *log_b, float z0x, float z0y, int T,
                  uint64_t seed, uint32_t human, int64_t i0, int64_t i1,
                  float gx0, float gy0, float res, int W, int H,
                  uint32_t *counts, uint32_t *oob, uint8_t *headings,
-                 float *states32, double *states64, int32_t *comp)
+                 float *states32, double *states64, int32_t *comp, int decide_f32)
 {
     orc_model m = ORC_MODEL(G, goals, B, beta);
     int J = G * B, U = S * K;
@@ -377,7 +381,8 @@ void orc_rollout(ORC_MODEL_ARGS, int G, const double *goals, int B, const double
         double zx = (double)z0x, zy = (double)z0y;
         float sx = z0x, sy = z0y;
         for (int t = 1; t <= T; ++t) {
-            orc_log_policy_raw(&m, zx, zy, bt, gx, gy, logpi);
+            if (decide_f32) orc_log_policy_raw(&m, (double)sx, (double)sy, bt, gx, gy, logpi);
+            else orc_log_policy_raw(&m, zx, zy, bt, gx, gy, logpi);
             for (int u = 0; u < U; ++u) e[u] = exp(logpi[u]);
             int k = orc_inverse_cdf(e, U, orc_uniform_step(seed, human, (uint64_t)i, t));
             zx += hc[k];

@@ -22,9 +22,10 @@ namespace {
 
 constexpr int kNoAllocChunks = 32;              // CTAs of one call at most
 constexpr size_t kTicketBytes = 256;            // one zero word, padded
-constexpr size_t kPartBytes = 5 * kNoAllocChunks * PM_MAX_COMPONENTS * sizeof(float) +
-                              PM_MAX_COMPONENTS * sizeof(double);
-constexpr size_t kScratchBytes = kTicketBytes + kPartBytes; // 165,888 bytes
+// five FP32 partial sums per (chunk, component), the belief kernel's layout
+constexpr size_t kPartBytes = 5 * kNoAllocChunks * PM_MAX_COMPONENTS * sizeof(float);
+constexpr size_t kScratchBytes = kTicketBytes + kPartBytes;
+static_assert(kScratchBytes == 164096, "the size stated in pm.h");
 
 // Shared by every call on a device; it keeps the last call's contents.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -34,13 +35,24 @@ std::mutex g_mu;
 void *g_addr[kMaxDevices] = {};
 
 // Device address of g_scratch on the current device (the host-side symbol is
-// only a stand-in); looked up once per device.
-pm_status scratch_address(int device, unsigned char **out)
+// only a stand-in). It is looked up again on every call made outside a stream
+// capture, so a device reset (which reloads the module at another address)
+// leaves no stale pointer behind; inside a capture the address of the last
+// lookup on this device is used, since a capture may forbid the lookup (the
+// first call on a device loads the module, which allocates).
+pm_status scratch_address(int device, cudaStream_t stream, unsigned char **out)
 {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(stream, &cap);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return PM_ECUDA;
+    }
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[device]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_addr[device]) {
+        if (cap != cudaStreamCaptureStatusNone) return PM_EINVAL; // first call inside a capture
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
             return PM_ECUDA;
@@ -65,7 +77,11 @@ extern "C" pm_status pm_update_posterior_noalloc(const pm_model *model, const fl
     if (device < 0 || device >= kMaxDevices)
         return pm_internal_error(PM_EINVAL, "pm_update_posterior_noalloc: device ordinal beyond 63");
     unsigned char *base = nullptr;
-    if (scratch_address(device, &base) != PM_OK)
+    const pm_status st = scratch_address(device, (cudaStream_t)stream, &base);
+    if (st == PM_EINVAL)
+        return pm_internal_error(PM_EINVAL, "pm_update_posterior_noalloc: the first call on a device must come "
+                                            "before any stream capture");
+    if (st != PM_OK)
         return pm_internal_error(PM_ECUDA, "pm_update_posterior_noalloc: cudaGetSymbolAddress of the scratch failed");
     unsigned *ticket = reinterpret_cast<unsigned *>(base);
     float *part = reinterpret_cast<float *>(base + kTicketBytes);

@@ -28,6 +28,9 @@ room grid centred on the human's cell (Algorithm 1, bootstrapped belief).
   seed, human id, speed mask and goal-departure state) back as plain host
   data; ``import_state`` re-admits a human from it, on this server or on a
   new one, and the frames that follow equal those of an uninterrupted run.
+* A frame in which a human has no new observation leaves its belief as it
+  was (the step applied is of length zero) and predicts again from the same
+  state.
 * Latency = host wall time from the start of the frame (observations in host
   memory) to the occupancy being ready on the device (event synchronised).
 
@@ -249,6 +252,10 @@ class Server:
                 self._enqueue()
             self.done.record(self.stream)
         self.done.synchronize()
+        # the frame has applied each live human's step (prev -> cur): a later
+        # frame without a new observation then applies a zero-length step,
+        # which leaves the belief unchanged (the copy above has completed)
+        self.obs_host[:, 0] = self.obs_host[:, 1]
         self.frames += 1
         return time.perf_counter() - t0
 

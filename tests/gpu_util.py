@@ -66,8 +66,12 @@ def predict(ctx, gh, log_b, z0, N, T, grid, seed, human, n_trace=0, hist=True):
     return out
 
 
-def explain_divergences(orc, m, lb, z0, seed, human, got, ref):
+def explain_divergences(orc, m, lb, z0, seed, human, got, ref, decide_f32=False):
     """Check each diverged particle at its first differing draw.
+
+    ``decide_f32``: the oracle run ``ref`` took its draws at the FP32 state
+    (``orc.rollout(..., decide_f32=True)``), so the state term of the budget
+    below is zero and the exact CDF is taken at that state.
 
     The GPU draws with the inverse CDF of its FP32 policy, evaluated at its
     FP32 state, with 22-bit fixed-point weights; the oracle with the exact
@@ -96,8 +100,8 @@ def explain_divergences(orc, m, lb, z0, seed, human, got, ref):
             continue
         g, b = divmod(ko, m.B)
         t = int(np.flatnonzero(got["headings"][i] != ref["headings"][i])[0])
-        z64 = np.asarray(z0, np.float64) if t == 0 else ref["states64"][i, t - 1]
         z32 = np.asarray(z0, np.float64) if t == 0 else ref["states32"][i, t - 1].astype(np.float64)
+        z64 = z32 if (decide_f32 or t == 0) else ref["states64"][i, t - 1]
         C = np.cumsum(np.exp(orc.log_policy(m, z64, m.beta[b], m.goals[g])))
         C /= C[-1]
         u = orc.uniform_step(seed, human, i, t + 1)

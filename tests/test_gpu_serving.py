@@ -236,3 +236,50 @@ def test_checkpoint_and_resume(ctx, orc):
         ref.close()
         a_srv.close()
         b_srv.close()
+
+
+def test_frame_without_observation_keeps_the_belief(ctx, orc):
+    """A frame in which a human gets no new observation leaves its belief bit
+    for bit as it was (the step applied has length zero), also for the first
+    frame after import_state; a human observed in every frame meanwhile
+    follows the oracle's posterior over its observed steps."""
+    from paper_2603_01122_gb300.serving import Server
+    from test_gpu_parity import assert_posterior_close
+    arr = workloads.serving(duration_s=6.0, rate_hz=3.0)["arrivals"][:2]
+    paths = []
+    models = []
+    for a in arr:
+        hu = a.human
+        m = orc.Model(hu.K, hu.speed, hu.dt, hu.goals, hu.beta)
+        models.append(m)
+        paths.append(orc.simulate(m, hu.true_j, hu.start, 12, hu.obs_seed, hu.human_id).astype(np.float32))
+    hu0 = arr[0].human
+    srv = Server(ctx, hu0.K, hu0.speed, hu0.dt, hu0.grid, max_live=4, n_particles=2000, horizon=20, window=31)
+    try:
+        sl = [srv.admit(i, a.human.goals, a.human.beta, paths[i][0], a.human.seed, a.human.human_id)
+              for i, a in enumerate(arr)]
+        J = [a.human.G * a.human.B for a in arr]
+        seen = [0, 0]  # index of each human's last observed state
+        for f in range(1, 11):
+            skip = f in (3, 4, 8)  # human 1 gets no observation in these frames
+            if f == 7:             # human 1 is checkpointed and re-admitted before the frame
+                st = srv.export_state(sl[1])
+                srv.retire(sl[1])
+                sl[1] = srv.import_state(st)
+            srv.stream.synchronize()
+            before = srv.log_b[sl[1], :J[1]].clone()
+            seen[0] += 1
+            srv.observe(sl[0], paths[0][seen[0]])
+            if not skip and f != 7:
+                seen[1] += 1
+                srv.observe(sl[1], paths[1][seen[1]])
+            srv.frame()
+            torch.cuda.synchronize()
+            if skip or f == 7:
+                assert torch.equal(srv.log_b[sl[1], :J[1]], before), f
+            for i in range(2):
+                want, _ = orc.update_posterior(models[i], paths[i][:seen[i] + 1].astype(np.float64),
+                                               np.full(J[i], -np.log(J[i])))
+                assert_posterior_close(srv.log_b[sl[i], :J[i]].cpu().numpy(), want)
+    finally:
+        srv.close()

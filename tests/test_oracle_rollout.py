@@ -216,3 +216,37 @@ def test_rollout_matches_exact_propagation_plain_small(orc):
     for t in range(1, T + 1):
         d = tv(out["counts"][t - 1], out["oob"][t - 1], N, p[t - 1], po[t - 1])
         assert d <= tv_bound(p[t - 1], po[t - 1], N) + em[t - 1], (t, d)
+
+
+# ----------------------------------------------------------- draws at the FP32 state
+def test_decide_f32_takes_each_draw_at_the_fp32_state(orc):
+    """With decide_f32 every draw is Eq. 2 evaluated at the FP32 shadow state
+    (the oracle's FP64 state is ignored for the draws), and without it at the
+    FP64 state: both are rebuilt draw by draw from the policy, the uniform and
+    the inverse-CDF rule. At beta = 300 near the goal the two states' policies
+    differ enough that the two runs part for some particles; a run whose
+    steps are dyadic (every state exact in FP32) is the same in both modes."""
+    hu = workloads.paper_scale()
+    beta = np.float32([300.0])
+    goals = np.float32([[5.3, 5.1]])
+    m = orc.Model(hu.K, hu.speed, hu.dt, goals, beta)
+    z0, T, n = np.float32([5.0, 5.0]), 40, 60
+    kw = dict(want_counts=False, want_headings=True, want_states32=True, want_states64=True, want_comp=True)
+    runs = {f: orc.rollout(m, [0.0], z0, T, 11, 2, 0, n, decide_f32=f, **kw) for f in (False, True)}
+    for f, r in runs.items():
+        for i in range(0, n, 7):
+            for t in (1, 2, T // 2, T):
+                if t == 1:
+                    z = np.asarray(z0, np.float64)
+                else:
+                    z = (r["states32"][i, t - 2].astype(np.float64) if f else r["states64"][i, t - 2])
+                lp = orc.log_policy(m, z, beta[0], goals[0])
+                k = orc.sample_index(np.exp(lp), orc.uniform_step(11, 2, i, t))
+                assert k == r["headings"][i, t - 1], (f, i, t)
+    assert np.any(runs[False]["headings"] != runs[True]["headings"])
+    # dyadic steps: s e_k exact for K = 4 with s = 1/8, every state exact in FP32
+    m4 = orc.Model(4, 1.0, 0.125, goals, np.float32([2.0]))
+    a = orc.rollout(m4, [0.0], z0, 30, 3, 4, 0, 200, decide_f32=False, **kw)
+    b = orc.rollout(m4, [0.0], z0, 30, 3, 4, 0, 200, decide_f32=True, **kw)
+    np.testing.assert_array_equal(a["headings"], b["headings"])
+    np.testing.assert_array_equal(a["states64"], b["states32"].astype(np.float64))
