@@ -222,13 +222,27 @@ void fill_rollout_tables(const pm_model *m, pm::RolloutArgs &a)
         a.tab.sy[k] = (float)(s * sn);
         a.tab.tx[k] = (float)(2.0 * s * c);
         a.tab.ty[k] = (float)(2.0 * s * sn);
+        a.tab.cdf[k][0] = (float)c;
+        a.tab.cdf[k][1] = (float)(c - (double)a.tab.cdf[k][0]);
+        a.tab.sdf[k][0] = (float)sn;
+        a.tab.sdf[k][1] = (float)(sn - (double)a.tab.sdf[k][0]);
     }
     a.enabled = enabled_mask(m);
     a.tab.s = (float)s;
+    a.tab.v = m->speed;
+    a.tab.dt = m->dt;
+    a.tab.w1 = m->w1;
+    a.tab.w2 = m->w2;
+    a.tab.K = m->K;
     a.tab.lb_gap = (float)(2.0 * s * std::sin(3.14159265358979323846 / (2.0 * m->K)));
     a.s2 = (float)(s * s);
-    a.w2_log2e = (float)((double)m->w2 * 1.4426950408889634);
-    a.w1_vdt_log2e = (float)((double)m->w1 * s * 1.4426950408889634);
+    const double w2l = (double)m->w2 * 1.4426950408889634, w1l = (double)m->w1 * s * 1.4426950408889634;
+    a.w2_log2e = (float)w2l;
+    a.w1_vdt_log2e = (float)w1l;
+    a.tab.w2l[0] = a.w2_log2e;
+    a.tab.w2l[1] = (float)(w2l - (double)a.w2_log2e);
+    a.tab.w1l[0] = a.w1_vdt_log2e;
+    a.tab.w1l[1] = (float)(w1l - (double)a.w1_vdt_log2e);
     a.tab.S = 0; // one speed: the heading kernels
     if (multi_speed(m)) {
         a.tab.S = m->n_speeds;

@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_rollout_kernel(cons
 // for the current batch, so that a CUDA graph captured on one batch stays
 // valid when humans with more components join later.
 constexpr size_t kWarpTableBytes = (size_t)kMaxJ * 20;
-// Several speeds: also cw1[kMaxJ] (4 B each) after cdf.
+// Several speeds: also the components' beta[kMaxJ] (4 B each) after cdf.
 constexpr size_t kWarpTableBytesMS = (size_t)kMaxJ * 24;
 
 // Persistent warps over all humans: each warp takes a 32-particle tile
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_warp_kernel(const _
     char *slab = reinterpret_cast<char *>(dyn) + (size_t)warp * (MS ? kWarpTableBytesMS : kWarpTableBytes);
     float4 *comp = reinterpret_cast<float4 *>(slab);
     uint32_t *cdf = reinterpret_cast<uint32_t *>(slab + (size_t)kMaxJ * 16);
-    float *cw1 = reinterpret_cast<float *>(slab + (size_t)kMaxJ * 20); // MS only
+    float *betas = reinterpret_cast<float *>(slab + (size_t)kMaxJ * 20); // MS only
     const int n_items = *a.n_items;
     int cur = -1;
     for (;;) {
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_warp_kernel(const _
                 const float gx = h->goals[2 * g], gy = h->goals[2 * g + 1];
                 comp[j] = make_float4(cbj, gx, gy, lb_flag(a.tab, cbj));
                 bad = bad || bad_component(cbj, gx, gy);
-                if constexpr (MS) cw1[j] = h->beta[b] * a.w1_vdt_log2e;
+                if constexpr (MS) betas[j] = h->beta[b];
             }
             // one latch per warp and human for unusable inputs
             const unsigned bits = belief_cdf(h->log_b, J, cdf, lane) | (__any_sync(0xffffffffu, bad) ? kStatusModel : 0u);
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_warp_kernel(const _
         c.fbx = h->fbx;
         c.fplane = h->fbx * h->fby;
         if constexpr (MS)
-            rollout_lane<KT, false, true>(a.tab, a.enabled, a.s2, c, comp, cdf, step, cw1, a.K, h->speed_on);
+            rollout_lane<KT, false, true>(a.tab, a.enabled, a.s2, c, comp, cdf, step, betas, a.K, h->speed_on);
         else rollout_lane<KT, FULL>(a.tab, a.enabled, a.s2, c, comp, cdf, step);
     }
 }

@@ -110,6 +110,26 @@ __device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b)
 }
 
 // Fire-and-forget global add (the result is not needed).
+// Fixed-point heading weights: a weight w in [0, 1] becomes the integer
+// round(w 2^23) in the low mantissa bits of fma(w, kWScale, kWMagic) (the
+// sum lies in [2^23, 2^24], where the float spacing is 1; w = 1 gives 2^24,
+// whose bits minus kWBits are again 2^23). Sums of up to 511 weights fit
+// 32 bits.
+constexpr float kWScale = 8388608.0f;    // 2^23
+constexpr float kWMagic = 8388608.0f;    // 2^23
+constexpr uint32_t kWBits = 0x4B000000u; // bits of kWMagic
+
+// Error-free sum (Knuth's TwoSum): a + b = s + e exactly, s = fl(a + b).
+// Written with explicitly rounded operations so that no contraction or
+// reassociation can change it.
+__device__ __forceinline__ float two_sum(float a, float b, float &e)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+
 __device__ __forceinline__ void red_add(uint32_t *p, uint32_t v)
 {
     asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -137,6 +157,15 @@ struct HeadingTab {
     float sl[PM_MAX_SPEEDS];        // v*mult[s]*dt
     float msx[PM_MAX_SPEEDS][kMaxK]; // Euler step of control (s, k), rounded once from double
     float msy[PM_MAX_SPEEDS][kMaxK];
+    // w2 log2(e) and w1 v dt log2(e), each as a high and a low float (their
+    // sum is the double value): the offsets between speeds are formed from
+    // beta times these exactly
+    float w2l[2], w1l[2];
+    // the model's own values and the unit heading vectors in double-float
+    // (hi, lo), for the settlement of a several-speed draw (draw_multi_exact)
+    float v, dt, w1, w2;
+    int K;
+    float cdf[kMaxK][2], sdf[kMaxK][2];
 };
 
 // Device status word of a context: kernels OR these bits into it when they

@@ -259,6 +259,13 @@ __device__ __forceinline__ void posterior_chunk(const PosteriorArgs &a, const Po
     // memory; the fold and the normalisation stay in FP32 arithmetic (this
     // GPU's FP64 unit retires about two lanes per clock per SM)
     __shared__ float2 L[kMaxJ];
+    // whether any observed step moved the belief: when every step was
+    // skipped (stationary or unusable), the update is the identity and the
+    // prior is returned verbatim, not renormalised in FP32 (which would move
+    // its last bits on every call)
+    __shared__ int moved;
+    if (threadIdx.x == 0) moved = 0;
+    __syncthreads();
     for (int j = warp; j < J; j += nwarp) {
         Acc acc;
         acc_init(acc);
@@ -278,6 +285,7 @@ __device__ __forceinline__ void posterior_chunk(const PosteriorArgs &a, const Po
             acc_merge(acc, q);
         }
         if (lane == 0) {
+            if (acc.mh != 0.0f || acc.ml != 0.0f || acc.ph != 1.0f || acc.pl != 0.0f || acc.e != 0) moved = 1;
             const float lb = h.log_prior[j];
             if (isnan(lb) || lb == INFINITY) flag_status(a.status, kStatusBelief);
             if (lb == -INFINITY) {
@@ -300,7 +308,10 @@ __device__ __forceinline__ void posterior_chunk(const PosteriorArgs &a, const Po
         }
     }
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 0 && !moved) {
+        for (int j = lane; j < J; j += 32) h.log_b[j] = h.log_prior[j];
+        if (lane == 0) *h.ticket = 0u;
+    } else if (warp == 0) {
         float mx = -INFINITY;
         for (int j = lane; j < J; j += 32) mx = fmaxf(mx, L[j].x);
         mx = warp_max(mx);

@@ -12,7 +12,7 @@
 //   beta = 100); logits beta*Q_k up to a common shift are -beta*w2*d_k (w1
 //   cancels, Eq. 2), shifted by a bound of the extreme distance (or the exact
 //   extreme) so that every exponent is <= 0, then ex2.approx on the SFU;
-//   weights are rounded to 22-bit fixed point so that the running sums C_k of
+//   weights are rounded to 23-bit fixed point so that the running sums C_k of
 //   the inverse CDF are exact integers (the sampling decision then depends
 //   only on the rounded weights, not on summation order).
 // The drawn heading moves the FP32 state by one Euler step (Eq. 1); the state
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kWarpCtaThreads, kWarpCtaMinBlocks)
     rollout_multi_kernel(const __grid_constant__ RolloutArgs a, unsigned *head)
 {
     __shared__ float4 comp[kMaxJ];
-    __shared__ float cw1[kMaxJ];
+    __shared__ float betas[kMaxJ];
     __shared__ uint32_t cdf[kMaxJ];
     __shared__ float2 step[PM_MAX_SPEEDS * kMaxK];
     const int tid = threadIdx.x, lane = tid & 31;
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kWarpCtaThreads, kWarpCtaMinBlocks)
         const float cbj = a.beta[b] * a.w2_log2e;
         comp[j] = make_float4(cbj, a.goals[2 * g], a.goals[2 * g + 1], lb_flag(a.tab, cbj));
         if (bad_component(cbj, comp[j].y, comp[j].z)) flag_status(a.status, kStatusModel);
-        cw1[j] = a.beta[b] * a.w1_vdt_log2e;
+        betas[j] = a.beta[b];
     }
     for (int u = tid; u < a.tab.S * a.K; u += blockDim.x)
         step[u] = make_float2(a.tab.msx[u / a.K][u % a.K], a.tab.msy[u / a.K][u % a.K]);
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kWarpCtaThreads, kWarpCtaMinBlocks)
         const int64_t i0 = (int64_t)item * 32;
         if (i0 >= a.N) break;
         c.i = i0 + lane;
-        rollout_lane<KT, false, true>(a.tab, a.enabled, a.s2, c, comp, cdf, step, cw1, a.K, a.tab.speed_on);
+        rollout_lane<KT, false, true>(a.tab, a.enabled, a.s2, c, comp, cdf, step, betas, a.K, a.tab.speed_on);
     }
 }
 

@@ -59,9 +59,11 @@ __device__ inline unsigned belief_cdf(const float *log_b, int J, uint32_t *cdf, 
 // One heading draw of Eq. 2 at state (x, y) for goal (gx, gy) and
 // cb = beta * w2 * log2(e). FULL: all KT headings enabled.
 //
-// d_k - d_0 is formed from the residual of the approximate square root, so
+// d_k - d_0 is formed from the residual of the approximate square root with
+// the per-heading factor 1/(2 d_k) (to first order in p_k, as in
+// corrected_minus: this draw serves the components of large |beta|), so
 // beta*w2*(d_j - d_k) keeps FP32 relative precision; the weights
-// exp(beta (Q_k - Q_max)) are rounded to 22-bit fixed point, so the running
+// exp(beta (Q_k - Q_max)) are rounded to 23-bit fixed point, so the running
 // sums C_k are exact and the draw (smallest k with C_k > (u24 * S) >> 24)
 // depends only on the rounded weights. For even KT with every heading
 // enabled the FP32 work runs on packed pairs of consecutive headings
@@ -75,9 +77,10 @@ __device__ __forceinline__ int draw_heading(const HeadingTab &tab, uint64_t enab
     const float dx = x - gx, dy = y - gy;
     const float D = fmaf(dx, dx, fmaf(dy, dy, s2));
     const float hD = 0.5f * rsqrt_approx(D); // 1/(2 d), D >= s^2 > 0
+    const float c3 = -2.0f * hD * hD * hD;    // 1/(2 d_k) = hD + c3 p_k to first order
     if constexpr (FULL && (KT % 2 == 0)) {
         const f32x2 DX = f2_pack(dx, dx), DY = f2_pack(dy, dy);
-        const f32x2 DD = f2_pack(D, D), NDD = f2_pack(-D, -D), HD = f2_pack(hD, hD);
+        const f32x2 DD = f2_pack(D, D), NDD = f2_pack(-D, -D), HD = f2_pack(hD, hD), C3 = f2_pack(c3, c3);
         const f32x2 *TX = reinterpret_cast<const f32x2 *>(tab.tx);
         const f32x2 *TY = reinterpret_cast<const f32x2 *>(tab.ty);
         f32x2 dv[KT / 2];
@@ -93,7 +96,7 @@ __device__ __forceinline__ int draw_heading(const HeadingTab &tab, uint64_t enab
             const f32x2 DK = f2_pack(d0, d1);
             if (q == 0) DREF = f2_pack(d0, d0);
             const f32x2 R = f2_sub(P, f2_fma(DK, DK, NDD));       // D + p - dk^2
-            dv[q] = f2_fma(R, HD, f2_sub(DK, DREF));                // d_k - d_0, corrected
+            dv[q] = f2_fma(R, f2_fma(P, C3, HD), f2_sub(DK, DREF)); // d_k - d_0, corrected
             float v0, v1;
             f2_unpack(dv[q], v0, v1);
             dmin[q & 3] = fminf(dmin[q & 3], fminf(v0, v1));
@@ -109,9 +112,9 @@ __device__ __forceinline__ int draw_heading(const HeadingTab &tab, uint64_t enab
             }
         }
         const f32x2 NC = f2_pack(-cb, -cb);
-        const float base = dm * cb;
+        const float base = __fmul_rd(dm, cb); // rounded down: every exponent below is <= 0
         const f32x2 BASE = f2_pack(base, base);
-        const f32x2 SC = f2_pack(4194304.0f, 4194304.0f), MG = f2_pack(12582912.0f, 12582912.0f);
+        const f32x2 SC = f2_pack(kWScale, kWScale), MG = f2_pack(kWMagic, kWMagic);
         constexpr int H2 = KT / 2; // the running sums restart at the half: two independent chains
         uint32_t bits[KT];
         uint32_t S0 = 0u, S1 = 0u;
@@ -121,13 +124,13 @@ __device__ __forceinline__ int draw_heading(const HeadingTab &tab, uint64_t enab
             f2_unpack(f2_fma(dv[q], NC, BASE), a0, a1);             // log2 of exp(beta (Q_k - Q_max))
             float w0, w1;
             f2_unpack(f2_fma(f2_pack(ex2_approx(a0), ex2_approx(a1)), SC, MG), w0, w1);
-            bits[2 * q] = __float_as_uint(w0);                      // 0x4B400000 + round(e * 2^22)
+            bits[2 * q] = __float_as_uint(w0);                      // kWBits + round(e * 2^23)
             bits[2 * q + 1] = __float_as_uint(w1);
             if (2 * q < H2) S0 += bits[2 * q]; else S1 += bits[2 * q];
             if (2 * q + 1 < H2) S0 += bits[2 * q + 1]; else S1 += bits[2 * q + 1];
         }
-        S0 -= (uint32_t)H2 * 0x4B400000u;                           // weight of headings [0, K/2)
-        S1 -= (uint32_t)(KT - H2) * 0x4B400000u;                    // weight of headings [K/2, K)
+        S0 -= (uint32_t)H2 * kWBits;                           // weight of headings [0, K/2)
+        S1 -= (uint32_t)(KT - H2) * kWBits;                    // weight of headings [K/2, K)
         const uint32_t S = S0 + S1;                                 // total weight (exact integer)
         const uint32_t thr = (uint32_t)(((uint64_t)(word >> 8) * (uint64_t)S) >> 24);
         // C_k - thr - 1 once E_k is added: negative iff C_k <= thr
@@ -135,9 +138,9 @@ __device__ __forceinline__ int draw_heading(const HeadingTab &tab, uint64_t enab
         int sel0 = 0, sel1 = 0;
 #pragma unroll
         for (int k = 0; k < H2; ++k) {
-            acc0 += bits[k] - 0x4B400000u;
+            acc0 += bits[k] - kWBits;
             sel0 += (int)(acc0 >> 31);
-            acc1 += bits[H2 + k] - 0x4B400000u;
+            acc1 += bits[H2 + k] - kWBits;
             sel1 += (int)(acc1 >> 31);
         }
         return sel0 + sel1;
@@ -150,7 +153,7 @@ __device__ __forceinline__ int draw_heading(const HeadingTab &tab, uint64_t enab
             const float dk = sqrt_approx(fmaxf(D + p, 0.0f));
             const float rk = fmaf(-dk, dk, D) + p;
             if (k == 0) dref = dk;
-            dv[k] = fmaf(rk, hD, dk - dref);
+            dv[k] = fmaf(rk, fmaf(p, c3, hD), dk - dref);
         }
         // the most probable heading: the nearest for beta >= 0, the farthest
         // for beta < 0, so that every exponent below is <= 0
@@ -158,14 +161,14 @@ __device__ __forceinline__ int draw_heading(const HeadingTab &tab, uint64_t enab
 #pragma unroll
         for (int k = 0; k < KT; ++k)
             if (FULL || ((enabled >> k) & 1ull)) dext = (cb >= 0.0f) ? fminf(dext, dv[k]) : fmaxf(dext, dv[k]);
-        const float base = dext * cb;
+        const float base = __fmul_rd(dext, cb); // rounded down: every exponent below is <= 0
         const float nc = -cb;
         uint32_t C[KT];
         uint32_t S = 0;
 #pragma unroll
         for (int k = 0; k < KT; ++k) {
             const float e = ex2_approx(fmaf(dv[k], nc, base));
-            uint32_t E = __float_as_uint(fmaf(e, 4194304.0f, 12582912.0f)) - 0x4B400000u;
+            uint32_t E = __float_as_uint(fmaf(e, kWScale, kWMagic)) - kWBits;
             if (!FULL && !((enabled >> k) & 1ull)) E = 0u;
             S += E;
             C[k] = S;
@@ -224,7 +227,7 @@ struct CdfSegs {
     static_assert(KT % G == 0 && G % 2 == 0, "segments hold whole pairs");
 };
 
-// Inverse CDF over the 22-bit fixed-point weights (bits = 0x4B400000 + w_k):
+// Inverse CDF over the 23-bit fixed-point weights (bits = kWBits + w_k):
 // the smallest k with C_k > (u24 * S) >> 24. Seg[q] is the raw sum of the
 // bits of segment q; each segment scans its own headings from the running
 // sum at its start, so the scan is KT/G short chains instead of one long one.
@@ -238,7 +241,7 @@ __device__ __forceinline__ int select_fixed(const uint32_t (&bits)[KT], const ui
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
         start[q] = S;
-        S += seg[q] - (uint32_t)G * 0x4B400000u;
+        S += seg[q] - (uint32_t)G * kWBits;
     }
     const uint32_t thr = (uint32_t)(((uint64_t)(word >> 8) * (uint64_t)S) >> 24);
     // C_k - thr - 1 once w_k is added: negative iff C_k <= thr
@@ -253,7 +256,7 @@ __device__ __forceinline__ int select_fixed(const uint32_t (&bits)[KT], const ui
     for (int k = 0; k < G; ++k) {
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
-            acc[q] += bits[q * G + k] - 0x4B400000u;
+            acc[q] += bits[q * G + k] - kWBits;
             sel[q] += (int)(acc[q] >> 31);
         }
     }
@@ -278,7 +281,7 @@ __device__ __forceinline__ int draw_heading_lb(const HeadingTab &tab, const LbSt
     const float hD = 0.5f * rsqrt_approx(q.D); // 1/(2 d), D >= s^2 > 0
     const f32x2 DX = f2_pack(q.dx, q.dx), DY = f2_pack(q.dy, q.dy);
     const f32x2 DD = f2_pack(q.D, q.D), NDD = f2_pack(-q.D, -q.D);
-    const f32x2 SC = f2_pack(4194304.0f, 4194304.0f), MG = f2_pack(12582912.0f, 12582912.0f);
+    const f32x2 SC = f2_pack(kWScale, kWScale), MG = f2_pack(kWMagic, kWMagic);
     const f32x2 *TX = reinterpret_cast<const f32x2 *>(tab.tx);
     const f32x2 *TY = reinterpret_cast<const f32x2 *>(tab.ty);
     constexpr int H2 = KT / 2;
@@ -314,7 +317,7 @@ __device__ __forceinline__ int draw_heading_lb(const HeadingTab &tab, const LbSt
 }
 
 // Component flag of the belief table: the bound-normalised draw keeps the
-// largest weight >= 1/2 (22-bit weights keep >= 21 significant bits).
+// largest weight >= 1/2 (23-bit weights keep >= 22 significant bits).
 __device__ __forceinline__ float lb_flag(const HeadingTab &tab, float cb)
 {
     return (fabsf(cb) * tab.lb_gap <= 1.0f) ? 1.0f : 0.0f;
@@ -351,46 +354,290 @@ __device__ __forceinline__ int draw(const HeadingTab &tab, uint64_t enabled, flo
 // speeds are tied together by C_s = cb (REF_s - REF_b) + cw1 (m_s - m_b) - min,
 // formed from differences of nearby floats (exact), so the exponent
 //   a_{k,s} = -cb U_{k,s} - C_s <= 0,  U_{k,s} = d_{k,s} - REF_s.
-// Pass 1 sums each speed's 22-bit fixed-point weights; the threshold picks
+// Pass 1 sums each speed's 23-bit fixed-point weights; the threshold picks
 // the speed from the running per-speed totals, and pass 2 recomputes that
 // speed's weights in heading order until the running sum passes it: the same
 // decision as the inverse CDF over all S*K controls, without storing them.
 // Heading loops run over the runtime K (K a multiple of 4, all enabled).
 // ---------------------------------------------------------------------------
+// D_q = r^2 + sl_q^2 from the common r^2, with its rounding residual eq
+// (exact: the smaller term minus what the sum kept of it, Fast2Sum).
+__device__ __forceinline__ float speed_D(const HeadingTab &tab, int q, float r2, float &eq)
+{
+    const float sl = tab.sl[q];
+    const float s2 = __fmul_rn(sl, sl);
+    const float D = __fadd_rn(r2, s2);
+    eq = __fsub_rn(fminf(r2, s2), __fsub_rn(D, fmaxf(r2, s2)));
+    return D;
+}
+
 struct SpeedStep {
-    float D[PM_MAX_SPEEDS], hD[PM_MAX_SPEEDS], REF[PM_MAX_SPEEDS], C[PM_MAX_SPEEDS];
+    float D[PM_MAX_SPEEDS], hD[PM_MAX_SPEEDS], c3[PM_MAX_SPEEDS], REF[PM_MAX_SPEEDS];
+    float C[PM_MAX_SPEEDS];  // offset of the speed's exponents (high part)
+    float SC[PM_MAX_SPEEDS]; // fixed-point scale 2^23 2^(-low part of the offset)
 };
+
+// Corrected distance of one control from the approximate square root dk of
+// D + P: dk + (D + P - dk^2) / (2 d_k), with 1/(2 d_k) = hD (1 + P/D)^(-1/2)
+// taken to first order, hD - 2 hD^3 P (hD = 1/(2 sqrt(D)), 1/D = 4 hD^2); a
+// common 1/(2 sqrt(D)) would leave (s/r) times the square root's error, which
+// beta w2 turns into 1e-4 of the logit at beta = 10^4. c3 = -2 hD^3.
+__device__ __forceinline__ float corrected_minus(float D, float P, float hD, float c3, float ref)
+{
+    const float dk = sqrt_approx(fabsf(D + P));
+    const float R = P - fmaf(dk, dk, -D);
+    return fmaf(R, fmaf(P, c3, hD), dk - ref);
+}
 
 __device__ __forceinline__ uint32_t multi_weight(const HeadingTab &tab, int k, int sp, float dx, float dy,
                                                  const SpeedStep &q, float cb)
 {
     const float P = __fmul_rn(fmaf(tab.tx[k], dx, tab.ty[k] * dy), tab.mult[sp]); // 2 s_s e_k.(z - g)
-    const float xk = q.D[sp] + P;
-    const float dk = sqrt_approx(fabsf(xk));
-    const float R = P - fmaf(dk, dk, -q.D[sp]);
-    const float U = fmaf(R, q.hD[sp], dk - q.REF[sp]);
+    const float U = corrected_minus(q.D[sp], P, q.hD[sp], q.c3[sp], q.REF[sp]);
     // <= 0 up to the rounding of REF (exact extreme form); the clamp keeps the
-    // weight within 22 bits for any beta
+    // weight within 23 bits for any beta
     const float a = fminf(fmaf(U, -cb, -q.C[sp]), 0.0f);
-    return __float_as_uint(fmaf(ex2_approx(a), 4194304.0f, 12582912.0f)) - 0x4B400000u;
+    return __float_as_uint(fmaf(ex2_approx(a), q.SC[sp], kWMagic)) - kWBits;
+}
+
+// Exact offsets between the speeds. Each speed's D_q = r^2 + sl_q^2 is
+// rounded on its own, so its residual eq_q (exact, by TwoSum from the common
+// r^2) shifts that speed's distances by hD_q eq_q; the offset of speed q is
+//   beta [W2 (REF_q - REF_b) + W1 (m_q - m_b)] + cb hD_q eq_q - min,
+// with W2 = w2 log2(e) and W1 = w1 v dt log2(e) given as high and low floats
+// and beta the component's (exact) FP32 value, carried as a high part (added
+// to the exponents) and a low part (folded into the fixed-point scale), every
+// product split exactly by an FMA. Without this, the independent roundings of
+// the D_q (beta w2 ulp(r^2) / 2d) and of beta w2, beta w1 v dt in FP32 move
+// the speeds' weights against one another.
+// heq[q] = cb hD_q eq_q.
+__device__ __forceinline__ void speed_offsets(const HeadingTab &tab, uint32_t speed_on, float refb, float mb,
+                                              float beta, const float (&REF)[PM_MAX_SPEEDS],
+                                              const float (&heq)[PM_MAX_SPEEDS], float (&hi)[PM_MAX_SPEEDS],
+                                              float (&lo)[PM_MAX_SPEEDS], float bias)
+{
+    float cmin = INFINITY;
+    const float w2h = tab.w2l[0], w2lo = tab.w2l[1], w1h = tab.w1l[0], w1lo = tab.w1l[1];
+#pragma unroll
+    for (int q = 0; q < PM_MAX_SPEEDS; ++q) {
+        float dl, ml, xl;
+        const float dr = two_sum(REF[q], -refb, dl);
+        const float dm = two_sum(tab.mult[q], -mb, ml);
+        const float x1 = __fmul_rn(w2h, dr), x2 = __fmul_rn(w1h, dm);
+        const float x1l = __fadd_rn(fmaf(w2h, dr, -x1), fmaf(w2h, dl, __fmul_rn(w2lo, dr)));
+        const float x2l = __fadd_rn(fmaf(w1h, dm, -x2), fmaf(w1h, ml, __fmul_rn(w1lo, dm)));
+        const float xh = two_sum(x1, x2, xl);
+        const float xlo = __fadd_rn(xl, __fadd_rn(x1l, x2l));
+        const float ch = __fmul_rn(beta, xh);
+        hi[q] = ch;
+        lo[q] = __fadd_rn(fmaf(beta, xh, -ch), fmaf(beta, xlo, heq[q]));
+        if (q < tab.S && ((speed_on >> q) & 1u)) cmin = fminf(cmin, ch);
+    }
+#pragma unroll
+    for (int q = 0; q < PM_MAX_SPEEDS; ++q) {
+        float l;
+        hi[q] = two_sum(hi[q], -cmin, l);
+        lo[q] = __fadd_rn(__fadd_rn(lo[q], l), bias);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic (a value is hi + lo, |lo| <= ulp(hi)/2: about 48
+// significant bits), from the error-free transformations of Knuth (TwoSum)
+// and Dekker (TwoProduct, here with one FMA). Every operation is explicitly
+// rounded so that no contraction or reassociation can change it.
+// ---------------------------------------------------------------------------
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_norm(float a, float b) // |a| >= |b| or a == 0
+{
+    const float s = __fadd_rn(a, b);
+    return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ DF df_add(DF x, DF y)
+{
+    float e;
+    const float s = two_sum(x.hi, y.hi, e);
+    return df_norm(s, __fadd_rn(e, __fadd_rn(x.lo, y.lo)));
+}
+
+__device__ __forceinline__ DF df_neg(DF x) { return DF{-x.hi, -x.lo}; }
+
+__device__ __forceinline__ DF df_mulf(DF x, float f)
+{
+    const float p = __fmul_rn(x.hi, f);
+    return df_norm(p, fmaf(x.lo, f, fmaf(x.hi, f, -p)));
+}
+
+__device__ __forceinline__ DF df_mul(DF x, DF y)
+{
+    const float p = __fmul_rn(x.hi, y.hi);
+    const float e = fmaf(x.hi, y.hi, -p);
+    return df_norm(p, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e)));
+}
+
+__device__ __forceinline__ DF df_sqrt(DF x) // x > 0: one Newton step from the rounded square root
+{
+    const float r = __fsqrt_rn(x.hi);
+    if (!(r > 0.0f)) return DF{r, 0.0f};
+    const float rr = __fmul_rn(r, r);
+    const float res = __fadd_rn(__fadd_rn(__fsub_rn(x.hi, rr), -fmaf(r, r, -rr)), x.lo); // x - r^2
+    return df_norm(r, __fdiv_rn(res, __fmul_rn(2.0f, r)));
+}
+
+__device__ __forceinline__ bool df_less(DF x, DF y) { return x.hi < y.hi || (x.hi == y.hi && x.lo < y.lo); }
+
+// e^x for a double-float x <= about 88: x = n ln 2 + r with |r| <= ln(2)/2,
+// e^r from its Taylor series (terms from r^6 on in FP32, where their size
+// keeps the absolute error below 1e-13; the first six in double-float),
+// scaled by 2^n. Relative error about 1e-13; 0 below e^-150.
+__device__ __forceinline__ DF df_exp(DF x)
+{
+    if (x.hi < -150.0f) return DF{0.0f, 0.0f};
+    const float n = rintf(__fmul_rn(x.hi, 1.44269502f));
+    const DF ln2{0.693147182f, -1.90465421e-09f}; // ln 2 = hi + lo
+    const DF r = df_add(x, df_neg(df_mulf(ln2, n)));
+    // 1/k! for k = 12 .. 6 in FP32, Horner in r.hi
+    float t = 2.08767559e-09f;
+    t = fmaf(t, r.hi, 2.50521079e-08f);
+    t = fmaf(t, r.hi, 2.75573200e-07f);
+    t = fmaf(t, r.hi, 2.75573188e-06f);
+    t = fmaf(t, r.hi, 2.48015876e-05f);
+    t = fmaf(t, r.hi, 1.98412701e-04f);
+    t = fmaf(t, r.hi, 1.38888892e-03f);
+    // then 1/5!, 1/4!, 1/3!, 1/2!, 1, 1 in double-float
+    DF p{t, 0.0f};
+    const DF c5{8.33333377e-03f, -4.34617203e-10f}, c4{4.16666679e-02f, -1.24176347e-09f};
+    const DF c3{1.66666672e-01f, -4.96705388e-09f}, c2{0.5f, 0.0f}, c1{1.0f, 0.0f};
+    p = df_add(df_mul(p, r), c5);
+    p = df_add(df_mul(p, r), c4);
+    p = df_add(df_mul(p, r), c3);
+    p = df_add(df_mul(p, r), c2);
+    p = df_add(df_mul(p, r), c1);
+    p = df_add(df_mul(p, r), c1);
+    const int ni = (int)n;
+    return DF{ldexpf(p.hi, ni), ldexpf(p.lo, ni)};
+}
+
+// Eq. 2 for the several-speed control set in double-float at the FP32
+// particle state of lane `src`, with the inverse-CDF rule of the FP32 draws
+// (the smallest u with u24 2^-24 S < C_u), computed by the whole warp: lane L
+// takes the controls [L per, L per + per) (per = ceil(U / 32)), a warp scan
+// of the lanes' sums gives the running sums, and the first lane whose range
+// holds the threshold names the control. Logits beta Q_u, Q_u = -w1 v m_q
+// dt - w2 ||z + v m_q dt e_k - g||, shifted by the logit of the control
+// `guess` (the FP32 draw's choice, whose weight is within 2^-23 of the
+// largest, so no weight overflows), with the unit heading vectors of the
+// double-float table. The several-speed draws ask for it only for a step
+// whose FP32 threshold falls within the error band of a CDF boundary (a few
+// in 10^6 steps), so that their decision does not rest on FP32 rounding
+// there: with 96 nearly equal weights (small |beta|) the ex2 and fixed-point
+// errors move the CDF by a few 10^-9; at |beta| ~ 10^4 the FP32 heading
+// table and products move the logits between speeds by ~3e-5. Every lane of
+// the warp must call it with the same src. Not inlined: its registers stay
+// out of the hot loop.
+static __device__ __noinline__ int settle_multi_warp(const HeadingTab &tab, uint32_t speed_on, int K, float x,
+                                                     float y, float gx, float gy, float beta, uint32_t word,
+                                                     int guess, int src)
+{
+    constexpr unsigned kAll = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    x = __shfl_sync(kAll, x, src);
+    y = __shfl_sync(kAll, y, src);
+    gx = __shfl_sync(kAll, gx, src);
+    gy = __shfl_sync(kAll, gy, src);
+    beta = __shfl_sync(kAll, beta, src);
+    word = __shfl_sync(kAll, word, src);
+    guess = __shfl_sync(kAll, guess, src);
+    float ex_lo, ey_lo;
+    const float ex_hi = two_sum(x, -gx, ex_lo), ey_hi = two_sum(y, -gy, ey_lo);
+    const DF zgx{ex_hi, ex_lo}, zgy{ey_hi, ey_lo};
+    const int U = tab.S * K;
+    auto logit = [&](int u) {
+        const int q = u / K, k = u - q * K;
+        const DF st = df_mulf(df_mulf(DF{tab.v, 0.0f}, tab.mult[q]), tab.dt); // v m_q dt
+        const DF dx = df_add(zgx, df_mul(st, DF{tab.cdf[k][0], tab.cdf[k][1]}));
+        const DF dy = df_add(zgy, df_mul(st, DF{tab.sdf[k][0], tab.sdf[k][1]}));
+        const DF d = df_sqrt(df_add(df_mul(dx, dx), df_mul(dy, dy)));
+        const DF Q = df_neg(df_add(df_mulf(st, tab.w1), df_mulf(d, tab.w2)));
+        return df_mulf(Q, beta);
+    };
+    const DF shift = df_neg(logit(guess));
+    const int per = (U + 31) / 32; // at most 8 (U <= 256)
+    DF e[8];
+    DF bs{0.0f, 0.0f};
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        e[j] = DF{0.0f, 0.0f};
+        const int u = lane * per + j;
+        if (j < per && u < U && ((speed_on >> (u / K)) & 1u)) {
+            e[j] = df_exp(df_add(logit(u), shift));
+            bs = df_add(bs, e[j]);
+        }
+    }
+    DF incl = bs; // inclusive scan over the lanes, earlier lanes first
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const DF v{__shfl_up_sync(kAll, incl.hi, o), __shfl_up_sync(kAll, incl.lo, o)};
+        if (lane >= o) incl = df_add(v, incl);
+    }
+    DF C{__shfl_up_sync(kAll, incl.hi, 1), __shfl_up_sync(kAll, incl.lo, 1)};
+    if (lane == 0) C = DF{0.0f, 0.0f};
+    const DF S{__shfl_sync(kAll, incl.hi, 31), __shfl_sync(kAll, incl.lo, 31)};
+    const DF target = df_mulf(S, (float)(word >> 8) * 0x1p-24f);
+    int cand = -1, lastpos = -1;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int u = lane * per + j;
+        if (j < per && u < U) {
+            if (e[j].hi > 0.0f) lastpos = u;
+            C = df_add(C, e[j]);
+            if (cand < 0 && e[j].hi > 0.0f && df_less(target, C)) cand = u;
+        }
+    }
+    const unsigned has = __ballot_sync(kAll, cand >= 0);
+    if (has) return __shfl_sync(kAll, cand, __ffs(has) - 1);
+    // rounding left the threshold at the total: the last control with weight
+    const unsigned pos = __ballot_sync(kAll, lastpos >= 0);
+    return pos ? __shfl_sync(kAll, lastpos, 31 - __clz(pos)) : guess;
+}
+
+// Whether an FP32 draw's threshold thr lies clear of both boundaries of the
+// chosen interval [lo, hi) of the fixed-point CDF (total S): by more than 24
+// units (the ex2 and quantisation errors of up to 256 weights accumulate to
+// a standard deviation of about 4 units at a boundary) plus |cb| S 2^-26
+// (the FP32 distance and table errors, a few 1e-9 m, turned into relative
+// weight errors by |cb| ln 2, with a factor 10 to spare).
+__device__ __forceinline__ bool draw_is_clear(uint32_t thr, uint32_t lo, uint32_t hi, uint32_t S, float cb)
+{
+    const float band = fmaf((float)S * 0x1p-26f, fabsf(cb), 24.0f);
+    return (float)(thr - lo) >= band && (float)(hi - 1u - thr) >= band;
 }
 
 __device__ __forceinline__ int draw_multi(const HeadingTab &tab, uint32_t speed_on, int K, float x, float y,
-                                          float gx, float gy, float cb, float cw1, bool lb, uint32_t word)
+                                          float gx, float gy, float beta, float cb, float cw1, bool lb,
+                                          uint32_t word, bool &settle)
 {
     const float dx = x - gx, dy = y - gy;
-    const float r2 = fmaf(dx, dx, dy * dy);
+    const float r2 = fmaf(dx, dx, dy * dy); // common to every speed
     const float r = sqrt_approx(r2);
     SpeedStep q;
+    float eq[PM_MAX_SPEEDS];
     int best = max(__ffs((int)speed_on) - 1, 0); // an enabled speed, whatever the inputs
-    float vbest = -INFINITY;
+    float vbest = -INFINITY, refb = 0.0f, mb = tab.mult[0];
 #pragma unroll
     for (int sp = 0; sp < PM_MAX_SPEEDS; ++sp) {
-        q.D[sp] = q.hD[sp] = q.REF[sp] = q.C[sp] = 0.0f;
+        q.D[sp] = q.hD[sp] = q.c3[sp] = q.REF[sp] = q.C[sp] = eq[sp] = 0.0f;
+        q.SC[sp] = 0.0f;
         if (sp >= tab.S || !((speed_on >> sp) & 1u)) continue;
         const float sl = tab.sl[sp];
-        q.D[sp] = fmaf(dx, dx, fmaf(dy, dy, sl * sl));
+        q.D[sp] = speed_D(tab, sp, r2, eq[sp]);
         q.hD[sp] = 0.5f * rsqrt_approx(q.D[sp]);
+        q.c3[sp] = -2.0f * q.hD[sp] * q.hD[sp] * q.hD[sp];
+        eq[sp] = __fmul_rn(__fmul_rn(cb, q.hD[sp]), eq[sp]); // cb hD eq
         if (lb) {
             const float margin = (r + sl) * 0x1p-20f;
             q.REF[sp] = (cb >= 0.0f) ? fabsf(r - sl) - margin : r + sl + margin;
@@ -400,8 +647,7 @@ __device__ __forceinline__ int draw_multi(const HeadingTab &tab, uint32_t speed_
             q.REF[sp] = 0.0f;
             for (int k = 0; k < K; ++k) {
                 const float P = __fmul_rn(fmaf(tab.tx[k], dx, tab.ty[k] * dy), tab.mult[sp]);
-                const float dk = sqrt_approx(fabsf(q.D[sp] + P));
-                const float d = fmaf(P - fmaf(dk, dk, -q.D[sp]), q.hD[sp], dk);
+                const float d = corrected_minus(q.D[sp], P, q.hD[sp], q.c3[sp], 0.0f);
                 ext = (cb >= 0.0f) ? fminf(ext, d) : fmaxf(ext, d);
             }
             q.REF[sp] = ext;
@@ -410,23 +656,23 @@ __device__ __forceinline__ int draw_multi(const HeadingTab &tab, uint32_t speed_
         if (v > vbest) {
             vbest = v;
             best = sp;
+            refb = q.REF[sp];
+            mb = tab.mult[sp];
         }
     }
-    // offsets between speeds from differences of nearby floats, shifted to >= 0
-    float cmin = INFINITY;
-#pragma unroll
-    for (int sp = 0; sp < PM_MAX_SPEEDS; ++sp) {
-        if (sp >= tab.S || !((speed_on >> sp) & 1u)) continue;
-        q.C[sp] = fmaf(cb, q.REF[sp] - q.REF[best], cw1 * (tab.mult[sp] - tab.mult[best]));
-        cmin = fminf(cmin, q.C[sp]);
-    }
+    // offsets between speeds (high part in the exponent, low part in the
+    // scale); a common factor 2^-2^-18 on every weight keeps the largest one
+    // below 2^23 whatever the sign of the low parts (it does not change the
+    // distribution)
+    float lo[PM_MAX_SPEEDS];
+    speed_offsets(tab, speed_on, refb, mb, beta, q.REF, eq, q.C, lo, 0x1p-18f);
     uint32_t W[PM_MAX_SPEEDS];
     uint32_t total = 0u;
 #pragma unroll
     for (int sp = 0; sp < PM_MAX_SPEEDS; ++sp) {
         W[sp] = 0u;
         if (sp >= tab.S || !((speed_on >> sp) & 1u)) continue;
-        q.C[sp] -= cmin;
+        q.SC[sp] = kWScale * exp2f(-lo[sp]);
         uint32_t w = 0u;
         for (int k = 0; k < K; ++k) w += multi_weight(tab, k, sp, dx, dy, q, cb);
         W[sp] = w;
@@ -453,15 +699,19 @@ __device__ __forceinline__ int draw_multi(const HeadingTab &tab, uint32_t speed_
         }
     }
     // that speed's headings in order until the running sum passes thr
-    uint32_t acc = C0;
+    uint32_t acc = C0, below = C0;
     int kk = K - 1;
+    bool hit = false;
     for (int k = 0; k < K; ++k) {
+        below = acc;
         acc += multi_weight(tab, k, ss, dx, dy, q, cb);
         if (thr < acc) {
             kk = k;
+            hit = true;
             break;
         }
     }
+    settle = !hit || !draw_is_clear(thr, below, acc, total, cb);
     return ss * K + kk;
 }
 
@@ -469,13 +719,17 @@ __device__ __forceinline__ int draw_multi(const HeadingTab &tab, uint32_t speed_
 // enabled (KT % 4 == 0) and a component with the bound-normalised flag.
 // Per enabled speed q the loop is the one-speed loop with that speed's
 // constants: P_{k,q} = 2 s e_k.(m_q (z - g)) (the scaled offset rounded once,
-// so heading k + K/2 still has exactly -P), D_q = ||z - g||^2 + sl_q^2 and the
-// bound REF_q of that speed. The exponent of control (q, k) is
+// so heading k + K/2 still has exactly -P), D_q = ||z - g||^2 + sl_q^2 (from
+// the common ||z - g||^2; its rounding residual is part of the offset) and
+// the bound REF_q of that speed. The exponent of control (q, k) is
 //   -cb (d_{k,q} - REF_q) - C_q,   C_q = cb (REF_q - REF_b) + cw1 (m_q - m_b) - min,
 // evaluated as fma(R, -cb/2d, fma(d~, -cb, RC_q)) with RC_q = round(cb REF_q);
-// the rounding e_q of RC_q and the offset C_q are folded into the fixed-point
-// scale 2^22 2^(e_q - C_q), so they cost nothing per control and the offsets
-// between speeds keep FP32 relative precision. Pass 1 keeps segment sums of G
+// the rounding e_q of RC_q, the shift -cb/(2d) eq_q of the residual eq_q of
+// D_q and the offset C_q are folded into the fixed-point scale
+// 2^23 2^(e_q - cb eq_q/2d - C_q), so they cost nothing per control and the
+// independent roundings of the D_q do not move the speeds against one
+// another (by beta w2 ulp(r^2)/2d, 1e-5 of the logit at beta = 100 and r = 5
+// m, before this correction). Pass 1 keeps segment sums of G
 // headings per speed (the bits are not stored); the threshold picks the
 // segment and pass 2 recomputes only its G weights, bit for bit.
 template <int KT>
@@ -483,17 +737,21 @@ struct MultiLbConsts {
     float D, HDNC, RC, SC, mx, my; // D_q, -cb/(2 d_q), round(cb REF_q), scale, m_q (z - g)
 };
 
+
+// The residual eq of D_q shifts every exponent of the speed by HDNC eq (the
+// distances' residual correction of the exact D_q); it goes into the scale
+// with the rounding e of RC and the speed's offset C.
 template <int KT>
-__device__ __forceinline__ MultiLbConsts<KT> multi_lb_consts(const HeadingTab &tab, int q, float dx, float dy,
-                                                             float cb, float REF, float C)
+__device__ __forceinline__ MultiLbConsts<KT> multi_lb_consts(const HeadingTab &tab, int q, float r2, float dx,
+                                                             float dy, float cb, float REF, float C)
 {
     MultiLbConsts<KT> c;
-    const float sl = tab.sl[q];
-    c.D = fmaf(dx, dx, fmaf(dy, dy, sl * sl));
+    float eq;
+    c.D = speed_D(tab, q, r2, eq);
     c.HDNC = -cb * (0.5f * rsqrt_approx(c.D));
     c.RC = cb * REF;
     const float e = fmaf(cb, REF, -c.RC); // cb REF - RC, exact
-    c.SC = 4194304.0f * exp2f(e - C);
+    c.SC = kWScale * exp2f(fmaf(c.HDNC, eq, e) - C);
     c.mx = __fmul_rn(dx, tab.mult[q]);
     c.my = __fmul_rn(dy, tab.mult[q]);
     return c;
@@ -507,17 +765,18 @@ __device__ __forceinline__ uint32_t multi_lb_weight(const HeadingTab &tab, int k
     const float P = fmaf(tab.tx[k], c.mx, __fmul_rn(tab.ty[k], c.my));
     const float d = sqrt_approx(fabsf(c.D + P));
     const float a = fmaf(P - fmaf(d, d, -c.D), c.HDNC, fmaf(d, -cb, c.RC));
-    return __float_as_uint(fmaf(ex2_approx(a), c.SC, 12582912.0f)) - 0x4B400000u;
+    return __float_as_uint(fmaf(ex2_approx(a), c.SC, kWMagic)) - kWBits;
 }
 
 template <int KT>
 __device__ __forceinline__ int draw_multi_lb(const HeadingTab &tab, uint32_t speed_on, float x, float y, float gx,
-                                             float gy, float cb, float cw1, uint32_t word)
+                                             float gy, float beta, float cb, float cw1, uint32_t word, bool &settle)
 {
     static_assert(KT % 4 == 0, "pairs of headings must not straddle the two halves");
     constexpr int G = CdfSegs<KT>::G, NS = KT / G, H2 = KT / 2;
     const float dx = x - gx, dy = y - gy;
-    const float r = sqrt_approx(fmaf(dx, dx, dy * dy));
+    const float r2 = fmaf(dx, dx, dy * dy); // common to every speed
+    const float r = sqrt_approx(r2);
     // bounds per speed and the offsets between speeds
     float REF[PM_MAX_SPEEDS], C[PM_MAX_SPEEDS];
     float vbest = -INFINITY, refb = 0.0f, mb = 0.0f;
@@ -539,7 +798,7 @@ __device__ __forceinline__ int draw_multi_lb(const HeadingTab &tab, uint32_t spe
         C[q] = fmaf(cb, REF[q] - refb, cw1 * (tab.mult[q] - mb));
         if (q < tab.S && ((speed_on >> q) & 1u)) cmin = fminf(cmin, C[q]);
     }
-    const f32x2 NC = f2_pack(-cb, -cb), MG = f2_pack(12582912.0f, 12582912.0f);
+    const f32x2 NC = f2_pack(-cb, -cb), MG = f2_pack(kWMagic, kWMagic);
     const f32x2 *TX = reinterpret_cast<const f32x2 *>(tab.tx);
     const f32x2 *TY = reinterpret_cast<const f32x2 *>(tab.ty);
     uint32_t seg[PM_MAX_SPEEDS][NS];
@@ -548,7 +807,7 @@ __device__ __forceinline__ int draw_multi_lb(const HeadingTab &tab, uint32_t spe
 #pragma unroll
         for (int i = 0; i < NS; ++i) seg[q][i] = 0u;
         if (q >= tab.S || !((speed_on >> q) & 1u)) continue;
-        const MultiLbConsts<KT> c = multi_lb_consts<KT>(tab, q, dx, dy, cb, REF[q], C[q] - cmin);
+        const MultiLbConsts<KT> c = multi_lb_consts<KT>(tab, q, r2, dx, dy, cb, REF[q], C[q] - cmin);
         const f32x2 MX = f2_pack(c.mx, c.mx), MY = f2_pack(c.my, c.my);
         const f32x2 DD = f2_pack(c.D, c.D), NDD = f2_pack(-c.D, -c.D);
         const f32x2 HDNC = f2_pack(c.HDNC, c.HDNC), NHDNC = f2_pack(-c.HDNC, -c.HDNC);
@@ -567,8 +826,8 @@ __device__ __forceinline__ int draw_multi_lb(const HeadingTab &tab, uint32_t spe
             float w0, w1, v0, v1;
             f2_unpack(f2_fma(f2_pack(ex2_approx(a0), ex2_approx(a1)), SC, MG), w0, w1);
             f2_unpack(f2_fma(f2_pack(ex2_approx(b0), ex2_approx(b1)), SC, MG), v0, v1);
-            seg[q][(2 * k2) / G] += (__float_as_uint(w0) - 0x4B400000u) + (__float_as_uint(w1) - 0x4B400000u);
-            seg[q][(H2 + 2 * k2) / G] += (__float_as_uint(v0) - 0x4B400000u) + (__float_as_uint(v1) - 0x4B400000u);
+            seg[q][(2 * k2) / G] += (__float_as_uint(w0) - kWBits) + (__float_as_uint(w1) - kWBits);
+            seg[q][(H2 + 2 * k2) / G] += (__float_as_uint(v0) - kWBits) + (__float_as_uint(v1) - kWBits);
         }
     }
     uint32_t S = 0u;
@@ -603,16 +862,20 @@ __device__ __forceinline__ int draw_multi_lb(const HeadingTab &tab, uint32_t spe
         REFs = (qs == q) ? REF[q] : REFs;
         Cs = (qs == q) ? C[q] : Cs;
     }
-    const MultiLbConsts<KT> c = multi_lb_consts<KT>(tab, qs, dx, dy, cb, REFs, Cs - cmin);
-    uint32_t acc = C0;
+    const MultiLbConsts<KT> c = multi_lb_consts<KT>(tab, qs, r2, dx, dy, cb, REFs, Cs - cmin);
+    uint32_t acc = C0, below = C0;
     int kk = is * G + G - 1;
+    bool hit = false;
     for (int k = is * G; k < is * G + G; ++k) {
+        below = acc;
         acc += multi_lb_weight<KT>(tab, k, c, cb);
         if (thr < acc) {
             kk = k;
+            hit = true;
             break;
         }
     }
+    settle = !hit || !draw_is_clear(thr, below, acc, S, cb);
     return qs * KT + kk;
 }
 
@@ -812,20 +1075,20 @@ __device__ __forceinline__ void rollout_tile(const HeadingTab &tab, uint64_t ena
 // emplaced with the lanes of the warp that land in the same cell combined
 // (match.any) into one global reduction. Every lane of the warp must call
 // it with the same c.T (idle lanes pass c.i >= c.N). No block barrier.
-// MS: the control set of several speeds (cw1 holds each component's
-// beta w1 v dt log2(e), step the S*K Euler steps, K the headings, speed_on the
-// enabled speeds); KT > 0 is then K itself, with draw_multi_lb for the
-// components it applies to, and KT = 0 runs draw_multi for any K.
+// MS: the control set of several speeds (betas holds each component's beta,
+// step the S*K Euler steps, K the headings, speed_on the enabled speeds); KT >
+// 0 is then K itself, with draw_multi_lb for the components it applies to,
+// and KT = 0 runs draw_multi for any K.
 template <int KT, bool FULL, bool MS = false>
 __device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t enabled, float s2, const TileCtx &c,
                                              const float4 *comp, const uint32_t *cdf, const float2 *step,
-                                             const float *cw1 = nullptr, int K = 0, uint32_t speed_on = 0u)
+                                             const float *betas = nullptr, int K = 0, uint32_t speed_on = 0u)
 {
     const int lane = threadIdx.x & 31;
     const uint64_t i = (uint64_t)c.i;
     const bool act = c.i < c.N;
     const bool trc = c.i < c.n_trace;
-    float x = c.z0x, y = c.z0y, cb = 0.0f, gx = 0.0f, gy = 0.0f, cw = 0.0f;
+    float x = c.z0x, y = c.z0y, cb = 0.0f, gx = 0.0f, gy = 0.0f, cw = 0.0f, bt = 0.0f;
     bool lb = false;
     // several speeds with exactly one enabled: its index (else -1)
     const int one_speed = (MS && __popc(speed_on) == 1) ? __ffs((int)speed_on) - 1 : -1;
@@ -843,7 +1106,10 @@ __device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t ena
         gx = cc.y;
         gy = cc.z;
         lb = cc.w != 0.0f;
-        if constexpr (MS) cw = cw1[lo];
+        if constexpr (MS) {
+            bt = betas[lo];
+            cw = bt * tab.w1l[0]; // beta w1 v dt log2(e)
+        }
         if (trc && c.tr_comp) c.tr_comp[i] = lo;
     }
     const size_t plane = (size_t)c.W * (size_t)c.H;
@@ -851,6 +1117,9 @@ __device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t ena
     for (int t = 1; t <= c.T; ++t) {
         uint32_t key = 0xFFFFFFFFu; // idle lane
         int fkey = 0;               // block of the cell (flags only)
+        int k = 0;
+        bool settle = false; // several speeds: the FP32 draw was too close to a CDF boundary
+        uint32_t word = 0u;
         if (act) {
             if (((t - 1) & 7) == 0) {
                 const U64x4 r = philox4x64_10(U64x4{i, (uint64_t)((t - 1) >> 3), kPurposeStep, 0ull}, c.seed, c.human);
@@ -859,9 +1128,8 @@ __device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t ena
                 q4 = (uint32_t)r.c; q5 = (uint32_t)(r.c >> 32);
                 q6 = (uint32_t)r.d; q7 = (uint32_t)(r.d >> 32);
             }
-            const uint32_t word = q0;
+            word = q0;
             q0 = q1; q1 = q2; q2 = q3; q3 = q4; q4 = q5; q5 = q6; q6 = q7;
-            int k;
             if constexpr (MS) {
                 if constexpr (KT > 0) { // K == KT, all headings enabled: the fused form where it applies
                     if (lb && one_speed >= 0) {
@@ -873,16 +1141,29 @@ __device__ __forceinline__ void rollout_lane(const HeadingTab &tab, uint64_t ena
                         k = one_speed * KT +
                             draw_heading_lb<KT>(tab, lb_step_d(tab, s2, (x - gx) * im, (y - gy) * im, cbm), cbm, word);
                     } else if (lb) {
-                        k = draw_multi_lb<KT>(tab, speed_on, x, y, gx, gy, cb, cw, word);
+                        k = draw_multi_lb<KT>(tab, speed_on, x, y, gx, gy, bt, cb, cw, word, settle);
                     } else {
-                        k = draw_multi(tab, speed_on, K, x, y, gx, gy, cb, cw, lb, word);
+                        k = draw_multi(tab, speed_on, K, x, y, gx, gy, bt, cb, cw, lb, word, settle);
                     }
                 } else {
-                    k = draw_multi(tab, speed_on, K, x, y, gx, gy, cb, cw, lb, word);
+                    k = draw_multi(tab, speed_on, K, x, y, gx, gy, bt, cb, cw, lb, word, settle);
                 }
             } else {
                 k = draw<KT, FULL>(tab, enabled, s2, x, y, gx, gy, cb, lb, word);
             }
+        }
+        if constexpr (MS) {
+            // a draw too close to a CDF boundary for FP32 is settled in
+            // double-float by the whole warp, one flagged lane at a time
+            unsigned need = __ballot_sync(0xffffffffu, settle);
+            while (need) {
+                const int src = __ffs((int)need) - 1;
+                const int u = settle_multi_warp(tab, speed_on, K, x, y, gx, gy, bt, word, k, src);
+                if (lane == src) k = u;
+                need &= need - 1u;
+            }
+        }
+        if (act) {
             const float2 st = step[k];
             x = __fadd_rn(x, st.x);
             y = __fadd_rn(y, st.y);

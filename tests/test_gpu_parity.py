@@ -84,9 +84,8 @@ def trajectory_parity(orc, m, lb, z0, T, seed, human, got, n, label, grid=None):
     and each must lie within the error budget of explain_divergences.
     Returns (d at the FP32 state, d at the FP64 state, the FP32-state run)."""
     kw = dict(want_headings=True, want_states32=True, want_states64=True, want_comp=True)
-    if grid is None:
-        kw["want_counts"] = False
-    ref32 = orc.rollout(m, lb, z0, T, seed, human, 0, n, grid=grid, decide_f32=True, **kw)
+    ref32 = orc.rollout(m, lb, z0, T, seed, human, 0, n, grid=grid, want_counts=grid is not None,
+                        decide_f32=True, **kw)
     d32 = compare_trajectories(got, ref32)
     assert explain_divergences(orc, m, lb, z0, seed, human, got, ref32, decide_f32=True) == d32
     ref64 = orc.rollout(m, lb, z0, T, seed, human, 0, n, grid=None, want_counts=False, **kw)
@@ -196,6 +195,33 @@ def test_posterior_out_of_place(ctx, orc):
     buf = torch.zeros(2 * hu.G * hu.B, device="cuda:0")
     with pytest.raises(pm.PmError):
         pm.pm_update_posterior_into(ctx, gh.model, obs_d, hu.n_obs, buf[:hu.G * hu.B], buf[1:hu.G * hu.B + 1])
+
+
+def test_posterior_of_stationary_steps_is_the_prior(ctx, orc):
+    """Steps shorter than 1e-6 m leave the belief unchanged (reading A4): a
+    history of only such steps returns the prior bit for bit (no FP32
+    renormalisation), and so does a batched update of such steps."""
+    import paper_2603_01122_gb300 as pm
+    hu = workloads.paper_scale()
+    gh = GpuHuman.of(hu)
+    rng = np.random.default_rng(2)
+    prior = np.log(rng.dirichlet(np.ones(hu.G * hu.B))).astype(np.float32)
+    obs = np.repeat(np.float32([[4.2, 6.1]]), 9, axis=0)
+    obs[3:] += np.float32(3e-7)  # one step of 4e-7 m, the rest of length zero
+    got = posterior(ctx, gh, obs, prior)
+    np.testing.assert_array_equal(got, prior)
+    lb = dev(prior)
+    obs_d = dev(obs)
+    batch = pm.pm_batch_create(ctx, gh.model, 1)
+    counts = torch.zeros((3, 4, 4), dtype=torch.int32, device="cuda:0")
+    oob = torch.zeros(3, dtype=torch.int32, device="cuda:0")
+    g = pm.make_grid(0.0, 0.0, 1.0, 4, 4)
+    pm.pm_batch_set(batch, [pm.make_human(gh.goals, gh.beta, lb, obs_d[-1], 10, 3, g, 1, 2, counts, oob,
+                                          obs_xy=obs_d, n_obs=8)])
+    pm.pm_batch_update_posterior(batch)
+    torch.cuda.synchronize()
+    pm.pm_batch_destroy(batch)
+    np.testing.assert_array_equal(lb.cpu().numpy(), prior)
 
 
 def test_posterior_large_history_max_components(ctx, orc):
