@@ -217,9 +217,10 @@ __device__ __forceinline__ LbStep lb_step(const HeadingTab &tab, float s2, float
     return lb_step_d(tab, s2, x - gx, y - gy, cb);
 }
 
-// Segments of the running sums of the inverse CDF: KT/G segments of G
-// headings (G even, so a pair of headings never straddles two), each an
-// independent chain of additions.
+// Segments of the several-speed fused draw (draw_multi_lb): KT/G segments of
+// G headings per speed (G even, so a pair of headings never straddles two);
+// pass 1 keeps their sums and pass 2 recomputes the G weights of the one
+// holding the threshold.
 template <int KT>
 struct CdfSegs {
     static constexpr int G = (KT == 8) ? 4 : (KT == 16) ? 4 : (KT == 36) ? 6 : 8;
@@ -227,15 +228,29 @@ struct CdfSegs {
     static_assert(KT % G == 0 && G % 2 == 0, "segments hold whole pairs");
 };
 
-// Inverse CDF over the 23-bit fixed-point weights (bits = kWBits + w_k):
-// the smallest k with C_k > (u24 * S) >> 24. Seg[q] is the raw sum of the
-// bits of segment q; each segment scans its own headings from the running
-// sum at its start, so the scan is KT/G short chains instead of one long one.
+// Segments of the one-speed draw's inverse CDF (draw_heading_lb): chosen to
+// minimise the instructions of select_fixed (its count grows with the
+// segments, for the search and the pick, and with their length, for the scan).
 template <int KT>
-__device__ __forceinline__ int select_fixed(const uint32_t (&bits)[KT], const uint32_t (&seg)[CdfSegs<KT>::N],
+struct SelSegs {
+    static constexpr int G = (KT == 8) ? 4 : (KT == 16) ? 8 : (KT == 36) ? 12 : 16;
+    static constexpr int N = KT / G;
+    static_assert(KT % G == 0 && G % 2 == 0, "segments hold whole pairs");
+};
+
+// Inverse CDF over the 23-bit fixed-point weights (bits = kWBits + w_k):
+// the smallest k with C_k > thr = (u24 * S) >> 24, i.e. the number of
+// running sums C_k <= thr. Seg[q] is the raw sum of the bits of segment q.
+// The segment holding thr is the last one whose start sum is <= thr (every
+// running sum before it is <= thr, every one after it is > thr); its G
+// weights are picked by predicated selects (registers cannot be indexed)
+// and scanned from its start sum: about NS + 3 NS + NS G + 2 G instructions
+// instead of 2 KT for counting every heading.
+template <int KT>
+__device__ __forceinline__ int select_fixed(const uint32_t (&bits)[KT], const uint32_t (&seg)[SelSegs<KT>::N],
                                             uint32_t word)
 {
-    constexpr int G = CdfSegs<KT>::G, NS = CdfSegs<KT>::N;
+    constexpr int G = SelSegs<KT>::G, NS = SelSegs<KT>::N;
     uint32_t start[NS]; // C at the start of each segment
     uint32_t S = 0u;
 #pragma unroll
@@ -244,26 +259,32 @@ __device__ __forceinline__ int select_fixed(const uint32_t (&bits)[KT], const ui
         S += seg[q] - (uint32_t)G * kWBits;
     }
     const uint32_t thr = (uint32_t)(((uint64_t)(word >> 8) * (uint64_t)S) >> 24);
+    int qs = 0;
+    uint32_t base = 0u;
+#pragma unroll
+    for (int q = 1; q < NS; ++q) {
+        const bool in = start[q] <= thr;
+        qs = in ? q : qs;
+        base = in ? start[q] : base;
+    }
+    uint32_t b[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) b[j] = bits[j];
+#pragma unroll
+    for (int q = 1; q < NS; ++q) {
+        const bool p = qs == q;
+#pragma unroll
+        for (int j = 0; j < G; ++j) b[j] = p ? bits[q * G + j] : b[j];
+    }
     // C_k - thr - 1 once w_k is added: negative iff C_k <= thr
-    int sel[NS];
-    uint32_t acc[NS];
+    uint32_t acc = base + ~thr;
+    int sel = 0;
 #pragma unroll
-    for (int q = 0; q < NS; ++q) {
-        acc[q] = start[q] + ~thr;
-        sel[q] = 0;
+    for (int j = 0; j < G; ++j) {
+        acc += b[j] - kWBits;
+        sel += (int)(acc >> 31);
     }
-#pragma unroll
-    for (int k = 0; k < G; ++k) {
-#pragma unroll
-        for (int q = 0; q < NS; ++q) {
-            acc[q] += bits[q * G + k] - kWBits;
-            sel[q] += (int)(acc[q] >> 31);
-        }
-    }
-    int total = 0;
-#pragma unroll
-    for (int q = 0; q < NS; ++q) total += sel[q];
-    return total;
+    return qs * G + sel;
 }
 
 // Bound-normalised draw with the distances from the approximate square root
@@ -285,11 +306,11 @@ __device__ __forceinline__ int draw_heading_lb(const HeadingTab &tab, const LbSt
     const f32x2 *TX = reinterpret_cast<const f32x2 *>(tab.tx);
     const f32x2 *TY = reinterpret_cast<const f32x2 *>(tab.ty);
     constexpr int H2 = KT / 2;
-    constexpr int G = CdfSegs<KT>::G;
+    constexpr int G = SelSegs<KT>::G;
     uint32_t bits[KT];
-    uint32_t seg[CdfSegs<KT>::N];
+    uint32_t seg[SelSegs<KT>::N];
 #pragma unroll
-    for (int q = 0; q < CdfSegs<KT>::N; ++q) seg[q] = 0u;
+    for (int q = 0; q < SelSegs<KT>::N; ++q) seg[q] = 0u;
     const f32x2 HDNC = f2_pack(-cb * hD, -cb * hD), NHDNC = f2_pack(cb * hD, cb * hD);
     const f32x2 NC = f2_pack(-cb, -cb), RC = f2_pack(cb * q.ref, cb * q.ref);
 #pragma unroll
