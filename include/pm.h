@@ -325,7 +325,8 @@ pm_status pm_batch_predict(pm_batch *b, void *stream);
  * overwritten). Synchronous. */
 pm_status pm_batch_autotune(pm_batch *b, void *stream);
 
-/* Read or set the launch shape: threads per CTA (multiple of 32, <= 256),
+/* Read or set the launch shape: threads per CTA (multiple of 32, <= 256;
+ * a new batch starts with 128 threads, warp-combined emplacement),
  * the emplacement mode, resident CTAs per SM used for the grid (0 = as many
  * as fit) and the window budget in KiB of shared memory. shared_window = 0:
  * persistent warps take 32-particle tiles and combine the lanes of a warp

@@ -72,7 +72,7 @@ struct pm_batch {
     size_t h_stage_bytes = 0;
     cudaEvent_t staged = nullptr;
     // launch shape
-    int threads = 256;
+    int threads = 128;
     bool warp_hist = true;  // warp-combined emplacement, persistent warps (else shared-memory window)
     int ctas_per_sm = 0;
     int window_kib = 48;
