@@ -13,7 +13,10 @@
 //
 // A CTA per (trajectory, group of eight components); a warp per component
 // (beta, g) with its lanes over the trajectory's steps and the headings
-// unrolled in registers. The
+// unrolled in registers. Each step is one pass over the headings: the
+// weights are normalised by a bound on the largest logit, so the distance,
+// its reciprocal and the exponential of each heading are formed once and go
+// straight into the softmax sum and the gradient's expectations. The
 // per-step log pi is FP32; its sum over a trajectory (up to hundreds of
 // steps of about -log K each) is accumulated in FP64, the one place where
 // FP32 would lose the differences between components. Per-trajectory
@@ -54,158 +57,174 @@ struct StepGrad {
     float logpi, gx, gy, gv, gw1, gw2;
 };
 
-// log pi_j(theta_obs | z) and its derivatives for one observed step.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// One pass over the headings of a step. The logit of heading k relative to
+// the observed heading, beta w2 (d_o - d_k), is formed as a difference of
+// squares, delta_k = d_o - d_k = 2 s (e_o - e_k).p / (d_o + d_k) with
+// p = z - g and s = v dt, which keeps its relative precision however close
+// the two headings are. Its largest value over k is bounded without looking
+// at the headings: every d_k lies between ||p| - s| and |p| + s (triangle
+// inequality), so with c the lower bound when beta w2 >= 0 and the upper one
+// otherwise (sg = +1 / -1),
+//   max_k beta w2 (d_o - d_k) <= beta w2 (d_o - c) = |beta w2| t_o,
+//   t_o = 2 s (|p| + sg e_o.p) / (c + d_o) >= 0.
+// The weights w_k = 2^(beta w2 log2(e) delta_k - B), B = |beta w2| log2(e) t_o,
+// are then all at most 1 (up to rounding), log pi(obs) = -(B + log2 sum w) ln 2,
+// and the softmax sum and every expectation of the gradient are formed in
+// the same pass while d_k and 1/d_k are in registers. Where the bound is
+// loose (sum w < 2^-8: the largest weight lies more than 8 binades below it,
+// which needs beta w2 s (1 - cos(pi/K)) of several units), the rounding of
+// the offset would show, and the step takes a second pass normalised by the
+// largest logit instead.
+struct StepGeo {
+    float px, py, D, ro, d_o, bl2, B;
+};
+
+__device__ __forceinline__ StepGeo step_geo(const AdjointArgs &a, float px, float py, float ex, float ey, float bw)
+{
+    StepGeo g;
+    g.px = px;
+    g.py = py;
+    const float P = fmaf(px, px, py * py);
+    g.D = P + a.s2;
+    const float pn = sqrtf(P);
+    const float sg = bw >= 0.0f ? 1.0f : -1.0f;
+    const float c = fabsf(pn - sg * a.s);
+    const float po = fmaf(ex, px, ey * py);
+    const float xo = fmaxf(fmaf(a.two_s, po, g.D), 0.0f);
+    g.ro = rsqrtf(fmaxf(xo, 1e-30f));
+    g.d_o = xo * g.ro;
+    g.bl2 = bw * kLog2e;
+    g.B = fabsf(g.bl2) * (a.two_s * fmaxf(fmaf(sg, po, pn), 0.0f) / fmaxf(c + g.d_o, 1e-30f));
+    return g;
+}
+
+// The gradient terms from the weighted sums (S, sum w r, sum w r ux,
+// sum w r uy, sum w r e.p, sum w delta) and the offset of the weights.
+__device__ __forceinline__ StepGrad step_finish(const AdjointArgs &a, const StepGeo &g, float ex, float ey, float beta,
+                                                float bw, float off, float S, float R, float RX, float RY, float RP,
+                                                float DL, bool grad)
+{
+    StepGrad r;
+    r.logpi = -(off + log2f(S)) * kLn2;
+    if (!grad) return r;
+    const float inv = 1.0f / S;
+    // sum pi u_k with u_k = (p + s e_k) / d_k; sum pi e_k.u_k = sum pi (e_k.p + s) / d_k
+    const float sux = fmaf(g.px, R, a.s * RX) * inv, suy = fmaf(g.py, R, a.s * RY) * inv;
+    const float seu = fmaf(a.s, R, RP) * inv;
+    const float uox = fmaf(a.s, ex, g.px) * g.ro, uoy = fmaf(a.s, ey, g.py) * g.ro;
+    r.gx = bw * (uox - sux);
+    r.gy = bw * (uoy - suy);
+    r.gv = bw * a.dt * (seu - fmaf(ex, uox, ey * uoy));
+    r.gw1 = 0.0f; // dQ/dw1 = -v dt for every heading: its expectation cancels
+    r.gw2 = -beta * DL * inv; // sum pi d_k - d_o = -sum pi delta_k
+    return r;
+}
+
+// log pi_j(theta_obs | z) and its derivatives for one observed step, over
+// runtime K and enabled mask (scalar form).
 template <int KT>
 __device__ __forceinline__ StepGrad step_terms(const AdjointArgs &a, float zx, float zy, float ex, float ey,
                                                float gx, float gy, float beta, bool grad)
 {
-    const float px = zx - gx, py = zy - gy;
-    const float D = fmaf(px, px, fmaf(py, py, a.s2));
-    const float xo = fmaxf(D + a.two_s * fmaf(ex, px, ey * py), 0.0f);
-    const float ro = rsqrtf(fmaxf(xo, 1e-30f));
-    const float d_o = xo * ro;
     const float bw = beta * a.w2;
-    const float bw2 = bw * kLog2e; // logits in base 2: exponentials on the SFU
-    float lg[KT];
-    float m = -INFINITY;
+    const StepGeo g = step_geo(a, zx - gx, zy - gy, ex, ey, bw);
+    // delta_k = d_o - d_k of heading k, with 1/d_k and e_k.p
+    auto delta = [&](int k, float &rk, float &pu) {
+        pu = fmaf(a.ux[k], g.px, a.uy[k] * g.py);
+        const float xk = fmaxf(fmaf(a.two_s, pu, g.D), 0.0f);
+        rk = rsqrtf(fmaxf(xk, 1e-30f));
+        const float num = a.two_s * fmaf(ex - a.ux[k], g.px, (ey - a.uy[k]) * g.py);
+        return num * rcp_approx(fmaxf(fmaf(xk, rk, g.d_o), 1e-30f));
+    };
+    auto sums = [&](float off, float &S, float &R, float &RX, float &RY, float &RP, float &DL) {
+        S = R = RX = RY = RP = DL = 0.0f;
 #pragma unroll
-    for (int k = 0; k < KT; ++k) {
-        const bool on = k < a.K && ((a.enabled >> k) & 1ull);
-        const float xk = fmaxf(D + a.two_s * fmaf(a.ux[k], px, a.uy[k] * py), 0.0f);
-        const float dk = xk * rsqrtf(fmaxf(xk, 1e-30f));
-        // beta w2 (d_obs - d_k), formed as a difference of squares
-        const float num = a.two_s * fmaf(ex - a.ux[k], px, (ey - a.uy[k]) * py);
-        lg[k] = on ? bw2 * __fdividef(num, fmaxf(d_o + dk, 1e-30f)) : -INFINITY;
-        m = fmaxf(m, lg[k]);
+        for (int k = 0; k < KT; ++k) {
+            if (k >= a.K || !((a.enabled >> k) & 1ull)) continue;
+            float rk, pu;
+            const float dl = delta(k, rk, pu);
+            const float w = ex2_approx(fmaf(g.bl2, dl, -off));
+            const float wr = w * rk;
+            S += w;
+            R += wr;
+            RX = fmaf(wr, a.ux[k], RX);
+            RY = fmaf(wr, a.uy[k], RY);
+            RP = fmaf(wr, pu, RP);
+            DL = fmaf(w, dl, DL);
+        }
+    };
+    float off = g.B, S, R, RX, RY, RP, DL;
+    sums(off, S, R, RX, RY, RP, DL);
+    if (!(S >= 0x1p-8f)) { // the bound is loose: normalise by the largest logit
+        off = -INFINITY;
+#pragma unroll 1
+        for (int k = 0; k < KT; ++k) {
+            if (k >= a.K || !((a.enabled >> k) & 1ull)) continue;
+            float rk, pu;
+            off = fmaxf(off, g.bl2 * delta(k, rk, pu));
+        }
+        sums(off, S, R, RX, RY, RP, DL);
     }
-    float S = 0.0f;
-#pragma unroll
-    for (int k = 0; k < KT; ++k) {
-        lg[k] = (lg[k] == -INFINITY) ? 0.0f : ex2_approx(lg[k] - m);
-        S += lg[k];
-    }
-    StepGrad r;
-    r.logpi = -(m + log2f(S)) * kLn2;
-    if (!grad) return r;
-    const float inv = 1.0f / S;
-    float sux = 0.f, suy = 0.f, seu = 0.f, sd = 0.f, sp = 0.f;
-#pragma unroll
-    for (int k = 0; k < KT; ++k) {
-        const float pk = lg[k] * inv;
-        const float xk = fmaxf(D + a.two_s * fmaf(a.ux[k], px, a.uy[k] * py), 0.0f);
-        const float rk = rsqrtf(fmaxf(xk, 1e-30f));
-        const float dk = xk * rk;
-        const float qx = fmaf(a.s, a.ux[k], px), qy = fmaf(a.s, a.uy[k], py); // z + s e_k - g
-        const float uxk = qx * rk, uyk = qy * rk;
-        sux = fmaf(pk, uxk, sux);
-        suy = fmaf(pk, uyk, suy);
-        seu = fmaf(pk, fmaf(a.ux[k], uxk, a.uy[k] * uyk), seu);
-        sd = fmaf(pk, dk, sd);
-        sp += pk;
-    }
-    const float qox = fmaf(a.s, ex, px), qoy = fmaf(a.s, ey, py);
-    const float uox = qox * ro, uoy = qoy * ro;
-    r.gx = bw * (uox - sux);
-    r.gy = bw * (uoy - suy);
-    r.gv = bw * a.dt * (seu - fmaf(ex, uox, ey * uoy));
-    r.gw1 = beta * a.v * a.dt * (sp - 1.0f); // dQ/dw1 is the same for every heading
-    r.gw2 = beta * (sd - d_o);
-    return r;
+    return step_finish(a, g, ex, ey, beta, bw, off, S, R, RX, RY, RP, DL, grad);
 }
 
-// The same terms for KT (even) headings that are all enabled, on packed FP32
-// pairs of consecutive headings (the same IEEE operations per element as
-// step_terms, in half the issue slots; only the order of the final sums of
-// the expectations differs: two interleaved partial sums).
+// The same pass for KT (even) headings that are all enabled, on packed FP32
+// pairs of consecutive headings (the same operations per element as
+// step_terms, in half the issue slots; only the order of the sums differs:
+// two interleaved partial sums). A step whose bound is loose is handed to
+// step_terms, which takes the second pass.
 template <int KT>
 __device__ __forceinline__ StepGrad step_terms_full(const AdjointArgs &a, float zx, float zy, float ex, float ey,
                                                     float gx, float gy, float beta, bool grad)
 {
     static_assert(KT % 2 == 0, "pairs of headings");
-    const float px = zx - gx, py = zy - gy;
-    const float D = fmaf(px, px, fmaf(py, py, a.s2));
-    const float xo = fmaxf(D + a.two_s * fmaf(ex, px, ey * py), 0.0f);
-    const float ro = rsqrtf(fmaxf(xo, 1e-30f));
-    const float d_o = xo * ro;
     const float bw = beta * a.w2;
-    const float bw2 = bw * kLog2e;
+    const StepGeo g = step_geo(a, zx - gx, zy - gy, ex, ey, bw);
     const f32x2 *UX = reinterpret_cast<const f32x2 *>(a.ux);
     const f32x2 *UY = reinterpret_cast<const f32x2 *>(a.uy);
-    const f32x2 PX = f2_pack(px, px), PY = f2_pack(py, py), EX = f2_pack(ex, ex), EY = f2_pack(ey, ey);
-    const f32x2 DD = f2_pack(D, D), TS = f2_pack(a.two_s, a.two_s), DO = f2_pack(d_o, d_o);
-    const f32x2 BW2 = f2_pack(bw2, bw2);
-    // X_k = D + 2 s e_k.(z - g), its reciprocal square root, d_k = X_k rsqrt(X_k)
-    auto dist = [&](int k2, f32x2 &X, f32x2 &RK) {
+    const f32x2 PX = f2_pack(g.px, g.px), PY = f2_pack(g.py, g.py), DD = f2_pack(g.D, g.D);
+    const f32x2 EX = f2_pack(ex, ex), EY = f2_pack(ey, ey), DO = f2_pack(g.d_o, g.d_o);
+    const f32x2 TS = f2_pack(a.two_s, a.two_s), BL = f2_pack(g.bl2, g.bl2), NB = f2_pack(-g.B, -g.B);
+    const f32x2 Z = f2_pack(0.0f, 0.0f);
+    f32x2 S2 = Z, R2 = Z, RX2 = Z, RY2 = Z, RP2 = Z, DL2 = Z;
+#pragma unroll
+    for (int k2 = 0; k2 < KT / 2; ++k2) {
         const f32x2 PU = f2_fma(UX[k2], PX, f2_mul(UY[k2], PY));
         float x0, x1;
         f2_unpack(f2_fma(TS, PU, DD), x0, x1);
         x0 = fmaxf(x0, 0.0f);
         x1 = fmaxf(x1, 0.0f);
-        X = f2_pack(x0, x1);
-        RK = f2_pack(rsqrtf(fmaxf(x0, 1e-30f)), rsqrtf(fmaxf(x1, 1e-30f)));
-    };
-    f32x2 LG[KT / 2];
-    float m = -INFINITY;
-#pragma unroll
-    for (int k2 = 0; k2 < KT / 2; ++k2) {
-        f32x2 X, RK;
-        dist(k2, X, RK);
-        const f32x2 DK = f2_mul(X, RK);
-        // beta w2 (d_obs - d_k) in base 2, formed as a difference of squares
+        const f32x2 RK = f2_pack(rsqrtf(fmaxf(x0, 1e-30f)), rsqrtf(fmaxf(x1, 1e-30f)));
+        float q0, q1;
+        f2_unpack(f2_fma(f2_pack(x0, x1), RK, DO), q0, q1);
         const f32x2 NUM = f2_mul(TS, f2_fma(f2_sub(EX, UX[k2]), PX, f2_mul(f2_sub(EY, UY[k2]), PY)));
-        float q0, q1, n0, n1;
-        f2_unpack(f2_add(DO, DK), q0, q1);
-        f2_unpack(NUM, n0, n1);
-        LG[k2] = f2_mul(BW2, f2_pack(__fdividef(n0, fmaxf(q0, 1e-30f)), __fdividef(n1, fmaxf(q1, 1e-30f))));
-        float l0, l1;
-        f2_unpack(LG[k2], l0, l1);
-        m = fmaxf(m, fmaxf(l0, l1));
-    }
-    f32x2 SS = f2_pack(0.0f, 0.0f);
-    const f32x2 NM = f2_pack(-m, -m);
-#pragma unroll
-    for (int k2 = 0; k2 < KT / 2; ++k2) {
-        float l0, l1;
-        f2_unpack(f2_add(LG[k2], NM), l0, l1);
-        LG[k2] = f2_pack(ex2_approx(l0), ex2_approx(l1));
-        SS = f2_add(SS, LG[k2]);
-    }
-    float s0, s1;
-    f2_unpack(SS, s0, s1);
-    const float S = s0 + s1;
-    StepGrad r;
-    r.logpi = -(m + log2f(S)) * kLn2;
-    if (!grad) return r;
-    const float inv = 1.0f / S;
-    const f32x2 INV = f2_pack(inv, inv), SV = f2_pack(a.s, a.s);
-    f32x2 SUX = f2_pack(0.f, 0.f), SUY = SUX, SEU = SUX, SD = SUX, SP = SUX;
-#pragma unroll
-    for (int k2 = 0; k2 < KT / 2; ++k2) {
-        const f32x2 PK = f2_mul(LG[k2], INV);
-        f32x2 X, RK;
-        dist(k2, X, RK);
-        const f32x2 DK = f2_mul(X, RK);
-        const f32x2 UXK = f2_mul(f2_fma(SV, UX[k2], PX), RK), UYK = f2_mul(f2_fma(SV, UY[k2], PY), RK);
-        SUX = f2_fma(PK, UXK, SUX);
-        SUY = f2_fma(PK, UYK, SUY);
-        SEU = f2_fma(PK, f2_fma(UX[k2], UXK, f2_mul(UY[k2], UYK)), SEU);
-        SD = f2_fma(PK, DK, SD);
-        SP = f2_add(SP, PK);
+        const f32x2 DL = f2_mul(NUM, f2_pack(rcp_approx(fmaxf(q0, 1e-30f)), rcp_approx(fmaxf(q1, 1e-30f))));
+        float e0, e1;
+        f2_unpack(f2_fma(BL, DL, NB), e0, e1);
+        const f32x2 W = f2_pack(ex2_approx(e0), ex2_approx(e1));
+        const f32x2 WR = f2_mul(W, RK);
+        S2 = f2_add(S2, W);
+        R2 = f2_add(R2, WR);
+        RX2 = f2_fma(WR, UX[k2], RX2);
+        RY2 = f2_fma(WR, UY[k2], RY2);
+        RP2 = f2_fma(WR, PU, RP2);
+        DL2 = f2_fma(W, DL, DL2);
     }
     auto fold = [](f32x2 v) {
         float lo, hi;
         f2_unpack(v, lo, hi);
         return lo + hi;
     };
-    const float sux = fold(SUX), suy = fold(SUY), seu = fold(SEU), sd = fold(SD), sp = fold(SP);
-    const float qox = fmaf(a.s, ex, px), qoy = fmaf(a.s, ey, py);
-    const float uox = qox * ro, uoy = qoy * ro;
-    r.gx = bw * (uox - sux);
-    r.gy = bw * (uoy - suy);
-    r.gv = bw * a.dt * (seu - fmaf(ex, uox, ey * uoy));
-    r.gw1 = beta * a.v * a.dt * (sp - 1.0f); // dQ/dw1 is the same for every heading
-    r.gw2 = beta * (sd - d_o);
-    return r;
+    const float S = fold(S2);
+    if (!(S >= 0x1p-8f)) return step_terms<KT>(a, zx, zy, ex, ey, gx, gy, beta, grad);
+    return step_finish(a, g, ex, ey, beta, bw, g.B, S, fold(R2), fold(RX2), fold(RY2), fold(RP2), fold(DL2), grad);
 }
 
 // Several speeds (control u = speed q x heading k moving sl_q = v m_q dt):
@@ -213,18 +232,23 @@ __device__ __forceinline__ StepGrad step_terms_full(const AdjointArgs &a, float 
 //   dQ_u/dg = w2 u_u, dQ_u/dv = -m_q dt (w1 + w2 e_k.u_u), dQ_u/dw1 = -v m_q dt,
 //   dQ_u/dw2 = -d_u,
 // and the observed control is the observed direction at the enabled speed
-// nearest to the step's length. cu[u] = (cos, sin of theta_k, sl_q, m_q or 0
-// when speed q is disabled); the controls are visited in three passes
-// (maximum, sum, expectations) instead of being held in registers.
-__device__ __forceinline__ StepGrad step_terms_ms(const AdjointArgs &a, const float4 *cu, int U, float zx, float zy,
-                                                  float ex, float ey, float len, float gx, float gy, float beta,
-                                                  bool grad)
+// nearest to the step's length. The logit relative to the observed control
+// is beta (w1 (s_o - sl_q) + w2 delta_u) with the difference of squares
+//   delta_u = d_o - d_u = ((s_o - sl)(s_o + sl) + 2 (s_o e_o - sl e_k).p) / (d_o + d_u),
+// and each speed bounds its logits as in the one-speed pass, with its own
+// c_q (from sl_q) and
+//   d_o - c_q = ((s_o - sl_q)(s_o + sl_q) + 2 s_o e_o.p + 2 sg sl_q |p|) / (d_o + c_q);
+// the weights are taken relative to the largest of these bounds in one pass
+// over the controls, which keeps per speed the sums of the one-speed pass and
+// combines them with the speed's constants.
+__device__ __forceinline__ StepGrad step_terms_ms(const AdjointArgs &a, int K, float zx, float zy, float ex, float ey,
+                                                  float len, float gx, float gy, float beta, bool grad)
 {
     int q0 = 0;
     float best = INFINITY;
-    const float r = len / a.s;
+    const float rl = len / a.s;
     for (int q = 0; q < a.sp.S; ++q) {
-        const float d = fabsf(a.sp.mult[q] - r);
+        const float d = fabsf(a.sp.mult[q] - rl);
         if (((a.sp.speed_on >> q) & 1u) && d < best) {
             best = d;
             q0 = q;
@@ -233,56 +257,79 @@ __device__ __forceinline__ StepGrad step_terms_ms(const AdjointArgs &a, const fl
     const float so = a.sp.sl[q0], mo = a.sp.mult[q0];
     const float px = zx - gx, py = zy - gy;
     const float P = fmaf(px, px, py * py);
-    const float xo = fmaxf(fmaf(so, so, P) + 2.0f * so * fmaf(ex, px, ey * py), 0.0f);
+    const float pn = sqrtf(P);
+    const float po = fmaf(ex, px, ey * py);
+    const float xo = fmaxf(fmaf(2.0f * so, po, fmaf(so, so, P)), 0.0f);
     const float ro = rsqrtf(fmaxf(xo, 1e-30f));
     const float d_o = xo * ro;
     const float bw2 = beta * a.w2;
+    const float sg = bw2 >= 0.0f ? 1.0f : -1.0f;
     // logits in base 2 (exponentials on the SFU)
     const float bl1 = beta * a.sp.w1 * kLog2e, bl2 = bw2 * kLog2e;
-    auto logit = [&](const float4 &c, float &du, float &rk) {
-        const float xk = fmaxf(fmaf(c.z, c.z, P) + 2.0f * c.z * fmaf(c.x, px, c.y * py), 0.0f);
-        rk = rsqrtf(fmaxf(xk, 1e-30f));
-        du = xk * rk;
-        const float num = fmaf(so - c.z, so + c.z, 2.0f * fmaf(fmaf(so, ex, -c.z * c.x), px, fmaf(so, ey, -c.z * c.y) * py));
-        return fmaf(bl1, so - c.z, bl2 * __fdividef(num, fmaxf(d_o + du, 1e-30f)));
-    };
-    float m = -INFINITY;
-    for (int u = 0; u < U; ++u) {
-        const float4 c = cu[u];
-        if (c.w == 0.0f) continue;
-        float du, rk;
-        m = fmaxf(m, logit(c, du, rk));
+    float B = -INFINITY;
+    for (int q = 0; q < a.sp.S; ++q) {
+        if (!((a.sp.speed_on >> q) & 1u)) continue;
+        const float sl = a.sp.sl[q];
+        const float c = fabsf(pn - sg * sl);
+        const float tq = fmaf(so - sl, so + sl, 2.0f * fmaf(so, po, sg * sl * pn)) / fmaxf(d_o + c, 1e-30f);
+        B = fmaxf(B, fmaf(bl1, so - sl, bl2 * tq));
     }
-    float S = 0.0f;
-    for (int u = 0; u < U; ++u) {
-        const float4 c = cu[u];
-        if (c.w == 0.0f) continue;
-        float du, rk;
-        S += ex2_approx(logit(c, du, rk) - m);
+    float S, SUX, SUY, SMEU, SM, SDL, E;
+    // one pass over the enabled controls with weights 2^(logit - off); E is
+    // the largest logit seen
+    auto sums = [&](float off) {
+        S = SUX = SUY = SMEU = SM = SDL = 0.0f;
+        E = -INFINITY;
+        for (int q = 0; q < a.sp.S; ++q) {
+            if (!((a.sp.speed_on >> q) & 1u)) continue;
+            const float sl = a.sp.sl[q], mq = a.sp.mult[q];
+            const float ts = 2.0f * sl, D = fmaf(sl, sl, P), dsq = (so - sl) * (so + sl);
+            const float lq = fmaf(bl1, so - sl, -off), sox = so * ex, soy = so * ey;
+            float Sq = 0.f, Rq = 0.f, RXq = 0.f, RYq = 0.f, RPq = 0.f, DLq = 0.f;
+#pragma unroll 4
+            for (int k = 0; k < K; ++k) {
+                const float ux = a.ux[k], uy = a.uy[k];
+                const float pu = fmaf(ux, px, uy * py);
+                const float xk = fmaxf(fmaf(ts, pu, D), 0.0f);
+                const float rk = rsqrtf(fmaxf(xk, 1e-30f));
+                const float num = fmaf(2.0f, fmaf(fmaf(-sl, ux, sox), px, fmaf(-sl, uy, soy) * py), dsq);
+                const float dl = num * rcp_approx(fmaxf(fmaf(xk, rk, d_o), 1e-30f));
+                const float e = fmaf(bl2, dl, lq);
+                E = fmaxf(E, e);
+                const float w = ex2_approx(e);
+                const float wr = w * rk;
+                Sq += w;
+                Rq += wr;
+                RXq = fmaf(wr, ux, RXq);
+                RYq = fmaf(wr, uy, RYq);
+                RPq = fmaf(wr, pu, RPq);
+                DLq = fmaf(w, dl, DLq);
+            }
+            S += Sq;
+            SUX += fmaf(px, Rq, sl * RXq);              // sum w (p + sl e_k)_x / d_u
+            SUY += fmaf(py, Rq, sl * RYq);
+            SMEU = fmaf(mq, fmaf(sl, Rq, RPq), SMEU);   // sum w m_q e_k.u_u
+            SM = fmaf(mq, Sq, SM);
+            SDL += DLq;
+        }
+    };
+    float off = B;
+    sums(off);
+    if (!(S >= 0x1p-8f)) { // the bounds are loose: normalise by the largest logit
+        off += E;
+        sums(off);
     }
     StepGrad res;
-    res.logpi = -(m + log2f(S)) * kLn2;
+    res.logpi = -(off + log2f(S)) * kLn2;
     if (!grad) return res;
     const float inv = 1.0f / S;
-    float sux = 0.f, suy = 0.f, smeu = 0.f, sm = 0.f, sd = 0.f;
-    for (int u = 0; u < U; ++u) {
-        const float4 c = cu[u];
-        if (c.w == 0.0f) continue;
-        float du, rk;
-        const float pk = ex2_approx(logit(c, du, rk) - m) * inv;
-        const float uxk = fmaf(c.z, c.x, px) * rk, uyk = fmaf(c.z, c.y, py) * rk; // (z + sl e_k - g) / d_u
-        sux = fmaf(pk, uxk, sux);
-        suy = fmaf(pk, uyk, suy);
-        smeu = fmaf(pk * c.w, fmaf(c.x, uxk, c.y * uyk), smeu);
-        sm = fmaf(pk, c.w, sm);
-        sd = fmaf(pk, du, sd);
-    }
+    const float sux = SUX * inv, suy = SUY * inv, smeu = SMEU * inv, sm = SM * inv;
     const float uox = fmaf(so, ex, px) * ro, uoy = fmaf(so, ey, py) * ro;
     res.gx = bw2 * (uox - sux);
     res.gy = bw2 * (uoy - suy);
     res.gv = beta * a.dt * fmaf(a.sp.w1, sm - mo, a.w2 * (smeu - mo * fmaf(ex, uox, ey * uoy)));
     res.gw1 = beta * a.v * a.dt * (sm - mo);
-    res.gw2 = beta * (sd - d_o);
+    res.gw2 = -beta * SDL * inv; // sum pi d_u - d_o = -sum pi delta_u
     return res;
 }
 
@@ -298,15 +345,6 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(const __grid_const
     __shared__ double A_s[kMaxJ];
     __shared__ float G_s[kMaxJ][5];
     __shared__ int last;
-    __shared__ float4 cu[MS ? PM_MAX_SPEEDS * kMaxK : 1];
-    const int U = MS ? a.sp.S * a.K : 0;
-    if constexpr (MS) {
-        for (int u = threadIdx.x; u < U; u += blockDim.x) {
-            const int q = u / a.K, k = u - q * a.K;
-            cu[u] = make_float4(a.ux[k], a.uy[k], a.sp.sl[q], ((a.sp.speed_on >> q) & 1u) ? a.sp.mult[q] : 0.0f);
-        }
-        __syncthreads();
-    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int J = a.G * a.B;
     const int m = blockIdx.x;
@@ -341,7 +379,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(const __grid_const
                 ey = e.y;
             }
             StepGrad s;
-            if constexpr (MS) s = step_terms_ms(a, cu, U, zx, zy, ex, ey, len, gx, gy, beta, grad);
+            if constexpr (MS) s = step_terms_ms(a, a.K, zx, zy, ex, ey, len, gx, gy, beta, grad);
             else if constexpr (FULL) s = step_terms_full<KT>(a, zx, zy, ex, ey, gx, gy, beta, grad);
             else s = step_terms<KT>(a, zx, zy, ex, ey, gx, gy, beta, grad);
             A += (double)s.logpi;

@@ -113,6 +113,60 @@ def test_deterministic_and_ragged(ctx, orc):
     check_grad(np.concatenate([a[1].ravel(), [a[2], a[3][1]]]), np.concatenate([dg64.ravel(), [dv64, dw64[1]]]))
 
 
+@pytest.mark.parametrize("K,sign", [(8, 1.0), (5, 1.0), (8, -1.0)])
+def test_large_beta_takes_the_second_pass(ctx, orc, K, sign):
+    """beta w2 s large against K: the bound on the largest logit is loose at
+    many steps (the sum of the bound-normalised weights below 2^-8), so those
+    steps are normalised by their largest logit in a second pass. K = 8 takes
+    the packed form, K = 5 the scalar one; sign -1 walks away from the goals.
+    Tolerance on L: the relative 1e-6 plus, per step, what the FP32 inputs
+    allow at this beta: a heading vector rounded to FP32 (the table's e_k, the
+    observed e_o = dz/|dz|) moves d = ||p + s e|| by at most s |de|, so a
+    logit beta w2 (d_o - d_k) by at most |beta| w2 s 2^-21, plus 4e-6 of
+    arithmetic rounding. The gradient keeps the A15 bounds."""
+    from types import SimpleNamespace
+    rng = np.random.default_rng(9)
+    goals = rng.uniform(2.0, 8.0, size=(3, 2)).astype(np.float32)
+    beta = (sign * np.array([300.0, 1000.0, 1500.0])).astype(np.float32)
+    ts = SimpleNamespace(K=K, speed=2.0, dt=np.float32(0.1), goals=goals, beta=beta)
+    m = orc.Model(K, 2.0, ts.dt, goals, beta)
+    trajs = []
+    for i in range(12):
+        z0 = rng.uniform(0.0, 10.0, size=2).astype(np.float32)
+        trajs.append(orc.simulate(m, (i % 3) * 3 + 2 - (i // 3) % 2, z0, 40, 77, i).astype(np.float32))
+    offsets = np.cumsum([0] + [len(t) for t in trajs]).astype(np.int32)
+    traj = np.concatenate(trajs)
+    # the inputs do exercise the second pass: loose steps in FP64
+    th = 2 * np.pi * np.arange(K) / K
+    E = np.stack([np.cos(th), np.sin(th)], 1)
+    s = 2.0 * float(ts.dt)
+    loose = 0
+    for t in trajs:
+        z = t[:-1].astype(np.float64)
+        dz = np.diff(t.astype(np.float64), axis=0)
+        eo = dz / np.linalg.norm(dz, axis=1, keepdims=True)
+        for g in goals.astype(np.float64):
+            p = z - g
+            pn = np.linalg.norm(p, axis=1)
+            do = np.linalg.norm(p + s * eo, axis=1)
+            d = np.linalg.norm(p[:, None, :] + s * E[None], axis=2)
+            for b in beta.astype(np.float64):
+                c = np.abs(pn - np.sign(b) * s)
+                lg = b * (do[:, None] - d)
+                Bnd = b * (do - c)
+                loose += int((np.exp(lg - Bnd[:, None]).sum(1) < 2.0 ** -8).sum())
+    assert loose > 50, loose
+    prior = np.full(9, -np.log(9.0), np.float32)
+    L64, dg64, dv64, dw64 = orc.loglik_grad(m, offsets, traj.astype(np.float64), prior)
+    L, dg, dv, dw = gpu_loglik(ctx, ts, offsets, traj, prior)
+    n_steps = len(traj) - len(trajs)
+    assert abs(L - L64) <= 1e-6 * abs(L64) + n_steps * (2.0 ** -21 * 1500.0 * s + 4e-6), (L, L64)
+    want = np.concatenate([dg64.ravel(), [dv64, dw64[1]]])
+    check_grad(np.concatenate([dg.ravel(), [dv, dw[1]]]), want)
+    assert abs(dw[0]) <= 1e-5 * np.linalg.norm(want)
+    assert gpu_loglik(ctx, ts, offsets, traj, prior, grad=False) == L
+
+
 def test_autograd_function(ctx, orc):
     from paper_2603_01122_gb300.autograd import marginal_loglik
     ts = workloads.differentiation()
