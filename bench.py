@@ -423,6 +423,7 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
                                 r["h"].seed, r["h"].human_id, r["counts"], r["oob"], obs_xy=r["obs"],
                                 n_obs=r["h"].n_obs) for r in recs]
         pm.pm_batch_set(batch, humans, stream)
+        pm.pm_batch_set_zeroing(batch, 1, stream)  # only reachable cells: the outputs are only read
         t0 = time.perf_counter()
         pm.pm_batch_autotune(batch, stream)
         tune_s = time.perf_counter() - t0

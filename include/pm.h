@@ -313,11 +313,27 @@ pm_status pm_batch_set(pm_batch *b, const pm_human *humans, int32_t n_humans, vo
 /* Belief update (Eq. 3 / Eq. 7) of every human with n_obs > 0, one launch. */
 pm_status pm_batch_update_posterior(pm_batch *b, void *stream);
 
-/* Zero every output, then one persistent launch of Algorithm 1 over all tiles
- * of all humans. Each human's counts equal those of pm_predict_occupancy with
- * the same inputs (bit-identical). Enqueues only a memset and two kernels:
- * it may be captured in a CUDA graph. */
+/* Zero the outputs (every cell, or the reachable ones: pm_batch_set_zeroing),
+ * then one persistent launch of Algorithm 1 over all tiles of all humans.
+ * Each human's counts equal those of pm_predict_occupancy with the same
+ * inputs (bit-identical). Enqueues only a memset and two kernels: it may be
+ * captured in a CUDA graph. */
 pm_status pm_batch_predict(pm_batch *b, void *stream);
+
+/* reach = 0 (the default): pm_batch_predict zeroes every cell of every
+ * human's counts before the rollout. reach = 1: it zeroes only the cells of
+ * step t that a particle can occupy after t steps of the longest control,
+ * from this prediction's start or from the previous prediction's start into
+ * the same slot (a box of radius t * max step plus rounding margins, clipped
+ * to the output); a particle never leaves that box, so every other cell
+ * still holds the zero of an earlier pass. The batch records each slot's
+ * start in device memory (so a graph replay with new starts is covered).
+ * The first prediction after this call, after pm_batch_set or after
+ * pm_batch_set_block_flags zeroes every cell. In this mode the caller must
+ * not write into the counts between predictions (reading them is fine);
+ * after it has, call this function again. Stream-ordered; PM_EINVAL for
+ * another value. */
+pm_status pm_batch_set_zeroing(pm_batch *b, int32_t reach, void *stream);
 
 /* Time candidate launch shapes (emplacement mode, threads per CTA and
  * shared-memory window size) on the current batch with CUDA events and keep

@@ -74,6 +74,7 @@ def _signatures(lib):
         "pm_version": ([], C.c_char_p),
         "pm_sync_status": ([_vp, _vp], C.c_int),
         "pm_batch_set_block_flags": ([_vp, C.c_int32, _vp], C.c_int),
+        "pm_batch_set_zeroing": ([_vp, C.c_int32, _vp], C.c_int),
         "pm_update_posterior": ([_vp, P(pm_model), _vp, C.c_int32, _vp, _vp], C.c_int),
         "pm_update_posterior_into": ([_vp, P(pm_model), _vp, C.c_int32, _vp, _vp, _vp], C.c_int),
         "pm_predict_occupancy": ([_vp, P(pm_model), _vp, C.c_float, C.c_float, C.c_int32, C.c_int32,
@@ -303,6 +304,10 @@ def pm_mppi_solve(ctx, params: pm_mppi, z0, u_ref, delta, prob, prob_T, grid, co
 
 def pm_batch_set_block_flags(batch, enable, stream=None):
     _check(library().pm_batch_set_block_flags(batch, int(enable), _stream(stream)))
+
+
+def pm_batch_set_zeroing(batch, reach, stream=None):
+    _check(library().pm_batch_set_zeroing(batch, int(reach), _stream(stream)))
 
 
 def pm_batch_autotune(batch, stream=None):

@@ -62,6 +62,10 @@ struct pm_batch {
     unsigned *d_head = nullptr;
     float *d_post_part = nullptr;
     unsigned *d_post_ticket = nullptr;
+    float2 *d_prev = nullptr;        // [max_humans] start of the last prediction per slot (NaN: none), then a ticket word
+    bool zero_reach = false;         // zero only the reachable cells (pm_batch_set_zeroing)
+    float step_max = 0.0f;           // longest Euler step of the shared control set (upper bound)
+    int t_max = 1;                   // longest horizon of the batch (sizes the zeroing grid)
     pm::SmoothSrc *d_srcs = nullptr; // union source records, one per human
     uint8_t *d_flags = nullptr;      // block occupancy flags of every human's histogram
     size_t flags_cap = 0;
@@ -593,10 +597,29 @@ size_t batch_dyn_smem(const pm_batch *b)
     return 2 * stride_words * 4 + 2 * (size_t)b->threads * 2;
 }
 
+unsigned *zero_ticket(pm_batch *b)
+{
+    return reinterpret_cast<unsigned *>(b->d_prev + b->max_humans);
+}
+
+// Forget the starts of the last predictions: the next prediction zeroes every
+// cell of every human (stream-ordered).
+cudaError_t forget_starts(pm_batch *b, cudaStream_t stream)
+{
+    return cudaMemsetAsync(b->d_prev, 0xFF, (size_t)b->max_humans * sizeof(float2), stream);
+}
+
 pm_status batch_upload(pm_batch *b, cudaStream_t stream)
 {
     const int n = (int)b->humans.size();
     const double s = max_step(b->shared); // reach of the fastest control
+    // an upper bound on every FP32 step of the table (each rounded once from s cos, s sin)
+    b->step_max = (float)(s * (1.0 + 0x1p-16));
+    // the slots may now hold other humans or other buffers
+    if (b->zero_reach) {
+        cudaError_t ef = forget_starts(b, stream);
+        if (ef != cudaSuccess) return cuda_fail(ef, "batch start records");
+    }
     std::vector<int2> items;
     for (int h = 0; h < n; ++h)
         for (int p0 = 0; p0 < b->humans[h].n_particles; p0 += (b->warp_hist ? 32 : b->threads))
@@ -705,7 +728,10 @@ pm_status batch_upload(pm_batch *b, cudaStream_t stream)
     char *p = b->h_stage;
     std::memcpy(p, hd.data(), bh);
     std::memcpy(p + bh, ph.data(), bp);
-    int meta[2] = {(int)items.size(), n};
+    int t_max = 1;
+    for (const pm_human &u : b->humans) t_max = std::max(t_max, (int)u.horizon);
+    b->t_max = t_max;
+    int meta[3] = {(int)items.size(), n, t_max};
     std::memcpy(p + bh + bp, meta, sizeof meta);
     if (bi) std::memcpy(p + bh + bp + 16, items.data(), bi);
     if (bh) e = cudaMemcpyAsync(b->d_humans, p, bh, cudaMemcpyHostToDevice, stream);
@@ -731,7 +757,8 @@ pm_status batch_predict_impl(pm_batch *b, cudaStream_t stream)
     pm_ctx *ctx = b->ctx;
     cudaError_t e = cudaMemsetAsync(b->d_head, 0, sizeof(unsigned), stream);
     if (e != cudaSuccess) return cuda_fail(e, "queue reset");
-    e = pm::launch_batch_zero(b->d_humans, b->d_meta + 1, b->max_humans, ctx->sm_count, stream);
+    e = pm::launch_batch_zero(b->d_humans, b->d_meta + 1, b->max_humans, ctx->sm_count, b->t_max,
+                              b->zero_reach ? b->d_prev : nullptr, zero_ticket(b), b->step_max, stream);
     if (e != cudaSuccess) return cuda_fail(e, "zero launch");
     pm::RolloutArgs t;
     std::memset(&t, 0, sizeof t);
@@ -1113,6 +1140,9 @@ pm_status pm_batch_create(pm_ctx *ctx, const pm_model *shared, int32_t max_human
     if (e == cudaSuccess) e = cudaMalloc(&b->d_post_part, (size_t)max_humans * b->post_stride * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_post_ticket, (size_t)max_humans * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(b->d_post_ticket, 0, (size_t)max_humans * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_prev, (size_t)max_humans * sizeof(float2) + 16);
+    if (e == cudaSuccess) e = cudaMemset(b->d_prev, 0xFF, (size_t)max_humans * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemset(reinterpret_cast<char *>(b->d_prev) + (size_t)max_humans * sizeof(float2), 0, 16);
     if (e == cudaSuccess) e = cudaMemset(b->d_meta, 0, 256);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -1142,6 +1172,7 @@ void pm_batch_destroy(pm_batch *b)
     cudaFree(b->d_head);
     cudaFree(b->d_post_part);
     cudaFree(b->d_post_ticket);
+    cudaFree(b->d_prev);
     if (b->h_stage) cudaFreeHost(b->h_stage);
     delete b;
 }
@@ -1172,6 +1203,18 @@ pm_status pm_batch_update_posterior(pm_batch *b, void *stream)
     cudaError_t e = pm::launch_posterior_batch(a, b->d_post, b->d_meta + 1, b->max_humans, b->max_chunks, b->max_J,
                                                (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "batched posterior launch");
+    return PM_OK;
+}
+
+pm_status pm_batch_set_zeroing(pm_batch *b, int32_t reach, void *stream)
+{
+    PM_RANGE("pm_batch_set_zeroing");
+    if (!b) return fail(PM_EINVAL, "batch is NULL");
+    if (reach != 0 && reach != 1) return fail(PM_EINVAL, "reach=%d: 0 or 1", reach);
+    DeviceScope dev(b->ctx->device);
+    b->zero_reach = reach != 0;
+    cudaError_t e = forget_starts(b, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch start records");
     return PM_OK;
 }
 

@@ -19,6 +19,9 @@
 // batch_rollout_kernel (CTAs take tiles of blockDim particles and count each
 // step in a shared-memory window around the human's start cell). The
 // autotuner times both.
+#include <algorithm>
+#include <climits>
+
 #include <cuda_runtime.h>
 
 #include "pm_kernels.cuh"
@@ -229,6 +232,35 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_warp_kernel(const _
     }
 }
 
+// Output cells [x0, x1] x [y0, y1] that a particle started at z can occupy
+// after t steps of at most smax each: the start cell (by the rollout's own
+// FP32 rule) widened by ceil(R / res) + 3 cells, R = t smax plus a bound on
+// the rounding the t FP32 position additions can accumulate; the extra cells
+// cover the rounding of the binning. Empty when x0 > x1 or y0 > y1.
+struct ReachBox {
+    int x0, x1, y0, y1;
+};
+
+__device__ __forceinline__ ReachBox reach_box(const BatchHuman &h, float zx, float zy, int t, float smax)
+{
+    const int gcx = __float2int_rd(__fmul_rn(__fsub_rn(zx, h.gx0), h.inv_res));
+    const int gcy = __float2int_rd(__fmul_rn(__fsub_rn(zy, h.gy0), h.inv_res));
+    int cx_off = h.cx_off, cy_off = h.cy_off;
+    if (h.center) {
+        cx_off = gcx - (h.W - 1) / 2;
+        cy_off = gcy - (h.H - 1) / 2;
+    }
+    const float R = (float)t * smax;
+    const float err = (float)t * (fabsf(zx) + fabsf(zy) + R) * 0x1p-22f;
+    const int rc = (int)fminf(ceilf((R + err) * h.inv_res), 4194304.0f) + 3;
+    ReachBox r;
+    r.x0 = max(gcx - cx_off - rc, 0);
+    r.x1 = min(gcx - cx_off + rc, h.W - 1);
+    r.y0 = max(gcy - cy_off - rc, 0);
+    r.y1 = min(gcy - cy_off + rc, h.H - 1);
+    return r;
+}
+
 // Zero every human's counts [T][H][W], oob [T] and block flags: blockIdx.y
 // strides over humans, the x dimension over 16-byte words of the counts
 // (scalar head and tail).
@@ -255,6 +287,75 @@ __global__ void batch_zero_kernel(const BatchHuman *humans, const int *n_dev)
             for (size_t q = t0; q < nf; q += stride) h.flags[q] = 0u;
         }
     }
+}
+
+// The reachable-cells form. A warp per (human, step t, row group g of
+// kReachGroups): it zeroes oob[t] and the step's block flags (g = 0) and, of
+// the counts of step t, the rows r = g mod kReachGroups of
+//  - the two boxes a particle can reach from this prediction's start z0 and
+//    from the previous prediction's start into the same buffers (prev), or
+//  - every row, when the human has no recorded previous start (NaN) or a
+//    non-finite start.
+// (the smallest rectangle holding both, in fact). Every other cell still
+// holds the zero of an earlier pass, because no particle leaves its box. The
+// last CTA to finish records each human's z0 in prev (ticket, no waiting;
+// every CTA has read prev before it takes its ticket).
+constexpr int kReachGroups = 4;
+
+__global__ void batch_zero_reach_kernel(const BatchHuman *humans, const int *n_dev, float2 *prev, unsigned *ticket,
+                                        float smax)
+{
+    const int n = n_dev[0], t_max = max(n_dev[1], 1); // humans and their longest horizon
+    const int lane = threadIdx.x & 31;
+    const long nwarp = ((long)gridDim.x * blockDim.x) >> 5;
+    const long items = (long)n * t_max * kReachGroups;
+    for (long it = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < items; it += nwarp) {
+        const int g = (int)(it % kReachGroups);
+        const int t = (int)((it / kReachGroups) % t_max);
+        const int hh = (int)(it / ((long)kReachGroups * t_max));
+        const BatchHuman &h = humans[hh];
+        if (t >= h.T) continue;
+        if (g == 0) {
+            if (lane == 0) h.oob[t] = 0u;
+            if (h.flags) {
+                const int nf = h.fbx * h.fby;
+                for (int q = lane; q < nf; q += 32) h.flags[(size_t)t * nf + q] = 0u;
+            }
+        }
+        const float zx = h.z0[0], zy = h.z0[1];
+        const float2 zp = prev[hh];
+        uint32_t *stepp = h.counts + (size_t)t * h.W * h.H;
+        if (!(isfinite(zp.x) && isfinite(zp.y) && isfinite(zx) && isfinite(zy))) {
+            for (int row = g; row < h.H; row += kReachGroups) {
+                uint32_t *rowp = stepp + (size_t)row * h.W;
+                for (int x = lane; x < h.W; x += 32) rowp[x] = 0u;
+            }
+            continue;
+        }
+        const ReachBox a = reach_box(h, zx, zy, t + 1, smax);
+        const ReachBox b = reach_box(h, zp.x, zp.y, t + 1, smax);
+        const bool ea = a.x0 <= a.x1 && a.y0 <= a.y1, eb = b.x0 <= b.x1 && b.y0 <= b.y1;
+        if (!ea && !eb) continue;
+        // the smallest rectangle holding both boxes (cells of it outside them
+        // are zero already, so zeroing them again is harmless)
+        const int x0 = min(ea ? a.x0 : INT_MAX, eb ? b.x0 : INT_MAX), x1 = max(ea ? a.x1 : -1, eb ? b.x1 : -1);
+        const int y0 = min(ea ? a.y0 : INT_MAX, eb ? b.y0 : INT_MAX), y1 = max(ea ? a.y1 : -1, eb ? b.y1 : -1);
+        for (int row = y0 + ((g - y0 % kReachGroups) + kReachGroups) % kReachGroups; row <= y1;
+             row += kReachGroups) {
+            uint32_t *rowp = stepp + (size_t)row * h.W;
+            for (int x = x0 + lane; x <= x1; x += 32) rowp[x] = 0u;
+        }
+    }
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1u;
+    }
+    __syncthreads();
+    if (!last) return;
+    for (int hh = threadIdx.x; hh < n; hh += blockDim.x) prev[hh] = make_float2(humans[hh].z0[0], humans[hh].z0[1]);
+    if (threadIdx.x == 0) *ticket = 0u;
 }
 
 // The single-human form of the above: the counts in 16-byte words (scalar
@@ -372,9 +473,18 @@ cudaError_t launch_zero_outputs(uint32_t *counts, size_t words, uint32_t *oob, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_zero(const BatchHuman *humans, const int *n_dev, int max_rows, int sm_count, cudaStream_t s)
+cudaError_t launch_batch_zero(const BatchHuman *humans, const int *n_dev, int max_rows, int sm_count, int t_max,
+                              float2 *prev, unsigned *ticket, float smax, cudaStream_t s)
 {
     if (max_rows <= 0) return cudaSuccess;
+    if (prev) {
+        // a warp per (human, step, row group), 8 warps per CTA; the kernel
+        // reads the live counts and strides over what this grid does not cover
+        const long warps = (long)max_rows * t_max * kReachGroups;
+        const long ctas = std::min<long>((warps + 7) / 8, (long)sm_count * 64);
+        batch_zero_reach_kernel<<<(unsigned)std::max<long>(ctas, 1), 256, 0, s>>>(humans, n_dev, prev, ticket, smax);
+        return cudaGetLastError();
+    }
     dim3 grid((unsigned)(sm_count * 2), (unsigned)(max_rows < 64 ? max_rows : 64));
     batch_zero_kernel<<<grid, 256, 0, s>>>(humans, n_dev);
     return cudaGetLastError();

@@ -205,7 +205,12 @@ cudaError_t launch_adjoint(const AdjointArgs &a, cudaStream_t s);
 int batch_rollout_occupancy(int K, uint64_t enabled, int S, bool marks, const RolloutShape &shape, size_t dyn);
 size_t batch_warp_tables_bytes(int threads, bool multi_speed); // dynamic shared memory of the warp form
 cudaError_t launch_batch_rollout(const BatchArgs &a, const RolloutShape &shape, int blocks, size_t dyn, cudaStream_t s);
-cudaError_t launch_batch_zero(const BatchHuman *humans, const int *n_dev, int max_rows, int sm_count, cudaStream_t s);
+// prev == NULL: every cell; else the reachable cells of humans with a
+// recorded previous start, and the call then records z0 in prev. n_dev[0]:
+// live humans, n_dev[1]: their longest horizon (device); max_rows and t_max
+// size the grid only.
+cudaError_t launch_batch_zero(const BatchHuman *humans, const int *n_dev, int max_rows, int sm_count, int t_max,
+                              float2 *prev, unsigned *ticket, float smax, cudaStream_t s);
 // One human's outputs before its rollout, in one launch: counts [words]
 // (or NULL), oob [T] (or NULL) and the chunk counter.
 cudaError_t launch_zero_outputs(uint32_t *counts, size_t words, uint32_t *oob, int T, unsigned *head, int sm_count,

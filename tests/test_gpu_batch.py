@@ -242,3 +242,66 @@ def test_batch_rejects_mixed_or_invalid(ctx, orc):
             pm.pm_batch_set(b, hs)
     finally:
         pm.pm_batch_destroy(b)
+
+
+@pytest.mark.parametrize("center", [0, 1])
+def test_reach_zeroing_equals_full_zeroing(ctx, orc, center):
+    """pm_batch_set_zeroing(1) zeroes only the cells the previous and the
+    current prediction of a slot can reach. Against a batch that zeroes every
+    cell (same humans, same starts, its own buffers): equal counts and oob
+    from garbage, with the starts moved between predictions (small steps, a
+    jump across the grid, no move), directly and from a replayed CUDA graph
+    whose starts change on the device; with the full grid and with centred
+    41 x 41 windows."""
+    import paper_2603_01122_gb300 as pm
+    hu = workloads.plain_small()
+    ds = _setup(orc, [hu, hu, hu], scale=0.5)
+    x0, y0, res, W, H = hu.grid
+    if center:
+        for d in ds:
+            d["grid"] = pm.make_grid(x0, y0, res, 41, 41)
+            d["counts"] = torch.full((d["T"], 41, 41), 0x3C3C3C3C, dtype=torch.int32, device="cuda:0")
+    full = [dict(d, counts=torch.full_like(d["counts"], 0x5A5A5A5A), oob=torch.full_like(d["oob"], 5)) for d in ds]
+    model = _shared_model(hu, ds[0]["gh"])
+    bf = pm.pm_batch_create(ctx, model, len(ds))
+    br = pm.pm_batch_create(ctx, model, len(ds))
+    try:
+        pm.pm_batch_set(bf, _pm_humans(full, center))
+        pm.pm_batch_set(br, _pm_humans(ds, center))
+        pm.pm_batch_set_zeroing(br, 1)
+        starts = [d["z0"].cpu().numpy().copy() for d in ds]
+        moves = [(0.0, 0.0), (0.3, -0.2), (0.0, 0.0), (-3.1, 2.4), (0.05, 0.05), (4.0, 4.0)]
+
+        def check():
+            torch.cuda.synchronize()
+            for d, f in zip(ds, full):
+                assert torch.equal(d["counts"], f["counts"])
+                assert torch.equal(d["oob"], f["oob"])
+                tot = d["counts"].view(d["T"], -1).sum(1, dtype=torch.int64) + d["oob"]
+                assert torch.all(tot == d["N"])
+
+        for k, (mx, my) in enumerate(moves):
+            for i, d in enumerate(ds):
+                starts[i] += np.float32([mx * (1 + 0.5 * i), my])
+                d["z0"].copy_(torch.tensor(starts[i], device="cuda:0"))
+            pm.pm_batch_predict(bf)
+            pm.pm_batch_predict(br)
+            check()
+        # graph replays: the starts change on the device between replays
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                pm.pm_batch_predict(br, s)
+        for mx, my in [(1.0, 0.0), (0.0, 0.0), (-2.5, -1.5)]:
+            for i, d in enumerate(ds):
+                starts[i] += np.float32([mx, my * (1 + i)])
+                d["z0"].copy_(torch.tensor(starts[i], device="cuda:0"))
+            torch.cuda.synchronize()
+            g.replay()
+            pm.pm_batch_predict(bf)
+            check()
+    finally:
+        pm.pm_batch_destroy(bf)
+        pm.pm_batch_destroy(br)
