@@ -149,7 +149,7 @@ constexpr size_t kWarpTableBytesMS = (size_t)kMaxJ * 24;
 // MARKS: also write the block occupancy flags (a separate instantiation, so
 // the kernel without marks carries none of their code).
 template <int KT, bool FULL, bool MS = false, bool MARKS = false>
-__global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_warp_kernel(const __grid_constant__ BatchArgs a)
+__device__ __forceinline__ void batch_warp_body(const BatchArgs &a)
 {
     __shared__ float2 step[MS ? PM_MAX_SPEEDS * kMaxK : kMaxK];
     extern __shared__ __align__(16) uint32_t dyn[];
@@ -230,6 +230,22 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_warp_kernel(const _
             rollout_lane<KT, false, true>(a.tab, a.enabled, a.s2, c, comp, cdf, step, betas, a.K, h->speed_on);
         else rollout_lane<KT, FULL>(a.tab, a.enabled, a.s2, c, comp, cdf, step);
     }
+}
+
+// Two register budgets of the same body: 80 registers (6 CTAs of 128 threads
+// per SM), and 72 (7 CTAs) for the one-speed instantiations with K <= 36,
+// which do not spill there (24 bytes with marks); the 64-human served frame
+// is 0.6 % faster with 7. K = 64 and several speeds spill at 72 and keep 80.
+template <int KT, bool FULL, bool MS = false, bool MARKS = false>
+__global__ void __launch_bounds__(kBatchMaxThreads, 3) batch_warp_kernel(const __grid_constant__ BatchArgs a)
+{
+    batch_warp_body<KT, FULL, MS, MARKS>(a);
+}
+
+template <int KT, bool FULL, bool MARKS = false>
+__global__ void __maxnreg__(72) batch_warp_kernel72(const __grid_constant__ BatchArgs a)
+{
+    batch_warp_body<KT, FULL, false, MARKS>(a);
 }
 
 // Output cells [x0, x1] x [y0, y1] that a particle started at z can occupy
@@ -397,8 +413,14 @@ template <int KT, bool FULL>
 cudaError_t batch_shape(const BatchArgs &a, const RolloutShape &sh, int blocks, size_t dyn, cudaStream_t s, int *occ)
 {
     if (sh.warp_hist) {
-        if (a.marks) return launch_or_query(batch_warp_kernel<KT, FULL, false, true>, a, blocks, sh.threads, dyn, s, occ);
-        return launch_or_query(batch_warp_kernel<KT, FULL>, a, blocks, sh.threads, dyn, s, occ);
+        if constexpr (KT <= 36) {
+            if (a.marks) return launch_or_query(batch_warp_kernel72<KT, FULL, true>, a, blocks, sh.threads, dyn, s, occ);
+            return launch_or_query(batch_warp_kernel72<KT, FULL>, a, blocks, sh.threads, dyn, s, occ);
+        } else {
+            if (a.marks)
+                return launch_or_query(batch_warp_kernel<KT, FULL, false, true>, a, blocks, sh.threads, dyn, s, occ);
+            return launch_or_query(batch_warp_kernel<KT, FULL>, a, blocks, sh.threads, dyn, s, occ);
+        }
     }
     return launch_or_query(batch_rollout_kernel<KT, FULL>, a, blocks, sh.threads, dyn, s, occ);
 }

@@ -252,12 +252,13 @@ class Server:
                 self._enqueue()
             self.done.record(self.stream)
         self.done.synchronize()
+        latency = time.perf_counter() - t0  # the occupancy is ready
         # the frame has applied each live human's step (prev -> cur): a later
         # frame without a new observation then applies a zero-length step,
         # which leaves the belief unchanged (the copy above has completed)
         self.obs_host[:, 0] = self.obs_host[:, 1]
         self.frames += 1
-        return time.perf_counter() - t0
+        return latency
 
     # -- checkpoint and resume ---------------------------------------------------
     def export_state(self, slot: int) -> dict:
