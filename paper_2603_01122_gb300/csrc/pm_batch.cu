@@ -318,6 +318,21 @@ __global__ void batch_zero_kernel(const BatchHuman *humans, const int *n_dev)
 // every CTA has read prev before it takes its ticket).
 constexpr int kReachGroups = 4;
 
+// Zero words [x0, x1] of a row with the lanes of a warp: 16-byte stores for
+// the aligned body, single words for the head and the tail.
+__device__ __forceinline__ void zero_row(uint32_t *rowp, int x0, int x1, int lane)
+{
+    const int n = x1 - x0 + 1;
+    if (n <= 0) return;
+    uint32_t *p = rowp + x0;
+    const int head = min((int)((4u - (((uintptr_t)p >> 2) & 3u)) & 3u), n);
+    const int body = (n - head) >> 2, tail = (n - head) & 3;
+    if (lane < head) p[lane] = 0u;
+    uint4 *v = reinterpret_cast<uint4 *>(p + head);
+    for (int i = lane; i < body; i += 32) v[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (lane < tail) p[head + 4 * body + lane] = 0u;
+}
+
 __global__ void batch_zero_reach_kernel(const BatchHuman *humans, const int *n_dev, float2 *prev, unsigned *ticket,
                                         float smax)
 {
@@ -342,10 +357,7 @@ __global__ void batch_zero_reach_kernel(const BatchHuman *humans, const int *n_d
         const float2 zp = prev[hh];
         uint32_t *stepp = h.counts + (size_t)t * h.W * h.H;
         if (!(isfinite(zp.x) && isfinite(zp.y) && isfinite(zx) && isfinite(zy))) {
-            for (int row = g; row < h.H; row += kReachGroups) {
-                uint32_t *rowp = stepp + (size_t)row * h.W;
-                for (int x = lane; x < h.W; x += 32) rowp[x] = 0u;
-            }
+            for (int row = g; row < h.H; row += kReachGroups) zero_row(stepp + (size_t)row * h.W, 0, h.W - 1, lane);
             continue;
         }
         const ReachBox a = reach_box(h, zx, zy, t + 1, smax);
@@ -357,10 +369,8 @@ __global__ void batch_zero_reach_kernel(const BatchHuman *humans, const int *n_d
         const int x0 = min(ea ? a.x0 : INT_MAX, eb ? b.x0 : INT_MAX), x1 = max(ea ? a.x1 : -1, eb ? b.x1 : -1);
         const int y0 = min(ea ? a.y0 : INT_MAX, eb ? b.y0 : INT_MAX), y1 = max(ea ? a.y1 : -1, eb ? b.y1 : -1);
         for (int row = y0 + ((g - y0 % kReachGroups) + kReachGroups) % kReachGroups; row <= y1;
-             row += kReachGroups) {
-            uint32_t *rowp = stepp + (size_t)row * h.W;
-            for (int x = x0 + lane; x <= x1; x += 32) rowp[x] = 0u;
-        }
+             row += kReachGroups)
+            zero_row(stepp + (size_t)row * h.W, x0, x1, lane);
     }
     __shared__ bool last;
     __syncthreads();
