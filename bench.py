@@ -77,7 +77,7 @@ def parse():
                     help="run the Poisson arrival process for this many simulated seconds (0: skip)")
     ap.add_argument("--serving-frames", type=int, default=250, help="frames of the forced-64-live run")
     ap.add_argument("--sections", default="all", type=lambda v: set(v.split(",")),
-                    help="extra sections to run: all, or a comma list of batched, serving, speeds, table1, "
+                    help="extra sections to run: all, or a comma list of batched, batched_small, serving, speeds, table1, "
                          "differentiation (plain_small always runs)")
     ap.add_argument("--workload", default="paper_scale", choices=sorted(MAIN_WORKLOADS),
                     help="the main line's workload (paper_scale: one speed, K = 36; multi_speed: |U| = 96)")
@@ -485,6 +485,58 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
                                     "batched_ms_with_marks": marked_batch_ms}}
         del recs
 
+    if want("batched_small"):
+        # -- 64 humans of the plain configuration's shape: one graph replay of the
+        # batched form vs the same humans through the single-human calls in sequence
+        hs = workloads.plain_crowd(64)
+        offs = np.cumsum([0] + [h.G * h.B for h in hs])
+        prior_flat = torch.tensor(np.concatenate([h.uniform_log_prior() for h in hs]), device=dev)
+        lb_flat = prior_flat.clone()
+        recs = []
+        for k, h in enumerate(hs):
+            gg, bb = torch.tensor(h.goals, device=dev), torch.tensor(h.beta, device=dev)
+            ob = gpu_paths(pm, ctx, torch, dev, h, h.n_obs, h.human_id)
+            x0, y0, res, W, H = h.grid
+            recs.append(dict(h=h, g=gg, b=bb, obs=ob, prior=prior_flat[offs[k]:offs[k + 1]],
+                             lb=lb_flat[offs[k]:offs[k + 1]], z0=ob[-1].clone(),
+                             z0h=[float(v) for v in ob[-1].cpu().numpy()], grid=pm.make_grid(x0, y0, res, W, H),
+                             counts=torch.empty((h.horizon, H, W), dtype=torch.int32, device=dev),
+                             oob=torch.empty(h.horizon, dtype=torch.int32, device=dev),
+                             model=pm.make_model(h.K, h.speed, h.dt, gg, bb)))
+        steps = sum(r["h"].n_particles * r["h"].horizon for r in recs)
+
+        def one_by_one():
+            for r in recs:
+                pm.pm_update_posterior_into(ctx, r["model"], r["obs"], r["h"].n_obs, r["prior"], r["lb"], stream)
+                pm.pm_predict_occupancy(ctx, r["model"], r["lb"], r["z0h"][0], r["z0h"][1], r["h"].n_particles,
+                                        r["h"].horizon, r["grid"], r["h"].seed, r["h"].human_id, r["counts"],
+                                        r["oob"], stream)
+        plain_ms = time_events(torch, stream, one_by_one, 10)
+        batch = pm.pm_batch_create(ctx, recs[0]["model"], len(recs))
+        try:
+            humans = [pm.make_human(r["g"], r["b"], r["lb"], r["z0"], r["h"].n_particles, r["h"].horizon, r["grid"],
+                                    r["h"].seed, r["h"].human_id, r["counts"], r["oob"], obs_xy=r["obs"],
+                                    n_obs=r["h"].n_obs) for r in recs]
+            pm.pm_batch_set(batch, humans, stream)
+            pm.pm_batch_set_zeroing(batch, 1, stream)
+            pm.pm_batch_autotune(batch, stream)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(stream):
+                torch.cuda.synchronize()
+                with torch.cuda.graph(graph, stream=stream):
+                    lb_flat.copy_(prior_flat)
+                    pm.pm_batch_update_posterior(batch, stream)
+                    pm.pm_batch_predict(batch, stream)
+            batch_ms = time_events(torch, stream, graph.replay, 20)
+            out["batched_small"] = {"humans": len(recs), "particle_steps": steps, "batched_ms": batch_ms,
+                                    "batched_particle_steps_per_s": steps / (batch_ms * 1e-3),
+                                    "one_by_one_ms": plain_ms,
+                                    "one_by_one_particle_steps_per_s": steps / (plain_ms * 1e-3),
+                                    "speedup_vs_one_by_one": plain_ms / batch_ms}
+        finally:
+            pm.pm_batch_destroy(batch)
+        del recs
+
     if want("serving"):
         # -- serving: 64 live humans forced, one frame per observation
         from paper_2603_01122_gb300.serving import Server, run_arrivals
@@ -691,8 +743,9 @@ def sig(x, n=4):
 def target_summary(line, extra):
     """The figures the targets are stated in, compact: the rollout's SFU
     fraction, the batched and served rates against the plain per-human path
-    (the plain configuration's rate, and the same humans issued one by one)
-    and the 64-human frame latency with and without the grid epilogue."""
+    (the plain configuration's rate, and the same humans issued one by one,
+    also for 64 humans of the plain configuration's shape) and the 64-human
+    frame latency with and without the grid epilogue."""
     t = {"rollout_sfu_frac": sig(line["roofline"]["frac"], 3), "value": sig(line["value"])}
     if not extra:
         return t
@@ -702,6 +755,10 @@ def target_summary(line, extra):
         t["batched"] = {"rate": sig(b["batched_particle_steps_per_s"]), "sfu_frac": sig(b["sfu_roofline_frac"], 3),
                         "x_plain_small": sig(b["rate_vs_plain_small"], 3),
                         "x_same_humans_one_by_one": sig(b["speedup_vs_plain"], 3), "ms": sig(b["batched_ms"])}
+    c = extra.get("batched_small")
+    if c:
+        t["batched_small_64"] = {"rate": sig(c["batched_particle_steps_per_s"]), "ms": sig(c["batched_ms"]),
+                                 "x_same_humans_one_by_one": sig(c["speedup_vs_one_by_one"], 3)}
     f = extra.get("serving_forced_64")
     if f:
         t["served_64"] = {"p50_ms": sig(f["p50_ms"]), "p99_ms": sig(f["p99_ms"]),

@@ -305,3 +305,33 @@ def test_reach_zeroing_equals_full_zeroing(ctx, orc, center):
     finally:
         pm.pm_batch_destroy(bf)
         pm.pm_batch_destroy(br)
+
+
+def test_plain_crowd_alone_equals_in_mix(ctx, orc):
+    """16 humans of the plain configuration's shape (K = 8: the 8-heading
+    instantiations of the batched kernels) in one batch, with reachable-cell
+    zeroing: every human's belief and counts equal its single-human calls."""
+    import paper_2603_01122_gb300 as pm
+    humans = workloads.plain_crowd(16)
+    ds = _setup(orc, humans)
+    b = pm.pm_batch_create(ctx, _shared_model(humans[0], ds[0]["gh"]), len(ds))
+    try:
+        pm.pm_batch_set(b, _pm_humans(ds))
+        pm.pm_batch_set_zeroing(b, 1)
+        singles = []
+        for d in ds:
+            lb = d["lb"].clone()
+            pm.pm_update_posterior(ctx, d["gh"].model, d["obs"], d["n_obs"], lb)
+            singles.append(lb)
+        pm.pm_batch_update_posterior(b)
+        for _ in range(2):  # the second prediction zeroes only the reachable cells
+            pm.pm_batch_predict(b)
+        torch.cuda.synchronize()
+        for d, lb in zip(ds, singles):
+            assert torch.equal(d["lb"], lb)
+            c, o = _single(ctx, d, lb)
+            torch.cuda.synchronize()
+            assert torch.equal(d["counts"], c), d["hu"].human_id
+            assert torch.equal(d["oob"], o)
+    finally:
+        pm.pm_batch_destroy(b)

@@ -99,6 +99,21 @@ def plain_small(seed: int = MASTER_SEED) -> Human:
                  seed=seed, human_id=0, obs_seed=seed + 1)
 
 
+def plain_crowd(n: int = 64, seed: int = MASTER_SEED) -> list:
+    """n humans of the plain configuration's shape (K = 8, v = 1, dt = 0.1, the same
+    goals and beta grid, N = 10k, T = 20, 100 x 100 grid at 0.1 m), each with its own
+    start uniform in [-3, 3]^2, true component, seed and human id: many small
+    humans, where one call per human is bound by launch latency."""
+    rng = np.random.default_rng([seed, 8])
+    base = plain_small(seed)
+    out = []
+    for i in range(n):
+        out.append(dataclasses.replace(base, start=rng.uniform(-3.0, 3.0, size=2).astype(np.float32),
+                                       true_j=int(rng.integers(0, 6)), seed=seed + 1000 + i, human_id=1000 + i,
+                                       obs_seed=seed + 2000 + i))
+    return out
+
+
 def paper_scale(seed: int = MASTER_SEED) -> Human:
     """1 human in a 10 m room: 3 goals uniform, 10 log-spaced beta 0.01..100, K = 36,
     dt = 0.02, N = 100k, T = 150, 200 x 200 grid at 0.05 m; 50 observed steps from a
