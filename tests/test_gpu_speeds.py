@@ -181,6 +181,23 @@ def test_batch_equals_single(ctx, orc):
         torch.cuda.synchronize()
         for d, (_, c1, _) in zip(ds, singles):
             np.testing.assert_array_equal(d["counts"].cpu().numpy(), c1)
+        # reachable-cell zeroing under several speeds (the fastest one, 1.5 v,
+        # sets the boxes), with the starts moved on the device between calls
+        pm.pm_batch_set_zeroing(b, 1)
+        for step in range(3):
+            for i, d in enumerate(ds):
+                if step:
+                    d["z0"].add_(torch.tensor([0.3 * (i + 1), -0.45 * step], device="cuda:0"))
+            pm.pm_batch_predict(b)
+            torch.cuda.synchronize()
+            for d, (lb1, _, _) in zip(ds, singles):
+                counts = torch.empty_like(d["counts"])
+                oob = torch.empty_like(d["oob"])
+                z0 = d["z0"].cpu().numpy()
+                pm.pm_predict_occupancy(ctx, d["gh"].model, dev(lb1), float(z0[0]), float(z0[1]), d["N"], d["T"],
+                                        d["grid"], hu.seed, d["human"], counts, oob)
+                torch.cuda.synchronize()
+                assert torch.equal(d["counts"], counts) and torch.equal(d["oob"], oob)
     finally:
         pm.pm_batch_destroy(b)
 
