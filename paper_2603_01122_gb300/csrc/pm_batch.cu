@@ -305,31 +305,38 @@ __global__ void batch_zero_kernel(const BatchHuman *humans, const int *n_dev)
     }
 }
 
-// The reachable-cells form. A warp per (human, step t, row group g of
-// kReachGroups): it zeroes oob[t] and the step's block flags (g = 0) and, of
-// the counts of step t, the rows r = g mod kReachGroups of
+// The reachable-cells form. A warp per (human, step t, part g of
+// kReachGroups): it zeroes oob[t] and the step's block flags (g = 0) and
+// part g of one contiguous span of step t's counts: from the first to the
+// last cell of the smallest rectangle holding
 //  - the two boxes a particle can reach from this prediction's start z0 and
 //    from the previous prediction's start into the same buffers (prev), or
-//  - every row, when the human has no recorded previous start (NaN) or a
-//    non-finite start.
-// (the smallest rectangle holding both, in fact). Every other cell still
-// holds the zero of an earlier pass, because no particle leaves its box. The
-// last CTA to finish records each human's z0 in prev (ticket, no waiting;
-// every CTA has read prev before it takes its ticket).
+//  - the whole plane, when the human has no recorded previous start (NaN) or
+//    a non-finite start.
+// The span's cells outside the boxes are zero already, so zeroing them again
+// is harmless, and a contiguous span is written with 16-byte stores. Where
+// the rectangle is more than kSpanSlack words narrower than the plane (the
+// span would zero that much more per row than the rectangle), the warp
+// zeroes the rectangle's rows r = g mod kReachGroups instead: the served
+// 121-cell windows take the span, full 400-cell grids the rows. Every cell
+// outside what is zeroed still holds the zero of an earlier pass, because no
+// particle leaves its box. The last CTA to finish records each human's z0 in
+// prev (ticket, no waiting; every CTA has read prev before it takes its
+// ticket).
 constexpr int kReachGroups = 4;
+constexpr int kSpanSlack = 128; // extra words per row a span may zero before the rows are cheaper
 
-// Zero words [x0, x1] of a row with the lanes of a warp: 16-byte stores for
+// Zero n consecutive words at p with the lanes of a warp: 16-byte stores for
 // the aligned body, single words for the head and the tail.
-__device__ __forceinline__ void zero_row(uint32_t *rowp, int x0, int x1, int lane)
+__device__ __forceinline__ void zero_span(uint32_t *p, long n, int lane)
 {
-    const int n = x1 - x0 + 1;
     if (n <= 0) return;
-    uint32_t *p = rowp + x0;
-    const int head = min((int)((4u - (((uintptr_t)p >> 2) & 3u)) & 3u), n);
-    const int body = (n - head) >> 2, tail = (n - head) & 3;
+    const int head = (int)min((long)((4u - (((uintptr_t)p >> 2) & 3u)) & 3u), n);
+    const long body = (n - head) >> 2;
+    const int tail = (int)((n - head) & 3);
     if (lane < head) p[lane] = 0u;
     uint4 *v = reinterpret_cast<uint4 *>(p + head);
-    for (int i = lane; i < body; i += 32) v[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (long i = lane; i < body; i += 32) v[i] = make_uint4(0u, 0u, 0u, 0u);
     if (lane < tail) p[head + 4 * body + lane] = 0u;
 }
 
@@ -355,22 +362,26 @@ __global__ void batch_zero_reach_kernel(const BatchHuman *humans, const int *n_d
         }
         const float zx = h.z0[0], zy = h.z0[1];
         const float2 zp = prev[hh];
-        uint32_t *stepp = h.counts + (size_t)t * h.W * h.H;
-        if (!(isfinite(zp.x) && isfinite(zp.y) && isfinite(zx) && isfinite(zy))) {
-            for (int row = g; row < h.H; row += kReachGroups) zero_row(stepp + (size_t)row * h.W, 0, h.W - 1, lane);
-            continue;
+        long lo = 0, hi = (long)h.W * h.H; // the span [lo, hi) of the step's plane
+        if (isfinite(zp.x) && isfinite(zp.y) && isfinite(zx) && isfinite(zy)) {
+            const ReachBox a = reach_box(h, zx, zy, t + 1, smax);
+            const ReachBox b = reach_box(h, zp.x, zp.y, t + 1, smax);
+            const bool ea = a.x0 <= a.x1 && a.y0 <= a.y1, eb = b.x0 <= b.x1 && b.y0 <= b.y1;
+            if (!ea && !eb) continue;
+            const int x0 = min(ea ? a.x0 : INT_MAX, eb ? b.x0 : INT_MAX), x1 = max(ea ? a.x1 : -1, eb ? b.x1 : -1);
+            const int y0 = min(ea ? a.y0 : INT_MAX, eb ? b.y0 : INT_MAX), y1 = max(ea ? a.y1 : -1, eb ? b.y1 : -1);
+            lo = (long)y0 * h.W + x0;
+            hi = (long)y1 * h.W + x1 + 1;
+            if (h.W - (x1 - x0 + 1) > kSpanSlack) { // a rectangle much narrower than the plane: its rows
+                uint32_t *stepp = h.counts + (size_t)t * h.W * h.H;
+                for (int row = y0 + ((g - y0 % kReachGroups) + kReachGroups) % kReachGroups; row <= y1;
+                     row += kReachGroups)
+                    zero_span(stepp + (size_t)row * h.W + x0, x1 - x0 + 1, lane);
+                continue;
+            }
         }
-        const ReachBox a = reach_box(h, zx, zy, t + 1, smax);
-        const ReachBox b = reach_box(h, zp.x, zp.y, t + 1, smax);
-        const bool ea = a.x0 <= a.x1 && a.y0 <= a.y1, eb = b.x0 <= b.x1 && b.y0 <= b.y1;
-        if (!ea && !eb) continue;
-        // the smallest rectangle holding both boxes (cells of it outside them
-        // are zero already, so zeroing them again is harmless)
-        const int x0 = min(ea ? a.x0 : INT_MAX, eb ? b.x0 : INT_MAX), x1 = max(ea ? a.x1 : -1, eb ? b.x1 : -1);
-        const int y0 = min(ea ? a.y0 : INT_MAX, eb ? b.y0 : INT_MAX), y1 = max(ea ? a.y1 : -1, eb ? b.y1 : -1);
-        for (int row = y0 + ((g - y0 % kReachGroups) + kReachGroups) % kReachGroups; row <= y1;
-             row += kReachGroups)
-            zero_row(stepp + (size_t)row * h.W, x0, x1, lane);
+        const long len = hi - lo, p0 = lo + len * g / kReachGroups, p1 = lo + len * (g + 1) / kReachGroups;
+        zero_span(h.counts + (size_t)t * h.W * h.H + p0, p1 - p0, lane);
     }
     __shared__ bool last;
     __syncthreads();

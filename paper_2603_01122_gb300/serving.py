@@ -31,6 +31,10 @@ room grid centred on the human's cell (Algorithm 1, bootstrapped belief).
 * A frame in which a human has no new observation leaves its belief as it
   was (the step applied is of length zero) and predicts again from the same
   state.
+* Each frame zeroes only the window cells that this frame's or the previous
+  frame's particles of a slot can reach (``pm_batch_set_zeroing``; a frame
+  after a membership change zeroes every cell): the occupancy tensors are the
+  server's buffers, to be read, not written.
 * Latency = host wall time from the start of the frame (observations in host
   memory) to the occupancy being ready on the device (event synchronised).
 
@@ -45,8 +49,8 @@ from typing import Dict, List, Optional
 import numpy as np
 
 from . import (make_grid, make_human, make_model, pm_batch_create, pm_batch_destroy,
-               pm_batch_predict, pm_batch_set, pm_batch_set_block_flags, pm_batch_union,
-               pm_batch_update_posterior)
+               pm_batch_predict, pm_batch_set, pm_batch_set_block_flags, pm_batch_set_zeroing,
+               pm_batch_union, pm_batch_update_posterior)
 
 
 @dataclasses.dataclass
@@ -146,6 +150,7 @@ class Server:
         self._shared = make_model(K, speed, dt, shared_goals, shared_beta, w1=w1, w2=w2, speeds=self.speeds,
                                   snap_heading=snap_heading)
         self.batch = pm_batch_create(ctx, self._shared, cap)
+        pm_batch_set_zeroing(self.batch, 1)
         if union_sigma is not None:  # the union reads only the blocks the rollout marks
             pm_batch_set_block_flags(self.batch, 1)
         self.union_sigma = union_sigma
