@@ -136,6 +136,15 @@ const char *pm_version(void);
  * latched, or PM_ECUDA. Synchronous. */
 pm_status pm_sync_status(pm_ctx *ctx, void *stream);
 
+/* Launch an instantiated CUDA graph (a cudaGraphExec_t, e.g. a captured
+ * serving frame) on `stream` and, when `done` (a cudaEvent_t) is not NULL,
+ * record it on the stream after the graph; with `wait` != 0 also wait for
+ * that event (for the stream when `done` is NULL) before returning: one
+ * native call per frame, so a frame loop pays no framework overhead. The
+ * caller owns the graph and the event. PM_EINVAL for a NULL graph, PM_ECUDA
+ * if the launch, the record or the wait fails. */
+pm_status pm_graph_launch(void *graph_exec, void *stream, void *done, int32_t wait);
+
 /* ---- the hot path -------------------------------------------------------- */
 
 /* Bayesian update of the joint belief (Eq. 3), in log space (Eq. 7), over

@@ -73,6 +73,7 @@ def _signatures(lib):
         "pm_last_error": ([], C.c_char_p),
         "pm_version": ([], C.c_char_p),
         "pm_sync_status": ([_vp, _vp], C.c_int),
+        "pm_graph_launch": ([_vp, _vp, _vp, C.c_int32], C.c_int),
         "pm_batch_set_block_flags": ([_vp, C.c_int32, _vp], C.c_int),
         "pm_batch_set_zeroing": ([_vp, C.c_int32, _vp], C.c_int),
         "pm_update_posterior": ([_vp, P(pm_model), _vp, C.c_int32, _vp, _vp], C.c_int),
@@ -172,6 +173,31 @@ def pm_sync_status(ctx, stream=None):
     """Wait for ``stream`` and raise PmError(PM_EDEVICE) if kernels of ``ctx``
     latched unusable inputs since the last call (the word is then cleared)."""
     _check(library().pm_sync_status(ctx, _stream(stream)))
+
+
+def graph_launcher(graph_exec, stream=None, done=None, wait=True):
+    """A zero-argument callable that runs pm_graph_launch with these arguments
+    bound once (a frame loop then spends no time converting them per frame)."""
+    fn = library().pm_graph_launch
+    args = (C.c_void_p(int(graph_exec)), _stream(stream), None if done is None else C.c_void_p(done.cuda_event),
+            1 if wait else 0)
+
+    def launch():
+        st = fn(*args)
+        if st != PM_OK:
+            _check(st)
+    return launch
+
+
+def pm_graph_launch(graph_exec, stream=None, done=None, wait=False):
+    """Launch an instantiated CUDA graph (its cudaGraphExec_t as an integer,
+    e.g. ``torch.cuda.CUDAGraph.raw_cuda_graph_exec()``) on ``stream``, record
+    ``done`` (a torch.cuda.Event) after it and, with ``wait``, wait for it:
+    one native call."""
+    ev = None
+    if done is not None:
+        ev = C.c_void_p(done.cuda_event)
+    _check(library().pm_graph_launch(C.c_void_p(int(graph_exec)), _stream(stream), ev, 1 if wait else 0))
 
 
 def pm_create(device: int = 0) -> int:

@@ -912,6 +912,23 @@ pm_status pm_sync_status(pm_ctx *ctx, void *stream)
     return fail(PM_EDEVICE, "kernels reported (status 0x%x):%s", word, what.c_str());
 }
 
+pm_status pm_graph_launch(void *graph_exec, void *stream, void *done, int32_t wait)
+{
+    PM_RANGE("pm_graph_launch");
+    if (!graph_exec) return fail(PM_EINVAL, "graph_exec is NULL");
+    cudaError_t e = cudaGraphLaunch((cudaGraphExec_t)graph_exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    if (done) {
+        e = cudaEventRecord((cudaEvent_t)done, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "event record");
+    }
+    if (wait) {
+        e = done ? cudaEventSynchronize((cudaEvent_t)done) : cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "graph wait");
+    }
+    return PM_OK;
+}
+
 pm_status pm_update_posterior(pm_ctx *ctx, const pm_model *model, const float *obs_xy, int32_t n_obs,
                               float *log_belief, void *stream)
 {

@@ -12,7 +12,8 @@ room grid centred on the human's cell (Algorithm 1, bootstrapped belief).
   updates it with the one new step (Eq. 3 / Eq. 7) and predicts from it.
 * One frame = upload of the newest observations (page-locked host buffer ->
   device), the batched belief update and the batched persistent rollout,
-  replayed as one captured CUDA graph. Membership changes re-upload the
+  replayed as one captured CUDA graph, launched with its completion event in
+  one native call (``pm_graph_launch``). Membership changes re-upload the
   batch descriptors only; the graph reads them from device memory.
 * Optionally (``union_sigma``) the frame also blurs every live human's window
   and max-unites them on the shared room grid (Sec. III-B, Sec. IV-B): the
@@ -50,7 +51,7 @@ import numpy as np
 
 from . import (make_grid, make_human, make_model, pm_batch_create, pm_batch_destroy,
                pm_batch_predict, pm_batch_set, pm_batch_set_block_flags, pm_batch_set_zeroing,
-               pm_batch_union, pm_batch_update_posterior)
+               pm_batch_union, pm_batch_update_posterior, graph_launcher)
 
 
 @dataclasses.dataclass
@@ -161,6 +162,7 @@ class Server:
             self.union = torch.zeros((horizon, RH, RW), dtype=torch.float32, device=self.dev)
         self.use_graph = use_graph
         self.graph = None
+        self._launch = None  # the captured frame, launched and awaited natively
         self.dirty = True
         self.frames = 0
 
@@ -246,17 +248,24 @@ class Server:
         if self.dirty:
             pm_batch_set(self.batch, self._humans(), self.stream)
             self.dirty = False
-        with t.cuda.stream(self.stream):
-            if self.use_graph and self.slots.live:
-                if self.graph is None:
-                    self.graph = t.cuda.CUDAGraph()
-                    with t.cuda.graph(self.graph, stream=self.stream):
-                        self._enqueue()
-                self.graph.replay()
-            elif self.slots.live:
-                self._enqueue()
-            self.done.record(self.stream)
-        self.done.synchronize()
+        if self._launch is not None and self.slots.live:
+            # the captured frame, its completion event and the wait in one native call
+            self._launch()
+        else:
+            with t.cuda.stream(self.stream):
+                if self.use_graph and self.slots.live:
+                    if self.graph is None:
+                        self.graph = t.cuda.CUDAGraph()
+                        with t.cuda.graph(self.graph, stream=self.stream):
+                            self._enqueue()
+                    self.graph.replay()
+                elif self.slots.live:
+                    self._enqueue()
+                self.done.record(self.stream)
+            self.done.synchronize()
+            raw = getattr(self.graph, "raw_cuda_graph_exec", None)
+            if self.graph is not None and raw is not None and self.done.cuda_event:
+                self._launch = graph_launcher(raw(), self.stream, self.done)
         latency = time.perf_counter() - t0  # the occupancy is ready
         # the frame has applied each live human's step (prev -> cur): a later
         # frame without a new observation then applies a zero-length step,

@@ -283,3 +283,10 @@ def test_frame_without_observation_keeps_the_belief(ctx, orc):
                 assert_posterior_close(srv.log_b[sl[i], :J[i]].cpu().numpy(), want)
     finally:
         srv.close()
+
+
+def test_graph_launch_rejects_a_null_graph():
+    import paper_2603_01122_gb300 as pm
+    with pytest.raises(pm.PmError) as e:
+        pm.pm_graph_launch(0)
+    assert e.value.status == pm.PM_EINVAL
