@@ -329,6 +329,17 @@ pm_status pm_batch_update_posterior(pm_batch *b, void *stream);
  * captured in a CUDA graph. */
 pm_status pm_batch_predict(pm_batch *b, void *stream);
 
+/* The two halves of pm_batch_predict, for a caller that overlaps the zeroing
+ * with other work (e.g. on a second stream, beside pm_batch_update_posterior,
+ * joined before the rollout): pm_batch_zero enqueues the zeroing of the
+ * outputs (by the mode of pm_batch_set_zeroing), pm_batch_rollout the
+ * persistent launch of Algorithm 1. pm_batch_rollout adds to the counts: the
+ * outputs must have been zeroed by pm_batch_zero after the previous
+ * prediction and before it (stream order or an event). Both may be captured
+ * in a CUDA graph. */
+pm_status pm_batch_zero(pm_batch *b, void *stream);
+pm_status pm_batch_rollout(pm_batch *b, void *stream);
+
 /* reach = 0 (the default): pm_batch_predict zeroes every cell of every
  * human's counts before the rollout. reach = 1: it zeroes only the cells of
  * step t that a particle can occupy after t steps of the longest control,

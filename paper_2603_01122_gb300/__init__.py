@@ -76,6 +76,8 @@ def _signatures(lib):
         "pm_graph_launch": ([_vp, _vp, _vp, C.c_int32], C.c_int),
         "pm_batch_set_block_flags": ([_vp, C.c_int32, _vp], C.c_int),
         "pm_batch_set_zeroing": ([_vp, C.c_int32, _vp], C.c_int),
+        "pm_batch_zero": ([_vp, _vp], C.c_int),
+        "pm_batch_rollout": ([_vp, _vp], C.c_int),
         "pm_update_posterior": ([_vp, P(pm_model), _vp, C.c_int32, _vp, _vp], C.c_int),
         "pm_update_posterior_into": ([_vp, P(pm_model), _vp, C.c_int32, _vp, _vp, _vp], C.c_int),
         "pm_predict_occupancy": ([_vp, P(pm_model), _vp, C.c_float, C.c_float, C.c_int32, C.c_int32,
@@ -334,6 +336,14 @@ def pm_batch_set_block_flags(batch, enable, stream=None):
 
 def pm_batch_set_zeroing(batch, reach, stream=None):
     _check(library().pm_batch_set_zeroing(batch, int(reach), _stream(stream)))
+
+
+def pm_batch_zero(batch, stream=None):
+    _check(library().pm_batch_zero(batch, _stream(stream)))
+
+
+def pm_batch_rollout(batch, stream=None):
+    _check(library().pm_batch_rollout(batch, _stream(stream)))
 
 
 def pm_batch_autotune(batch, stream=None):

@@ -752,14 +752,19 @@ pm_status batch_upload(pm_batch *b, cudaStream_t stream)
     return PM_OK;
 }
 
-pm_status batch_predict_impl(pm_batch *b, cudaStream_t stream)
+pm_status batch_zero_impl(pm_batch *b, cudaStream_t stream)
+{
+    cudaError_t e = pm::launch_batch_zero(b->d_humans, b->d_meta + 1, b->max_humans, b->ctx->sm_count, b->t_max,
+                                          b->zero_reach ? b->d_prev : nullptr, zero_ticket(b), b->step_max, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "zero launch");
+    return PM_OK;
+}
+
+pm_status batch_rollout_impl(pm_batch *b, cudaStream_t stream)
 {
     pm_ctx *ctx = b->ctx;
     cudaError_t e = cudaMemsetAsync(b->d_head, 0, sizeof(unsigned), stream);
     if (e != cudaSuccess) return cuda_fail(e, "queue reset");
-    e = pm::launch_batch_zero(b->d_humans, b->d_meta + 1, b->max_humans, ctx->sm_count, b->t_max,
-                              b->zero_reach ? b->d_prev : nullptr, zero_ticket(b), b->step_max, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "zero launch");
     pm::RolloutArgs t;
     std::memset(&t, 0, sizeof t);
     fill_rollout_tables(&b->shared, t);
@@ -787,6 +792,12 @@ pm_status batch_predict_impl(pm_batch *b, cudaStream_t stream)
     e = pm::launch_batch_rollout(a, batch_shape_of(b), ctx->sm_count * occ, dyn, stream);
     if (e != cudaSuccess) return cuda_fail(e, "batch rollout launch");
     return PM_OK;
+}
+
+pm_status batch_predict_impl(pm_batch *b, cudaStream_t stream)
+{
+    pm_status st = batch_zero_impl(b, stream);
+    return st != PM_OK ? st : batch_rollout_impl(b, stream);
 }
 
 } // namespace
@@ -1233,6 +1244,22 @@ pm_status pm_batch_set_zeroing(pm_batch *b, int32_t reach, void *stream)
     cudaError_t e = forget_starts(b, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "batch start records");
     return PM_OK;
+}
+
+pm_status pm_batch_zero(pm_batch *b, void *stream)
+{
+    PM_RANGE("pm_batch_zero");
+    if (!b) return fail(PM_EINVAL, "batch is NULL");
+    DeviceScope dev(b->ctx->device);
+    return batch_zero_impl(b, (cudaStream_t)stream);
+}
+
+pm_status pm_batch_rollout(pm_batch *b, void *stream)
+{
+    PM_RANGE("pm_batch_rollout");
+    if (!b) return fail(PM_EINVAL, "batch is NULL");
+    DeviceScope dev(b->ctx->device);
+    return batch_rollout_impl(b, (cudaStream_t)stream);
 }
 
 pm_status pm_batch_predict(pm_batch *b, void *stream)

@@ -11,7 +11,8 @@ room grid centred on the human's cell (Algorithm 1, bootstrapped belief).
 * Posteriors stay on the device: each slot keeps its log-belief; a frame
   updates it with the one new step (Eq. 3 / Eq. 7) and predicts from it.
 * One frame = upload of the newest observations (page-locked host buffer ->
-  device), the batched belief update and the batched persistent rollout,
+  device), the batched belief update beside the zeroing of the outputs (two
+  streams) and the batched persistent rollout,
   replayed as one captured CUDA graph, launched with its completion event in
   one native call (``pm_graph_launch``). Membership changes re-upload the
   batch descriptors only; the graph reads them from device memory.
@@ -50,8 +51,8 @@ from typing import Dict, List, Optional
 import numpy as np
 
 from . import (make_grid, make_human, make_model, pm_batch_create, pm_batch_destroy,
-               pm_batch_predict, pm_batch_set, pm_batch_set_block_flags, pm_batch_set_zeroing,
-               pm_batch_union, pm_batch_update_posterior, graph_launcher)
+               pm_batch_rollout, pm_batch_set, pm_batch_set_block_flags, pm_batch_set_zeroing,
+               pm_batch_union, pm_batch_update_posterior, pm_batch_zero, graph_launcher)
 
 
 @dataclasses.dataclass
@@ -139,6 +140,7 @@ class Server:
         self.obs_host = torch.zeros((cap, 2, 2), dtype=torch.float32).pin_memory()
         self.meta: Dict[int, dict] = {}
         self.stream = torch.cuda.Stream(device=self.dev)
+        self.side = torch.cuda.Stream(device=self.dev)
         self.done = torch.cuda.Event()
         shared_goals = torch.zeros((1, 2), device=self.dev)
         shared_beta = torch.ones(1, device=self.dev)
@@ -236,8 +238,13 @@ class Server:
 
     def _enqueue(self):
         self.obs_dev.copy_(self.obs_host, non_blocking=True)
+        # the zeroing (it reads the starts just copied) on a second stream,
+        # beside the belief update; the rollout waits for both
+        self.side.wait_stream(self.stream)
+        pm_batch_zero(self.batch, self.side)
         pm_batch_update_posterior(self.batch, self.stream)
-        pm_batch_predict(self.batch, self.stream)
+        self.stream.wait_stream(self.side)
+        pm_batch_rollout(self.batch, self.stream)
         if self.union is not None:
             pm_batch_union(self.batch, self.union_sigma, self.T, self.union_grid, self.union, self.stream)
 

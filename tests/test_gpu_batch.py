@@ -335,3 +335,34 @@ def test_plain_crowd_alone_equals_in_mix(ctx, orc):
             assert torch.equal(d["oob"], o)
     finally:
         pm.pm_batch_destroy(b)
+
+
+def test_zero_and_rollout_halves_equal_predict(ctx, orc):
+    """pm_batch_zero + pm_batch_rollout on two streams joined by an event
+    equal pm_batch_predict; a second rollout without zeroing adds the same
+    counts again (the documented contract of pm_batch_rollout)."""
+    import paper_2603_01122_gb300 as pm
+    humans = workloads.plain_crowd(6)
+    ds = _setup(orc, humans)
+    b = pm.pm_batch_create(ctx, _shared_model(humans[0], ds[0]["gh"]), len(ds))
+    try:
+        pm.pm_batch_set(b, _pm_humans(ds))
+        pm.pm_batch_predict(b)
+        torch.cuda.synchronize()
+        want = [(d["counts"].clone(), d["oob"].clone()) for d in ds]
+        for d in ds:
+            d["counts"].fill_(0x3C3C3C3C)
+        main, side = torch.cuda.Stream(), torch.cuda.Stream()
+        side.wait_stream(main)
+        pm.pm_batch_zero(b, side)
+        main.wait_stream(side)
+        pm.pm_batch_rollout(b, main)
+        torch.cuda.synchronize()
+        for d, (c, o) in zip(ds, want):
+            assert torch.equal(d["counts"], c) and torch.equal(d["oob"], o)
+        pm.pm_batch_rollout(b, main)
+        torch.cuda.synchronize()
+        for d, (c, o) in zip(ds, want):
+            assert torch.equal(d["counts"], 2 * c) and torch.equal(d["oob"], 2 * o)
+    finally:
+        pm.pm_batch_destroy(b)
