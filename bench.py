@@ -428,14 +428,22 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
         pm.pm_batch_autotune(batch, stream)
         tune_s = time.perf_counter() - t0
         tuned = pm.pm_batch_get_config(batch)
+        side = torch.cuda.Stream()
+
+        def batched_step():
+            # the zeroing on a second stream, beside the belief update
+            lb_flat.copy_(prior_flat)
+            side.wait_stream(stream)
+            pm.pm_batch_zero(batch, side)
+            pm.pm_batch_update_posterior(batch, stream)
+            stream.wait_stream(side)
+            pm.pm_batch_rollout(batch, stream)
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.stream(stream):
             lb_flat.copy_(prior_flat)
             torch.cuda.synchronize()
             with torch.cuda.graph(graph, stream=stream):
-                lb_flat.copy_(prior_flat)
-                pm.pm_batch_update_posterior(batch, stream)
-                pm.pm_batch_predict(batch, stream)
+                batched_step()
         batch_ms = time_events(torch, stream, graph.replay, 10)
         # grid epilogue: every human's counts blurred (sigma 1.5 cells) and
         # max-united on the shared 400 x 400 grid
@@ -453,9 +461,7 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
         with torch.cuda.stream(stream):
             torch.cuda.synchronize()
             with torch.cuda.graph(graph_m, stream=stream):
-                lb_flat.copy_(prior_flat)
-                pm.pm_batch_update_posterior(batch, stream)
-                pm.pm_batch_predict(batch, stream)
+                batched_step()
         marked_batch_ms = time_events(torch, stream, graph_m.replay, 10)
         union_ms = time_events(torch, stream, do_union, 10)
         pm.pm_batch_set_block_flags(batch, 0, stream)
@@ -520,13 +526,17 @@ def run_extra(args, pm, ctx, torch, dev, stream, sfu_peak):
             pm.pm_batch_set(batch, humans, stream)
             pm.pm_batch_set_zeroing(batch, 1, stream)
             pm.pm_batch_autotune(batch, stream)
+            side = torch.cuda.Stream()
             graph = torch.cuda.CUDAGraph()
             with torch.cuda.stream(stream):
                 torch.cuda.synchronize()
                 with torch.cuda.graph(graph, stream=stream):
                     lb_flat.copy_(prior_flat)
+                    side.wait_stream(stream)
+                    pm.pm_batch_zero(batch, side)  # beside the belief update
                     pm.pm_batch_update_posterior(batch, stream)
-                    pm.pm_batch_predict(batch, stream)
+                    stream.wait_stream(side)
+                    pm.pm_batch_rollout(batch, stream)
             batch_ms = time_events(torch, stream, graph.replay, 20)
             out["batched_small"] = {"humans": len(recs), "particle_steps": steps, "batched_ms": batch_ms,
                                     "batched_particle_steps_per_s": steps / (batch_ms * 1e-3),
