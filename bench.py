@@ -833,10 +833,26 @@ def run_native(args):
     oob = torch.empty((T,), dtype=torch.int32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step():
+    side = torch.cuda.Stream()
+
+    def step(ev=None):
+        """One step: the outputs zeroed on a second stream beside the belief
+        update, then the rollout; ev = (start, after the update, rollout
+        start, end) events on the main stream."""
+        if ev:
+            ev[0].record(stream)
+        side.wait_stream(stream)
+        pm.pm_zero_occupancy(ctx, T, grid, counts, oob, side)
         pm.pm_update_posterior_into(ctx, model, obs, hu.n_obs, prior, lb, stream)
-        pm.pm_predict_occupancy(ctx, model, lb, float(z0[0]), float(z0[1]), N, T, grid, hu.seed, human_id,
+        if ev:
+            ev[1].record(stream)
+        stream.wait_stream(side)
+        if ev:
+            ev[2].record(stream)
+        pm.pm_rollout_occupancy(ctx, model, lb, float(z0[0]), float(z0[1]), N, T, grid, hu.seed, human_id,
                                 counts, oob, stream)
+        if ev:
+            ev[3].record(stream)
 
     # SFU peak (roofline denominator), measured before the timed region
     sfu = {"ex2": pm.pm_probe_sfu(ctx, 0), "sqrt": pm.pm_probe_sfu(ctx, 1), "rsqrt": pm.pm_probe_sfu(ctx, 2)}
@@ -848,8 +864,7 @@ def run_native(args):
             step()
     torch.cuda.synchronize()
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(4)) for _ in range(args.steps)]
     if world > 1:
         tdist.barrier()
     torch.cuda.synchronize()
@@ -874,21 +889,16 @@ def run_native(args):
         with torch.cuda.stream(stream):
             for i in range(args.steps):
                 flush.fill_(float(i))
-                ev[i][0].record(stream)
-                pm.pm_update_posterior_into(ctx, model, obs, hu.n_obs, prior, lb, stream)
-                ev[i][1].record(stream)
-                pm.pm_predict_occupancy(ctx, model, lb, float(z0[0]), float(z0[1]), N, T, grid, hu.seed,
-                                        human_id, counts, oob, stream)
-                ev[i][2].record(stream)
+                step(ev[i])
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
         clk.mark(pre_t0, time.time())
         time.sleep(0.3)
     if world > 1:
         tdist.barrier()
-    step_ms = [a.elapsed_time(c) for a, b, c in ev]
-    roll_ms = [b.elapsed_time(c) for a, b, c in ev]
-    post_ms = [a.elapsed_time(b) for a, b, c in ev]
+    step_ms = [a.elapsed_time(d) for a, b, c, d in ev]
+    roll_ms = [c.elapsed_time(d) for a, b, c, d in ev]
+    post_ms = [a.elapsed_time(b) for a, b, c, d in ev]
     total_ms = max_over_ranks(sum(step_ms), world, tdist, dev)
     ms_per_step = total_ms / args.steps
     value = job_throughput(world, N * T, ms_per_step * 1e-3)

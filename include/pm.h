@@ -196,6 +196,21 @@ pm_status pm_predict_occupancy(pm_ctx *ctx, const pm_model *model, const float *
                                const pm_grid *grid, uint64_t seed, uint32_t human_id,
                                uint32_t *counts, uint32_t *oob, void *stream);
 
+/* The two halves of pm_predict_occupancy, for a caller that overlaps the
+ * zeroing with other work: pm_zero_occupancy zeroes counts [horizon][H][W]
+ * and oob [horizon] (it touches no scratch of the context, so it may run on
+ * a second stream beside the context's other calls, e.g. the belief update);
+ * pm_rollout_occupancy is pm_predict_occupancy without the zeroing: it adds
+ * to counts and oob, which must have been zeroed since their last rollout
+ * (stream order or an event). Arguments, layout and errors as for
+ * pm_predict_occupancy (pm_zero_occupancy checks horizon, grid and the two
+ * pointers). Asynchronous. */
+pm_status pm_zero_occupancy(pm_ctx *ctx, int32_t horizon, const pm_grid *grid, uint32_t *counts, uint32_t *oob,
+                            void *stream);
+pm_status pm_rollout_occupancy(pm_ctx *ctx, const pm_model *model, const float *log_belief, float z0x, float z0y,
+                               int32_t n_particles, int32_t horizon, const pm_grid *grid, uint64_t seed,
+                               uint32_t human_id, uint32_t *counts, uint32_t *oob, void *stream);
+
 /* The same launch as pm_predict_occupancy, also recording the trajectories
  * of particles [0, n_trace):
  *   states      [n_trace][horizon][2] FP32 state after each step, or NULL;

@@ -82,6 +82,9 @@ def _signatures(lib):
         "pm_update_posterior_into": ([_vp, P(pm_model), _vp, C.c_int32, _vp, _vp, _vp], C.c_int),
         "pm_predict_occupancy": ([_vp, P(pm_model), _vp, C.c_float, C.c_float, C.c_int32, C.c_int32,
                                   P(pm_grid), C.c_uint64, C.c_uint32, _vp, _vp, _vp], C.c_int),
+        "pm_rollout_occupancy": ([_vp, P(pm_model), _vp, C.c_float, C.c_float, C.c_int32, C.c_int32,
+                                  P(pm_grid), C.c_uint64, C.c_uint32, _vp, _vp, _vp], C.c_int),
+        "pm_zero_occupancy": ([_vp, C.c_int32, P(pm_grid), _vp, _vp, _vp], C.c_int),
         "pm_predict_occupancy_traced": ([_vp, P(pm_model), _vp, C.c_float, C.c_float, C.c_int32,
                                          C.c_int32, P(pm_grid), C.c_uint64, C.c_uint32, _vp, _vp,
                                          C.c_int32, _vp, _vp, _vp, _vp], C.c_int),
@@ -244,6 +247,17 @@ def pm_update_posterior_into(ctx, model: pm_model, obs_xy, n_obs, log_prior, log
 def pm_predict_occupancy(ctx, model: pm_model, log_belief, z0x, z0y, n_particles, horizon,
                          grid: pm_grid, seed, human_id, counts, oob, stream=None):
     _check(library().pm_predict_occupancy(ctx, C.byref(model), _p(log_belief), float(z0x), float(z0y),
+                                          int(n_particles), int(horizon), C.byref(grid), int(seed),
+                                          int(human_id), _p(counts), _p(oob), _stream(stream)))
+
+
+def pm_zero_occupancy(ctx, horizon, grid: pm_grid, counts, oob, stream=None):
+    _check(library().pm_zero_occupancy(ctx, int(horizon), C.byref(grid), _p(counts), _p(oob), _stream(stream)))
+
+
+def pm_rollout_occupancy(ctx, model: pm_model, log_belief, z0x, z0y, n_particles, horizon,
+                         grid: pm_grid, seed, human_id, counts, oob, stream=None):
+    _check(library().pm_rollout_occupancy(ctx, C.byref(model), _p(log_belief), float(z0x), float(z0y),
                                           int(n_particles), int(horizon), C.byref(grid), int(seed),
                                           int(human_id), _p(counts), _p(oob), _stream(stream)))
 

@@ -362,7 +362,7 @@ pm_status predict_impl(pm_ctx *ctx, const pm_model *model, const float *log_beli
                        float z0y, int32_t n_particles, int32_t horizon, const pm_grid *grid,
                        uint64_t seed, uint32_t human_id, uint32_t *counts, uint32_t *oob,
                        int32_t n_trace, float *states, uint8_t *headings, int32_t *components,
-                       cudaStream_t stream)
+                       cudaStream_t stream, bool zero = true)
 {
     if (!ctx) return fail(PM_EINVAL, "ctx is NULL");
     pm_status st = check_model(model);
@@ -418,8 +418,9 @@ pm_status predict_impl(pm_ctx *ctx, const pm_model *model, const float *log_beli
     if (st != PM_OK) return st;
     unsigned *head = ctx->ticket + 2;
     const size_t words = hist ? (size_t)grid->W * (size_t)grid->H * (size_t)horizon : 0;
-    cudaError_t ez = pm::launch_zero_outputs(hist ? counts : nullptr, words, hist ? oob : nullptr, horizon, head,
-                                             ctx->sm_count, stream);
+    cudaError_t ez = zero ? pm::launch_zero_outputs(hist ? counts : nullptr, words, hist ? oob : nullptr, horizon,
+                                                    head, ctx->sm_count, stream)
+                          : cudaMemsetAsync(head, 0, sizeof(unsigned), stream); // the caller zeroed the outputs
     if (ez != cudaSuccess) return cuda_fail(ez, "zeroing counts, oob and the chunk counter");
     cudaError_t e = pm::launch_rollout(a, head, ctx->sm_count, stream);
     if (e != cudaSuccess) return cuda_fail(e, "rollout launch");
@@ -963,6 +964,35 @@ pm_status pm_predict_occupancy(pm_ctx *ctx, const pm_model *model, const float *
     if (!counts || !oob) return fail(PM_EINVAL, "counts and oob are required");
     return predict_impl(ctx, model, log_belief, z0x, z0y, n_particles, horizon, grid, seed, human_id,
                         counts, oob, 0, nullptr, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+
+pm_status pm_zero_occupancy(pm_ctx *ctx, int32_t horizon, const pm_grid *grid, uint32_t *counts, uint32_t *oob,
+                            void *stream)
+{
+    PM_RANGE("pm_zero_occupancy");
+    if (!ctx) return fail(PM_EINVAL, "ctx is NULL");
+    if (!counts || !oob) return fail(PM_EINVAL, "counts and oob are required");
+    if (horizon < 1 || horizon > PM_MAX_HORIZON)
+        return fail(PM_EINVAL, "horizon=%d outside [1, %d]", horizon, PM_MAX_HORIZON);
+    pm_status st = check_grid(grid);
+    if (st != PM_OK) return st;
+    DeviceScope dev(ctx->device);
+    const size_t words = (size_t)grid->W * (size_t)grid->H * (size_t)horizon;
+    cudaError_t e = pm::launch_zero_outputs(counts, words, oob, horizon, nullptr, ctx->sm_count, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "zeroing counts and oob");
+    return PM_OK;
+}
+
+pm_status pm_rollout_occupancy(pm_ctx *ctx, const pm_model *model, const float *log_belief, float z0x,
+                               float z0y, int32_t n_particles, int32_t horizon, const pm_grid *grid,
+                               uint64_t seed, uint32_t human_id, uint32_t *counts, uint32_t *oob,
+                               void *stream)
+{
+    PM_RANGE("pm_rollout_occupancy");
+    if (!counts || !oob) return fail(PM_EINVAL, "counts and oob are required");
+    return predict_impl(ctx, model, log_belief, z0x, z0y, n_particles, horizon, grid, seed, human_id,
+                        counts, oob, 0, nullptr, nullptr, nullptr, (cudaStream_t)stream, false);
 }
 
 pm_status pm_predict_occupancy_traced(pm_ctx *ctx, const pm_model *model, const float *log_belief,

@@ -414,7 +414,7 @@ __global__ void zero_outputs_kernel(uint32_t *counts, size_t words, uint32_t *oo
     }
     if (oob)
         for (size_t q = t0; q < (size_t)T; q += stride) oob[q] = 0u;
-    if (t0 == 0) *head = 0u;
+    if (head && t0 == 0) *head = 0u;
 }
 
 template <typename Kern>

@@ -395,6 +395,45 @@ def test_determinism_and_streams(ctx, orc):
     assert not np.array_equal(a["counts"], c["counts"])
 
 
+def test_zero_and_rollout_halves_equal_predict(ctx, orc):
+    """pm_zero_occupancy on a second stream beside pm_update_posterior_into,
+    then pm_rollout_occupancy, equals pm_update_posterior + pm_predict_occupancy
+    from garbage outputs; a second rollout without zeroing adds the counts
+    again."""
+    import paper_2603_01122_gb300 as pm
+    hu = workloads.paper_scale()
+    m = orc.Model(hu.K, hu.speed, hu.dt, hu.goals, hu.beta)
+    obs = dev(orc.simulate(m, hu.true_j, hu.start, hu.n_obs, hu.obs_seed, hu.human_id).astype(np.float32))
+    gh = GpuHuman.of(hu)
+    x0, y0, res, W, H = hu.grid
+    grid = pm.make_grid(x0, y0, res, W, H)
+    N, T = 30000, 60
+    prior = dev(hu.uniform_log_prior())
+    z0 = obs[-1].cpu().numpy()
+    lb1 = prior.clone()
+    pm.pm_update_posterior(ctx, gh.model, obs, hu.n_obs, lb1)
+    c1 = torch.full((T, H, W), 0x3C3C3C3C, dtype=torch.int32, device="cuda:0")
+    o1 = torch.full((T,), 7, dtype=torch.int32, device="cuda:0")
+    pm.pm_predict_occupancy(ctx, gh.model, lb1, float(z0[0]), float(z0[1]), N, T, grid, hu.seed, 5, c1, o1)
+    lb2 = torch.empty_like(prior)
+    c2 = torch.full_like(c1, 0x5A5A5A5A)
+    o2 = torch.full_like(o1, 9)
+    main, side = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    side.wait_stream(main)
+    pm.pm_zero_occupancy(ctx, T, grid, c2, o2, side)
+    pm.pm_update_posterior_into(ctx, gh.model, obs, hu.n_obs, prior, lb2, main)
+    main.wait_stream(side)
+    pm.pm_rollout_occupancy(ctx, gh.model, lb2, float(z0[0]), float(z0[1]), N, T, grid, hu.seed, 5, c2, o2, main)
+    torch.cuda.synchronize()
+    assert torch.equal(lb1, lb2) and torch.equal(c1, c2) and torch.equal(o1, o2)
+    pm.pm_rollout_occupancy(ctx, gh.model, lb2, float(z0[0]), float(z0[1]), N, T, grid, hu.seed, 5, c2, o2)
+    torch.cuda.synchronize()
+    assert torch.equal(c2, 2 * c1) and torch.equal(o2, 2 * o1)
+    with pytest.raises(pm.PmError):
+        pm.pm_zero_occupancy(ctx, 0, grid, c2, o2)
+
+
 def test_host_api_matches_device_path(ctx, orc):
     import paper_2603_01122_gb300 as pm
     hu = workloads.paper_scale()
