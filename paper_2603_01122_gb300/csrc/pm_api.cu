@@ -412,15 +412,19 @@ pm_status predict_impl(pm_ctx *ctx, const pm_model *model, const float *log_beli
         a.W = a.H = 1;
         a.inv_res = 1.0f;
     }
-    // persistent warps take 32-particle chunks from a context-owned counter;
-    // one launch zeroes it with the counts and oob
+    // persistent warps take 32-particle chunks from a context-owned counter
+    // (word 2 of the counter block, word 4 counts the warps that are done);
+    // the last warp leaves both at zero, and the zeroing launch resets the
+    // counter too
     st = ensure_posterior_scratch(ctx, 0);
     if (st != PM_OK) return st;
     unsigned *head = ctx->ticket + 2;
     const size_t words = hist ? (size_t)grid->W * (size_t)grid->H * (size_t)horizon : 0;
+    // (the rollout leaves its chunk counter at zero; without `zero` the
+    // caller has zeroed the outputs)
     cudaError_t ez = zero ? pm::launch_zero_outputs(hist ? counts : nullptr, words, hist ? oob : nullptr, horizon,
                                                     head, ctx->sm_count, stream)
-                          : cudaMemsetAsync(head, 0, sizeof(unsigned), stream); // the caller zeroed the outputs
+                          : cudaSuccess;
     if (ez != cudaSuccess) return cuda_fail(ez, "zeroing counts, oob and the chunk counter");
     cudaError_t e = pm::launch_rollout(a, head, ctx->sm_count, stream);
     if (e != cudaSuccess) return cuda_fail(e, "rollout launch");

@@ -34,6 +34,20 @@ namespace {
 constexpr int kWarpCtaThreads = 128; // 4 warps: one per SM sub-partition
 constexpr int kWarpCtaMinBlocks = 6;
 
+// Every warp leaves the chunk loop once, after its last (failed) grab; the
+// last one to leave resets the counter head[0] and its own count head[2], so
+// each launch finds both at zero without a memset before it (the counters
+// are zeroed when the context allocates them).
+__device__ __forceinline__ void release_counter(unsigned *head, int lane)
+{
+    if (lane != 0) return;
+    const unsigned warps = gridDim.x * (blockDim.x >> 5);
+    if (atomicAdd(head + 2, 1u) == warps - 1u) {
+        atomicExch(head, 0u);
+        atomicExch(head + 2, 0u);
+    }
+}
+
 // Persistent warps over one human: the CTA loads the component table, the
 // belief CDF and the Euler steps into shared memory once, then each warp
 // takes chunks of 32 particles (one per lane) from a global counter until the
@@ -92,6 +106,7 @@ __global__ void __launch_bounds__(kWarpCtaThreads, kWarpCtaMinBlocks)
         c.i = i0 + lane;
         rollout_lane<KT, FULL>(a.tab, a.enabled, a.s2, c, comp, cdf, step);
     }
+    release_counter(head, lane);
 }
 
 // The same persistent warps for a control set of several speeds: KT > 0 is
@@ -152,6 +167,7 @@ __global__ void __launch_bounds__(kWarpCtaThreads, kWarpCtaMinBlocks)
         c.i = i0 + lane;
         rollout_lane<KT, false, true>(a.tab, a.enabled, a.s2, c, comp, cdf, step, betas, a.K, a.tab.speed_on);
     }
+    release_counter(head, lane);
 }
 
 template <int KT>
