@@ -291,3 +291,33 @@ def test_rejected_speed_sets(ctx):
         with pytest.raises(pm.PmError) as e:
             pm.pm_predict_occupancy(ctx, model, lb, 0.0, 0.0, 16, 2, grid, 1, 0, counts, oob)
         assert e.value.status == pm.PM_EINVAL, kw
+
+
+def test_rollout_half_after_zeroing_several_speeds(ctx, orc):
+    """The several-speed kernel through the two halves: pm_zero_occupancy on a
+    second stream, then pm_rollout_occupancy, three times in a row (each launch
+    leaves the chunk counter at zero for the next); every call equals
+    pm_predict_occupancy."""
+    import paper_2603_01122_gb300 as pm
+    hu = workloads.multi_speed()
+    m, gh = _models(orc, hu.K, hu.speed, hu.dt, hu.goals, hu.beta, hu.speeds)
+    x0, y0, res, W, H = hu.grid
+    grid = pm.make_grid(x0, y0, res, W, H)
+    N, T = 20000, 40
+    lb = dev(hu.uniform_log_prior())
+    want = torch.empty((T, H, W), dtype=torch.int32, device="cuda:0")
+    want_oob = torch.empty(T, dtype=torch.int32, device="cuda:0")
+    pm.pm_predict_occupancy(ctx, gh.model, lb, float(hu.start[0]), float(hu.start[1]), N, T, grid, hu.seed, 3,
+                            want, want_oob)
+    got = torch.full_like(want, 0x3C3C3C3C)
+    got_oob = torch.full_like(want_oob, 5)
+    main, side = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    for _ in range(3):
+        side.wait_stream(main)
+        pm.pm_zero_occupancy(ctx, T, grid, got, got_oob, side)
+        main.wait_stream(side)
+        pm.pm_rollout_occupancy(ctx, gh.model, lb, float(hu.start[0]), float(hu.start[1]), N, T, grid, hu.seed, 3,
+                                got, got_oob, main)
+        torch.cuda.synchronize()
+        assert torch.equal(got, want) and torch.equal(got_oob, want_oob)
